@@ -1,0 +1,304 @@
+/*
+ * ps.h -- C ABI of the GB300 phase-space library.
+ *
+ * The library maps uniform random numbers to weighted collider events on an
+ * sm_103a GPU: the data-parallel hot path of "MadSpace -- Event Generation for
+ * the Era of GPUs and ML" (arXiv 2602.06895).  Its calls follow the paper's
+ * compute-graph formulation (Sec. 3.1, Fig. compute_graph): a channel is an
+ * ordered list of inputs (random numbers), instructions in static single
+ * assignment form with inline immediate constants, and outputs.  A *program*
+ * compiles the graphs of one or more channels for one device; a single fused
+ * kernel then evaluates every instruction of an event in that event's own thread,
+ * with intermediate values in shared memory and registers, and writes only the
+ * outputs (SoA) and per-tile partial sums.
+ *
+ * Conventions (after the UMAMI interface of Sec. 3.3):
+ *   - every function returns an int status: PS_OK (0) or a negative PS_ERR_*;
+ *     nothing throws or aborts; ps_last_error() returns a thread-local message;
+ *   - pointers named *_dev are device pointers owned by the caller; *_host are
+ *     host pointers owned by the caller; the library owns graphs and programs
+ *     (and their device constants) until the matching *_free call;
+ *   - streams are passed as void* (a cudaStream_t; NULL = legacy default stream);
+ *   - inputs are never modified (Sec. 3.1: operations consume immutable inputs).
+ *
+ * All floating point is IEEE binary64 unless a function says otherwise.
+ */
+#ifndef PS_H
+#define PS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define PS_OK 0
+#define PS_ERR_INVALID_ARGUMENT (-1) /* null handle/pointer, bad size, bad id      */
+#define PS_ERR_GRAPH (-2)            /* malformed graph: arity, type, undefined id */
+#define PS_ERR_CUDA (-3)             /* a CUDA runtime call failed                  */
+#define PS_ERR_DEVICE_STATUS (-4)    /* the device status word reports a fault      */
+#define PS_ERR_CAPACITY (-5)         /* a fixed limit of the library was exceeded   */
+#define PS_ERR_NO_DEVICE (-6)        /* no usable CUDA device                       */
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* ps_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int ps_version(void);
+
+/* ---------------------------------------------------------------- graphs */
+typedef struct ps_graph_s* ps_graph;
+typedef struct ps_program_s* ps_program;
+
+/* Value types of graph values. */
+#define PS_TYPE_SCALAR 0 /* one f64 per event          */
+#define PS_TYPE_MOMENTUM 1 /* four f64 (E, px, py, pz) */
+
+/* Argument of an instruction: a previously defined value, or an immediate f64. */
+#define PS_ARG_VALUE 0
+#define PS_ARG_IMM 1
+typedef struct {
+    int32_t kind; /* PS_ARG_VALUE or PS_ARG_IMM */
+    int32_t id;   /* value id (PS_ARG_VALUE)    */
+    double imm;   /* constant (PS_ARG_IMM)      */
+} ps_arg;
+
+/* Opcodes.  "(a, b) -> (c, d)" lists argument and result types: s = scalar,
+ * p = momentum, i = must be immediate; "..." marks a variadic tail.  Paper
+ * citations are sections / equations of arXiv 2602.06895. */
+enum {
+    /* VEGAS grid lookup (Sec. 3.2.2; Lepage 1978):
+     * (s r_0, ..., s r_{k-1}) -> (s r'_0, ..., s r'_{k-1}, s J).  Uses the channel's grid
+     * (ps_program_set_vegas); dimension j of the op uses grid row j. */
+    PS_OP_VEGAS = 1,
+    /* Power-law invariant map G_nu, Eqs. prop_stable_nu / prop_stable_nu1 (Sec. 2.2.1),
+     * stable_invariant_nu of the example graph:
+     * (s r, s|i m, i nu, s|i x_min, s|i x_max, i a) -> (s x, s J).  m <= 0 selects the
+     * auxiliary mass m^2 = -a; nu = 1 is the logarithmic map.  J = dx/dr. */
+    PS_OP_INVARIANT_NU = 2,
+    /* Breit-Wigner map G_BW, Eq. prop_massive (Sec. 2.2.1):
+     * (s r, i M, i Gamma, s|i x_min, s|i x_max) -> (s x, s J). */
+    PS_OP_INVARIANT_BW = 3,
+    /* r_to_x1x2, Eq. pdf_sampling (Sec. 2.2.2): (s r, s shat, i S) -> (s x1, s x2, s J),
+     * J = -log(shat/S)/S. */
+    PS_OP_R_TO_X1X2 = 4,
+    /* com_p_in (Sec. 3.2): (s sqrt_shat) -> (p p_a, p p_b) along +-z. */
+    PS_OP_COM_P_IN = 5,
+    /* t_inv_min_max (Sec. 2.2.4, Eq. t_invariant_theta):
+     * (s s, s|i mA^2, s|i mB^2, s|i m1, s|i m2) -> (s |t|_min, s |t|_max).
+     * The block invariant s and the incoming invariant masses are passed as scalars
+     * (the paper passes the momenta) so that they keep the precision they were sampled with. */
+    PS_OP_T_INV_MIN_MAX = 6,
+    /* two_to_two_particle_scattering_com (Sec. 2.2.4, Eqs. 2_to_2_mapping, ps2_phi_t):
+     * (s r_phi, p pA, p pB, s |t|, s|i m1, s|i m2, s s, s|i mA^2, s|i mB^2) -> (p p1, p p2, s J),
+     * J = 2 pi / (4 sqrt(lambda(s, mA^2, mB^2))). */
+    PS_OP_TWO_TO_TWO_COM = 7,
+    /* two_body_decay (Sec. 2.2.3, Eq. ps2_phi_theta), boosted to the frame of p0:
+     * (s r_phi, s r_theta, s s0, s|i m1, s|i m2, p p0) -> (p p1, p p2, s J),
+     * J = pi sqrt(lambda(s0, m1^2, m2^2)) / (2 s0). */
+    PS_OP_TWO_BODY_DECAY = 8,
+    /* the same decay with the parent at rest: (s r_phi, s r_theta, s s0, s|i m1, s|i m2)
+     * -> (p p1, p p2, s J). */
+    PS_OP_TWO_BODY_DECAY_COM = 9,
+    /* boost_beam (Sec. 3.2): (p q_0, ..., p q_{k-1}, s x1, s x2) -> (p q'_0, ..., p q'_{k-1}):
+     * the longitudinal boost with rapidity log(x1/x2)/2, E' +- p_z' = (E +- p_z) (x1/x2)^(+-1/2). */
+    PS_OP_BOOST_BEAM = 10,
+    /* reduce_product (Sec. 3.2): (s|i a_0, ...) -> (s a_0 a_1 ...), left to right. */
+    PS_OP_REDUCE_PRODUCT = 11,
+    /* cut_unphysical (Sec. 3.2): (s w, s x1, s x2, p q_0, ...) -> (s w').  w' = 0 if w or any
+     * momentum component is not finite, or x1 or x2 is outside (0, 1]. */
+    PS_OP_CUT_UNPHYSICAL = 12,
+    /* scalar arithmetic used for the s-channel ordering bounds (Sec. 2.2.7) */
+    PS_OP_ADD = 13,    /* (s|i a, s|i b) -> (s a + b)   */
+    PS_OP_SUB = 14,    /* (s|i a, s|i b) -> (s a - b)   */
+    PS_OP_MUL = 15,    /* (s|i a, s|i b) -> (s a b)     */
+    PS_OP_DIV = 16,    /* (s|i a, s|i b) -> (s a / b)   */
+    PS_OP_SQRT = 17,   /* (s a) -> (s sqrt(a))          */
+    PS_OP_SQUARE = 18, /* (s a) -> (s a^2)              */
+    PS_OP_MAX = 19,    /* (s|i a, s|i b) -> (s max(a,b)) */
+    PS_OP_MOM_ADD = 20, /* (p a, p b) -> (p a + b)      */
+    PS_OP_MOM_SUB = 21, /* (p a, p b) -> (p a - b)      */
+    /* synthetic parton density (x^alpha (1-x)^beta): (s x, i alpha, i beta) -> (s f). */
+    PS_OP_PDF_POWER = 22,
+    /* propagator denominator 1/((s - M^2)^2 + M^2 Gamma^2): (s s, i M, i Gamma) -> (s P). */
+    PS_OP_PROPAGATOR = 23,
+    /* 1 + cos^2(theta) of a momentum w.r.t. the z axis: (p q) -> (s f). */
+    PS_OP_ONE_PLUS_COS2 = 24,
+    /* SDE channel weight of another channel (Sec. 2.1, products of propagator denominators),
+     * from momenta: (i k, p p_a, p q_1, ..., p q_k, then for each propagator four immediates
+     * i kind, i mask, i M, i Gamma) -> (s P).  kind 0: s = (sum_{i in mask} q_i)^2, factor
+     * 1/((s-M^2)^2 + M^2 Gamma^2); kind 1: t = (p_a - sum_{i in mask} q_i)^2, factor 1/(t-M^2)^2.
+     * Bit i of mask (0-based) selects q_{i+1}. */
+    PS_OP_CHANNEL_WEIGHT = 25,
+    PS_OP_COUNT_ = 26
+};
+
+/* Create an empty graph with `n_random` inputs: ids 0 .. n_random-1 are the scalar
+ * components of the input %0 : float[batch, n_random] (the paper's unstack). */
+int ps_graph_create(int n_random, ps_graph* out);
+
+/* Append one instruction.  out_ids receives the ids of the n_out new values (SSA:
+ * ids are never redefined).  Returns PS_ERR_GRAPH for an unknown opcode, a wrong
+ * number or type of arguments, or an undefined id. */
+int ps_graph_add(ps_graph g, int opcode, const ps_arg* args, int n_args, int* out_ids, int n_out);
+
+/* Output roles. */
+#define PS_ROLE_MOMENTUM 0 /* momentum outputs, in order (event record [p_a, p_b, p_1..p_n]) */
+#define PS_ROLE_X1 1
+#define PS_ROLE_X2 2
+#define PS_ROLE_WEIGHT 3
+#define PS_ROLE_ALPHA 4
+
+/* Declare the outputs: ids[k] with role roles[k].  Exactly one WEIGHT is required. */
+int ps_graph_set_outputs(ps_graph g, const int* ids, const int* roles, int n);
+
+/* Number of instructions / values / random inputs of a graph. */
+int ps_graph_info(ps_graph g, int* n_instructions, int* n_values, int* n_random);
+
+/* Text listing of the graph in the style of the paper's example (Fig. compute_graph).
+ * Writes at most cap bytes (NUL-terminated) into buf; *needed receives the full size. */
+int ps_graph_dump(ps_graph g, char* buf, size_t cap, size_t* needed);
+
+int ps_graph_free(ps_graph g);
+
+/* ----------------------------------------------------- topology builder */
+/* A channel topology (Sec. 2.2, Eq. ps_decomposition) from which the builder emits the
+ * instruction list: s-channel invariants in a given order with recursive bounds
+ * (Sec. 2.2.7), an inward t-channel chain (Sec. 2.2.8), two-body decays, the PDF
+ * convolution and beam boost, the Jacobian product, an integrand and cut_unphysical. */
+#define PS_MAX_NODES 32
+#define PS_MAX_LEGS 10
+#define PS_NODE_LEAF 0   /* final-state particle                       */
+#define PS_NODE_DECAY 1  /* s-channel 1 -> 2 node (the root: shat)      */
+#define PS_NODE_TCHAIN 2 /* the root as a t-channel chain of legs       */
+
+#define PS_INTEGRAND_NONE 0          /* f = 1                                          */
+#define PS_INTEGRAND_ONE_PLUS_COS2 1 /* f = 1 + cos^2 theta of final-state particle 1  */
+#define PS_INTEGRAND_PDF_PROPS 2     /* f = f(x1) f(x2) prod(resonant s-propagators)   */
+#define PS_INTEGRAND_PDF_SDE 3       /* f = f(x1) f(x2) sum_c P_c, w = w_ps f alpha_c  */
+
+typedef struct {
+    int32_t kind;                 /* PS_NODE_*                                         */
+    int32_t n_children;
+    int32_t children[PS_MAX_LEGS];/* node ids; t-chain legs ordered from leg A to leg B */
+    int32_t leaf_index;           /* leaf: final-state index 0..n-1                    */
+    int32_t in_sde;               /* decay: propagator enters the SDE product           */
+    double mass;                  /* leaf: on-shell mass                               */
+    double prop_mass, prop_width; /* decay: Breit-Wigner if width > 0                  */
+    double nu;                    /* decay with width 0: power-law exponent            */
+} ps_node_desc;
+
+typedef struct {
+    int32_t n_out;       /* final-state multiplicity n                                  */
+    int32_t hadronic;    /* 1: shat map, r_to_x1x2 and boost_beam; 0: fixed sqrt_s      */
+    int32_t lab_frame;   /* hadronic: 1 = boost to the lab, 0 = stay in the parton frame */
+    int32_t integrand;   /* PS_INTEGRAND_*                                              */
+    int32_t n_nodes;     /* node 0 is the root                                          */
+    int32_t n_sorder;
+    int32_t sorder[PS_MAX_NODES]; /* decay nodes (not the root) in sampling order        */
+    int32_t tside[PS_MAX_LEGS];   /* t-chain step i = 1..kappa-1 in tside[i]: 0 = A, 1 = B */
+    int32_t vegas_dims, vegas_bins;
+    double sqrt_s;       /* fixed energy                                                */
+    double s_beam;       /* hadronic S                                                  */
+    double a_shift;      /* auxiliary m^2 = -a for massless maps                         */
+    double shat_mass, shat_width, shat_nu;
+    double t_nu, ts_nu;  /* |t| map exponent; exponent of the t-chain invariants         */
+    double t_prop_mass;  /* t-channel propagator mass in the SDE product                 */
+    double pdf_alpha, pdf_beta;
+    ps_node_desc nodes[PS_MAX_NODES];
+} ps_channel_desc;
+
+/* Random dimension count of a channel: 3n-2 (hadronic) or 3n-4. */
+int ps_channel_dims(const ps_channel_desc* ch, int* n_random);
+
+/* Build the graph of channel `which` of the set ch[0..n_ch-1] (the whole set is needed
+ * for PS_INTEGRAND_PDF_SDE, whose alpha_c uses every channel's propagators).
+ * Dimension order (generalising Fig. compute_graph): shat, the s-channel invariants in
+ * sampling order, the t-chain invariants, x1x2, (r_phi, r_t) per t-block, (r_phi, r_theta)
+ * per decay in depth-first order; VEGAS maps the first vegas_dims of them. */
+int ps_graph_build_channel(const ps_channel_desc* ch, int n_ch, int which, ps_graph* out);
+
+/* ---------------------------------------------------------------- programs */
+#define PS_PRECISION_F64 0 /* every step in binary64 */
+
+typedef struct {
+    int32_t block_threads; /* events per tile = threads per CTA (multiple of 32; 0 = default 128) */
+    int32_t ctas_per_sm;   /* resident CTAs requested per SM (0 = as many as fit, up to 4)      */
+    int32_t precision;     /* PS_PRECISION_*                                                  */
+    int32_t reserved;
+} ps_options;
+
+/* Compile n_ch graphs (channel c = graphs[c]) for `device`.  Every channel must declare
+ * the same outputs.  Allocates the program's device constants on that device. */
+int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, int device, ps_program* out);
+
+/* Upload a VEGAS grid for channel ch: edges_host[dims][bins+1], each row increasing from 0 to 1. */
+int ps_program_set_vegas(ps_program p, int ch, int dims, int bins, const double* edges_host);
+int ps_program_get_vegas(ps_program p, int ch, int dims, int bins, double* edges_host);
+
+/* Output buffers (device, caller-owned, 16-byte aligned).  Event e of channel c is stored at
+ * column off_c + e, off_c = sum of the event counts of channels < c.  Momentum k, component
+ * mu lives at momenta[(4k + mu) * ld + column].  Pointers for roles a graph does not have may
+ * be NULL; so may any output the caller does not want (it is then not written). */
+typedef struct {
+    double* momenta;
+    double* x1;
+    double* x2;
+    double* weight;
+    double* alpha;
+    int64_t ld; /* leading dimension of momenta (>= total events) */
+} ps_out_buffers;
+
+/* Scratch memory needed by ps_generate / ps_map for these event counts (bytes). */
+int ps_workspace_size(ps_program p, const int64_t* events_per_ch, size_t* bytes);
+
+/* Generate events_per_ch[c] events of every channel in one launch, random numbers drawn
+ * in-kernel by Philox4x32-10 with key = seed and counter = (event_lo, event_hi, channel,
+ * dimension/2), event = event_offset + index within the channel.  Asynchronous on `stream`;
+ * no allocation and no host synchronisation.  workspace: caller-owned device scratch of at
+ * least ps_workspace_size bytes (256-byte aligned).  Per-channel statistics of this call are
+ * kept in the program (ps_stats). */
+int ps_generate(ps_program p, const int64_t* events_per_ch, uint64_t seed, uint64_t event_offset,
+                const ps_out_buffers* out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Explicit-input form: map `batch` given points r_dev[j * ld_r + e] (SoA, j < n_random) of
+ * channel ch.  Outputs start at column 0. */
+int ps_map(ps_program p, int ch, int64_t batch, const double* r_dev, int64_t ld_r,
+           const ps_out_buffers* out, void* workspace, size_t workspace_bytes, void* stream);
+
+typedef struct {
+    double n;          /* events                */
+    double n_nonzero;  /* events with w != 0    */
+    double sum_w;
+    double sum_w2;
+    double max_w;
+} ps_channel_stats;
+
+/* Copy the statistics of the last ps_generate / ps_map (synchronises `stream`). */
+int ps_stats(ps_program p, ps_channel_stats* host_out, int n_ch, void* stream);
+
+/* VEGAS training: while enabled, ps_generate also accumulates, per channel, mapped
+ * dimension j and bin k, the sum of w^2 over events whose r_j falls in bin k. */
+int ps_vegas_training(ps_program p, int enable);
+/* Copy channel ch's accumulated histogram [dims][bins] (synchronises). */
+int ps_vegas_histogram(ps_program p, int ch, double* hist_host, void* stream);
+/* Rebin channel ch from its histogram (Lepage: 3-point smoothing, compression exponent
+ * alpha), upload the new grid and clear the histogram (synchronises). */
+int ps_vegas_adapt(ps_program p, int ch, double alpha, void* stream);
+
+/* Device status counters of the program since the last reset: [0] non-finite weights
+ * before the cut, [1] events cut by cut_unphysical, [2] grid index clamps.  Synchronises. */
+int ps_status(ps_program p, int64_t* counters_host, int n, void* stream);
+int ps_status_reset(ps_program p, void* stream);
+
+int ps_program_free(ps_program p);
+
+/* Number of kernel launches issued by the library since load (all programs). */
+int64_t ps_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PS_H */

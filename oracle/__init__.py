@@ -24,8 +24,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MAXN, MAXK, MAXP, MAXC, NAUX = 32, 10, 16, 32, 8
-AUX = {"shat": 0, "w_ps": 1, "f": 2, "jac_vegas": 3, "p_own": 4, "cut": 5, "fail": 6, "p_own_momenta": 7}
+MAXN, MAXK, MAXP, MAXC, NAUX = 32, 10, 16, 32, 10
+AUX = {"shat": 0, "w_ps": 1, "f": 2, "jac_vegas": 3, "p_own": 4, "cut": 5, "fail": 6, "p_own_momenta": 7, "cond": 8, "cond_p": 9}
 
 
 def build(force=False):

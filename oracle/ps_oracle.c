@@ -34,7 +34,7 @@
 #define ORC_MAXK 10   /* children per node (t-chain legs) */
 #define ORC_MAXP 16   /* propagators per channel in the multichannel table */
 #define ORC_MAXC 32   /* channels in the multichannel table */
-#define ORC_NAUX 8
+#define ORC_NAUX 10
 
 /* ------------------------------------------------------------------------ */
 /* Topology description (oracle-private layout; filled by oracle/__init__.py) */
@@ -135,9 +135,12 @@ void orc_random_batch(uint64_t seed, uint32_t ch, uint64_t ev0, int64_t B, int d
 /* ------------------------------------------------------------------------ */
 /* Kinematic helpers                                                          */
 /* ------------------------------------------------------------------------ */
-/* Kallen function lambda(x,y,z) = (x-y-z)^2 - 4yz (Sec. 2.2.3).  For y,z >= 0 the
- * factorised form (x-(sqrt y+sqrt z)^2)(x-(sqrt y-sqrt z)^2) is used, which has no
- * cancellation at threshold; the result is clamped at 0. */
+/* Kallen function lambda(x,y,z) = (x-y-z)^2 - 4yz (Sec. 2.2.3), in a form without
+ * cancellation for each sign pattern of y, z (x >= 0):
+ *   y, z >= 0:  (x-(sqrt y+sqrt z)^2)(x-(sqrt y-sqrt z)^2)   (factorised; exact at threshold)
+ *   y, z <= 0:  x^2 + 2x(|y|+|z|) + (|y|-|z|)^2              (sum of non-negative terms)
+ *   otherwise:  (x-y-z)^2 - 4yz                             (-4yz >= 0)
+ * The result is clamped at 0. */
 double orc_kallen(double x, double y, double z)
 {
     double l;
@@ -145,6 +148,9 @@ double orc_kallen(double x, double y, double z)
         double sy = sqrt(y), sz = sqrt(z);
         double p = sy + sz, m = sy - sz;
         l = (x - p * p) * (x - m * m);
+    } else if (y <= 0.0 && z <= 0.0) {
+        double Y = -y, Z = -z, d = Y - Z;
+        l = x * x + 2.0 * x * (Y + Z) + d * d;
     } else {
         double u = x - y - z;
         l = u * u - 4.0 * y * z;
@@ -241,6 +247,7 @@ int orc_map_nu(double r, double m, double nu, double xmin, double xmax, double a
         *x = m2 + xm;
         *jac = -xm * rho / (w * (1.0 + z));
     }
+    *x = fmin(fmax(*x, xmin), xmax); /* G maps into [x_min, x_max] (rounding at the ends) */
     return 0;
 }
 
@@ -289,6 +296,7 @@ int orc_map_bw(double r, double M, double G, double xmin, double xmax, double* x
         *x = m2 + mg * t;
         *jac = D * mg * (1.0 + t * t);
     }
+    *x = fmin(fmax(*x, xmin), xmax); /* G maps into [x_min, x_max] (rounding at the ends) */
     return 0;
 }
 
@@ -405,26 +413,27 @@ double orc_two_to_two(double rphi, const double* pA, const double* pB, double ta
     return 2.0 * ORC_PI / (4.0 * sqrt(orc_kallen(s, mA2, mB2)));
 }
 
-/* Longitudinal boost from the partonic rest frame to the lab (boost_beam, Sec. 3.2):
- * beta = (x1-x2)/(x1+x2), gamma = (x1+x2)/(2 sqrt(x1 x2)). */
+/* Longitudinal boost from the partonic rest frame to the lab (boost_beam, Sec. 3.2) with
+ * beta = (x1-x2)/(x1+x2), gamma = (x1+x2)/(2 sqrt(x1 x2)), written on the light cone:
+ * E' + p_z' = rho (E + p_z), E' - p_z' = (E - p_z)/rho, rho = sqrt(x1/x2).  The same boost
+ * without the cancellation of gamma E + gamma beta p_z for extreme boosts (the incoming
+ * partons come out as exactly x_i sqrt(S)/2). */
 static void boost_beam(double* p, double x1, double x2)
 {
-    double rt = sqrt(x1 * x2);
-    double g = (x1 + x2) / (2.0 * rt);
-    double gb = (x1 - x2) / (2.0 * rt);
-    double e = p[0], z = p[3];
-    p[0] = g * e + gb * z;
-    p[3] = g * z + gb * e;
+    double rho = sqrt(x1 / x2);
+    double plus = rho * (p[0] + p[3]);
+    double minus = (p[0] - p[3]) / rho;
+    p[0] = 0.5 * (plus + minus);
+    p[3] = 0.5 * (plus - minus);
 }
 
 static void unboost_beam(double* p, double x1, double x2)
 {
-    double rt = sqrt(x1 * x2);
-    double g = (x1 + x2) / (2.0 * rt);
-    double gb = (x1 - x2) / (2.0 * rt);
-    double e = p[0], z = p[3];
-    p[0] = g * e - gb * z;
-    p[3] = g * z - gb * e;
+    double rho = sqrt(x1 / x2);
+    double plus = (p[0] + p[3]) / rho;
+    double minus = rho * (p[0] - p[3]);
+    p[0] = 0.5 * (plus + minus);
+    p[3] = 0.5 * (plus - minus);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -576,7 +585,8 @@ static double min_mass(const orc_channel* ch, int j, const int* sampled, const d
 
 /* Maximal mass of node i (Sec. 2.2.7 step 3): walk towards the root until a sampled
  * node r; subtract the minimal masses of every node branching off the path. */
-static double max_mass(const orc_channel* ch, const layout* L, int i, const int* sampled, const double* s)
+static double max_mass(const orc_channel* ch, const layout* L, int i, const int* sampled, const double* s,
+                       double* subtracted)
 {
     double sum = 0.0;
     int cur = i;
@@ -585,7 +595,10 @@ static double max_mass(const orc_channel* ch, const layout* L, int i, const int*
         const orc_node* pn = &ch->node[p];
         for (int k = 0; k < pn->nchild; ++k)
             if (pn->child[k] != cur) sum += min_mass(ch, pn->child[k], sampled, s);
-        if (sampled[p]) return sqrt(s[p]) - sum;
+        if (sampled[p]) {
+            if (subtracted) *subtracted = sum;
+            return sqrt(s[p]) - sum;
+        }
         cur = p;
     }
 }
@@ -625,7 +638,7 @@ static double sde_from_momenta(const orc_sde* sde, int j, const double* mom)
 }
 
 /* aux outputs per event */
-enum { AUX_SHAT = 0, AUX_WPS, AUX_F, AUX_JV, AUX_POWN, AUX_CUT, AUX_FAIL, AUX_SPARE };
+enum { AUX_SHAT = 0, AUX_WPS, AUX_F, AUX_JV, AUX_POWN, AUX_CUT, AUX_FAIL, AUX_SPARE, AUX_COND, AUX_CONDP };
 
 /* Forward map of one event.  r: d random numbers in (0,1).  mom: (n+2)*4 lab momenta
  * [p_a, p_b, p_1..p_n]; x[2]: x1, x2 (1, 1 at fixed energy); returns the weight. */
@@ -645,6 +658,10 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
         r[j] = orc_vegas_map(r[j], grid + j * (ch->vegas_bins + 1), ch->vegas_bins, &jv);
 
     double jac = pow(2.0 * ORC_PI, 4 - 3 * n) * jv; /* (2 pi)^(4-3n), Sec. 2.2 */
+    double cond = 1.0;  /* weight: largest condition number of a range width, threshold or x factor */
+    double condp = 1.0; /* momenta: rounding amplification -- threshold and backward-t condition numbers
+                         * (both propagate through the later legs of a t-chain), gamma^2 of boosts into
+                         * rest frames of composite momenta */
     double s[ORC_MAXN];
     int sampled[ORC_MAXN];
     memset(sampled, 0, sizeof sampled);
@@ -671,16 +688,31 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
         int j = ch->sorder[i];
         const orc_node* nd = &ch->node[j];
         double mlo = min_mass(ch, j, sampled, s);
-        double mhi = max_mass(ch, &L, j, sampled, s);
+        double max_mass_sub = 0.0;
+        double mhi = max_mass(ch, &L, j, sampled, s, &max_mass_sub);
         double smin = mlo * mlo, smax = mhi > 0.0 ? mhi * mhi : 0.0;
         if (mhi < mlo) { fail = 1; smax = smin; }
+        /* condition number of the range width: sqrt(s_r) / (m_max - m_min), with sqrt(s_r) = m_max + (the
+         * masses subtracted); a rounding of the masses is amplified by it in the width */
+        {
+            double top = mhi + (max_mass_sub);
+            double wdt = mhi - mlo;
+            double k = wdt > 0.0 ? top / wdt : 1e300;
+            if (k > cond) cond = k;
+        }
         double sv;
         if (nd->G > 0.0) fail |= orc_map_bw(r[L.d_s[j]], nd->M, nd->G, smin, smax, &sv, &j1);
         else fail |= orc_map_nu(r[L.d_s[j]], nd->M, nd->nu, smin, smax, ch->a, &sv, &j1);
         jac *= j1;
         s[j] = sv;
         sampled[j] = 1;
-        if (nd->sde) P_own *= prop_factor(sv, nd->M, nd->G);
+        if (nd->sde) {
+            P_own *= prop_factor(sv, nd->M, nd->G);
+            /* a propagator near a narrow peak amplifies an ulp of s by 2 s |s-M^2| / ((s-M^2)^2 + M^2 G^2) */
+            double dd = sv - nd->M * nd->M;
+            double k = 2.0 * sv * fabs(dd) / (dd * dd + nd->M * nd->M * nd->G * nd->G);
+            if (k > cond) cond = k;
+        }
     }
 
     /* t-chain invariants s_1..s_{kappa-1} (Sec. 2.2.8): legs are taken inwards from
@@ -710,6 +742,11 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
             double mx = sqrt(sts[i - 1]) - mi;
             double smax = mx > 0.0 ? mx * mx : 0.0;
             if (smax < smin) { fail = 1; smax = smin; }
+            {
+                double wdt = mx - msum;
+                double k = wdt > 0.0 ? sqrt(sts[i - 1]) / wdt : 1e300;
+                if (k > cond) cond = k;
+            }
             double sv;
             fail |= orc_map_nu(r[L.d_ts[i]], 0.0, ch->ts_nu, smin, smax, ch->a, &sv, &j1);
             jac *= j1;
@@ -722,6 +759,10 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
     if (ch->hadronic) {
         orc_r_to_x1x2(r[L.d_x], shat, ch->S, &x1, &x2, &j1);
         jac *= j1;
+        /* J_x = -log(tau)/S: shat carries up to ~30 ulps (an exponential of an argument up to
+         * log(S/a)), which 1/|log tau| amplifies as tau -> 1 */
+        double k = 30.0 / fabs(log(shat / ch->S));
+        if (k > cond) cond = k;
     }
 
     /* incoming partons in the partonic rest frame (com_p_in) */
@@ -759,6 +800,22 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
             fail |= orc_map_nu(r[L.d_tt[i]], 0.0, ch->t_nu, tlo, thi, ch->a, &tabs, &jt);
             double q1[4], q2[4];
             double j22 = orc_two_to_two(r[L.d_tphi[i]], pA, pB, tabs, mt1, mt2, scur, mA2, mB2, q1, q2);
+            {   /* the legs' components and the sampled block invariant agree only to eps E0^2, which the
+                 * boost into and out of the block rest frame amplifies by gamma^2 = E0^2/s */
+                double e0 = pA[0] + pB[0];
+                double g2 = e0 * e0 / scur;
+                if (g2 > condp) condp = g2;
+            }
+            {
+                double gap = scur - (mt1 + mt2) * (mt1 + mt2);
+                double k = gap > 0.0 ? scur / gap : 1e300;
+                if (k > cond) cond = k;
+                if (k > condp) condp = k;
+                /* 1 + cos(theta) = (|t|_max - |t|)/B: |t| has ulp error relative to |t|_max; the
+                 * backward leg's p_T and the next blocks' frames inherit it */
+                double kt = (thi - tabs) > 0.0 ? thi / (thi - tabs) : 1e300;
+                if (kt > condp) condp = kt;
+            }
             jac *= jt * j22;
             {   /* t-propagator of the SDE product, from the sampled invariant */
                 double dd = -tabs - ch->Mt * ch->Mt;
@@ -790,6 +847,16 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
         double jd = orc_two_body_decay(r[L.d_dphi[j]], r[L.d_dth[j]], s[j], m1, m2,
                                        j == 0 ? NULL : p[j], p[c1], p[c2]);
         jac *= jd;
+        if (j != 0) {   /* the parent momentum's rounding, boosted with gamma = E0/m0 */
+            double g2 = p[j][0] * p[j][0] / s[j];
+            if (g2 > condp) condp = g2;
+        }
+        {   /* closeness to threshold: lambda's factor s0 - (m1+m2)^2 amplifies rounding by s0/(...) */
+            double gap = s[j] - (m1 + m2) * (m1 + m2);
+            double k = gap > 0.0 ? s[j] / gap : 1e300;
+            if (k > cond) cond = k;
+            if (k > condp) condp = k;
+        }
     }
 
     /* stack [p_a, p_b, p_1..p_n] and boost to the lab (boost_beam) */
@@ -804,6 +871,11 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
 
     /* integrand and multichannel weight */
     double f = 1.0, alpha = 1.0, p_mom = 0.0;
+    if (ch->hadronic && (ch->integrand == 2 || ch->integrand == 3 || ch->integrand == 4)) {
+        /* (1-x)^beta of the parton density: an ulp of x is amplified by beta x/(1-x) */
+        double k = fabs(ch->pdf_b) * fmax(x1 / (1.0 - x1), x2 / (1.0 - x2));
+        if (k > cond) cond = k;
+    }
     if (ch->integrand == 1) {
         const double* q = mom + 8;
         double c = q[3] / sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
@@ -823,11 +895,10 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
     }
     double w = jac * f * alpha;
 
-    /* cut_unphysical (reading: non-finite weight or momenta, x outside (0,1], E < 0) */
+    /* cut_unphysical (reading: non-finite weight or momenta, or x1, x2 outside (0,1]) */
     int cut = 0;
     if (!isfinite(w)) cut = 1;
     for (int i = 0; i < 4 * (n + 2); ++i) if (!isfinite(mom[i])) cut = 1;
-    for (int i = 0; i < n + 2; ++i) if (mom[4 * i] < 0.0) cut = 1;
     if (!(x1 > 0.0 && x1 <= 1.0 && x2 > 0.0 && x2 <= 1.0)) cut = 1;
     if (cut) w = 0.0;
 
@@ -835,6 +906,8 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
     if (aux) {
         aux[AUX_SHAT] = shat; aux[AUX_WPS] = jac; aux[AUX_F] = f; aux[AUX_JV] = jv;
         aux[AUX_POWN] = P_own * own_t_props; aux[AUX_CUT] = cut; aux[AUX_FAIL] = fail; aux[AUX_SPARE] = p_mom;
+        aux[AUX_COND] = cond;
+        aux[AUX_CONDP] = condp;
     }
     return w;
 }
@@ -969,7 +1042,7 @@ static void inverse_event(const orc_channel* ch, const double* grid, const doubl
         int j = ch->sorder[i];
         const orc_node* nd = &ch->node[j];
         double mlo = min_mass(ch, j, sampled, s);
-        double mhi = max_mass(ch, &L, j, sampled, s);
+        double mhi = max_mass(ch, &L, j, sampled, s, NULL);
         double smin = mlo * mlo, smax = mhi * mhi;
         r[L.d_s[j]] = (nd->G > 0.0) ? orc_inv_bw(s[j], nd->M, nd->G, smin, smax)
                                     : orc_inv_nu(s[j], nd->M, nd->nu, smin, smax, ch->a);

@@ -1,0 +1,677 @@
+// kernels.cu -- sm_103a kernels of the phase-space library.
+//
+// ps_map_kernel evaluates the compiled instruction list of a channel (the
+// paper's compute graph, Sec. 3.1 / Fig. compute_graph) for one event per
+// thread.  All instructions of an event run back to back in that thread: the
+// values live in a per-thread slot file in shared memory (slot s of thread t at
+// smem[s * block + t], conflict-free), the byte-code, immediates and VEGAS grid
+// of the channel are staged in shared memory once per channel change, and only
+// the declared outputs (SoA, coalesced) and one partial-sum record per tile of
+// `block` events reach global memory.  Tiles of all channels are distributed
+// over a persistent grid; tile -> channel is a scan of at most 32 prefix sums
+// held in the kernel parameters.
+//
+// Every branch inside an op depends only on the op's immediates (warp-uniform)
+// or is resolved by selects, so the warps of a channel never diverge.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+
+#include "ps_internal.h"
+
+namespace ps {
+
+static unsigned long long g_launches = 0;
+
+namespace dev {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+struct P4 {
+    double e, x, y, z;
+};
+
+__device__ __forceinline__ P4 p4_add(P4 a, P4 b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ P4 p4_sub(P4 a, P4 b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ double p4_sq(P4 a) { return a.e * a.e - a.x * a.x - a.y * a.y - a.z * a.z; }
+
+// Kallen lambda(x, y, z) = (x - y - z)^2 - 4 y z (x >= 0), without cancellation:
+//   y, z >= 0: (x - (sqrt y + sqrt z)^2)(x - (sqrt y - sqrt z)^2)
+//   y, z <= 0: x^2 + 2x(|y| + |z|) + (|y| - |z|)^2  (space-like legs of a t-chain)
+//   mixed:     (x - y - z)^2 - 4 y z                (-4yz >= 0)
+// clamped at zero.
+__device__ __forceinline__ double kallen(double x, double y, double z) {
+    double l;
+    if (y >= 0.0 && z >= 0.0) {
+        double ry = sqrt(y), rz = sqrt(z);
+        double hi = ry + rz, lo = ry - rz;
+        l = (x - hi * hi) * (x - lo * lo);
+    } else if (y <= 0.0 && z <= 0.0) {
+        double d = z - y;
+        l = x * x - 2.0 * x * (y + z) + d * d;
+    } else {
+        double d = x - y - z;
+        l = d * d - 4.0 * y * z;
+    }
+    return fmax(l, 0.0);
+}
+
+// Pure boost of p from the rest frame of q (invariant mass mq) to the frame where q is given.
+__device__ __forceinline__ P4 boost_out(P4 p, P4 q, double mq) {
+    double qp = q.x * p.x + q.y * p.y + q.z * p.z;
+    double inv = 1.0 / mq;
+    double c = qp / (mq * (q.e + mq)) + p.e * inv;
+    return {(q.e * p.e + qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
+}
+
+// The inverse boost: p given in the frame of q -> rest frame of q.
+__device__ __forceinline__ P4 boost_in(P4 p, P4 q, double mq) {
+    double qp = q.x * p.x + q.y * p.y + q.z * p.z;
+    double inv = 1.0 / mq;
+    double c = qp / (mq * (q.e + mq)) - p.e * inv;
+    return {(q.e * p.e - qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al., SC'11: two 32x32 multiplies per round, Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// (k + 1/2) 2^-52 for the top 52 bits k of (hi:lo), exactly: the double 1 + k 2^-52 is
+// assembled from bits and (1 - 2^-53) subtracted, which is exact by Sterbenz's lemma.
+__device__ __forceinline__ double unit_from_bits(uint32_t hi, uint32_t lo) {
+    unsigned long long k = ((static_cast<unsigned long long>(hi) << 32) | lo) >> 12;
+    double one_plus = __longlong_as_double(0x3FF0000000000000ULL | k);
+    return one_plus - 0x1.fffffffffffffp-1;
+}
+
+// ---------------------------------------------------------------- invariant maps (Sec. 2.2.1)
+// Power law G_nu / log map, anchored at x_min for nu <= 1 and at m^2 for nu > 1, so that
+// 1 + z >= 1 and x - m^2 (and, for nu <= 1, x - x_min) keep full precision:
+//   L = log1p((x_max - x_min)/lo), lo = x_min - m^2, hi = x_max - m^2, w = 1 - nu
+//   nu == 1: x = x_min + lo expm1(r L),              J = (x - m^2) L
+//   nu <  1: z = r expm1(w L),  x = x_min + lo expm1(log1p(z)/w),  J = (x - m^2) rho/(w (1+z))
+//   nu >  1: z = (1-r) expm1(-w L), x - m^2 = hi exp(log1p(z)/w), J = -(x - m^2) rho'/(w (1+z))
+__device__ __forceinline__ bool map_nu(double r, double m, double nu, double xmin, double xmax, double a,
+                                       double& x, double& jac) {
+    double m2 = (m > 0.0) ? m * m : -a;
+    double lo = xmin - m2, hi = xmax - m2;
+    bool ok = (lo > 0.0) && (hi >= lo);
+    double L = log1p((xmax - xmin) / lo);
+    if (nu == 1.0) {
+        double e = expm1(r * L);
+        double xm = fma(lo, e, lo);
+        x = fma(lo, e, xmin);
+        jac = xm * L;
+    } else if (nu < 1.0) {
+        double w = 1.0 - nu;
+        double rho = expm1(w * L);
+        double z = r * rho;
+        double e = expm1(log1p(z) / w);
+        double xm = fma(lo, e, lo);
+        x = fma(lo, e, xmin);
+        jac = xm * rho / (w * (1.0 + z));
+    } else {
+        double w = 1.0 - nu;
+        double rho = expm1(-w * L);
+        double z = (1.0 - r) * rho;
+        double xm = hi * exp(log1p(z) / w);
+        x = m2 + xm;
+        jac = -xm * rho / (w * (1.0 + z));
+    }
+    x = fmin(fmax(x, xmin), xmax);  // the map lands in [x_min, x_max] (rounding at the ends)
+    if (!ok) { x = xmin; jac = 0.0; }
+    return ok;
+}
+
+// Breit-Wigner G_BW with a = tan u1, b = tan u2, D = atan2(b - a, 1 + ab), u = u1 + D r.
+// One tan per event, argument and combination chosen by selects:
+//   u < -pi/4: T = tan(D r),     x = x_min + mG T(1+a^2)/(1-aT), 1+tan^2u = (1+a^2)(1+T^2)/(1-aT)^2
+//   u >  pi/4: T = tan(D (1-r)), tan u = (b-T)/(1+bT), 1+tan^2u = (1+b^2)(1+T^2)/(1+bT)^2
+//   otherwise: T = tan(u).        J = D mG (1 + tan^2 u)
+__device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin, double xmax,
+                                       double& x, double& jac) {
+    double mg = M * G, m2 = M * M;
+    bool ok = (mg > 0.0) && (xmax >= xmin);
+    double inv_mg = 1.0 / mg;
+    double a = (xmin - m2) * inv_mg, b = (xmax - m2) * inv_mg;
+    double D = atan2((xmax - xmin) * inv_mg, fma(a, b, 1.0));
+    double u = atan(a) + D * r;
+    bool low = u < -0.25 * kPi, high = u > 0.25 * kPi;
+    double arg = low ? D * r : (high ? D * (1.0 - r) : u);
+    double T = tan(arg);
+    double sec2;
+    if (low) {
+        double den = 1.0 - a * T;
+        double rd = 1.0 / den;
+        x = xmin + mg * (T * (1.0 + a * a) * rd);
+        sec2 = (1.0 + a * a) * (1.0 + T * T) * (rd * rd);
+    } else if (high) {
+        double den = 1.0 + b * T;
+        double rd = 1.0 / den;
+        x = m2 + mg * ((b - T) * rd);
+        sec2 = (1.0 + b * b) * (1.0 + T * T) * (rd * rd);
+    } else {
+        x = m2 + mg * T;
+        sec2 = 1.0 + T * T;
+    }
+    jac = D * mg * sec2;
+    x = fmin(fmax(x, xmin), xmax);
+    if (!ok) { x = xmin; jac = 0.0; }
+    return ok;
+}
+
+// t range of a 2->2 block (Eq. t_invariant_theta): t = A + B cos(theta); the root of larger
+// magnitude directly, the other from t+ t- =
+//   (m1^2 - mA^2)(m2^2 - mB^2) + (m1^2 mB^2 - m2^2 mA^2)(m1^2 - m2^2 - mA^2 + mB^2)/s.
+__device__ __forceinline__ void t_range(double s, double mA2, double mB2, double m1, double m2,
+                                        double& tabs_min, double& tabs_max, double& B) {
+    double m12 = m1 * m1, m22 = m2 * m2;
+    double inv2s = 0.5 / s;
+    double A = mA2 + m12 - (s + mA2 - mB2) * (s + m12 - m22) * inv2s;
+    B = sqrt(kallen(s, mA2, mB2) * kallen(s, m12, m22)) * inv2s;
+    double prod = (m12 - mA2) * (m22 - mB2) + (m12 * mB2 - m22 * mA2) * (m12 - m22 - mA2 + mB2) / s;
+    double big = (A <= 0.0) ? A - B : A + B;   // root without cancellation
+    double small = (big != 0.0) ? prod / big : 0.0;
+    double tplus = (A <= 0.0) ? small : big;  // closest to zero
+    double tminus = (A <= 0.0) ? big : small;
+    tabs_min = -tplus;
+    tabs_max = -tminus;
+}
+
+// 2->2 block in (phi, t), Sec. 2.2.4: the polar axis is the direction of pA in the rest
+// frame of p0 = pA + pB; cos(theta) from |t| via 1 -+ cos = (|t| - |t|_min)/B resp.
+// (|t|_max - |t|)/B, whichever is smaller; the momentum is rotated by R(phi_A, theta_A)
+// = Rz(phi_A) Ry(theta_A) (Sec. 2.2.6) and boosted back.
+__device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double tabs, double m1, double m2,
+                                             double s, double mA2, double mB2, P4& p1, P4& p2) {
+    P4 p0 = p4_add(pA, pB);
+    double m0 = sqrt(s);
+    P4 a = boost_in(pA, p0, m0);
+    double pt2 = a.x * a.x + a.y * a.y;
+    double pt = sqrt(pt2);
+    double rp = rsqrt(pt2 + a.z * a.z);
+    double ca = a.z * rp, sa = pt * rp;
+    bool has_pt = pt > 0.0;
+    double ipt = has_pt ? 1.0 / pt : 0.0;
+    double cpa = has_pt ? a.x * ipt : 1.0, spa = has_pt ? a.y * ipt : 0.0;
+
+    double tlo, thi, B;
+    t_range(s, mA2, mB2, m1, m2, tlo, thi, B);
+    double dlo = tabs - tlo, dhi = thi - tabs;
+    bool near_lo = dlo <= dhi;
+    double iB = (B > 0.0) ? 1.0 / B : 0.0;
+    double first = (near_lo ? dlo : dhi) * iB;  // 1 - cos (near_lo) or 1 + cos
+    double omc = (B > 0.0) ? (near_lo ? first : 2.0 - first) : 1.0;
+    double opc = (B > 0.0) ? (near_lo ? 2.0 - first : first) : 1.0;
+    double cth = (omc <= opc) ? 1.0 - omc : opc - 1.0;
+    double sth = sqrt(fmax(omc * opc, 0.0));
+    double sph, cph;
+    sincospi(2.0 * rphi, &sph, &cph);
+
+    double m12 = m1 * m1, m22 = m2 * m2;
+    double i2m0 = 0.5 / m0;
+    double pabs = sqrt(kallen(s, m12, m22)) * i2m0;
+    double e1 = (s + m12 - m22) * i2m0, e2 = (s + m22 - m12) * i2m0;
+    double vx = pabs * sth * cph, vy = pabs * sth * sph, vz = pabs * cth;
+    // Ry(theta_A) then Rz(phi_A)
+    double rx = ca * vx + sa * vz, rz = -sa * vx + ca * vz;
+    P4 q1 = {e1, cpa * rx - spa * vy, spa * rx + cpa * vy, rz};
+    P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
+    p1 = boost_out(q1, p0, m0);
+    p2 = boost_out(q2, p0, m0);
+    return 0.5 * kPi / sqrt(kallen(s, mA2, mB2));
+}
+
+// 1->2 decay in (phi, theta), Sec. 2.2.3: cos = 2 r_theta - 1, sin = 2 sqrt(r_theta (1 - r_theta)),
+// phi = 2 pi r_phi, built at rest and optionally boosted to the frame of p0.
+template <bool kBoost>
+__device__ __forceinline__ double two_body(double rphi, double rth, double s0, double m1, double m2, P4 p0,
+                                           P4& p1, P4& p2) {
+    double m0 = sqrt(s0);
+    double m12 = m1 * m1, m22 = m2 * m2;
+    double sl = sqrt(kallen(s0, m12, m22));
+    double i2m0 = 0.5 / m0;
+    double pabs = sl * i2m0;
+    double e1 = (s0 + m12 - m22) * i2m0, e2 = (s0 + m22 - m12) * i2m0;
+    double cth = 2.0 * rth - 1.0;
+    double sth = 2.0 * sqrt(rth * (1.0 - rth));
+    double sph, cph;
+    sincospi(2.0 * rphi, &sph, &cph);
+    P4 q1 = {e1, pabs * sth * cph, pabs * sth * sph, pabs * cth};
+    P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
+    if (kBoost) {
+        p1 = boost_out(q1, p0, m0);
+        p2 = boost_out(q2, p0, m0);
+    } else {
+        p1 = q1;
+        p2 = q2;
+    }
+    return 0.5 * kPi * sl / s0;
+}
+
+// ---------------------------------------------------------------- interpreter
+struct Frame {
+    double* S;            // slot file base for this thread: slot k at S[k * block]
+    const double* imm;    // channel immediates (shared memory)
+    int block;
+};
+
+__device__ __forceinline__ double ld(const Frame& f, int a) { return a >= 0 ? f.S[a * f.block] : f.imm[~a]; }
+__device__ __forceinline__ void st(const Frame& f, int slot, double v) { f.S[slot * f.block] = v; }
+__device__ __forceinline__ P4 ldp(const Frame& f, int a) {
+    const double* q = f.S + a * f.block;
+    return {q[0], q[f.block], q[2 * f.block], q[3 * f.block]};
+}
+__device__ __forceinline__ void stp(const Frame& f, int slot, P4 p) {
+    double* q = f.S + slot * f.block;
+    q[0] = p.e;
+    q[f.block] = p.x;
+    q[2 * f.block] = p.y;
+    q[3 * f.block] = p.z;
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// Executes one channel's instruction list for the calling thread's event.
+__device__ void run_code(const int32_t* code, int len, const Frame& f, const double* grid, int vbins,
+                         unsigned long long* cut_count, bool active) {
+    int pc = 0;
+    while (pc < len) {
+        const int op = code[pc], na = code[pc + 1], no = code[pc + 2];
+        const int32_t* a = code + pc + 3;
+        const int32_t* o = a + na;
+        switch (op) {
+            case PS_OP_VEGAS: {
+                double jac = 1.0;
+                const double nb = static_cast<double>(vbins);
+                for (int j = 0; j < na; ++j) {
+                    double r = ld(f, a[j]);
+                    double rn = r * nb;
+                    int k = min(static_cast<int>(rn), vbins - 1);
+                    k = max(k, 0);
+                    const double* e = grid + j * (vbins + 1);
+                    double e0 = e[k], wdt = e[k + 1] - e0;
+                    st(f, o[j], fma(rn - static_cast<double>(k), wdt, e0));
+                    jac *= nb * wdt;
+                }
+                st(f, o[na], jac);
+                break;
+            }
+            case PS_OP_INVARIANT_NU: {
+                double x, j;
+                map_nu(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), ld(f, a[5]), x, j);
+                st(f, o[0], x);
+                st(f, o[1], j);
+                break;
+            }
+            case PS_OP_INVARIANT_BW: {
+                double x, j;
+                map_bw(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), x, j);
+                st(f, o[0], x);
+                st(f, o[1], j);
+                break;
+            }
+            case PS_OP_R_TO_X1X2: {
+                double r = ld(f, a[0]), shat = ld(f, a[1]), S = ld(f, a[2]);
+                double L = log(shat / S);
+                st(f, o[0], exp(r * L));
+                st(f, o[1], exp((1.0 - r) * L));
+                st(f, o[2], -L / S);
+                break;
+            }
+            case PS_OP_COM_P_IN: {
+                double h = 0.5 * ld(f, a[0]);
+                stp(f, o[0], P4{h, 0.0, 0.0, h});
+                stp(f, o[1], P4{h, 0.0, 0.0, -h});
+                break;
+            }
+            case PS_OP_T_INV_MIN_MAX: {
+                double lo, hi, B;
+                t_range(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), lo, hi, B);
+                st(f, o[0], lo);
+                st(f, o[1], hi);
+                break;
+            }
+            case PS_OP_TWO_TO_TWO_COM: {
+                P4 p1, p2;
+                double j = two_to_two(ld(f, a[0]), ldp(f, a[1]), ldp(f, a[2]), ld(f, a[3]), ld(f, a[4]),
+                                      ld(f, a[5]), ld(f, a[6]), ld(f, a[7]), ld(f, a[8]), p1, p2);
+                stp(f, o[0], p1);
+                stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_TWO_BODY_DECAY: {
+                P4 p1, p2;
+                double j = two_body<true>(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]),
+                                          ldp(f, a[5]), p1, p2);
+                stp(f, o[0], p1);
+                stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_TWO_BODY_DECAY_COM: {
+                P4 p1, p2;
+                double j = two_body<false>(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]),
+                                           P4{0, 0, 0, 0}, p1, p2);
+                stp(f, o[0], p1);
+                stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_BOOST_BEAM: {
+                // light-cone form of the longitudinal boost: E+p_z scales by rho = sqrt(x1/x2),
+                // E-p_z by 1/rho (no cancellation for extreme boosts)
+                double x1 = ld(f, a[na - 2]), x2 = ld(f, a[na - 1]);
+                double rho = sqrt(x1 / x2);
+                double irho = 1.0 / rho;
+                for (int k = 0; k < na - 2; ++k) {
+                    P4 p = ldp(f, a[k]);
+                    double plus = rho * (p.e + p.z), minus = (p.e - p.z) * irho;
+                    stp(f, o[k], P4{0.5 * (plus + minus), p.x, p.y, 0.5 * (plus - minus)});
+                }
+                break;
+            }
+            case PS_OP_REDUCE_PRODUCT: {
+                double v = ld(f, a[0]);
+                for (int k = 1; k < na; ++k) v *= ld(f, a[k]);
+                st(f, o[0], v);
+                break;
+            }
+            case PS_OP_CUT_UNPHYSICAL: {
+                double w = ld(f, a[0]), x1 = ld(f, a[1]), x2 = ld(f, a[2]);
+                bool bad = !finite(w) || !(x1 > 0.0 && x1 <= 1.0 && x2 > 0.0 && x2 <= 1.0);
+                for (int k = 3; k < na; ++k) {
+                    P4 p = ldp(f, a[k]);
+                    bad |= !(finite(p.e) && finite(p.x) && finite(p.y) && finite(p.z));
+                }
+                if (bad && active) atomicAdd(cut_count, 1ULL);
+                st(f, o[0], bad ? 0.0 : w);
+                break;
+            }
+            case PS_OP_ADD: st(f, o[0], ld(f, a[0]) + ld(f, a[1])); break;
+            case PS_OP_SUB: st(f, o[0], ld(f, a[0]) - ld(f, a[1])); break;
+            case PS_OP_MUL: st(f, o[0], ld(f, a[0]) * ld(f, a[1])); break;
+            case PS_OP_DIV: st(f, o[0], ld(f, a[0]) / ld(f, a[1])); break;
+            case PS_OP_SQRT: st(f, o[0], sqrt(ld(f, a[0]))); break;
+            case PS_OP_SQUARE: { double v = ld(f, a[0]); st(f, o[0], v * v); break; }
+            case PS_OP_MAX: st(f, o[0], fmax(ld(f, a[0]), ld(f, a[1]))); break;
+            case PS_OP_MOM_ADD: stp(f, o[0], p4_add(ldp(f, a[0]), ldp(f, a[1]))); break;
+            case PS_OP_MOM_SUB: stp(f, o[0], p4_sub(ldp(f, a[0]), ldp(f, a[1]))); break;
+            case PS_OP_PDF_POWER: {
+                double x = ld(f, a[0]), al = ld(f, a[1]), be = ld(f, a[2]);
+                double fx = exp(al * log(x));
+                double y = 1.0 - x;
+                double fy;
+                if (be == 3.0) fy = y * y * y;
+                else if (be == 2.0) fy = y * y;
+                else if (be == 1.0) fy = y;
+                else if (be == 0.0) fy = 1.0;
+                else fy = pow(y, be);
+                st(f, o[0], fx * fy);
+                break;
+            }
+            case PS_OP_PROPAGATOR: {
+                double s = ld(f, a[0]), M = ld(f, a[1]), G = ld(f, a[2]);
+                double d = s - M * M;
+                st(f, o[0], 1.0 / (d * d + M * M * G * G));
+                break;
+            }
+            case PS_OP_ONE_PLUS_COS2: {
+                P4 p = ldp(f, a[0]);
+                double c2 = p.z * p.z / (p.x * p.x + p.y * p.y + p.z * p.z);
+                st(f, o[0], 1.0 + c2);
+                break;
+            }
+            case PS_OP_CHANNEL_WEIGHT: {
+                const int k = static_cast<int>(ld(f, a[0]));
+                P4 pa = ldp(f, a[1]);
+                double P = 1.0;
+                for (int j = 2 + k; j + 3 < na; j += 4) {
+                    int kind = static_cast<int>(ld(f, a[j]));
+                    int mask = static_cast<int>(ld(f, a[j + 1]));
+                    double M = ld(f, a[j + 2]), G = ld(f, a[j + 3]);
+                    P4 q = (kind == 1) ? pa : P4{0.0, 0.0, 0.0, 0.0};
+                    for (int i = 0; i < k; ++i)
+                        if (mask & (1 << i)) q = (kind == 1) ? p4_sub(q, ldp(f, a[2 + i])) : p4_add(q, ldp(f, a[2 + i]));
+                    double inv = p4_sq(q);
+                    double d = inv - M * M;
+                    P *= (kind == 1) ? 1.0 / (d * d) : 1.0 / (d * d + M * M * G * G);
+                }
+                st(f, o[0], P);
+                break;
+            }
+            default: break;
+        }
+        pc += 3 + na + no;
+    }
+}
+
+// Locate the output descriptor [kOpOutput, n, 0, (role, slot)...] after the instructions.
+__device__ __forceinline__ int find_output(const int32_t* code, int len) {
+    int pc = 0;
+    while (pc < len && code[pc] != kOpOutput) pc += 3 + code[pc + 1] + code[pc + 2];
+    return pc;
+}
+
+}  // namespace dev
+
+__global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ LaunchParams lp) {
+    extern __shared__ __align__(16) double smem[];
+    const int B = lp.block;
+    const int tid = threadIdx.x;
+    double* s_imm = smem;
+    double* s_grid = s_imm + lp.smem_imm;
+    double* s_slots = s_grid + lp.smem_grid;
+    double* s_red = s_slots + static_cast<size_t>(lp.smem_slots) * B;
+    int32_t* s_code = reinterpret_cast<int32_t*>(s_red + 4 * (B / 32));
+
+    dev::Frame f{s_slots + tid, s_imm, B};
+    int cur = -1;
+    int out_pc = 0;
+    for (int64_t tile = blockIdx.x; tile < lp.n_tiles; tile += gridDim.x) {
+        int c = 0;
+        while (c + 1 < lp.n_ch && tile >= lp.ch[c + 1].tile_begin) ++c;
+        const ChannelLaunch& C = lp.ch[c];
+        if (c != cur) {
+            __syncthreads();
+            for (int i = tid; i < C.code_len; i += B) s_code[i] = lp.code[C.code_off + i];
+            for (int i = tid; i < C.imm_len; i += B) s_imm[i] = lp.imm[C.imm_off + i];
+            const int ng = C.vdims * (C.vbins + 1);
+            for (int i = tid; i < ng; i += B) s_grid[i] = lp.grid[C.grid_off + i];
+            __syncthreads();
+            cur = c;
+            out_pc = dev::find_output(s_code, C.code_len);
+        }
+        const int64_t local = (tile - C.tile_begin) * B + tid;
+        const bool active = local < C.n_events;
+        const int64_t ev = C.ev_offset + local;
+
+        // inputs: explicit SoA or Philox4x32-10 with counter (ev_lo, ev_hi, channel, j/2)
+        if (lp.r != nullptr) {
+            for (int j = 0; j < C.n_random; ++j)
+                dev::st(f, j, active ? lp.r[j * lp.ld_r + local] : 0.5);
+        } else {
+            for (int j = 0; j < C.n_random; j += 2) {
+                uint4 o = dev::philox4x32_10(make_uint4(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32),
+                                                        static_cast<uint32_t>(c), static_cast<uint32_t>(j >> 1)),
+                                             static_cast<uint32_t>(lp.seed), static_cast<uint32_t>(lp.seed >> 32));
+                dev::st(f, j, dev::unit_from_bits(o.y, o.x));
+                if (j + 1 < C.n_random) dev::st(f, j + 1, dev::unit_from_bits(o.w, o.z));
+            }
+        }
+
+        dev::run_code(s_code, out_pc, f, s_grid, C.vbins, lp.status + 1, active);
+
+        // outputs
+        const int n_out = s_code[out_pc + 1];
+        const int32_t* od = s_code + out_pc + 3;
+        double w = 0.0;
+        int mom_k = 0;
+        const int64_t col = C.col_off + local;
+        for (int k = 0; k < n_out; ++k) {
+            const int role = od[2 * k], slot = od[2 * k + 1];
+            if (role == PS_ROLE_MOMENTUM) {
+                if (active && lp.mom != nullptr) {
+                    dev::P4 p = dev::ldp(f, slot);
+                    double* m = lp.mom + static_cast<int64_t>(4 * mom_k) * lp.ld + col;
+                    __stcs(m, p.e);
+                    __stcs(m + lp.ld, p.x);
+                    __stcs(m + 2 * lp.ld, p.y);
+                    __stcs(m + 3 * lp.ld, p.z);
+                }
+                ++mom_k;
+            } else {
+                double v = dev::ld(f, slot);
+                double* dst = role == PS_ROLE_X1 ? lp.x1 : role == PS_ROLE_X2 ? lp.x2
+                            : role == PS_ROLE_WEIGHT ? lp.w : lp.alpha;
+                if (role == PS_ROLE_WEIGHT) w = v;
+                if (active && dst != nullptr) __stcs(dst + col, v);
+            }
+        }
+        if (!active) w = 0.0;
+        if (active && !isfinite(w)) atomicAdd(lp.status + 0, 1ULL);
+
+        // VEGAS training: sum of w^2 per (dimension, bin of the unmapped r)
+        if (lp.hist != nullptr && C.vdims > 0 && active) {
+            for (int j = 0; j < C.vdims; ++j) {
+                double r;
+                if (lp.r != nullptr) {
+                    r = lp.r[j * lp.ld_r + local];
+                } else {
+                    uint4 o = dev::philox4x32_10(make_uint4(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32),
+                                                            static_cast<uint32_t>(c), static_cast<uint32_t>(j >> 1)),
+                                                 static_cast<uint32_t>(lp.seed), static_cast<uint32_t>(lp.seed >> 32));
+                    r = (j & 1) ? dev::unit_from_bits(o.w, o.z) : dev::unit_from_bits(o.y, o.x);
+                }
+                int k = min(max(static_cast<int>(r * C.vbins), 0), C.vbins - 1);
+                atomicAdd(lp.hist + C.hist_off + j * C.vbins + k, w * w);
+            }
+        }
+
+        // per-tile partial statistics: nonzero count, sum w, sum w^2, max w
+        double v0 = (w != 0.0) ? 1.0 : 0.0, v1 = w, v2 = w * w, v3 = w;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v0 += __shfl_down_sync(0xffffffffu, v0, off);
+            v1 += __shfl_down_sync(0xffffffffu, v1, off);
+            v2 += __shfl_down_sync(0xffffffffu, v2, off);
+            v3 = fmax(v3, __shfl_down_sync(0xffffffffu, v3, off));
+        }
+        const int warp = tid >> 5, lane = tid & 31;
+        __syncthreads();  // s_red reuse across tiles
+        if (lane == 0) {
+            s_red[4 * warp + 0] = v0;
+            s_red[4 * warp + 1] = v1;
+            s_red[4 * warp + 2] = v2;
+            s_red[4 * warp + 3] = v3;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            for (int k = 0; k < B / 32; ++k) {
+                a0 += s_red[4 * k];
+                a1 += s_red[4 * k + 1];
+                a2 += s_red[4 * k + 2];
+                a3 = fmax(a3, s_red[4 * k + 3]);
+            }
+            double* tp = lp.tile_partials + 4 * tile;
+            tp[0] = a0;
+            tp[1] = a1;
+            tp[2] = a2;
+            tp[3] = a3;
+        }
+    }
+}
+
+// One CTA per channel sums the channel's tile partials in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) ps_reduce_kernel(const __grid_constant__ LaunchParams lp, double* stats) {
+    const int c = blockIdx.x;
+    const ChannelLaunch& C = lp.ch[c];
+    const int64_t t0 = C.tile_begin;
+    const int64_t t1 = (c + 1 < lp.n_ch) ? lp.ch[c + 1].tile_begin : lp.n_tiles;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const double* tp = lp.tile_partials + 4 * t;
+        a0 += tp[0];
+        a1 += tp[1];
+        a2 += tp[2];
+        a3 = fmax(a3, tp[3]);
+    }
+    __shared__ double red[4][256];
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    red[2][threadIdx.x] = a2;
+    red[3][threadIdx.x] = a3;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+            red[2][threadIdx.x] += red[2][threadIdx.x + s];
+            red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double* o = stats + 5 * c;
+        o[0] = static_cast<double>(C.n_events);
+        o[1] = red[0][0];
+        o[2] = red[1][0];
+        o[3] = red[2][0];
+        o[4] = red[3][0];
+    }
+}
+
+size_t smem_bytes_for(const LaunchParams& lp) {
+    size_t doubles = static_cast<size_t>(lp.smem_imm) + lp.smem_grid + static_cast<size_t>(lp.smem_slots) * lp.block +
+                     4 * (lp.block / 32);
+    return doubles * sizeof(double) + static_cast<size_t>(lp.smem_code_ints) * sizeof(int32_t);
+}
+
+static int cuda_fail(cudaError_t e, const char* what, std::string* err) {
+    *err = std::string(what) + ": " + cudaGetErrorString(e);
+    return PS_ERR_CUDA;
+}
+
+int max_ctas_per_sm(int block, size_t smem, int* out, std::string* err) {
+    cudaError_t e = cudaFuncSetAttribute(ps_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", err);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, ps_map_kernel, block, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", err);
+    return PS_OK;
+}
+
+int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem, void* stream, std::string* err) {
+    if (lp.n_tiles == 0) return PS_OK;
+    ps_map_kernel<<<grid_ctas, lp.block, smem, static_cast<cudaStream_t>(stream)>>>(lp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ps_map_kernel launch", err);
+    __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+    return PS_OK;
+}
+
+int launch_reduce(const LaunchParams& lp, double* stats, void* stream, std::string* err) {
+    ps_reduce_kernel<<<lp.n_ch, 256, 0, static_cast<cudaStream_t>(stream)>>>(lp, stats);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ps_reduce_kernel launch", err);
+    __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+    return PS_OK;
+}
+
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+}  // namespace ps

@@ -1,0 +1,101 @@
+// ps_internal.h -- structures shared by the host compiler (graph.cpp) and the
+// device interpreter (kernels.cu) of the GB300 phase-space library.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ps.h"
+
+namespace ps {
+
+constexpr int kMaxChannels = 32;
+constexpr int kMaxOutMomenta = 24;
+constexpr int kOpOutput = 1000;  // pseudo-op closing each channel's byte-code
+
+// ---------------------------------------------------------------- graph IR
+struct Arg {
+    int kind;  // PS_ARG_VALUE / PS_ARG_IMM
+    int id;
+    double imm;
+};
+
+struct Instr {
+    int op;
+    std::vector<Arg> args;
+    std::vector<int> outs;  // value ids
+};
+
+struct Graph {
+    int n_random = 0;
+    std::vector<int> type;  // value id -> PS_TYPE_*
+    std::vector<Instr> code;
+    std::vector<int> out_ids, out_roles;
+    bool outputs_set = false;
+};
+
+// ---------------------------------------------------------------- compiled channel
+// Byte-code: per instruction [op, n_args, n_out, args..., outs...]; an argument >= 0 is a
+// slot index (momenta occupy 4 consecutive slots), < 0 encodes immediate ~arg.  The code
+// ends with [kOpOutput, n, 0, (role, slot) x n].
+struct Compiled {
+    std::vector<int32_t> code;
+    std::vector<double> imm;
+    int n_slots = 0;
+    int n_random = 0;
+    int vegas_dims = 0;  // dims of the VEGAS op (0 if none)
+    int n_momenta_out = 0;
+    bool has_x1 = false, has_x2 = false, has_alpha = false;
+};
+
+int compile_graph(const Graph& g, Compiled* out, std::string* err);
+
+// ---------------------------------------------------------------- launch description
+struct ChannelLaunch {
+    int32_t code_off, code_len;    // ints in the code buffer
+    int32_t imm_off, imm_len;      // doubles in the immediates buffer
+    int32_t grid_off;              // doubles in the grid buffer
+    int32_t vdims, vbins;
+    int32_t n_slots;
+    int32_t n_random;
+    int32_t hist_off;              // doubles in the histogram buffer
+    int64_t n_events;
+    int64_t col_off;               // first output column
+    int64_t tile_begin;            // first global tile index
+    int64_t ev_offset;             // event id of the channel's first event
+};
+
+struct LaunchParams {
+    int32_t n_ch;
+    int32_t block;                 // threads per CTA = events per tile
+    int32_t smem_code_ints, smem_imm, smem_grid, smem_slots;  // per-CTA staging sizes
+    int64_t n_tiles;
+    const int32_t* code;
+    const double* imm;
+    const double* grid;
+    // inputs
+    const double* r;               // explicit-input mode (SoA), or nullptr for Philox
+    int64_t ld_r;
+    uint64_t seed;
+    // outputs
+    double* mom;
+    double* x1;
+    double* x2;
+    double* w;
+    double* alpha;
+    int64_t ld;
+    // scratch and program state
+    double* tile_partials;         // [n_tiles][4]
+    double* hist;                  // VEGAS histograms (program-owned), or nullptr
+    unsigned long long* status;    // [4]
+    ChannelLaunch ch[kMaxChannels];
+};
+
+// kernels.cu
+int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem_bytes, void* stream, std::string* err);
+int launch_reduce(const LaunchParams& lp, double* stats_dev, void* stream, std::string* err);
+size_t smem_bytes_for(const LaunchParams& lp);
+int max_ctas_per_sm(int block, size_t smem_bytes, int* out, std::string* err);
+
+}  // namespace ps

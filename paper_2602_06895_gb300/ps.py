@@ -1,0 +1,387 @@
+"""Python binding of the C ABI in include/ps.h (ctypes; argument marshalling only).
+
+Every computation runs in the native library ``libps.so`` (sm_103a kernels and
+its host compiler).  There is no Python or CPU fallback: if the library is
+missing or no CUDA device is present the calls raise.
+
+The raw C functions are exported under their C names (``ps_graph_create``,
+``ps_generate`` ...); :class:`Program` and :func:`build_channel` wrap them for
+torch tensors (device memory and streams come from PyTorch).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libps.so")
+
+PS_OK = 0
+MAX_NODES, MAX_LEGS = 32, 10
+
+# opcodes (include/ps.h)
+OPS = dict(VEGAS=1, INVARIANT_NU=2, INVARIANT_BW=3, R_TO_X1X2=4, COM_P_IN=5, T_INV_MIN_MAX=6, TWO_TO_TWO_COM=7,
+           TWO_BODY_DECAY=8, TWO_BODY_DECAY_COM=9, BOOST_BEAM=10, REDUCE_PRODUCT=11, CUT_UNPHYSICAL=12, ADD=13,
+           SUB=14, MUL=15, DIV=16, SQRT=17, SQUARE=18, MAX=19, MOM_ADD=20, MOM_SUB=21, PDF_POWER=22,
+           PROPAGATOR=23, ONE_PLUS_COS2=24, CHANNEL_WEIGHT=25)
+ROLE_MOMENTUM, ROLE_X1, ROLE_X2, ROLE_WEIGHT, ROLE_ALPHA = range(5)
+ARG_VALUE, ARG_IMM = 0, 1
+INTEGRAND = {"none": 0, "one_plus_cos2": 1, "pdf_props": 2, "pdf_sde": 3}
+NODE = {"leaf": 0, "decay": 1, "tchain": 2}
+
+
+class PSError(RuntimeError):
+    pass
+
+
+class Arg(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("id", C.c_int32), ("imm", C.c_double)]
+
+
+class NodeDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_children", C.c_int32), ("children", C.c_int32 * MAX_LEGS),
+                ("leaf_index", C.c_int32), ("in_sde", C.c_int32), ("mass", C.c_double),
+                ("prop_mass", C.c_double), ("prop_width", C.c_double), ("nu", C.c_double)]
+
+
+class ChannelDesc(C.Structure):
+    _fields_ = [("n_out", C.c_int32), ("hadronic", C.c_int32), ("lab_frame", C.c_int32), ("integrand", C.c_int32),
+                ("n_nodes", C.c_int32), ("n_sorder", C.c_int32), ("sorder", C.c_int32 * MAX_NODES),
+                ("tside", C.c_int32 * MAX_LEGS), ("vegas_dims", C.c_int32), ("vegas_bins", C.c_int32),
+                ("sqrt_s", C.c_double), ("s_beam", C.c_double), ("a_shift", C.c_double),
+                ("shat_mass", C.c_double), ("shat_width", C.c_double), ("shat_nu", C.c_double),
+                ("t_nu", C.c_double), ("ts_nu", C.c_double), ("t_prop_mass", C.c_double),
+                ("pdf_alpha", C.c_double), ("pdf_beta", C.c_double), ("nodes", NodeDesc * MAX_NODES)]
+
+
+class Options(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("precision", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class OutBuffers(C.Structure):
+    _fields_ = [("momenta", C.c_void_p), ("x1", C.c_void_p), ("x2", C.c_void_p), ("weight", C.c_void_p),
+                ("alpha", C.c_void_p), ("ld", C.c_int64)]
+
+
+class ChannelStats(C.Structure):
+    _fields_ = [("n", C.c_double), ("n_nonzero", C.c_double), ("sum_w", C.c_double), ("sum_w2", C.c_double),
+                ("max_w", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "ps_last_error": (C.c_char_p, []),
+    "ps_version": (C.c_int, []),
+    "ps_graph_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "ps_graph_add": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Arg), C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "ps_graph_set_outputs": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
+    "ps_graph_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ps_graph_dump": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "ps_graph_free": (C.c_int, [C.c_void_p]),
+    "ps_channel_dims": (C.c_int, [C.POINTER(ChannelDesc), C.POINTER(C.c_int)]),
+    "ps_graph_build_channel": (C.c_int, [C.POINTER(ChannelDesc), C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "ps_program_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(Options), C.c_int,
+                                    C.POINTER(C.c_void_p)]),
+    "ps_program_set_vegas": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "ps_program_get_vegas": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "ps_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
+    "ps_generate": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64, C.POINTER(OutBuffers),
+                              C.c_void_p, C.c_size_t, C.c_void_p]),
+    "ps_map": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.POINTER(OutBuffers), C.c_void_p,
+                         C.c_size_t, C.c_void_p]),
+    "ps_stats": (C.c_int, [C.c_void_p, C.POINTER(ChannelStats), C.c_int, C.c_void_p]),
+    "ps_vegas_training": (C.c_int, [C.c_void_p, C.c_int]),
+    "ps_vegas_histogram": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    "ps_vegas_adapt": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
+    "ps_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int, C.c_void_p]),
+    "ps_status_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ps_program_free": (C.c_int, [C.c_void_p]),
+    "ps_launch_count": (C.c_int64, []),
+}
+
+
+def lib():
+    """Load libps.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise PSError(f"native library not built: {LIB_PATH} (run __graft_entry__.build())")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status, what=""):
+    if status != PS_OK:
+        msg = lib().ps_last_error().decode(errors="replace")
+        raise PSError(f"{what} failed ({status}): {msg}")
+
+
+def __getattr__(name):
+    # raw C entry points under their C names (ps_graph_create, ps_generate, ...)
+    if name in _SIGS:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+# ------------------------------------------------------------------ descriptions
+def channel_desc(ch):
+    """Workload channel dictionary -> ps_channel_desc."""
+    d = ChannelDesc()
+    d.n_out = ch["n"]
+    d.hadronic = 1 if ch["hadronic"] else 0
+    d.lab_frame = 0 if ch.get("partonic", False) else 1
+    d.integrand = INTEGRAND[ch["integrand"]]
+    nodes = ch["nodes"]
+    d.n_nodes = len(nodes)
+    for j, nd in enumerate(nodes):
+        o = d.nodes[j]
+        o.kind = NODE[nd["kind"]]
+        kids = nd.get("children", [])
+        o.n_children = len(kids)
+        for k, kid in enumerate(kids):
+            o.children[k] = kid
+        o.leaf_index = nd.get("leaf", -1)
+        o.in_sde = 1 if nd.get("sde", False) else 0
+        o.mass = nd.get("mass", 0.0)
+        o.prop_mass = nd.get("M", 0.0)
+        o.prop_width = nd.get("G", 0.0)
+        o.nu = nd.get("nu", 0.8)
+    d.n_sorder = len(ch["sorder"])
+    for i, j in enumerate(ch["sorder"]):
+        d.sorder[i] = j
+    for i, sd in enumerate(ch["tside"]):
+        d.tside[i + 1] = sd
+    d.vegas_dims = ch["vegas_dims"]
+    d.vegas_bins = ch["vegas_bins"]
+    d.sqrt_s = ch["sqrt_s"]
+    d.s_beam = ch["S"]
+    d.a_shift = ch["a"]
+    d.shat_mass = ch["shat"]["M"]
+    d.shat_width = ch["shat"]["G"]
+    d.shat_nu = ch["shat"]["nu"]
+    d.t_nu = ch["t_nu"]
+    d.ts_nu = ch["ts_nu"]
+    d.t_prop_mass = ch["Mt"]
+    d.pdf_alpha, d.pdf_beta = ch["pdf"]
+    return d
+
+
+def channel_dims(ch):
+    n = C.c_int()
+    _check(lib().ps_channel_dims(C.byref(channel_desc(ch)), C.byref(n)), "ps_channel_dims")
+    return n.value
+
+
+class Graph:
+    """Owning wrapper of a ps_graph handle."""
+
+    def __init__(self, handle):
+        self.h = C.c_void_p(handle)
+
+    @classmethod
+    def create(cls, n_random):
+        h = C.c_void_p()
+        _check(lib().ps_graph_create(n_random, C.byref(h)), "ps_graph_create")
+        return cls(h.value)
+
+    def add(self, opcode, args, n_out):
+        """args: list of ("v", id) / ("i", value) or plain ints (values) / floats (immediates)."""
+        arr = (Arg * max(len(args), 1))()
+        for k, a in enumerate(args):
+            if isinstance(a, tuple):
+                kind, val = a
+            else:
+                kind, val = ("v", a) if isinstance(a, int) else ("i", a)
+            if kind == "v":
+                arr[k] = Arg(ARG_VALUE, int(val), 0.0)
+            else:
+                arr[k] = Arg(ARG_IMM, -1, float(val))
+        outs = (C.c_int * max(n_out, 1))()
+        _check(lib().ps_graph_add(self.h, OPS[opcode] if isinstance(opcode, str) else opcode, arr, len(args), outs,
+                                  n_out), "ps_graph_add")
+        return list(outs[:n_out])
+
+    def set_outputs(self, ids, roles):
+        n = len(ids)
+        _check(lib().ps_graph_set_outputs(self.h, (C.c_int * n)(*ids), (C.c_int * n)(*roles), n),
+               "ps_graph_set_outputs")
+
+    def info(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().ps_graph_info(self.h, C.byref(a), C.byref(b), C.byref(c)), "ps_graph_info")
+        return {"instructions": a.value, "values": b.value, "random": c.value}
+
+    def dump(self):
+        need = C.c_size_t()
+        _check(lib().ps_graph_dump(self.h, None, 0, C.byref(need)), "ps_graph_dump")
+        buf = C.create_string_buffer(need.value)
+        _check(lib().ps_graph_dump(self.h, buf, need.value, C.byref(need)), "ps_graph_dump")
+        return buf.value.decode()
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.ps_graph_free(self.h)
+            self.h = C.c_void_p()
+
+
+def build_channel(channels, which=0):
+    """Graph of channel `which` of a list of workload channel dictionaries."""
+    arr = (ChannelDesc * len(channels))(*[channel_desc(c) for c in channels])
+    h = C.c_void_p()
+    _check(lib().ps_graph_build_channel(arr, len(channels), which, C.byref(h)), "ps_graph_build_channel")
+    return Graph(h.value)
+
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Program:
+    """A compiled multi-channel program on one device (ps_program)."""
+
+    def __init__(self, graphs, block_threads=128, ctas_per_sm=0, device=0):
+        self.graphs = list(graphs)
+        self.n_ch = len(self.graphs)
+        hs = (C.c_void_p * self.n_ch)(*[g.h.value for g in self.graphs])
+        opt = Options(block_threads, ctas_per_sm, 0, 0)
+        h = C.c_void_p()
+        _check(lib().ps_program_create(hs, self.n_ch, C.byref(opt), device, C.byref(h)), "ps_program_create")
+        self.h = h
+        self.device = device
+        self.n_random = [g.info()["random"] for g in self.graphs]
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.ps_program_free(self.h)
+            self.h = C.c_void_p()
+
+    # -- VEGAS
+    def set_vegas(self, ch, edges):
+        import numpy as np
+
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        _check(lib().ps_program_set_vegas(self.h, ch, e.shape[0], e.shape[1] - 1,
+                                          e.ctypes.data_as(C.POINTER(C.c_double))), "ps_program_set_vegas")
+
+    def get_vegas(self, ch, dims, bins=64):
+        import numpy as np
+
+        e = np.zeros((dims, bins + 1))
+        _check(lib().ps_program_get_vegas(self.h, ch, dims, bins, e.ctypes.data_as(C.POINTER(C.c_double))),
+               "ps_program_get_vegas")
+        return e
+
+    def vegas_training(self, on):
+        _check(lib().ps_vegas_training(self.h, 1 if on else 0), "ps_vegas_training")
+
+    def vegas_histogram(self, ch, dims, bins=64, stream=None):
+        import numpy as np
+
+        h = np.zeros((dims, bins))
+        _check(lib().ps_vegas_histogram(self.h, ch, h.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr(stream)),
+               "ps_vegas_histogram")
+        return h
+
+    def vegas_adapt(self, ch, alpha=1.5, stream=None):
+        _check(lib().ps_vegas_adapt(self.h, ch, alpha, _stream_ptr(stream)), "ps_vegas_adapt")
+
+    # -- buffers
+    def workspace_size(self, events):
+        ev = (C.c_int64 * self.n_ch)(*[int(e) for e in events])
+        n = C.c_size_t()
+        _check(lib().ps_workspace_size(self.h, ev, C.byref(n)), "ps_workspace_size")
+        return n.value
+
+    def alloc(self, events, n_momenta, x=True, alpha=False, device=None):
+        """Output tensors (float64, CUDA) for `events` (list per channel) and a workspace."""
+        import torch
+
+        dev = torch.device("cuda", self.device if device is None else device)
+        tot = int(sum(events))
+        out = {"momenta": torch.empty((4 * n_momenta, max(tot, 1)), dtype=torch.float64, device=dev),
+               "weight": torch.empty(max(tot, 1), dtype=torch.float64, device=dev)}
+        if x:
+            out["x1"] = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
+            out["x2"] = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
+        if alpha:
+            out["alpha"] = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
+        ws = torch.empty(self.workspace_size(events) // 8 + 32, dtype=torch.float64, device=dev)
+        return out, ws
+
+    @staticmethod
+    def _out_struct(out):
+        m = out.get("momenta")
+        if m is not None and m.shape[1] > 1 and m.stride(1) != 1:
+            raise PSError("momenta must have unit stride along the events")
+        ld = (m.stride(0) if m.shape[0] > 1 else m.shape[1]) if m is not None else 0
+        return OutBuffers(_ptr(m), _ptr(out.get("x1")), _ptr(out.get("x2")), _ptr(out.get("weight")),
+                          _ptr(out.get("alpha")), ld)
+
+    @staticmethod
+    def _ws(ws):
+        base = ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        return C.c_void_p(aligned), ws.numel() * ws.element_size() - (aligned - base)
+
+    def generate(self, events, seed, out, ws, event_offset=0, stream=None):
+        ev = (C.c_int64 * self.n_ch)(*[int(e) for e in events])
+        o = self._out_struct(out)
+        wp, wn = self._ws(ws)
+        _check(lib().ps_generate(self.h, ev, seed, event_offset, C.byref(o), wp, wn, _stream_ptr(stream)),
+               "ps_generate")
+
+    def map(self, ch, r, out, ws, stream=None):
+        """r: float64 CUDA tensor [n_random, batch] (SoA, unit stride along the events)."""
+        if r.dim() != 2 or (r.shape[1] > 1 and r.stride(1) != 1):
+            raise PSError("r must be a [n_random, batch] tensor with unit stride along the batch")
+        ld = r.stride(0) if r.shape[0] > 1 else r.shape[1]  # a size-1 dimension may carry any stride
+        o = self._out_struct(out)
+        wp, wn = self._ws(ws)
+        _check(lib().ps_map(self.h, ch, r.shape[1], _ptr(r), ld, C.byref(o), wp, wn, _stream_ptr(stream)),
+               "ps_map")
+
+    def stats(self, stream=None):
+        arr = (ChannelStats * self.n_ch)()
+        _check(lib().ps_stats(self.h, arr, self.n_ch, _stream_ptr(stream)), "ps_stats")
+        return [{"n": s.n, "n_nonzero": s.n_nonzero, "sum_w": s.sum_w, "sum_w2": s.sum_w2, "max_w": s.max_w}
+                for s in arr]
+
+    def status(self, stream=None):
+        arr = (C.c_int64 * 4)()
+        _check(lib().ps_status(self.h, arr, 4, _stream_ptr(stream)), "ps_status")
+        return {"nonfinite": arr[0], "cut": arr[1], "clamped": arr[2]}
+
+    def status_reset(self, stream=None):
+        _check(lib().ps_status_reset(self.h, _stream_ptr(stream)), "ps_status_reset")
+
+
+def launch_count():
+    return lib().ps_launch_count()
+
+
+def program_for(channels, block_threads=128, ctas_per_sm=0, device=0):
+    """Build every channel of a workload list and compile them into one program."""
+    graphs = [build_channel(channels, c) for c in range(len(channels))]
+    return Program(graphs, block_threads=block_threads, ctas_per_sm=ctas_per_sm, device=device)

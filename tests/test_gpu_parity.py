@@ -1,0 +1,333 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated per quantity; the derivation is in the design notes):
+  momenta   |p_gpu - p_orc| <= max(1e-12, 32 eps kappa_p) * (largest energy of the event), per
+            component; kappa_p is the oracle's rounding amplification: kappa of a decay or block at
+            threshold, |t|_max/(|t|_max - |t|) for backward 2->2 scattering (1 + cos(theta) from
+            |t|_max - |t|) -- both reach the later legs of a t-chain -- and gamma^2 = E0^2/s of a
+            boost into the rest frame of a composite momentum (its components and its sampled
+            invariant agree only to eps E0^2) -- the small-s, small-t tail of the paper's Sec. 4.1
+  x1, x2    relative 1e-12
+  weight    relative max(1e-12, 32 eps kappa): kappa is the oracle's per-event condition number
+            (a sampled range width sqrt(s_r)/(m_max - m_min), or a decay/block at threshold
+            s/(s - (m1+m2)^2)); two correct FP64 evaluations cannot agree better than eps kappa
+            there.  For ~98% of events the 1e-12 floor applies.  Zero weights agree exactly.
+  alpha     relative 1e-12, or the conditioning bound of a propagator evaluated from
+            momenta (see _alpha_tolerance)
+  integers  (cut decisions, counts, VEGAS bin indices, Philox bits) bit-exact
+In addition, at least 95% of the events whose random numbers are not pushed to within 1e-8 of
+0 or 1 meet the flat 1e-12 bar on momenta and weights (the conditioning-aware bounds only cover
+the ill-conditioned tail; t-chains through light clusters are the bulk of it).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_06895_gb300 import ps
+from paper_2602_06895_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+EPS = 2.0 ** -52
+
+
+def weight_tol(orc):
+    return np.maximum(RTOL, 32.0 * EPS * orc["aux"][:, O.AUX["cond"]])
+
+
+def momentum_tol(orc):
+    return np.maximum(RTOL, 32.0 * EPS * orc["aux"][:, O.AUX["cond_p"]])
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2602_06895_gb300 import build
+
+    build.build()
+    return torch
+
+
+def run_map(torch, channels, which, r, grid=None, block=128):
+    """Explicit-input map of channel `which` on the GPU; r [B, d] numpy."""
+    prog = ps.program_for(channels, block_threads=block)
+    ch = channels[which]
+    if grid is not None:
+        prog.set_vegas(which, grid)
+    B = r.shape[0]
+    n_mom = ch["n"] + 2
+    out, ws = prog.alloc([B if c == which else 0 for c in range(len(channels))], n_mom, x=ch["hadronic"],
+                         alpha=ch["integrand"] == "pdf_sde")
+    rt = torch.from_numpy(np.ascontiguousarray(r.T)).to("cuda")
+    prog.map(which, rt, out, ws)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["mom"] = res["momenta"][:, :B].reshape(n_mom, 4, B).transpose(2, 0, 1)
+    res["w"] = res["weight"][:B]
+    if "x1" in res:
+        res["x"] = np.stack([res["x1"][:B], res["x2"][:B]], axis=1)
+    if "alpha" in res:
+        res["alpha"] = res["alpha"][:B]
+    res["stats"] = prog.stats()[which]
+    res["status"] = prog.status()
+    return res
+
+
+def compare(gpu, orc, ch, label, alpha_tol=None, r=None):
+    mom_g, mom_o = gpu["mom"], orc["mom"]
+    scale = np.max(np.abs(mom_o[:, :, 0]), axis=1)
+    # zero weights (cuts, empty ranges) are integer outcomes and must agree -- except at an exact
+    # threshold, where the weight itself is undetermined (its bound 32 eps kappa reaches 1)
+    bad = np.flatnonzero((gpu["w"] == 0) != (orc["w"] == 0))
+    n_threshold = 0
+    if "aux" in orc:
+        n_threshold = int(np.sum(weight_tol(orc)[bad] >= 1.0))
+        bad = bad[weight_tol(orc)[bad] < 1.0]
+    assert bad.size == 0, (label, "zero weights differ", bad[:5].tolist(), gpu["w"][bad[:5]].tolist(),
+                           orc["w"][bad[:5]].tolist(), orc["aux"][bad[:5]].tolist() if "aux" in orc else None)
+    ok = (orc["w"] != 0) & (gpu["w"] != 0)
+    dm = np.max(np.abs(mom_g - mom_o), axis=(1, 2))
+    ptol = momentum_tol(orc)[ok] if "aux" in orc else RTOL
+    flat_ok = (dm[ok] <= RTOL * scale[ok]) & (np.abs(gpu["w"][ok] / orc["w"][ok] - 1.0) <= RTOL)
+    interior = np.ones(ok.sum(), bool) if r is None else np.all((r[ok] > 1e-8) & (r[ok] < 1 - 1e-8), axis=1)
+    frac = float(flat_ok[interior].mean()) if interior.any() else 1.0
+    assert frac >= 0.95, (label, "fraction of interior events within the flat 1e-12 bar", frac)
+    ratio = dm[ok] / (ptol * scale[ok])
+    worst = int(np.flatnonzero(ok)[np.argmax(ratio)])
+    assert np.all(ratio <= 1.0), (label, "momenta", "worst event", worst, "rel err", dm[worst] / scale[worst],
+                                  "bound ratio", float(ratio.max()), int(np.sum(dm[ok] > RTOL * scale[ok])))
+    if ch["hadronic"]:
+        rx = np.abs(gpu["x"] / orc["x"] - 1.0)
+        assert np.all(rx[ok] <= RTOL), (label, "x", rx[ok].max())
+    rw = np.abs(gpu["w"][ok] / orc["w"][ok] - 1.0)
+    tol = weight_tol(orc)[ok]
+    assert np.all(rw <= tol), (label, "weight", "worst event", int(np.flatnonzero(ok)[np.argmax(rw / tol)]),
+                               float(np.max(rw / tol)), rw.max(), int(np.sum(rw > RTOL)))
+    if alpha_tol is not None:
+        ra = np.abs(gpu["alpha"][ok] - orc["alpha"][ok])
+        bound = alpha_tol[ok] * np.maximum(orc["alpha"][ok], 1e-300) + 1e-300
+        k = int(np.argmax(ra / bound))
+        assert np.all(ra <= bound), (label, "alpha", "worst", int(np.flatnonzero(ok)[k]), float(orc["alpha"][ok][k]),
+                                     float(gpu["alpha"][ok][k]), float((ra / bound)[k]),
+                                     float(orc["aux"][ok][k, O.AUX["cond_p"]]) if "aux" in orc else None)
+    return n_threshold
+
+
+def parity_channels():
+    out = [("2to2_fixed", [W.two_body_fixed()], 0, None),
+           ("2to2_fixed_none", [W.two_body_fixed(integrand="none")], 0, None),
+           ("ww_2to4", [W.ww_hadronic()], 0, W.vegas_grid_random(11, 8, 64))]
+    for t in W.volume_topologies(3) + W.volume_topologies(4):
+        out.append((t["name"], [t], 0, None))
+        m = W.with_masses(t, [173.0, 173.0] + [0.0] * (t["n"] - 2))
+        out.append((t["name"] + "_massive", [m], 0, None))
+    multi = W.multichannel_2to5()
+    for i in range(len(multi)):
+        out.append((multi[i]["name"], multi, i, None))
+    return out
+
+
+def _alpha_tolerance(orc):
+    # alpha_c = P_c / sum_j P_j with the other channels' P_j from momenta.  A propagator
+    # 1/((s-M^2)^2 + M^2 G^2) evaluated from momenta inherits the rounding of s = (sum p)^2:
+    # the momenta agree to 32 eps kappa_p E (E the event's energy scale), so s to ~4 of that
+    # times E, and P_j moves by that over M G near its peak -- at worst the Higgs, M G = 0.5 GeV^2.
+    # alpha moves by at most (1 - alpha) times the relative change of the other channels' sum.
+    a = orc["alpha"]
+    e = np.max(np.abs(orc["mom"][:, :, 0]), axis=1)
+    kp = np.maximum(1.0, orc["aux"][:, O.AUX["cond_p"]])
+    rel_s = 4.0 * 32.0 * EPS * kp * e * e / 0.5
+    return np.maximum(RTOL, np.minimum(1.0, rel_s) * (1.0 - a))
+
+
+@pytest.mark.parametrize("case", parity_channels(), ids=lambda c: c[0])
+def test_explicit_input_parity(torch_cuda, case):
+    name, chans, which, grid = case
+    ch = chans[which]
+    d = O.dims(ch)
+    # 4999 events: 39 full tiles of 128 and a ragged tail; 2% of coordinates near 0 or 1
+    r = W.uniform_r(4242 + which, 4999, d, edge_fraction=0.02)
+    gpu = run_map(torch_cuda, chans, which, r, grid=grid)
+    orc = O.forward(ch, r, grid=grid, channels=chans, chan=which, aux=True)
+    at = _alpha_tolerance(orc) if ch["integrand"] == "pdf_sde" else None
+    n_thr = compare(gpu, orc, ch, name, alpha_tol=at, r=r)
+    st = O.stats(orc["w"])
+    s = gpu["stats"]
+    assert s["n"] == st["n"] and abs(s["n_nonzero"] - st["n_nonzero"]) <= n_thr
+    for k in ("sum_w", "sum_w2", "max_w"):
+        assert abs(s[k] - st[k]) <= max(RTOL, float(np.max(weight_tol(orc)))) * abs(st[k]), (name, k)
+
+
+@pytest.mark.parametrize("B", [0, 1, 31, 33, 127, 128, 129, 1000])
+def test_ragged_sizes(torch_cuda, B):
+    ch = W.ww_hadronic()
+    grid = W.vegas_grid_random(12, 8, 64)
+    r = W.uniform_r(77 + B, max(B, 1), 10)[:B]
+    if B == 0:
+        prog = ps.program_for([ch])
+        out, ws = prog.alloc([1], 6)
+        rt = torch_cuda.zeros((10, 1), dtype=torch_cuda.float64, device="cuda")[:, :0]
+        prog.map(0, rt.contiguous() if rt.numel() else torch_cuda.zeros((10, 1), dtype=torch_cuda.float64,
+                                                                          device="cuda")[:, :0], out, ws)
+        torch_cuda.cuda.synchronize()
+        assert prog.stats()[0]["n"] == 0.0 and prog.stats()[0]["sum_w"] == 0.0
+        return
+    gpu = run_map(torch_cuda, [ch], 0, r, grid=grid)
+    orc = O.forward(ch, r, grid=grid, aux=True)
+    compare(gpu, orc, ch, f"B={B}")
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_block_sizes(torch_cuda, block):
+    ch = W.multichannel_2to5()
+    r = W.uniform_r(90 + block, 777, 13)
+    gpu = run_map(torch_cuda, ch, 3, r, block=block)
+    orc = O.forward(ch[3], r, channels=ch, chan=3, aux=True)
+    compare(gpu, orc, ch[3], f"block={block}", alpha_tol=_alpha_tolerance(orc))
+
+
+def test_philox_bits_exact(torch_cuda):
+    """The in-kernel Philox4x32-10 stream is bit-identical to the oracle's."""
+    d = 13
+    for j in (0, 1, 6, 12):
+        g = ps.Graph.create(d)
+        (v,) = g.add("REDUCE_PRODUCT", [j], 1)
+        g.set_outputs([v], [ps.ROLE_WEIGHT])
+        prog = ps.Program([g])
+        B = 3000
+        w = torch_cuda.empty(B, dtype=torch_cuda.float64, device="cuda")
+        ws = torch_cuda.empty(prog.workspace_size([B]) // 8 + 32, dtype=torch_cuda.float64, device="cuda")
+        prog.generate([B], 0x1234_5678_9ABC_DEF0, {"weight": w}, ws, event_offset=(1 << 32) - 1000)
+        torch_cuda.cuda.synchronize()
+        ref = O.random(0x1234_5678_9ABC_DEF0, 0, (1 << 32) - 1000, B, d)[:, j]
+        assert np.array_equal(w.cpu().numpy().view(np.uint64), ref.view(np.uint64)), j
+
+
+def test_generate_parity_single_channel(torch_cuda):
+    ch = W.ww_hadronic()
+    grid = W.vegas_grid_random(13, 8, 64)
+    prog = ps.program_for([ch])
+    prog.set_vegas(0, grid)
+    B = 20_011
+    out, ws = prog.alloc([B], 6)
+    prog.generate([B], 1002, out, ws, event_offset=5)
+    torch_cuda.cuda.synchronize()
+    orc = O.forward(ch, O.random(1002, 0, 5, B, 10), grid=grid, aux=True)
+    gpu = {"mom": out["momenta"].cpu().numpy().reshape(6, 4, B).transpose(2, 0, 1),
+           "x": np.stack([out["x1"].cpu().numpy(), out["x2"].cpu().numpy()], axis=1),
+           "w": out["weight"].cpu().numpy()}
+    compare(gpu, orc, ch, "generate")
+
+
+def test_generate_parity_multichannel(torch_cuda):
+    chans = W.multichannel_2to5()
+    counts = [257, 1000, 3, 0, 640, 1501]
+    prog = ps.program_for(chans)
+    out, ws = prog.alloc(counts, 7, alpha=True)
+    prog.generate(counts, 1003, out, ws)
+    torch_cuda.cuda.synchronize()
+    tot = sum(counts)
+    mom = out["momenta"].cpu().numpy().reshape(7, 4, tot).transpose(2, 0, 1)
+    stats = prog.stats()
+    col = 0
+    for c, n in enumerate(counts):
+        if n:
+            orc = O.forward(chans[c], O.random(1003, c, 0, n, 13), channels=chans, chan=c, aux=True)
+            sl = slice(col, col + n)
+            gpu = {"mom": mom[sl], "w": out["weight"].cpu().numpy()[sl],
+                   "x": np.stack([out["x1"].cpu().numpy()[sl], out["x2"].cpu().numpy()[sl]], axis=1),
+                   "alpha": out["alpha"].cpu().numpy()[sl]}
+            compare(gpu, orc, chans[c], chans[c]["name"], alpha_tol=_alpha_tolerance(orc))
+            st = O.stats(orc["w"])
+            assert stats[c]["n_nonzero"] == st["n_nonzero"]
+            assert abs(stats[c]["sum_w"] - st["sum_w"]) <= RTOL * st["sum_w"]
+        else:
+            assert stats[c]["n"] == 0 and stats[c]["sum_w"] == 0
+        col += n
+
+
+def test_determinism_and_partition_invariance(torch_cuda):
+    ch = W.ww_hadronic()
+    prog = ps.program_for([ch])
+    N = 10_000
+    a, ws = prog.alloc([N], 6)
+    prog.generate([N], 7, a, ws)
+    b, _ = prog.alloc([N], 6)
+    prog.generate([N], 7, b, ws)
+    h1, _ = prog.alloc([N // 2], 6)
+    h2, _ = prog.alloc([N - N // 2], 6)
+    prog.generate([N // 2], 7, h1, ws, event_offset=0)
+    prog.generate([N - N // 2], 7, h2, ws, event_offset=N // 2)
+    torch_cuda.cuda.synchronize()
+    for k in ("momenta", "weight", "x1"):
+        assert torch_cuda.equal(a[k], b[k])
+    joined = torch_cuda.cat([h1["weight"], h2["weight"]])
+    assert torch_cuda.equal(a["weight"], joined)
+
+
+def test_vegas_training_histogram_and_rebin(torch_cuda):
+    ch = W.ww_hadronic()
+    grid = W.vegas_grid_random(21, 8, 64)
+    prog = ps.program_for([ch])
+    prog.set_vegas(0, grid)
+    prog.vegas_training(True)
+    B = 50_000
+    out, ws = prog.alloc([B], 6)
+    prog.generate([B], 31, out, ws)
+    torch_cuda.cuda.synchronize()
+    hist = prog.vegas_histogram(0, 8)
+    r = O.random(31, 0, 0, B, 10)
+    orc = O.forward(ch, r, grid=grid)
+    ref = O.vegas_accumulate(r, orc["w"], 8, 64)
+    nz = ref > 0
+    assert np.array_equal(hist > 0, nz)
+    assert np.all(np.abs(hist[nz] / ref[nz] - 1.0) <= 1e-12)
+    prog.vegas_adapt(0, alpha=1.5)
+    new = prog.get_vegas(0, 8)
+    ref_new = O.vegas_rebin(ref, grid, alpha=1.5)
+    assert np.max(np.abs(new - ref_new)) <= 1e-12
+    assert np.all(prog.vegas_histogram(0, 8) == 0.0)
+
+
+def test_full_size_sampled(torch_cuda):
+    """1e7 events of the 2->4 W W workload in the benchmark's launch configuration:
+    sampled events against the oracle one by one, and the channel sums against a full
+    oracle pass."""
+    ch = W.ww_hadronic()
+    grid = W.vegas_grid_random(41, 8, 64)
+    prog = ps.program_for([ch])
+    prog.set_vegas(0, grid)
+    N = 10_000_000
+    out, ws = prog.alloc([N], 6)
+    prog.generate([N], 1002, out, ws)
+    torch_cuda.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(N, 3000, replace=False))
+    idx = np.concatenate([idx, [0, 1, N - 2, N - 1]])
+    w = out["weight"].cpu().numpy()
+    mom = out["momenta"][:, idx].cpu().numpy().reshape(6, 4, idx.size).transpose(2, 0, 1)
+    x = np.stack([out["x1"][idx].cpu().numpy(), out["x2"][idx].cpu().numpy()], axis=1)
+    r = np.vstack([O.random(1002, 0, int(i), 1, 10) for i in idx])
+    orc = O.forward(ch, r, grid=grid, aux=True)
+    compare({"mom": mom, "x": x, "w": w[idx]}, orc, ch, "full-size")
+    full = O.generate(ch, 1002, 0, N, grid=grid, keep_momenta=False)
+    s = prog.stats()[0]
+    assert s["n_nonzero"] == np.count_nonzero(full["w"])
+    # channel sums against the exactly rounded sums of the oracle's weights; the allowance is
+    # the sum of the per-event weight bounds, estimated on the sampled events (x3)
+    est = float(np.sum(weight_tol(orc) * orc["w"]) / np.sum(orc["w"]))
+    s1 = math.fsum(full["w"])
+    s2 = math.fsum(full["w"] * full["w"])
+    assert abs(s["sum_w"] - s1) <= (RTOL + 3 * est) * s1, (s["sum_w"] / s1 - 1, est)
+    assert abs(s["sum_w2"] - s2) <= (RTOL + 6 * est) * s2, (s["sum_w2"] / s2 - 1, est)
+    k = int(np.argmax(full["w"]))
+    orc_k = O.forward(ch, O.random(1002, 0, k, 1, 10), grid=grid, aux=True)
+    assert abs(s["max_w"] / full["w"][k] - 1.0) <= weight_tol(orc_k)[0]
+    assert np.array_equal(w == 0, full["w"] == 0)
+    assert prog.status()["nonfinite"] == 0

@@ -1,0 +1,93 @@
+"""Host-side tests of the native library (no GPU needed): it loads, exports every
+function declared in include/ps.h, validates graphs, and the topology builder
+lays out the random dimensions as the oracle does."""
+import os
+import re
+
+import pytest
+
+from paper_2602_06895_gb300 import build as B
+from paper_2602_06895_gb300 import ps
+from paper_2602_06895_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    B.build()
+    return ps.lib()
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "ps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ps_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_function(built):
+    declared = header_functions()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(built, name), name
+    assert set(ps.exported_symbols()) == set(declared)
+
+
+def test_graph_validation_errors(built):
+    g = ps.Graph.create(2)
+    with pytest.raises(ps.PSError):
+        g.add("TWO_BODY_DECAY_COM", [0, 1, 1e6, 0.0], 3)  # too few arguments
+    with pytest.raises(ps.PSError):
+        g.add("SQRT", [99], 1)  # undefined id
+    with pytest.raises(ps.PSError):
+        g.add(12345, [0], 1)  # unknown opcode
+    p1, p2, j = g.add("TWO_BODY_DECAY_COM", [0, 1, 1e6, 0.0, 0.0], 3)
+    with pytest.raises(ps.PSError):
+        g.add("SQRT", [p1], 1)  # momentum where a scalar is expected
+    with pytest.raises(ps.PSError):
+        g.set_outputs([p1], [ps.ROLE_MOMENTUM])  # no weight
+    g.set_outputs([p1, p2, j], [ps.ROLE_MOMENTUM, ps.ROLE_MOMENTUM, ps.ROLE_WEIGHT])
+    with pytest.raises(ps.PSError):
+        g.add("SQRT", [j], 1)  # graph is closed
+
+
+def test_builder_dimensions_match_oracle(built, oracle_mod):
+    chans = [W.two_body_fixed(), W.ww_hadronic()] + W.volume_topologies(3) + W.volume_topologies(4)
+    chans += W.multichannel_2to5()
+    for ch in chans:
+        assert ps.channel_dims(ch) == oracle_mod.dims(ch) == W.n_random_dims(ch)
+
+
+def test_builder_graph_listing(built):
+    g = ps.build_channel([W.ww_hadronic()], 0)
+    info = g.info()
+    assert info["random"] == 10
+    txt = g.dump()
+    for op in ("vegas", "stable_invariant_nu", "breit_wigner_invariant", "r_to_x1x2", "com_p_in",
+               "two_body_decay", "boost_beam", "reduce_product", "cut_unphysical"):
+        assert op in txt, op
+    multi = W.multichannel_2to5()
+    txt = ps.build_channel(multi, 0).dump()
+    for op in ("t_inv_min_max", "two_to_two_particle_scattering_com", "channel_weight", "momentum_sub"):
+        assert op in txt, op
+
+
+def test_builder_rejects_bad_topology(built):
+    ch = W.ww_hadronic()
+    ch["sorder"] = ch["sorder"][:1]
+    with pytest.raises(ps.PSError):
+        ps.build_channel([ch], 0)
+    ch = W.ww_hadronic()
+    ch["nodes"][1]["children"] = [3, 3]
+    with pytest.raises(ps.PSError):
+        ps.build_channel([ch], 0)
+
+
+def test_program_without_device_fails_loudly(built):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    g = ps.build_channel([W.two_body_fixed()], 0)
+    with pytest.raises(ps.PSError):
+        ps.Program([g])
