@@ -263,6 +263,22 @@ int ps_workspace_size(ps_program p, const int64_t* events_per_ch, size_t* bytes)
 int ps_generate(ps_program p, const int64_t* events_per_ch, uint64_t seed, uint64_t event_offset,
                 const ps_out_buffers* out, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Allocation-free form of ps_generate (the paper has no counterpart): the same generation,
+ * with the per-tile scratch taken from a fixed array that the library keeps in device memory
+ * (131072 tiles of block_threads events each -- 16,777,216 events per call at the default block
+ * of 128 -- 4 MiB held on every device that loads the library, until the process exits).  For
+ * callers that cannot call cudaMalloc or hand out device memory: code running inside a host
+ * framework that owns every device allocation, or a loop that must not let an allocation
+ * synchronise the device.  The call allocates nothing.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - Event counts needing more tiles than the array holds are rejected with PS_ERR_CAPACITY.
+ *  - All calls share the one array, which keeps the last call's contents; every tile record is
+ *    written before it is read, so nothing needs clearing.  Calls whose kernels overlap on the
+ *    GPU (different streams, or different threads, without ordering) race on it: order them. */
+int ps_generate_noalloc(ps_program p, const int64_t* events_per_ch, uint64_t seed, uint64_t event_offset,
+                        const ps_out_buffers* out, void* stream);
+
 /* Explicit-input form: map `batch` given points r_dev[j * ld_r + e] (SoA, j < n_random) of
  * channel ch.  Outputs start at column 0. */
 int ps_map(ps_program p, int ch, int64_t batch, const double* r_dev, int64_t ld_r,

@@ -1201,6 +1201,28 @@ int ps_generate(ps_program p, const int64_t* events, uint64_t seed, uint64_t eve
     return PS_OK;
 }
 
+int ps_generate_noalloc(ps_program p, const int64_t* events, uint64_t seed, uint64_t event_offset,
+                        const ps_out_buffers* out, void* stream) {
+    if (!p || !events || !out) return fail(PS_ERR_INVALID_ARGUMENT, "ps_generate_noalloc: bad arguments");
+    int64_t tiles = 0;
+    for (int c = 0; c < p->n_ch; ++c) {
+        if (events[c] < 0) return fail(PS_ERR_INVALID_ARGUMENT, "ps_generate_noalloc: negative event count");
+        tiles += tiles_of(events[c], p->block);
+    }
+    if (tiles > ps::kNoallocTiles)
+        return fail(PS_ERR_CAPACITY, "ps_generate_noalloc: " + std::to_string(tiles) + " tiles of " +
+                                         std::to_string(p->block) + " events exceed the fixed scratch of " +
+                                         std::to_string(ps::kNoallocTiles) + " tiles; use ps_generate with a workspace");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(PS_ERR_CUDA, "cudaSetDevice failed");
+    void* scratch = nullptr;
+    size_t bytes = 0;
+    std::string err;
+    int st = ps::noalloc_scratch(p->device, &scratch, &bytes, &err);
+    if (st != PS_OK) return fail(st, err);
+    return ps_generate(p, events, seed, event_offset, out, scratch, bytes, stream);
+}
+
 int ps_map(ps_program p, int ch, int64_t batch, const double* r, int64_t ld_r, const ps_out_buffers* out,
            void* workspace, size_t ws_bytes, void* stream) {
     if (!p || !out || ch < 0 || ch >= p->n_ch || batch < 0 || (batch > 0 && !r) || ld_r < batch)

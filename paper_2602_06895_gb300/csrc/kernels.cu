@@ -17,6 +17,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "ps_internal.h"
@@ -673,5 +674,35 @@ int launch_reduce(const LaunchParams& lp, double* stats, void* stream, std::stri
 }
 
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+// ---------------------------------------------------------------- allocation-free scratch
+// Fixed scratch for ps_generate_noalloc: kNoallocTiles per-tile partial-sum records (4 doubles
+// each, 4 MiB) in a file-scope device array.  Every device that loads the library holds it until
+// the process exits.  Host code must not hand the symbol itself to a kernel (on the host it is
+// only a stand-in); its device address is fetched once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[static_cast<size_t>(kNoallocTiles) * 4];
+
+namespace {
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+int noalloc_scratch(int device, void** ptr, size_t* bytes, std::string* err) {
+    if (device < 0 || device >= kMaxDevices) {
+        *err = "device index beyond the library's limit";
+        return PS_ERR_INVALID_ARGUMENT;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_ptr[device] == nullptr) {
+        // set-up: the calling thread has `device` current (the caller guarantees it)
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)", err);
+        g_noalloc_ptr[device] = p;
+    }
+    *ptr = g_noalloc_ptr[device];
+    *bytes = sizeof(g_noalloc_scratch);
+    return PS_OK;
+}
 
 }  // namespace ps

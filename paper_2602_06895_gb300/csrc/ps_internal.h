@@ -13,6 +13,8 @@ namespace ps {
 constexpr int kMaxChannels = 32;
 constexpr int kMaxOutMomenta = 24;
 constexpr int kOpOutput = 1000;  // pseudo-op closing each channel's byte-code
+constexpr int kNoallocTiles = 131072;  // tiles of the allocation-free entry point's fixed scratch
+constexpr int kMaxDevices = 64;
 
 // ---------------------------------------------------------------- graph IR
 struct Arg {
@@ -97,5 +99,8 @@ int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem_bytes, void* s
 int launch_reduce(const LaunchParams& lp, double* stats_dev, void* stream, std::string* err);
 size_t smem_bytes_for(const LaunchParams& lp);
 int max_ctas_per_sm(int block, size_t smem_bytes, int* out, std::string* err);
+// Device address and size of the fixed scratch of ps_generate_noalloc on `device` (which must be
+// current); the first call on a device looks the address up.
+int noalloc_scratch(int device, void** ptr, size_t* bytes, std::string* err);
 
 }  // namespace ps

@@ -91,6 +91,8 @@ _SIGS = {
     "ps_workspace_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
     "ps_generate": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64, C.POINTER(OutBuffers),
                               C.c_void_p, C.c_size_t, C.c_void_p]),
+    "ps_generate_noalloc": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_uint64, C.c_uint64,
+                                      C.POINTER(OutBuffers), C.c_void_p]),
     "ps_map": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.POINTER(OutBuffers), C.c_void_p,
                          C.c_size_t, C.c_void_p]),
     "ps_stats": (C.c_int, [C.c_void_p, C.POINTER(ChannelStats), C.c_int, C.c_void_p]),
@@ -351,6 +353,13 @@ class Program:
         wp, wn = self._ws(ws)
         _check(lib().ps_generate(self.h, ev, seed, event_offset, C.byref(o), wp, wn, _stream_ptr(stream)),
                "ps_generate")
+
+    def generate_noalloc(self, events, seed, out, event_offset=0, stream=None):
+        """ps_generate_noalloc: the same generation without a workspace (fixed library scratch)."""
+        ev = (C.c_int64 * self.n_ch)(*[int(e) for e in events])
+        o = self._out_struct(out)
+        _check(lib().ps_generate_noalloc(self.h, ev, seed, event_offset, C.byref(o), _stream_ptr(stream)),
+               "ps_generate_noalloc")
 
     def map(self, ch, r, out, ws, stream=None):
         """r: float64 CUDA tensor [n_random, batch] (SoA, unit stride along the events)."""
