@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--events", type=int, default=EVENTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -270,6 +271,32 @@ def main():
         e2e = {"value": world * N * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": 16,
                "d2h_bytes_per_step": int(d2h + 40)}
 
+    # mixed precision (FP32 bulk, FP64 islands) on the same events: same step, same grid
+    mixed = None
+    if not args.no_mixed:
+        mprog = ps.program_for([ch], device=local, precision="mixed")
+        mprog.set_vegas(0, grid)
+        mout, mws = mprog.alloc([N], 6, device=local)
+        for k in range(args.warmup):
+            mprog.generate([N], SEED, mout, mws, event_offset=offset + k * N)
+        torch.cuda.synchronize()
+        mev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        mev[0].record(stream)
+        for k in range(args.steps):
+            mprog.generate([N], SEED, mout, mws, event_offset=offset + (args.warmup + k) * N)
+            mev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        mms = mev[0].elapsed_time(mev[-1]) / args.steps
+        mst = mprog.stats()[0]
+        # the last FP64 step and the last mixed step drew the same events
+        mess = mst["sum_w"] ** 2 / mst["sum_w2"]
+        mixed = {"value": world * N / (mms / 1e3), "ms_per_step": mms, "dtype": "f32 bulk + f64 islands",
+                 "effective_events_per_s": mess / (mms / 1e3),
+                 "integral_rel_diff_vs_fp64_same_events": mst["sum_w"] / st["sum_w"] - 1.0 if world == 1 else None,
+                 "speedup_vs_fp64": ms / mms,
+                 "bytes_per_event": 6 * 4 * 4 + 4 + 4 + 8,
+                 "hbm_gbs": (6 * 4 * 4 + 4 + 4 + 8) * N / (mms / 1e3) / 1e9}
+
     flop = FP64_FLOP_PER_EVENT
     achieved = None if flop is None else flop * N / (ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
@@ -294,7 +321,7 @@ def main():
                                                         "ess_per_step": ess, "events_for_0.5pct": n_half_pct},
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
-            "cpu_baseline": cpu}
+            "cpu_baseline": cpu, "mixed_precision": mixed}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -221,7 +221,11 @@ int ps_channel_dims(const ps_channel_desc* ch, int* n_random);
 int ps_graph_build_channel(const ps_channel_desc* ch, int n_ch, int which, ps_graph* out);
 
 /* ---------------------------------------------------------------- programs */
-#define PS_PRECISION_F64 0 /* every step in binary64 */
+#define PS_PRECISION_F64 0   /* every step in binary64 */
+#define PS_PRECISION_MIXED 1 /* bulk kinematics in binary32, binary64 islands: invariant assembly and
+                              * s - m^2, the Kallen function at threshold, the t range and small |t|,
+                              * the s-order bounds and every Jacobian product; momenta, x1, x2 and
+                              * alpha are written as binary32, weights as binary64 */
 
 typedef struct {
     int32_t block_threads; /* events per tile = threads per CTA (multiple of 32; 0 = default 128) */
@@ -240,15 +244,17 @@ int ps_program_get_vegas(ps_program p, int ch, int dims, int bins, double* edges
 
 /* Output buffers (device, caller-owned, 16-byte aligned).  Event e of channel c is stored at
  * column off_c + e, off_c = sum of the event counts of channels < c.  Momentum k, component
- * mu lives at momenta[(4k + mu) * ld + column].  Pointers for roles a graph does not have may
- * be NULL; so may any output the caller does not want (it is then not written). */
+ * mu lives at momenta[(4k + mu) * ld + column].  momenta, x1, x2 and alpha hold double for a
+ * PS_PRECISION_F64 program and float for a PS_PRECISION_MIXED program; weight is always double.
+ * Pointers for roles a graph does not have may be NULL; so may any output the caller does not
+ * want (it is then not written). */
 typedef struct {
-    double* momenta;
-    double* x1;
-    double* x2;
+    void* momenta;
+    void* x1;
+    void* x2;
     double* weight;
-    double* alpha;
-    int64_t ld; /* leading dimension of momenta (>= total events) */
+    void* alpha;
+    int64_t ld; /* leading dimension of momenta, in elements (>= total events) */
 } ps_out_buffers;
 
 /* Scratch memory needed by ps_generate / ps_map for these event counts (bytes). */

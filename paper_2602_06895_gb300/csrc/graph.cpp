@@ -1000,6 +1000,7 @@ int fill_launch(ps_program p, const int* chans, const int64_t* counts, int n, co
         return fail(PS_ERR_INVALID_ARGUMENT, "workspace must be 256-byte aligned");
     lp->tile_partials = static_cast<double*>(workspace);
     lp->status = p->d_status;
+    lp->mixed = p->opt.precision == PS_PRECISION_MIXED ? 1 : 0;
     lp->hist = p->training ? p->d_hist : nullptr;
     if (out) {
         const Compiled& C0 = p->ch[chans[0]];
@@ -1046,7 +1047,7 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
         delete p;
         return fail(PS_ERR_INVALID_ARGUMENT, "block_threads must be a multiple of 32 and at most 256");
     }
-    if (p->opt.precision != PS_PRECISION_F64) {
+    if (p->opt.precision != PS_PRECISION_F64 && p->opt.precision != PS_PRECISION_MIXED) {
         delete p;
         return fail(PS_ERR_INVALID_ARGUMENT, "unsupported precision mode");
     }
@@ -1128,7 +1129,7 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
     }
     int per_sm = 0;
     std::string err;
-    st = ps::max_ctas_per_sm(p->block, p->smem, &per_sm, &err);
+    st = ps::max_ctas_per_sm(p->block, p->smem, p->opt.precision == PS_PRECISION_MIXED, &per_sm, &err);
     if (st != PS_OK || per_sm < 1) {
         free_device(p);
         delete p;

@@ -460,6 +460,410 @@ __device__ void run_code(const int32_t* code, int len, const Frame& f, const dou
     }
 }
 
+
+// ================================================================ mixed precision
+// PS_PRECISION_MIXED: bulk kinematics in FP32 (momenta are carried as float in the slot file,
+// angles, boosts, rotations, transcendentals of the maps, parton densities), FP64 kept for the
+// islands that are sensitive to cancellation: invariant assembly x = x_min + lo e and s - m^2,
+// the Kallen function at threshold, the t range and 1 - cos(theta) for small |t|, the s-order
+// bounds, and every Jacobian product.  Scalars stay FP64 in the slot file.
+namespace mx {
+
+struct F4 {
+    float e, x, y, z;
+};
+
+__device__ __forceinline__ F4 f4_add(F4 a, F4 b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ F4 f4_sub(F4 a, F4 b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
+
+// float momentum in 4 consecutive slots (low half of each 8-byte slot)
+__device__ __forceinline__ F4 ldp(const Frame& f, int a) {
+    const float* q = reinterpret_cast<const float*>(f.S + a * f.block);
+    const int st = 2 * f.block;
+    return {q[0], q[st], q[2 * st], q[3 * st]};
+}
+__device__ __forceinline__ void stp(const Frame& f, int slot, F4 p) {
+    float* q = reinterpret_cast<float*>(f.S + slot * f.block);
+    const int st = 2 * f.block;
+    q[0] = p.e;
+    q[st] = p.x;
+    q[2 * st] = p.y;
+    q[3 * st] = p.z;
+}
+__device__ __forceinline__ float ldf(const Frame& f, int a) { return static_cast<float>(ld(f, a)); }
+
+// sqrt in FP64 from a float reciprocal-square-root seed and one Newton step in FP64:
+// s = x r, e = x - s^2, s += e r/2 (relative error ~ 1.5 delta^2 for a seed error delta).
+__device__ __forceinline__ double sqrt64(double x) {
+    if (!(x > 0.0)) return 0.0;
+    double r = static_cast<double>(rsqrtf(static_cast<float>(x)));
+    double s = x * r;
+    double e = fma(-s, s, x);
+    return fma(e, 0.5 * r, s);
+}
+
+// 1/x in FP64 from a float reciprocal seed and one Newton step.
+__device__ __forceinline__ double rcp64(double x) {
+    double r = static_cast<double>(__frcp_rn(static_cast<float>(x)));
+    double e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+__device__ __forceinline__ double kallen64(double x, double y, double z) {
+    double l;
+    if (y == 0.0 && z == 0.0) {
+        l = x * x;
+    } else if (y >= 0.0 && z >= 0.0) {
+        double ry = sqrt64(y), rz = sqrt64(z);
+        double hi = ry + rz, lo = ry - rz;
+        l = (x - hi * hi) * (x - lo * lo);
+    } else if (y <= 0.0 && z <= 0.0) {
+        double d = z - y;
+        l = x * x - 2.0 * x * (y + z) + d * d;
+    } else {
+        double d = x - y - z;
+        l = d * d - 4.0 * y * z;
+    }
+    return fmax(l, 0.0);
+}
+
+__device__ __forceinline__ F4 boost_out(F4 p, F4 q, float mq) {
+    float qp = q.x * p.x + q.y * p.y + q.z * p.z;
+    float inv = 1.0f / mq;
+    float c = qp / (mq * (q.e + mq)) + p.e * inv;
+    return {(q.e * p.e + qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
+}
+__device__ __forceinline__ F4 boost_in(F4 p, F4 q, float mq) {
+    float qp = q.x * p.x + q.y * p.y + q.z * p.z;
+    float inv = 1.0f / mq;
+    float c = qp / (mq * (q.e + mq)) - p.e * inv;
+    return {(q.e * p.e - qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
+}
+
+// power law / log map: transcendentals in float, x = x_min + lo e assembled in FP64
+__device__ __forceinline__ void map_nu(float r, double m, double nu, double xmin, double xmax, double a,
+                                       double& x, double& jac) {
+    double m2 = (m > 0.0) ? m * m : -a;
+    double lo = xmin - m2, hi = xmax - m2;
+    bool ok = (lo > 0.0) && (hi >= lo);
+    float L = log1pf(static_cast<float>(xmax - xmin) / static_cast<float>(lo));
+    float e, jf;
+    if (nu == 1.0) {
+        e = expm1f(r * L);
+        jf = (1.0f + e) * L;
+        x = fma(lo, static_cast<double>(e), xmin);
+        jac = lo * static_cast<double>(jf);
+    } else if (nu < 1.0) {
+        float w = static_cast<float>(1.0 - nu);
+        float rho = expm1f(w * L);
+        float z = r * rho;
+        e = expm1f(log1pf(z) / w);
+        jf = (1.0f + e) * rho / (w * (1.0f + z));
+        x = fma(lo, static_cast<double>(e), xmin);
+        jac = lo * static_cast<double>(jf);
+    } else {
+        float w = static_cast<float>(1.0 - nu);
+        float rho = expm1f(-w * L);
+        float z = (1.0f - r) * rho;
+        float g = expf(log1pf(z) / w);
+        double xm = hi * static_cast<double>(g);
+        x = m2 + xm;
+        jac = -xm * static_cast<double>(rho / (w * (1.0f + z)));
+    }
+    x = fmin(fmax(x, xmin), xmax);
+    if (!ok) { x = xmin; jac = 0.0; }
+}
+
+// Breit-Wigner: angles and tan in float (same endpoint-relative branches as the FP64 form),
+// s - m^2 and the assembly of x in FP64
+__device__ __forceinline__ void map_bw(float r, double M, double G, double xmin, double xmax, double& x, double& jac) {
+    double mg = M * G, m2 = M * M;
+    bool ok = (mg > 0.0) && (xmax >= xmin);
+    float mgf = static_cast<float>(mg);
+    float imgf = 1.0f / mgf;
+    float a = static_cast<float>(xmin - m2) * imgf, b = static_cast<float>(xmax - m2) * imgf;
+    float D = atan2f(static_cast<float>(xmax - xmin) * imgf, fmaf(a, b, 1.0f));
+    float u = atanf(a) + D * r;
+    bool low = u < -0.785398163f, high = u > 0.785398163f;
+    float arg = low ? D * r : (high ? D * (1.0f - r) : u);
+    float T = tanf(arg);
+    float sec2;
+    if (low) {
+        float rd = 1.0f / (1.0f - a * T);
+        x = xmin + static_cast<double>(mgf * (T * (1.0f + a * a) * rd));
+        sec2 = (1.0f + a * a) * (1.0f + T * T) * (rd * rd);
+    } else if (high) {
+        float rd = 1.0f / (1.0f + b * T);
+        x = m2 + static_cast<double>(mgf * ((b - T) * rd));
+        sec2 = (1.0f + b * b) * (1.0f + T * T) * (rd * rd);
+    } else {
+        x = m2 + static_cast<double>(mgf * T);
+        sec2 = 1.0f + T * T;
+    }
+    jac = static_cast<double>(D * mgf * sec2);
+    x = fmin(fmax(x, xmin), xmax);
+    if (!ok) { x = xmin; jac = 0.0; }
+}
+
+// t range: FP64 island (small |t|), with the fast sqrt/reciprocal
+__device__ __forceinline__ void t_range(double s, double mA2, double mB2, double m1, double m2, double& tabs_min,
+                                        double& tabs_max, double& B) {
+    double m12 = m1 * m1, m22 = m2 * m2;
+    double is = rcp64(s);
+    double A = mA2 + m12 - 0.5 * (s + mA2 - mB2) * (s + m12 - m22) * is;
+    B = 0.5 * sqrt64(kallen64(s, mA2, mB2) * kallen64(s, m12, m22)) * is;
+    double prod = (m12 - mA2) * (m22 - mB2) + (m12 * mB2 - m22 * mA2) * (m12 - m22 - mA2 + mB2) * is;
+    double big = (A <= 0.0) ? A - B : A + B;
+    double small = (big != 0.0) ? prod * rcp64(big) : 0.0;
+    tabs_min = -((A <= 0.0) ? small : big);
+    tabs_max = -((A <= 0.0) ? big : small);
+}
+
+__device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double tabs, double m1, double m2, double s,
+                                             double mA2, double mB2, F4& p1, F4& p2) {
+    F4 p0 = f4_add(pA, pB);
+    float m0 = static_cast<float>(sqrt64(s));
+    F4 a = boost_in(pA, p0, m0);
+    float pt = sqrtf(a.x * a.x + a.y * a.y);
+    float rp = rsqrtf(pt * pt + a.z * a.z);
+    float ca = a.z * rp, sa = pt * rp;
+    bool has_pt = pt > 0.0f;
+    float ipt = has_pt ? 1.0f / pt : 0.0f;
+    float cpa = has_pt ? a.x * ipt : 1.0f, spa = has_pt ? a.y * ipt : 0.0f;
+    double tlo, thi, B;
+    t_range(s, mA2, mB2, m1, m2, tlo, thi, B);
+    double dlo = tabs - tlo, dhi = thi - tabs;
+    bool near_lo = dlo <= dhi;
+    double first = (B > 0.0) ? (near_lo ? dlo : dhi) * rcp64(B) : 1.0;  // 1 - cos or 1 + cos (FP64)
+    float f1 = static_cast<float>(first);
+    float omc = (B > 0.0) ? (near_lo ? f1 : 2.0f - f1) : 1.0f;
+    float opc = (B > 0.0) ? (near_lo ? 2.0f - f1 : f1) : 1.0f;
+    float cth = (omc <= opc) ? 1.0f - omc : opc - 1.0f;
+    float sth = sqrtf(fmaxf(omc * opc, 0.0f));
+    float sph, cph;
+    sincospif(2.0f * rphi, &sph, &cph);
+    double m12 = m1 * m1, m22 = m2 * m2;
+    float i2m0 = 0.5f / m0;
+    float pabs = static_cast<float>(sqrt64(kallen64(s, m12, m22))) * i2m0;
+    float e1 = static_cast<float>(s + m12 - m22) * i2m0, e2 = static_cast<float>(s + m22 - m12) * i2m0;
+    float vx = pabs * sth * cph, vy = pabs * sth * sph, vz = pabs * cth;
+    float rx = ca * vx + sa * vz, rz = -sa * vx + ca * vz;
+    F4 q1 = {e1, cpa * rx - spa * vy, spa * rx + cpa * vy, rz};
+    F4 q2 = {e2, -q1.x, -q1.y, -q1.z};
+    p1 = boost_out(q1, p0, m0);
+    p2 = boost_out(q2, p0, m0);
+    return 0.5 * kPi * rcp64(sqrt64(kallen64(s, mA2, mB2)));
+}
+
+template <bool kBoost>
+__device__ __forceinline__ double two_body(float rphi, float rth, double s0, double m1, double m2, F4 p0, F4& p1,
+                                           F4& p2) {
+    double m12 = m1 * m1, m22 = m2 * m2;
+    double lam = kallen64(s0, m12, m22);                   // FP64 island at threshold
+    float sl = sqrtf(static_cast<float>(lam));
+    float m0 = sqrtf(static_cast<float>(s0));
+    float i2m0 = 0.5f / m0;
+    float pabs = sl * i2m0;
+    float e1 = static_cast<float>(s0 + m12 - m22) * i2m0, e2 = static_cast<float>(s0 + m22 - m12) * i2m0;
+    float cth = 2.0f * rth - 1.0f;
+    float sth = 2.0f * sqrtf(rth * (1.0f - rth));
+    float sph, cph;
+    sincospif(2.0f * rphi, &sph, &cph);
+    F4 q1 = {e1, pabs * sth * cph, pabs * sth * sph, pabs * cth};
+    F4 q2 = {e2, -q1.x, -q1.y, -q1.z};
+    if (kBoost) {
+        p1 = boost_out(q1, p0, m0);
+        p2 = boost_out(q2, p0, m0);
+    } else {
+        p1 = q1;
+        p2 = q2;
+    }
+    return static_cast<double>(0.5f * static_cast<float>(kPi) * sl / static_cast<float>(s0));
+}
+
+}  // namespace mx
+
+// Mixed-precision interpreter: same byte-code, same slot file; scalar slots hold FP64, momentum
+// slots hold FP32.
+__device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, const float* gridf, int vbins,
+                               unsigned long long* cut_count, bool active) {
+    using mx::F4;
+    int pc = 0;
+    while (pc < len) {
+        const int op = code[pc], na = code[pc + 1], no = code[pc + 2];
+        const int32_t* a = code + pc + 3;
+        const int32_t* o = a + na;
+        switch (op) {
+            case PS_OP_VEGAS: {
+                float jac = 1.0f;
+                const float nb = static_cast<float>(vbins);
+                for (int j = 0; j < na; ++j) {
+                    float r = mx::ldf(f, a[j]);
+                    float rn = r * nb;
+                    int k = max(min(static_cast<int>(rn), vbins - 1), 0);
+                    const float* e = gridf + j * (vbins + 1);
+                    float e0 = e[k], wdt = e[k + 1] - e0;
+                    st(f, o[j], static_cast<double>(fmaf(rn - static_cast<float>(k), wdt, e0)));
+                    jac *= nb * wdt;
+                }
+                st(f, o[na], static_cast<double>(jac));
+                break;
+            }
+            case PS_OP_INVARIANT_NU: {
+                double x, j;
+                mx::map_nu(mx::ldf(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), ld(f, a[5]), x, j);
+                st(f, o[0], x);
+                st(f, o[1], j);
+                break;
+            }
+            case PS_OP_INVARIANT_BW: {
+                double x, j;
+                mx::map_bw(mx::ldf(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), x, j);
+                st(f, o[0], x);
+                st(f, o[1], j);
+                break;
+            }
+            case PS_OP_R_TO_X1X2: {
+                float r = mx::ldf(f, a[0]);
+                float S = mx::ldf(f, a[2]);
+                float L = logf(mx::ldf(f, a[1]) / S);
+                st(f, o[0], static_cast<double>(fminf(expf(r * L), 1.0f)));
+                st(f, o[1], static_cast<double>(fminf(expf((1.0f - r) * L), 1.0f)));
+                st(f, o[2], static_cast<double>(-L / S));
+                break;
+            }
+            case PS_OP_COM_P_IN: {
+                float h = 0.5f * mx::ldf(f, a[0]);
+                mx::stp(f, o[0], F4{h, 0.0f, 0.0f, h});
+                mx::stp(f, o[1], F4{h, 0.0f, 0.0f, -h});
+                break;
+            }
+            case PS_OP_T_INV_MIN_MAX: {
+                double lo, hi, B;
+                mx::t_range(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), lo, hi, B);
+                st(f, o[0], lo);
+                st(f, o[1], hi);
+                break;
+            }
+            case PS_OP_TWO_TO_TWO_COM: {
+                F4 p1, p2;
+                double j = mx::two_to_two(mx::ldf(f, a[0]), mx::ldp(f, a[1]), mx::ldp(f, a[2]), ld(f, a[3]),
+                                          ld(f, a[4]), ld(f, a[5]), ld(f, a[6]), ld(f, a[7]), ld(f, a[8]), p1, p2);
+                mx::stp(f, o[0], p1);
+                mx::stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_TWO_BODY_DECAY: {
+                F4 p1, p2;
+                double j = mx::two_body<true>(mx::ldf(f, a[0]), mx::ldf(f, a[1]), ld(f, a[2]), ld(f, a[3]),
+                                              ld(f, a[4]), mx::ldp(f, a[5]), p1, p2);
+                mx::stp(f, o[0], p1);
+                mx::stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_TWO_BODY_DECAY_COM: {
+                F4 p1, p2;
+                double j = mx::two_body<false>(mx::ldf(f, a[0]), mx::ldf(f, a[1]), ld(f, a[2]), ld(f, a[3]),
+                                               ld(f, a[4]), F4{0, 0, 0, 0}, p1, p2);
+                mx::stp(f, o[0], p1);
+                mx::stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_BOOST_BEAM: {
+                float x1 = mx::ldf(f, a[na - 2]), x2 = mx::ldf(f, a[na - 1]);
+                float rho = sqrtf(x1 / x2);
+                float irho = 1.0f / rho;
+                for (int k = 0; k < na - 2; ++k) {
+                    F4 p = mx::ldp(f, a[k]);
+                    float plus = rho * (p.e + p.z), minus = (p.e - p.z) * irho;
+                    mx::stp(f, o[k], F4{0.5f * (plus + minus), p.x, p.y, 0.5f * (plus - minus)});
+                }
+                break;
+            }
+            case PS_OP_REDUCE_PRODUCT: {
+                double v = ld(f, a[0]);
+                for (int k = 1; k < na; ++k) v *= ld(f, a[k]);
+                st(f, o[0], v);
+                break;
+            }
+            case PS_OP_CUT_UNPHYSICAL: {
+                double w = ld(f, a[0]), x1 = ld(f, a[1]), x2 = ld(f, a[2]);
+                bool bad = !isfinite(w) || !(x1 > 0.0 && x1 <= 1.0 && x2 > 0.0 && x2 <= 1.0);
+                for (int k = 3; k < na; ++k) {
+                    F4 p = mx::ldp(f, a[k]);
+                    bad |= !(isfinite(p.e) && isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
+                }
+                if (bad && active) atomicAdd(cut_count, 1ULL);
+                st(f, o[0], bad ? 0.0 : w);
+                break;
+            }
+            case PS_OP_ADD: st(f, o[0], ld(f, a[0]) + ld(f, a[1])); break;
+            case PS_OP_SUB: st(f, o[0], ld(f, a[0]) - ld(f, a[1])); break;
+            case PS_OP_MUL: st(f, o[0], ld(f, a[0]) * ld(f, a[1])); break;
+            case PS_OP_DIV: st(f, o[0], ld(f, a[0]) / ld(f, a[1])); break;
+            case PS_OP_SQRT: st(f, o[0], mx::sqrt64(ld(f, a[0]))); break;
+            case PS_OP_SQUARE: { double v = ld(f, a[0]); st(f, o[0], v * v); break; }
+            case PS_OP_MAX: st(f, o[0], fmax(ld(f, a[0]), ld(f, a[1]))); break;
+            case PS_OP_MOM_ADD: mx::stp(f, o[0], mx::f4_add(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
+            case PS_OP_MOM_SUB: mx::stp(f, o[0], mx::f4_sub(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
+            case PS_OP_PDF_POWER: {
+                double xd = ld(f, a[0]);
+                float x = static_cast<float>(xd), al = mx::ldf(f, a[1]), be = mx::ldf(f, a[2]);
+                float fx = expf(al * logf(x));
+                float y = static_cast<float>(1.0 - xd);
+                float fy;
+                if (be == 3.0f) fy = y * y * y;
+                else if (be == 2.0f) fy = y * y;
+                else if (be == 1.0f) fy = y;
+                else if (be == 0.0f) fy = 1.0f;
+                else fy = powf(y, be);
+                st(f, o[0], static_cast<double>(fx * fy));
+                break;
+            }
+            case PS_OP_PROPAGATOR: {
+                double M = ld(f, a[1]);
+                float d = static_cast<float>(ld(f, a[0]) - M * M);   // s - M^2 in FP64
+                float mg = static_cast<float>(M * ld(f, a[2]));
+                st(f, o[0], static_cast<double>(1.0f / (d * d + mg * mg)));
+                break;
+            }
+            case PS_OP_ONE_PLUS_COS2: {
+                F4 p = mx::ldp(f, a[0]);
+                float c2 = p.z * p.z / (p.x * p.x + p.y * p.y + p.z * p.z);
+                st(f, o[0], static_cast<double>(1.0f + c2));
+                break;
+            }
+            case PS_OP_CHANNEL_WEIGHT: {
+                const int k = static_cast<int>(ld(f, a[0]));
+                F4 paf = mx::ldp(f, a[1]);
+                P4 pa = {paf.e, paf.x, paf.y, paf.z};
+                double P = 1.0;
+                for (int j = 2 + k; j + 3 < na; j += 4) {
+                    int kind = static_cast<int>(ld(f, a[j]));
+                    int mask = static_cast<int>(ld(f, a[j + 1]));
+                    double M = ld(f, a[j + 2]), G = ld(f, a[j + 3]);
+                    P4 q = (kind == 1) ? pa : P4{0.0, 0.0, 0.0, 0.0};
+                    for (int i = 0; i < k; ++i)
+                        if (mask & (1 << i)) {
+                            F4 qf = mx::ldp(f, a[2 + i]);
+                            P4 qi = {qf.e, qf.x, qf.y, qf.z};
+                            q = (kind == 1) ? p4_sub(q, qi) : p4_add(q, qi);
+                        }
+                    double d = p4_sq(q) - M * M;
+                    P *= (kind == 1) ? 1.0 / (d * d) : 1.0 / (d * d + M * M * G * G);
+                }
+                st(f, o[0], P);
+                break;
+            }
+            default: break;
+        }
+        pc += 3 + na + no;
+    }
+}
+
 // Locate the output descriptor [kOpOutput, n, 0, (role, slot)...] after the instructions.
 __device__ __forceinline__ int find_output(const int32_t* code, int len) {
     int pc = 0;
@@ -469,6 +873,7 @@ __device__ __forceinline__ int find_output(const int32_t* code, int len) {
 
 }  // namespace dev
 
+template <bool kMix>
 __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ LaunchParams lp) {
     extern __shared__ __align__(16) double smem[];
     const int B = lp.block;
@@ -478,6 +883,7 @@ __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ Lau
     double* s_slots = s_grid + lp.smem_grid;
     double* s_red = s_slots + static_cast<size_t>(lp.smem_slots) * B;
     int32_t* s_code = reinterpret_cast<int32_t*>(s_red + 4 * (B / 32));
+    float* s_gridf = reinterpret_cast<float*>(s_grid);  // mixed mode: the grid staged as float
 
     dev::Frame f{s_slots + tid, s_imm, B};
     int cur = -1;
@@ -491,7 +897,11 @@ __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ Lau
             for (int i = tid; i < C.code_len; i += B) s_code[i] = lp.code[C.code_off + i];
             for (int i = tid; i < C.imm_len; i += B) s_imm[i] = lp.imm[C.imm_off + i];
             const int ng = C.vdims * (C.vbins + 1);
-            for (int i = tid; i < ng; i += B) s_grid[i] = lp.grid[C.grid_off + i];
+            if (kMix) {
+                for (int i = tid; i < ng; i += B) s_gridf[i] = static_cast<float>(lp.grid[C.grid_off + i]);
+            } else {
+                for (int i = tid; i < ng; i += B) s_grid[i] = lp.grid[C.grid_off + i];
+            }
             __syncthreads();
             cur = c;
             out_pc = dev::find_output(s_code, C.code_len);
@@ -514,9 +924,10 @@ __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ Lau
             }
         }
 
-        dev::run_code(s_code, out_pc, f, s_grid, C.vbins, lp.status + 1, active);
+        if (kMix) dev::run_code_mixed(s_code, out_pc, f, s_gridf, C.vbins, lp.status + 1, active);
+        else dev::run_code(s_code, out_pc, f, s_grid, C.vbins, lp.status + 1, active);
 
-        // outputs
+        // outputs: FP64 mode writes f64 everywhere; mixed mode writes momenta, x and alpha as f32
         const int n_out = s_code[out_pc + 1];
         const int32_t* od = s_code + out_pc + 3;
         double w = 0.0;
@@ -526,20 +937,35 @@ __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ Lau
             const int role = od[2 * k], slot = od[2 * k + 1];
             if (role == PS_ROLE_MOMENTUM) {
                 if (active && lp.mom != nullptr) {
-                    dev::P4 p = dev::ldp(f, slot);
-                    double* m = lp.mom + static_cast<int64_t>(4 * mom_k) * lp.ld + col;
-                    __stcs(m, p.e);
-                    __stcs(m + lp.ld, p.x);
-                    __stcs(m + 2 * lp.ld, p.y);
-                    __stcs(m + 3 * lp.ld, p.z);
+                    if (kMix) {
+                        dev::mx::F4 p = dev::mx::ldp(f, slot);
+                        float* m = static_cast<float*>(lp.mom) + static_cast<int64_t>(4 * mom_k) * lp.ld + col;
+                        __stcs(m, p.e);
+                        __stcs(m + lp.ld, p.x);
+                        __stcs(m + 2 * lp.ld, p.y);
+                        __stcs(m + 3 * lp.ld, p.z);
+                    } else {
+                        dev::P4 p = dev::ldp(f, slot);
+                        double* m = static_cast<double*>(lp.mom) + static_cast<int64_t>(4 * mom_k) * lp.ld + col;
+                        __stcs(m, p.e);
+                        __stcs(m + lp.ld, p.x);
+                        __stcs(m + 2 * lp.ld, p.y);
+                        __stcs(m + 3 * lp.ld, p.z);
+                    }
                 }
                 ++mom_k;
             } else {
                 double v = dev::ld(f, slot);
-                double* dst = role == PS_ROLE_X1 ? lp.x1 : role == PS_ROLE_X2 ? lp.x2
-                            : role == PS_ROLE_WEIGHT ? lp.w : lp.alpha;
-                if (role == PS_ROLE_WEIGHT) w = v;
-                if (active && dst != nullptr) __stcs(dst + col, v);
+                if (role == PS_ROLE_WEIGHT) {
+                    w = v;
+                    if (active && lp.w != nullptr) __stcs(lp.w + col, v);
+                } else {
+                    void* dst = role == PS_ROLE_X1 ? lp.x1 : role == PS_ROLE_X2 ? lp.x2 : lp.alpha;
+                    if (active && dst != nullptr) {
+                        if (kMix) __stcs(static_cast<float*>(dst) + col, static_cast<float>(v));
+                        else __stcs(static_cast<double*>(dst) + col, v);
+                    }
+                }
             }
         }
         if (!active) w = 0.0;
@@ -647,18 +1073,20 @@ static int cuda_fail(cudaError_t e, const char* what, std::string* err) {
     return PS_ERR_CUDA;
 }
 
-int max_ctas_per_sm(int block, size_t smem, int* out, std::string* err) {
-    cudaError_t e = cudaFuncSetAttribute(ps_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+int max_ctas_per_sm(int block, size_t smem, int mixed, int* out, std::string* err) {
+    const void* fn = mixed ? reinterpret_cast<const void*>(ps_map_kernel<true>)
+                           : reinterpret_cast<const void*>(ps_map_kernel<false>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", err);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, ps_map_kernel, block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, block, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", err);
     return PS_OK;
 }
 
 int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem, void* stream, std::string* err) {
     if (lp.n_tiles == 0) return PS_OK;
-    ps_map_kernel<<<grid_ctas, lp.block, smem, static_cast<cudaStream_t>(stream)>>>(lp);
+    if (lp.mixed) ps_map_kernel<true><<<grid_ctas, lp.block, smem, static_cast<cudaStream_t>(stream)>>>(lp);
+    else ps_map_kernel<false><<<grid_ctas, lp.block, smem, static_cast<cudaStream_t>(stream)>>>(lp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ps_map_kernel launch", err);
     __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);

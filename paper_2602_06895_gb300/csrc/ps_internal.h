@@ -80,13 +80,14 @@ struct LaunchParams {
     const double* r;               // explicit-input mode (SoA), or nullptr for Philox
     int64_t ld_r;
     uint64_t seed;
-    // outputs
-    double* mom;
-    double* x1;
-    double* x2;
+    // outputs: f64 in FP64 programs; momenta, x1, x2 and alpha are f32 in mixed programs
+    void* mom;
+    void* x1;
+    void* x2;
     double* w;
-    double* alpha;
+    void* alpha;
     int64_t ld;
+    int32_t mixed;
     // scratch and program state
     double* tile_partials;         // [n_tiles][4]
     double* hist;                  // VEGAS histograms (program-owned), or nullptr
@@ -98,7 +99,7 @@ struct LaunchParams {
 int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem_bytes, void* stream, std::string* err);
 int launch_reduce(const LaunchParams& lp, double* stats_dev, void* stream, std::string* err);
 size_t smem_bytes_for(const LaunchParams& lp);
-int max_ctas_per_sm(int block, size_t smem_bytes, int* out, std::string* err);
+int max_ctas_per_sm(int block, size_t smem_bytes, int mixed, int* out, std::string* err);
 // Device address and size of the fixed scratch of ps_generate_noalloc on `device` (which must be
 // current); the first call on a device looks the address up.
 int noalloc_scratch(int device, void** ptr, size_t* bytes, std::string* err);

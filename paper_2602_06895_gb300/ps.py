@@ -260,14 +260,18 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+PRECISION = {"f64": 0, "mixed": 1}
+
+
 class Program:
     """A compiled multi-channel program on one device (ps_program)."""
 
-    def __init__(self, graphs, block_threads=128, ctas_per_sm=0, device=0):
+    def __init__(self, graphs, block_threads=128, ctas_per_sm=0, device=0, precision="f64"):
         self.graphs = list(graphs)
         self.n_ch = len(self.graphs)
+        self.precision = precision
         hs = (C.c_void_p * self.n_ch)(*[g.h.value for g in self.graphs])
-        opt = Options(block_threads, ctas_per_sm, 0, 0)
+        opt = Options(block_threads, ctas_per_sm, PRECISION[precision], 0)
         h = C.c_void_p()
         _check(lib().ps_program_create(hs, self.n_ch, C.byref(opt), device, C.byref(h)), "ps_program_create")
         self.h = h
@@ -322,13 +326,14 @@ class Program:
 
         dev = torch.device("cuda", self.device if device is None else device)
         tot = int(sum(events))
-        out = {"momenta": torch.empty((4 * n_momenta, max(tot, 1)), dtype=torch.float64, device=dev),
+        ft = torch.float32 if self.precision == "mixed" else torch.float64  # momenta, x, alpha
+        out = {"momenta": torch.empty((4 * n_momenta, max(tot, 1)), dtype=ft, device=dev),
                "weight": torch.empty(max(tot, 1), dtype=torch.float64, device=dev)}
         if x:
-            out["x1"] = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
-            out["x2"] = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
+            out["x1"] = torch.empty(max(tot, 1), dtype=ft, device=dev)
+            out["x2"] = torch.empty(max(tot, 1), dtype=ft, device=dev)
         if alpha:
-            out["alpha"] = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
+            out["alpha"] = torch.empty(max(tot, 1), dtype=ft, device=dev)
         ws = torch.empty(self.workspace_size(events) // 8 + 32, dtype=torch.float64, device=dev)
         return out, ws
 
@@ -390,7 +395,8 @@ def launch_count():
     return lib().ps_launch_count()
 
 
-def program_for(channels, block_threads=128, ctas_per_sm=0, device=0):
+def program_for(channels, block_threads=128, ctas_per_sm=0, device=0, precision="f64"):
     """Build every channel of a workload list and compile them into one program."""
     graphs = [build_channel(channels, c) for c in range(len(channels))]
-    return Program(graphs, block_threads=block_threads, ctas_per_sm=ctas_per_sm, device=device)
+    return Program(graphs, block_threads=block_threads, ctas_per_sm=ctas_per_sm, device=device,
+                   precision=precision)
