@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-multichannel", action="store_true")
     return ap.parse_args()
 
 
@@ -297,6 +298,38 @@ def main():
                  "bytes_per_event": 6 * 4 * 4 + 4 + 4 + 8,
                  "hbm_gbs": (6 * 4 * 4 + 4 + 4 + 8) * N / (mms / 1e3) / 1e9}
 
+    # multichannel 2->5: six channels of mixed topology, uneven counts (1e5 .. 4e6, 2e7 in all), one
+    # persistent launch per step, tiles and schedule from the autotuner, replayed as a CUDA graph
+    multi = None
+    if not args.no_multichannel:
+        chans = W.multichannel_2to5()
+        counts = list(W.MULTICHANNEL_EVENTS)
+        best, table = ps.autotune(chans, [c // 8 for c in counts], blocks=(64, 128, 256), ctas=(1, 2, 3, 4),
+                                  reps=2, device=local)
+        mprog = ps.program_for(chans, device=local, **best)
+        mout, mws = mprog.alloc(counts, 7, alpha=True, device=local)
+        ex = mprog.exec_create(counts, mout, mws)
+        for k in range(args.warmup):
+            ex.launch(1003, offset + k * sum(counts))
+        torch.cuda.synchronize()
+        l0 = ps.launch_count()
+        cev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        cev[0].record(stream)
+        for k in range(args.steps):
+            ex.launch(1003, offset + (args.warmup + k) * sum(counts), stream)
+            cev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        cms = cev[0].elapsed_time(cev[-1]) / args.steps
+        cst = mprog.stats()
+        multi = {"workload": "2->5 massless at sqrt(S)=13 TeV, 6 channels (t-chains with Z/H/T resonances, "
+                             "pure s), SDE multichannel weights in-kernel, events " + str(counts),
+                 "value": world * sum(counts) / (cms / 1e3), "unit": UNIT, "ms_per_step": cms,
+                 "precision": "fp64", "map_launches_per_step": 1,
+                 "gpu_launches": int(ps.launch_count() - l0), "cuda_graph": True,
+                 "autotuned": best, "autotune_table": table,
+                 "integral": sum(c["sum_w"] for c in cst) / 1.0,
+                 "per_channel_sum_w": [c["sum_w"] for c in cst]}
+
     flop = FP64_FLOP_PER_EVENT
     achieved = None if flop is None else flop * N / (ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
@@ -321,7 +354,7 @@ def main():
                                                         "ess_per_step": ess, "events_for_0.5pct": n_half_pct},
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
-            "cpu_baseline": cpu, "mixed_precision": mixed}
+            "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

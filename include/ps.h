@@ -290,6 +290,18 @@ int ps_generate_noalloc(ps_program p, const int64_t* events_per_ch, uint64_t see
 int ps_map(ps_program p, int ch, int64_t batch, const double* r_dev, int64_t ld_r,
            const ps_out_buffers* out, void* workspace, size_t workspace_bytes, void* stream);
 
+/* CUDA-graph executor of ps_generate.  ps_exec_create captures one ps_generate call (the map
+ * kernel and the reduction) for fixed event counts, output buffers and workspace into a CUDA
+ * graph and instantiates it; ps_exec_launch replays it on `stream` with a new seed and event
+ * offset, which it writes into the captured kernel nodes, so that successive replays draw new
+ * events without a new capture.  The buffers given at creation must stay valid while the
+ * executor is used.  Capture happens on a private stream of the program's device. */
+typedef struct ps_exec_s* ps_exec;
+int ps_exec_create(ps_program p, const int64_t* events_per_ch, const ps_out_buffers* out, void* workspace,
+                   size_t workspace_bytes, ps_exec* exec_out);
+int ps_exec_launch(ps_exec e, uint64_t seed, uint64_t event_offset, void* stream);
+int ps_exec_free(ps_exec e);
+
 typedef struct {
     double n;          /* events                */
     double n_nonzero;  /* events with w != 0    */

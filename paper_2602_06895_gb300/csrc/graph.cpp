@@ -18,6 +18,8 @@
 
 namespace ps {
 unsigned long long launch_count();
+void count_launches(int n);
+bool is_map_kernel(const void* func);
 }
 
 using ps::Arg;
@@ -1199,6 +1201,103 @@ int ps_generate(ps_program p, const int64_t* events, uint64_t seed, uint64_t eve
     }
     st = ps::launch_reduce(lp, p->d_stats, stream, &err);
     if (st != PS_OK) return fail(st, err);
+    return PS_OK;
+}
+
+}  // extern "C"
+
+struct ps_exec_s {
+    ps_program p = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t map_node = nullptr, reduce_node = nullptr;
+    ps::LaunchParams lp;
+    double* stats = nullptr;
+    int grid = 0;
+};
+
+extern "C" {
+
+int ps_exec_create(ps_program p, const int64_t* events, const ps_out_buffers* out, void* workspace,
+                   size_t ws_bytes, ps_exec* exec_out) {
+    if (!p || !events || !out || !exec_out) return fail(PS_ERR_INVALID_ARGUMENT, "ps_exec_create: bad arguments");
+    ps_exec e = new (std::nothrow) ps_exec_s;
+    if (!e) return fail(PS_ERR_CAPACITY, "out of host memory");
+    e->p = p;
+    std::vector<int> chans(p->n_ch);
+    for (int c = 0; c < p->n_ch; ++c) chans[c] = c;
+    int st = fill_launch(p, chans.data(), events, p->n_ch, out, workspace, ws_bytes, &e->lp);
+    if (st != PS_OK) { delete e; return st; }
+    e->lp.r = nullptr;
+    e->stats = p->d_stats;
+    e->grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>(e->lp.n_tiles, 1), p->grid_ctas));
+    DeviceGuard dg(p->device);
+    cudaStream_t cs;
+    st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (st != PS_OK) { delete e; return st; }
+    std::string err;
+    st = cuda_check(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    if (st == PS_OK && e->lp.n_tiles > 0) st = ps::launch_map(e->lp, e->grid, p->smem, cs, &err);
+    if (st == PS_OK) st = ps::launch_reduce(e->lp, e->stats, cs, &err);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (st != PS_OK) { if (g) cudaGraphDestroy(g); delete e; return fail(st, err.empty() ? t_err : err); }
+    st = cuda_check(ce, "cudaStreamEndCapture");
+    if (st != PS_OK) { delete e; return st; }
+    e->graph = g;
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(g, nodes.data(), &n);
+    for (size_t k = 0; k < n; ++k) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(nodes[k], &t);
+        if (t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(nodes[k], &kp) != cudaSuccess) continue;
+        if (ps::is_map_kernel(kp.func)) e->map_node = nodes[k];
+        else e->reduce_node = nodes[k];
+    }
+    if (e->lp.n_tiles > 0 && !e->map_node) {
+        cudaGraphDestroy(g);
+        delete e;
+        return fail(PS_ERR_CUDA, "ps_exec_create: the captured graph has no map kernel node");
+    }
+    st = cuda_check(cudaGraphInstantiate(&e->exec, g, 0), "cudaGraphInstantiate");
+    if (st != PS_OK) { cudaGraphDestroy(g); delete e; return st; }
+    *exec_out = e;
+    return PS_OK;
+}
+
+int ps_exec_launch(ps_exec e, uint64_t seed, uint64_t event_offset, void* stream) {
+    if (!e) return fail(PS_ERR_INVALID_ARGUMENT, "ps_exec_launch: null executor");
+    e->lp.seed = seed;
+    for (int c = 0; c < e->lp.n_ch; ++c) e->lp.ch[c].ev_offset = static_cast<int64_t>(event_offset);
+    DeviceGuard dg(e->p->device);
+    if (e->map_node) {
+        cudaKernelNodeParams kp;
+        int st = cuda_check(cudaGraphKernelNodeGetParams(e->map_node, &kp), "cudaGraphKernelNodeGetParams");
+        if (st != PS_OK) return st;
+        void* args[1] = {&e->lp};
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        st = cuda_check(cudaGraphExecKernelNodeSetParams(e->exec, e->map_node, &kp), "cudaGraphExecKernelNodeSetParams");
+        if (st != PS_OK) return st;
+    }
+    int st = cuda_check(cudaGraphLaunch(e->exec, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
+    if (st == PS_OK) ps::count_launches(e->map_node ? 2 : 1);
+    return st;
+}
+
+int ps_exec_free(ps_exec e) {
+    if (!e) return PS_OK;
+    {
+        DeviceGuard dg(e->p->device);
+        if (e->exec) cudaGraphExecDestroy(e->exec);
+        if (e->graph) cudaGraphDestroy(e->graph);
+    }
+    delete e;
     return PS_OK;
 }
 

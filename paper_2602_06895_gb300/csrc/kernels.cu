@@ -1102,6 +1102,11 @@ int launch_reduce(const LaunchParams& lp, double* stats, void* stream, std::stri
 }
 
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+void count_launches(int n) { __atomic_add_fetch(&g_launches, static_cast<unsigned long long>(n), __ATOMIC_RELAXED); }
+bool is_map_kernel(const void* func) {
+    return func == reinterpret_cast<const void*>(ps_map_kernel<true>) ||
+           func == reinterpret_cast<const void*>(ps_map_kernel<false>);
+}
 
 // ---------------------------------------------------------------- allocation-free scratch
 // Fixed scratch for ps_generate_noalloc: kNoallocTiles per-tile partial-sum records (4 doubles

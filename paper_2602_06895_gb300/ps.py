@@ -95,6 +95,10 @@ _SIGS = {
                                       C.POINTER(OutBuffers), C.c_void_p]),
     "ps_map": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.POINTER(OutBuffers), C.c_void_p,
                          C.c_size_t, C.c_void_p]),
+    "ps_exec_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(OutBuffers), C.c_void_p, C.c_size_t,
+                                 C.POINTER(C.c_void_p)]),
+    "ps_exec_launch": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p]),
+    "ps_exec_free": (C.c_int, [C.c_void_p]),
     "ps_stats": (C.c_int, [C.c_void_p, C.POINTER(ChannelStats), C.c_int, C.c_void_p]),
     "ps_vegas_training": (C.c_int, [C.c_void_p, C.c_int]),
     "ps_vegas_histogram": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
@@ -376,6 +380,10 @@ class Program:
         _check(lib().ps_map(self.h, ch, r.shape[1], _ptr(r), ld, C.byref(o), wp, wn, _stream_ptr(stream)),
                "ps_map")
 
+    def exec_create(self, events, out, ws):
+        """Capture one generation for these counts and buffers into a CUDA graph (ps_exec)."""
+        return Exec(self, events, out, ws)
+
     def stats(self, stream=None):
         arr = (ChannelStats * self.n_ch)()
         _check(lib().ps_stats(self.h, arr, self.n_ch, _stream_ptr(stream)), "ps_stats")
@@ -389,6 +397,62 @@ class Program:
 
     def status_reset(self, stream=None):
         _check(lib().ps_status_reset(self.h, _stream_ptr(stream)), "ps_status_reset")
+
+
+class Exec:
+    """CUDA-graph executor of one generation (ps_exec): replay with a new seed and offset."""
+
+    def __init__(self, prog, events, out, ws):
+        self.prog = prog
+        self.out, self.ws = out, ws  # the captured graph refers to these buffers
+        ev = (C.c_int64 * prog.n_ch)(*[int(e) for e in events])
+        o = Program._out_struct(out)
+        wp, wn = Program._ws(ws)
+        h = C.c_void_p()
+        _check(lib().ps_exec_create(prog.h, ev, C.byref(o), wp, wn, C.byref(h)), "ps_exec_create")
+        self.h = h
+
+    def launch(self, seed, event_offset=0, stream=None):
+        _check(lib().ps_exec_launch(self.h, seed, event_offset, _stream_ptr(stream)), "ps_exec_launch")
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.ps_exec_free(self.h)
+            self.h = C.c_void_p()
+
+
+def autotune(channels, events, precision="f64", blocks=(64, 128, 256), ctas=(1, 2, 3, 4), seed=1, reps=3,
+             device=0):
+    """Pick block_threads and CTAs per SM for a workload by timing ps_generate on it.
+
+    Every candidate compiles the program, generates the full event counts `reps` times after
+    one warm-up and keeps the median CUDA-event time; returns (best options, table)."""
+    import torch
+
+    table = []
+    for b in blocks:
+        for k in ctas:
+            try:
+                prog = program_for(channels, block_threads=b, ctas_per_sm=k, device=device, precision=precision)
+            except PSError:
+                continue
+            n_mom = channels[0]["n"] + 2
+            out, ws = prog.alloc(events, n_mom, x=channels[0]["hadronic"],
+                                 alpha=channels[0]["integrand"] == "pdf_sde", device=device)
+            prog.generate(events, seed, out, ws)
+            times = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                prog.generate(events, seed, out, ws)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            times.sort()
+            table.append({"block_threads": b, "ctas_per_sm": k, "ms": times[len(times) // 2]})
+            del prog, out, ws
+    best = min(table, key=lambda t: t["ms"])
+    return {"block_threads": best["block_threads"], "ctas_per_sm": best["ctas_per_sm"]}, table
 
 
 def launch_count():
