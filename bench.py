@@ -193,6 +193,7 @@ def main():
     import torch
 
     from paper_2602_06895_gb300 import build as B
+    from paper_2602_06895_gb300 import distributed as D
     from paper_2602_06895_gb300 import ps
     from paper_2602_06895_gb300 import workloads as W
 
@@ -212,11 +213,11 @@ def main():
     prog.set_vegas(0, grid)
     out, ws = prog.alloc([N], 6, device=local)
     stream = torch.cuda.current_stream()
-    offset = rank * N * (args.steps + args.warmup + 1)
+    off = lambda step: D.step_offset(rank, world, N, step)  # disjoint event ranges per rank and step
 
     # warm-up
     for k in range(args.warmup):
-        prog.generate([N], SEED, out, ws, event_offset=offset + k * N)
+        prog.generate([N], SEED, out, ws, event_offset=off(k))
     torch.cuda.synchronize()
 
     # timed region: K steps, CUDA events on the launching stream, barrier + sync both sides
@@ -231,7 +232,7 @@ def main():
     launches0 = ps.launch_count()
     ev[0].record(stream)
     for k in range(args.steps):
-        prog.generate([N], SEED, out, ws, event_offset=offset + (args.warmup + k) * N)
+        prog.generate([N], SEED, out, ws, event_offset=off(args.warmup + k))
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
     launches = ps.launch_count() - launches0
@@ -243,9 +244,7 @@ def main():
         t = torch.tensor([total_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-        s = torch.tensor([st["n"], st["n_nonzero"], st["sum_w"], st["sum_w2"]], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(s)
-        st = dict(zip(["n", "n_nonzero", "sum_w", "sum_w2"], s.tolist()))
+        st = D.combine_stats([st], device="cuda")[0]  # the one exchange: the global per-channel sums
     ms = total_ms / args.steps
     value = world * N * args.steps / (total_ms / 1e3)
     mean = st["sum_w"] / st["n"]
@@ -263,7 +262,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            prog.generate([N], SEED, out, ws, event_offset=offset + k * N)
+            prog.generate([N], SEED, out, ws, event_offset=off(k))
             for key, v in out.items():
                 host[key].copy_(v, non_blocking=True)
             prog.stats()  # per-channel sums to the host (synchronises the stream)
@@ -279,12 +278,12 @@ def main():
         mprog.set_vegas(0, grid)
         mout, mws = mprog.alloc([N], 6, device=local)
         for k in range(args.warmup):
-            mprog.generate([N], SEED, mout, mws, event_offset=offset + k * N)
+            mprog.generate([N], SEED, mout, mws, event_offset=off(k))
         torch.cuda.synchronize()
         mev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         mev[0].record(stream)
         for k in range(args.steps):
-            mprog.generate([N], SEED, mout, mws, event_offset=offset + (args.warmup + k) * N)
+            mprog.generate([N], SEED, mout, mws, event_offset=off(args.warmup + k))
             mev[k + 1].record(stream)
         torch.cuda.synchronize()
         mms = mev[0].elapsed_time(mev[-1]) / args.steps
@@ -310,13 +309,13 @@ def main():
         mout, mws = mprog.alloc(counts, 7, alpha=True, device=local)
         ex = mprog.exec_create(counts, mout, mws)
         for k in range(args.warmup):
-            ex.launch(1003, offset + k * sum(counts))
+            ex.launch(1003, D.step_offset(rank, world, sum(counts), k))
         torch.cuda.synchronize()
         l0 = ps.launch_count()
         cev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         cev[0].record(stream)
         for k in range(args.steps):
-            ex.launch(1003, offset + (args.warmup + k) * sum(counts), stream)
+            ex.launch(1003, D.step_offset(rank, world, sum(counts), args.warmup + k), stream)
             cev[k + 1].record(stream)
         torch.cuda.synchronize()
         cms = cev[0].elapsed_time(cev[-1]) / args.steps
