@@ -329,6 +329,79 @@ int ps_status_reset(ps_program p, void* stream);
 
 int ps_program_free(ps_program p);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned proposal: rational-quadratic-spline coupling flow (neural importance sampling with
+ * rational-quadratic spline transformations, Sec. 3.2.2; spline of Durkan et al. 2019, whose
+ * single-bin case is the RQF of Sec. 2.3).  The flow maps z in (0,1)^d, drawn from Philox,
+ * to r in (0,1)^d, which feeds ps_map's explicit-input mode; the event weight becomes
+ * w = w_map |dr/dz|  (the flow density in r is |dz/dr|).
+ *
+ * Coupling layer l transforms the dims whose index has bit (l mod nbits) different from
+ * ((l div nbits) mod 2), nbits = ceil(log2 d), conditioned on the other dims through the MLP
+ *     A -> Linear(hidden) -> SiLU -> Linear(hidden) -> SiLU -> Linear(n_B (3 bins + 1)),
+ * giving per transformed dim `bins` width logits, `bins` height logits and bins+1 derivative
+ * pre-activations:  widths/heights = 1e-3 + (1 - bins 1e-3) softmax(.), knot derivatives =
+ * 1e-3 + softplus(.).  The GEMMs run on tensor cores with bfloat16 operands and FP32
+ * accumulation; splines, log-determinants and the backward pass run in FP32.
+ *
+ * Parameters (logical layout of get/set/gradients, float32, per layer l in order):
+ *     W1 [hidden][n_A], b1 [hidden], W2 [hidden][hidden], b2 [hidden],
+ *     W3 [n_B (3 bins + 1)][hidden], b3 [n_B (3 bins + 1)]
+ * (rows of W3/b3: transformed dim q in ps_flow_mask order, then widths, heights,
+ * derivatives).  A new flow starts at the identity: W3 = 0 and derivative biases
+ * log(expm1(1 - 1e-3)); hidden weights uniform in +-1/sqrt(fan_in) from `init_seed`.
+ *
+ * Training minimises the importance-weighted forward KL divergence, on the last sampled
+ * batch:  L = - sum_b (w_b / sum w) log g(r_b),  w_b = w_map_b |dr/dz|_b, with w_b held fixed
+ * (its gradient is not taken), by Adam (beta 0.9, 0.999, eps 1e-8).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct ps_flow_s* ps_flow;
+
+/* Message of the last failed flow call on this thread. */
+const char* ps_flow_last_error(void);
+
+/* Create a flow on `device`: 2 <= dims <= 16, 1 <= n_layers <= 8, 1 <= bins <= 32,
+ * hidden a multiple of 16 in [16, 512], 1 <= max_batch <= 2^24 events per sample chunk.
+ * Allocates the parameters, Adam state and the activations of max_batch events
+ * (about (L (10 hidden + 4 P) + 4 P + 20 hidden) bytes per event).  Synchronises. */
+int ps_flow_create(int dims, int n_layers, int bins, int hidden, int64_t max_batch, uint64_t init_seed, int device,
+                   ps_flow* out);
+int ps_flow_free(ps_flow f);
+/* Shape and the number of logical parameters. Any output pointer may be null. */
+int ps_flow_info(ps_flow f, int* dims, int* n_layers, int* bins, int* hidden, int64_t* n_params);
+/* Transformed dims of `layer` (ascending) into transformed[<= dims]. */
+int ps_flow_mask(ps_flow f, int layer, int* transformed, int* n_transformed);
+/* Copy the FP32 master parameters to/from host memory in the logical layout (n must equal
+ * n_params).  Synchronous. */
+int ps_flow_get_params(ps_flow f, float* host, int64_t n);
+int ps_flow_set_params(ps_flow f, const float* host, int64_t n);
+
+/* Draw `batch` events on `stream`: z from Philox4x32-10 with counter (event lo, event hi,
+ * 0x466C6F77, j/2) and key (seed lo, seed hi), dims 2i and 2i+1 from words 0 and 1 of the
+ * block i, z = (top 23 bits + 1/2) 2^-23; then r = flow(z), clamped to [1e-7, 1 - 1e-7].
+ * Device outputs (SoA, column = event, leading dimension ld_r >= batch):
+ *     r[j ld_r + b] (double, required), logdet[b] = log |dr/dz| (double, may be null),
+ *     z[j ld_r + b] (double, may be null).
+ * Batches above max_batch run in chunks; a later ps_flow_train_step needs batch <= max_batch
+ * (it uses the activations of this call).  Asynchronous. */
+int ps_flow_sample(ps_flow f, int64_t batch, uint64_t seed, uint64_t event_offset, double* r, int64_t ld_r,
+                   double* logdet, double* z, void* stream);
+/* The inverse map: z = flow^-1(r) and logq[b] = log g(r_b) = -log |dr/dz| for `batch` points r
+ * (device, SoA [dims][ld_r], double); z has the layout of r; logq may be null.  Runs in chunks
+ * of max_batch; discards the activations of the last sample.  Asynchronous. */
+int ps_flow_inverse(ps_flow f, int64_t batch, const double* r, int64_t ld_r, double* z, double* logq,
+                    void* stream);
+/* w[b] = w_map[b] exp(logdet[b]) (non-finite -> 0); device pointers.  Asynchronous. */
+int ps_flow_weights(ps_flow f, int64_t batch, const double* w_map, const double* logdet, double* w, void* stream);
+/* One Adam step with learning rate lr on the loss of the last sampled batch, whose phase-space
+ * weights w_map (device, [batch]) the caller computed from that batch's r.  Asynchronous. */
+int ps_flow_train_step(ps_flow f, const double* w_map, double lr, void* stream);
+/* The loss gradient of the last sampled batch in the logical layout (host, n = n_params) and
+ * the loss value, without updating parameters.  Synchronises `stream`. */
+int ps_flow_gradients(ps_flow f, const double* w_map, float* host, int64_t n, double* loss, void* stream);
+/* Loss and sum of w of the last train_step / gradients call.  Synchronises `stream`. */
+int ps_flow_loss(ps_flow f, double* loss, double* sum_w, void* stream);
+
 /* Number of kernel launches issued by the library since load (all programs). */
 int64_t ps_launch_count(void);
 

@@ -158,4 +158,4 @@ class Flow:
         for p in self.params:
             for t in p.values():
                 t.requires_grad_(False)
-        return float(L), grads
+        return float(L.detach()), grads

@@ -1,0 +1,1075 @@
+// flow.cu -- rational-quadratic-spline coupling flow on the GPU: the learned proposal that
+// replaces or refines the VEGAS grid (neural importance sampling with rational-quadratic spline
+// transformations, Sec. 3.2.2; the spline of Durkan et al. 2019, whose single-bin case is the
+// RQF of Sec. 2.3).
+//
+// Layer l transforms the dims B_l with a monotone spline on [0,1] whose K widths, K heights and
+// K+1 knot derivatives come from an MLP of the other dims A_l:
+//     A -> Linear(H) -> SiLU -> Linear(H) -> SiLU -> Linear(|B| (3K+1)).
+// The MLP GEMMs run on the tensor cores in bfloat16 with FP32 accumulation (warp-level
+// mma.sync m16n8k16, with bias, SiLU and the bfloat16 copy of the activation fused into the
+// epilogue); the spline, its log-determinant and the backward pass run in FP32.
+//
+// Training minimises the importance-weighted forward KL  L = sum_b c_b sum_l sum_{j in B_l}
+// log F_l'(x_j^(l)),  c_b = w_b / sum w,  w_b = f J_map / g  on samples the flow itself drew
+// (r fixed).  The inverse chain r -> z is the stored forward chain; the backward sweep runs
+// l = 0 .. L-1 with the implicit-function rule  d x^(l) / d x^(l+1) = 1/F',  d x^(l)/d theta =
+// -F_theta/F',  and the derivatives F_theta, F'_theta, F'' of the bin formula are obtained by
+// forward-mode differentiation (dual numbers with 7 tangents) of the spline formula itself.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "philox.cuh"
+#include "ps.h"
+
+namespace ps {
+void count_launches(int n);
+namespace flow {
+
+constexpr int kMaxDims = 16;
+constexpr int kMaxLayers = 8;
+constexpr int kMaxBins = 32;
+constexpr float kMinW = 1e-3f, kMinH = 1e-3f, kMinD = 1e-3f;
+constexpr int kInPad = 16;  // MLP input width (conditioning dims, zero padded)
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------------------------------------
+// BF16 tensor-core GEMM: C[m, n] = sum_k A(m, k) B(n, k) (+ bias[n]), A(m,k) = A[m*lam + k*lak],
+// B(n,k) = B[n*lbn + k*lbk]; 64x64 tile per CTA (4 warps of 32x32), K in steps of 32 through
+// shared memory; FP32 accumulate; epilogue: fp32 store or atomic add, and a bfloat16 copy of
+// the (optionally SiLU-activated) result.  grid.z splits K (for the batch-long weight
+// gradients, which accumulate with atomics).
+struct GemmArgs {
+    const bf16* A;
+    int64_t lam, lak;
+    const bf16* B;
+    int64_t lbn, lbk;
+    int M, N, K;
+    int kchunk;
+    const float* bias;
+    float* C;
+    int64_t ldc;
+    bf16* Cb;
+    int64_t ldcb;
+    int act;      // 1: SiLU on the bf16 copy
+    int atomic;   // 1: atomicAdd into C
+    int trans_c;  // 1: C(m, n) stored at C[n * ldc + m] (fp32 only)
+};
+
+__device__ __forceinline__ float silu(float x) { return x / (1.0f + __expf(-x)); }
+
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
+    __shared__ __align__(16) bf16 As[64][40];
+    __shared__ __align__(16) bf16 Bs[64][40];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    const int k_begin = blockIdx.z * g.kchunk;
+    const int k_end = min(g.K, k_begin + g.kchunk);
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+    const bf16 zero = __float2bfloat16(0.0f);
+    for (int k0 = k_begin; k0 < k_end; k0 += 32) {
+        for (int idx = tid; idx < 64 * 32; idx += 128) {
+            int m, k;
+            if (g.lak == 1) { m = idx >> 5; k = idx & 31; } else { m = idx & 63; k = idx >> 6; }
+            int gm = m0 + m, gk = k0 + k;
+            As[m][k] = (gm < g.M && gk < k_end) ? g.A[gm * g.lam + gk * g.lak] : zero;
+            int n;
+            if (g.lbk == 1) { n = idx >> 5; k = idx & 31; } else { n = idx & 63; k = idx >> 6; }
+            int gn = n0 + n;
+            gk = k0 + k;
+            Bs[n][k] = (gn < g.N && gk < k_end) ? g.B[gn * g.lbn + gk * g.lbk] : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < 32; ks += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                int r = wm + i * 16 + gq;
+                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tq]);
+                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tq]);
+                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tq + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int n = wn + j * 8 + gq;
+                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * tq]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                int row = m0 + wm + i * 16 + gq + (e >= 2 ? 8 : 0);
+                int col = n0 + wn + j * 8 + 2 * tq + (e & 1);
+                if (row >= g.M || col >= g.N) continue;
+                float v = acc[i][j][e];
+                if (g.bias && blockIdx.z == 0) v += g.bias[col];
+                if (g.atomic) {
+                    atomicAdd(g.C + row * g.ldc + col, v);
+                } else if (g.trans_c) {
+                    g.C[col * g.ldc + row] = v;
+                } else {
+                    if (g.C) g.C[row * g.ldc + col] = v;
+                    if (g.Cb) g.Cb[row * g.ldcb + col] = __float2bfloat16(g.act ? silu(v) : v);
+                }
+            }
+}
+
+// ------------------------------------------------------------------------------------------
+// dual numbers with 7 tangents: (x, x_k, w_k, y_k, h_k, d_k, d_{k+1})
+struct Dual {
+    float v;
+    float t[7];
+};
+__device__ __forceinline__ Dual dconst(float v) {
+    Dual r;
+    r.v = v;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r.t[i] = 0.0f;
+    return r;
+}
+__device__ __forceinline__ Dual dvar(float v, int i) {
+    Dual r = dconst(v);
+    r.t[i] = 1.0f;
+    return r;
+}
+__device__ __forceinline__ Dual operator+(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r.t[i] = a.t[i] + b.t[i];
+    return r;
+}
+__device__ __forceinline__ Dual operator-(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r.t[i] = a.t[i] - b.t[i];
+    return r;
+}
+__device__ __forceinline__ Dual operator*(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r.t[i] = a.t[i] * b.v + a.v * b.t[i];
+    return r;
+}
+__device__ __forceinline__ Dual operator/(const Dual& a, const Dual& b) {
+    Dual r;
+    float ib = 1.0f / b.v;
+    r.v = a.v * ib;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r.t[i] = (a.t[i] - r.v * b.t[i]) * ib;
+    return r;
+}
+__device__ __forceinline__ Dual operator*(float s, const Dual& a) {
+    Dual r;
+    r.v = s * a.v;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r.t[i] = s * a.t[i];
+    return r;
+}
+
+__device__ __forceinline__ Dual operator-(const Dual& a, float b) {
+    Dual r = a;
+    r.v -= b;
+    return r;
+}
+__device__ __forceinline__ Dual operator*(const Dual& a, float b) { return b * a; }
+
+// The bin formula: y = y_k + h [s xi^2 + d0 xi(1-xi)] / [s + (d1 + d0 - 2s) xi (1-xi)] and its
+// derivative F' = s^2 [d1 xi^2 + 2 s xi (1-xi) + d0 (1-xi)^2] / [..]^2, s = h/w, xi = (x-x_k)/w.
+template <typename T>
+__device__ __forceinline__ void bin_eval(const T& x, const T& x0, const T& w, const T& y0, const T& h, const T& d0,
+                                         const T& d1, T& F, T& Fp) {
+    T xi = (x - x0) / w;
+    T s = h / w;
+    T om = xi - xi * xi;
+    T xm = xi - 1.0f;
+    T den = s + (d1 + d0 - 2.0f * s) * om;
+    F = y0 + h * (s * xi * xi + d0 * om) / den;
+    Fp = s * s * (d1 * xi * xi + 2.0f * s * om + d0 * (xm * xm)) / (den * den);
+}
+
+__device__ __forceinline__ float softplus(float a) { return a > 20.0f ? a : log1pf(__expf(a)); }
+__device__ __forceinline__ float sigmoid(float a) { return 1.0f / (1.0f + __expf(-a)); }
+
+// Raw MLP outputs of one transformed dim are read as raw[i * ld] (parameter-major layout: the
+// events of a warp read one parameter row, coalesced): widths 0..K-1, heights K..2K-1, knot
+// derivatives 2K..3K.
+__device__ __forceinline__ void softmax_norm(const float* raw, int64_t ld, int K, float& m, float& iz) {
+    m = -INFINITY;
+    for (int i = 0; i < K; ++i) m = fmaxf(m, raw[i * ld]);
+    float z = 0.0f;
+    for (int i = 0; i < K; ++i) z += __expf(raw[i * ld] - m);
+    iz = 1.0f / z;
+}
+
+// The bin holding v among the width knots (v = x) or the height knots (v = y, inverse), with
+// its parameters and the softmax quantities the backward pass needs.
+struct Bin {
+    int k;
+    float x0, w, y0, h, d0, d1;
+    float mw, iw, mh, ih;  // softmax maxima and inverse sums
+    float pw, ph;          // softmax probabilities of bin k
+    float sx, sy;          // sums of the softmax probabilities of the bins before k
+    float sg0, sg1;        // softplus' (= sigmoid) at the derivative pre-activations of k, k+1
+};
+
+__device__ __forceinline__ Bin locate(const float* raw, int64_t ld, int K, float v, bool by_height) {
+    Bin b;
+    softmax_norm(raw, ld, K, b.mw, b.iw);
+    softmax_norm(raw + K * ld, ld, K, b.mh, b.ih);
+    const float cw = 1.0f - K * kMinW, chh = 1.0f - K * kMinH;
+    float x0 = 0.0f, y0 = 0.0f, sx = 0.0f, sy = 0.0f;
+    int k = 0;
+    for (;; ++k) {
+        float pw = __expf(raw[k * ld] - b.mw) * b.iw;
+        float ph = __expf(raw[(K + k) * ld] - b.mh) * b.ih;
+        float w = kMinW + cw * pw, h = kMinH + chh * ph;
+        if (k == K - 1 || (by_height ? v < y0 + h : v < x0 + w)) {
+            b.w = w;
+            b.h = h;
+            b.pw = pw;
+            b.ph = ph;
+            break;
+        }
+        x0 += w;
+        y0 += h;
+        sx += pw;
+        sy += ph;
+    }
+    b.k = k;
+    b.x0 = x0;
+    b.y0 = y0;
+    b.sx = sx;
+    b.sy = sy;
+    float a0 = raw[(2 * K + k) * ld], a1 = raw[(2 * K + k + 1) * ld];
+    b.d0 = kMinD + softplus(a0);
+    b.d1 = kMinD + softplus(a1);
+    b.sg0 = sigmoid(a0);
+    b.sg1 = sigmoid(a1);
+    return b;
+}
+
+// ------------------------------------------------------------------------------------------
+struct LayerDesc {
+    int nb, na;             // transformed / conditioning dims
+    int tb[kMaxDims];       // transformed dim indices
+    int ta[kMaxDims];       // conditioning dim indices
+    int P, Ppad;            // raw params per event (nb (3K+1)) and padded row length
+    int64_t off_W1, off_b1, off_W2, off_b2, off_W3, off_b3;  // parameter offsets (floats)
+};
+
+struct FlowDesc {
+    int d, L, K, H;
+    LayerDesc layer[kMaxLayers];
+};
+
+// z from Philox: dims 2c, 2c+1 from counter (ev_lo, ev_hi, 0x466C6F77 ("Flow"), c), key (seed);
+// the top 23 bits k of a word give (k + 1/2) 2^-23 in (0, 1), exact in FP32.
+__global__ void k_init_z(int64_t B, int d, uint64_t seed, uint64_t ev0, float* X) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    uint64_t ev = ev0 + static_cast<uint64_t>(b);
+    for (int j = 0; j < d; j += 2) {
+        uint4 o = rng::philox4x32_10(make_uint4(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32), 0x466C6F77u,
+                                                static_cast<uint32_t>(j >> 1)),
+                                     static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+        X[b * d + j] = (static_cast<float>(o.x >> 9) + 0.5f) * 0x1p-23f;
+        if (j + 1 < d) X[b * d + j + 1] = (static_cast<float>(o.y >> 9) + 0.5f) * 0x1p-23f;
+    }
+}
+
+__global__ void k_gather(int64_t B, int d, const float* X, const __grid_constant__ LayerDesc ld, bf16* In) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    for (int i = 0; i < kInPad; ++i)
+        In[b * kInPad + i] = __float2bfloat16(i < ld.na ? X[b * d + ld.ta[i]] : 0.0f);
+}
+
+// forward spline of one layer: Xout = Xin with the B dims through F; logdet += sum log F'.
+// Praw is parameter-major: raw parameter p of event b at Praw[p * ldp + b].
+__global__ void k_spline_forward(int64_t B, int d, int K, const float* Xin, float* Xout, const float* Praw,
+                                 int64_t ldp, const __grid_constant__ LayerDesc ld, float* logdet) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    for (int j = 0; j < d; ++j) Xout[b * d + j] = Xin[b * d + j];
+    float acc = 0.0f;
+    for (int q = 0; q < ld.nb; ++q) {
+        const float* raw = Praw + static_cast<int64_t>(q) * (3 * K + 1) * ldp + b;
+        int j = ld.tb[q];
+        float x = fminf(fmaxf(Xin[b * d + j], 0.0f), 1.0f);
+        Bin bn = locate(raw, ldp, K, x, false);
+        float F, Fp;
+        bin_eval<float>(x, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
+        Xout[b * d + j] = fminf(fmaxf(F, 1e-7f), 1.0f - 1e-7f);
+        acc += logf(Fp);
+    }
+    logdet[b] += acc;
+}
+
+// inverse spline of one layer: Xout = Xin with the B dims through F^-1; logq -= sum log F'(x)
+__global__ void k_spline_inverse(int64_t B, int d, int K, const float* Xin, float* Xout, const float* Praw,
+                                 int64_t ldp, const __grid_constant__ LayerDesc ld, float* logq) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    for (int j = 0; j < d; ++j) Xout[b * d + j] = Xin[b * d + j];
+    float acc = 0.0f;
+    for (int q = 0; q < ld.nb; ++q) {
+        const float* raw = Praw + static_cast<int64_t>(q) * (3 * K + 1) * ldp + b;
+        int j = ld.tb[q];
+        float y = fminf(fmaxf(Xin[b * d + j], 0.0f), 1.0f);
+        Bin bn = locate(raw, ldp, K, y, true);
+        // y - y_k = h [s xi^2 + d0 xi (1-xi)] / [s + (d1 + d0 - 2s) xi (1-xi)] is a quadratic in xi;
+        // the root in [0,1] in the form free of cancellation: xi = 2c / (-b - sqrt(b^2 - 4ac))
+        float s = bn.h / bn.w, dy = y - bn.y0, e = bn.d1 + bn.d0 - 2.0f * s;
+        float qa = bn.h * (s - bn.d0) + dy * e, qb = bn.h * bn.d0 - dy * e, qc = -s * dy;
+        float disc = fmaxf(qb * qb - 4.0f * qa * qc, 0.0f);
+        float den = -qb - sqrtf(disc);
+        float xi = den != 0.0f ? fminf(fmaxf(2.0f * qc / den, 0.0f), 1.0f) : 0.0f;
+        float x = bn.x0 + xi * bn.w;
+        float F, Fp;
+        bin_eval<float>(x, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
+        Xout[b * d + j] = fminf(fmaxf(x, 0.0f), 1.0f);
+        acc += logf(Fp);
+    }
+    logq[b] -= acc;
+}
+
+// backward of one layer (see the header): inputs x^(l) (Xl), raw params, the adjoint gX of x^(l)
+// and the event coefficient c_b = w_b / sum w; outputs the raw-parameter adjoint G (fp32 and
+// bf16, parameter-major like Praw, padding rows zeroed) and the adjoint of x^(l+1) in gXn (the
+// conditioning dims get the MLP part later).
+__global__ void k_spline_backward(int64_t B, int d, int K, const float* Xl, const float* Praw, int64_t ldp,
+                                  const __grid_constant__ LayerDesc ld, const float* gX, const double* wtot,
+                                  const double* wsum, float* G, bf16* Gb, float* gXn, double* loss) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    float lsum = 0.0f;
+    if (b < B) {
+        const float c = wsum[0] > 0.0 ? static_cast<float>(wtot[b] / wsum[0]) : 0.0f;
+        for (int j = 0; j < d; ++j) gXn[b * d + j] = gX[b * d + j];  // A dims pass through
+        const float cw = 1.0f - K * kMinW, chh = 1.0f - K * kMinH;
+        for (int q = 0; q < ld.nb; ++q) {
+            const int64_t row0 = static_cast<int64_t>(q) * (3 * K + 1);
+            const float* raw = Praw + row0 * ldp + b;
+            int j = ld.tb[q];
+            float xv = fminf(fmaxf(Xl[b * d + j], 0.0f), 1.0f);
+            Bin bn = locate(raw, ldp, K, xv, false);
+            Dual F, Fp;
+            bin_eval<Dual>(dvar(xv, 0), dvar(bn.x0, 1), dvar(bn.w, 2), dvar(bn.y0, 3), dvar(bn.h, 4), dvar(bn.d0, 5),
+                           dvar(bn.d1, 6), F, Fp);
+            float ifp = 1.0f / Fp.v;
+            lsum += c * logf(Fp.v);
+            float ax = gX[b * d + j] + c * Fp.t[0] * ifp;  // adjoint of x^(l)_j incl. d(c log F')/dx
+            gXn[b * d + j] = ax * ifp;                       // d x^(l) / d x^(l+1) = 1/F'
+            // bin-parameter adjoints: -a_x F_theta / F' + c F'_theta / F'
+            float gt[7];
+#pragma unroll
+            for (int i = 1; i < 7; ++i) gt[i] = (-ax * F.t[i] + c * Fp.t[i]) * ifp;
+            // chain to the raw parameters: x_k = sum_{i<k} w_i and w_k through the width softmax,
+            // y_k and h_k through the height softmax, d_k and d_{k+1} through softplus
+            const float dotw = gt[1] * bn.sx + gt[2] * bn.pw;
+            const float doth = gt[3] * bn.sy + gt[4] * bn.ph;
+            float* g = G + row0 * ldp + b;
+            bf16* gb = Gb + row0 * ldp + b;
+            for (int i = 0; i < K; ++i) {
+                float pw = __expf(raw[i * ldp] - bn.mw) * bn.iw;
+                float ph = __expf(raw[(K + i) * ldp] - bn.mh) * bn.ih;
+                float aw = i < bn.k ? gt[1] : (i == bn.k ? gt[2] : 0.0f);
+                float ah = i < bn.k ? gt[3] : (i == bn.k ? gt[4] : 0.0f);
+                float vw = cw * pw * (aw - dotw), vh = chh * ph * (ah - doth);
+                g[i * ldp] = vw;
+                gb[i * ldp] = __float2bfloat16(vw);
+                g[(K + i) * ldp] = vh;
+                gb[(K + i) * ldp] = __float2bfloat16(vh);
+            }
+            for (int i = 0; i <= K; ++i) {
+                float v = i == bn.k ? gt[5] * bn.sg0 : (i == bn.k + 1 ? gt[6] * bn.sg1 : 0.0f);
+                g[(2 * K + i) * ldp] = v;
+                gb[(2 * K + i) * ldp] = __float2bfloat16(v);
+            }
+        }
+        for (int p = ld.P; p < ld.Ppad; ++p) {
+            G[p * ldp + b] = 0.0f;
+            Gb[p * ldp + b] = __float2bfloat16(0.0f);
+        }
+    }
+    // loss = sum_b c_b sum log F'  (one atomic per warp)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, static_cast<double>(lsum));
+}
+
+// row sums of an [n][ldm] fp32 matrix over its first B columns into out[n] (atomic; bias
+// gradients of the last layer)
+__global__ void k_rowsum(int64_t B, int64_t ldm, const float* M, float* out) {
+    const int row = blockIdx.y;
+    float s = 0.0f;
+    for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < B;
+         c += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        s += M[row * ldm + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out + row, s);
+}
+
+// column sums of a [B, n] fp32 matrix into out[n] (atomic; bias gradients)
+__global__ void k_colsum(int64_t B, int n, const float* M, float* out) {
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= n) return;
+    int64_t rows = (B + gridDim.y - 1) / gridDim.y;
+    int64_t r0 = blockIdx.y * rows, r1 = min(B, r0 + rows);
+    float s = 0.0f;
+    for (int64_t r = r0; r < r1; ++r) s += M[r * n + col];
+    atomicAdd(out + col, s);
+}
+
+// dZ = dA * SiLU'(Z) (fp32 -> bf16)
+__global__ void k_silu_backward(int64_t count, const float* dA, const float* Z, float* dZ, bf16* dZb) {
+    int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= count) return;
+    float z = Z[i];
+    float s = 1.0f / (1.0f + __expf(-z));
+    float v = dA[i] * s * (1.0f + z * (1.0f - s));
+    dZ[i] = v;
+    dZb[i] = __float2bfloat16(v);
+}
+
+__global__ void k_scatter(int64_t B, int d, const __grid_constant__ LayerDesc ld, const float* dIn, float* gXn) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    for (int i = 0; i < ld.na; ++i) gXn[b * d + ld.ta[i]] += dIn[b * kInPad + i];
+}
+
+// w_b = w_map_b exp(logdet_b) (the flow density is 1/|dr/dz|); block sums into wsum
+__global__ void k_weights(int64_t B, const double* wmap, const float* logdet, double* wtot, double* wsum) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    double w = 0.0;
+    if (b < B) {
+        w = wmap[b] * exp(static_cast<double>(logdet[b]));
+        if (!isfinite(w)) w = 0.0;
+        wtot[b] = w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(wsum, w);
+}
+
+// X[L] <- r (SoA double -> event-major float)
+__global__ void k_load_r(int64_t B, int d, int64_t col0, int64_t ldr, const double* r, float* X) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    for (int j = 0; j < d; ++j) X[b * d + j] = static_cast<float>(r[j * ldr + col0 + b]);
+}
+
+// r (and optionally z) in the SoA layout of the phase-space map's explicit-input mode
+__global__ void k_store_r(int64_t B, int d, int64_t col0, int64_t ldr, const float* X, const float* X0,
+                          const float* logdet, double* r, double* ld_out, double* z) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    for (int j = 0; j < d; ++j) r[j * ldr + col0 + b] = static_cast<double>(X[b * d + j]);
+    if (z)
+        for (int j = 0; j < d; ++j) z[j * ldr + col0 + b] = static_cast<double>(X0[b * d + j]);
+    if (ld_out) ld_out[col0 + b] = static_cast<double>(logdet[b]);
+}
+
+__global__ void k_combine(int64_t B, const double* wmap, const double* logdet, double* w) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    double v = wmap[b] * exp(logdet[b]);
+    w[b] = isfinite(v) ? v : 0.0;
+}
+
+// Adam on the FP32 master parameters, then the bf16 copy
+__global__ void k_adam(int64_t n, float* p, const float* g, float* m, float* v, bf16* pb, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    float gi = g[i];
+    if (!isfinite(gi)) gi = 0.0f;
+    float mi = b1 * m[i] + (1.0f - b1) * gi;
+    float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pb[i] = __float2bfloat16(pi);
+}
+
+__global__ void k_to_bf16(int64_t n, const float* p, bf16* pb) {
+    int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < n) pb[i] = __float2bfloat16(p[i]);
+}
+
+}  // namespace flow
+}  // namespace ps
+
+// ===========================================================================================
+// host side
+using namespace ps::flow;
+
+namespace {
+thread_local std::string f_err;
+int ffail(int code, const std::string& m) {
+    f_err = m;
+    return code;
+}
+int fcheck(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return PS_OK;
+    return ffail(PS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+struct Guard {
+    int prev = -1;
+    explicit Guard(int d) {
+        if (cudaGetDevice(&prev) == cudaSuccess) cudaSetDevice(d);
+    }
+    ~Guard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+inline unsigned blocks(int64_t n, int t) { return static_cast<unsigned>((n + t - 1) / t); }
+}  // namespace
+
+struct ps_flow_s {
+    FlowDesc fd;
+    int device = 0;
+    int64_t max_batch = 0;
+    int64_t n_params = 0;
+    // parameters and optimiser state (device)
+    float* p = nullptr;
+    float* grad = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    bf16* pb = nullptr;
+    int64_t step = 0;
+    // activations of the last sampled batch
+    int64_t batch = 0;
+    float* X = nullptr;      // [L+1][max_batch][d]
+    bf16* In = nullptr;      // [L][max_batch][16]
+    float* Z1 = nullptr;     // [L][max_batch][H]
+    float* Z2 = nullptr;
+    bf16* A1 = nullptr;
+    bf16* A2 = nullptr;
+    float* Praw = nullptr;   // [L][Pmax][max_batch] (parameter-major)
+    float* logdet = nullptr; // [max_batch]
+    // backward scratch
+    float* G = nullptr;      // [Pmax][max_batch]
+    bf16* Gb = nullptr;
+    float* dA = nullptr;     // [max_batch][H]
+    float* dZ = nullptr;
+    bf16* dZb = nullptr;
+    float* dIn = nullptr;    // [max_batch][16]
+    float* gX = nullptr;     // [max_batch][d]
+    float* gXn = nullptr;
+    double* wtot = nullptr;  // [max_batch]
+    double* scal = nullptr;  // [0] sum w, [1] loss
+    int Pmax = 0;
+};
+
+namespace {
+
+void free_flow(ps_flow f) {
+    for (void* q : {static_cast<void*>(f->p), static_cast<void*>(f->grad), static_cast<void*>(f->m),
+                    static_cast<void*>(f->v), static_cast<void*>(f->pb), static_cast<void*>(f->X),
+                    static_cast<void*>(f->In), static_cast<void*>(f->Z1), static_cast<void*>(f->Z2),
+                    static_cast<void*>(f->A1), static_cast<void*>(f->A2), static_cast<void*>(f->Praw),
+                    static_cast<void*>(f->logdet), static_cast<void*>(f->G), static_cast<void*>(f->Gb),
+                    static_cast<void*>(f->dA), static_cast<void*>(f->dZ), static_cast<void*>(f->dZb),
+                    static_cast<void*>(f->dIn), static_cast<void*>(f->gX), static_cast<void*>(f->gXn),
+                    static_cast<void*>(f->wtot), static_cast<void*>(f->scal)})
+        cudaFree(q);
+}
+
+uint64_t splitmix(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// launch one GEMM; kchunk = K unless split
+int gemm(const GemmArgs& a0, int splits, cudaStream_t st) {
+    GemmArgs a = a0;
+    splits = std::max(1, splits);
+    a.kchunk = ((a.K + splits - 1) / splits + 31) / 32 * 32;
+    int nz = (a.K + a.kchunk - 1) / a.kchunk;
+    dim3 grid((a.M + 63) / 64, (a.N + 63) / 64, nz);
+    k_gemm<<<grid, 128, 0, st>>>(a);
+    ps::count_launches(1);
+    return fcheck(cudaGetLastError(), "k_gemm");
+}
+
+// MLP of layer l on the conditioning dims of Xl (activations kept for the backward pass)
+int mlp(ps_flow f, int l, int64_t B, const float* Xl, cudaStream_t st) {
+    const FlowDesc& fd = f->fd;
+    const int d = fd.d, H = fd.H, T = 256;
+    {
+        const LayerDesc& ld = fd.layer[l];
+        bf16* In = f->In + static_cast<int64_t>(l) * f->max_batch * kInPad;
+        float* Z1 = f->Z1 + static_cast<int64_t>(l) * f->max_batch * H;
+        float* Z2 = f->Z2 + static_cast<int64_t>(l) * f->max_batch * H;
+        bf16* A1 = f->A1 + static_cast<int64_t>(l) * f->max_batch * H;
+        bf16* A2 = f->A2 + static_cast<int64_t>(l) * f->max_batch * H;
+        float* P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
+        k_gather<<<blocks(B, T), T, 0, st>>>(B, d, Xl, ld, In);
+        int s;
+        GemmArgs g{};
+        g.A = In; g.lam = kInPad; g.lak = 1; g.B = f->pb + ld.off_W1; g.lbn = kInPad; g.lbk = 1;
+        g.M = static_cast<int>(B); g.N = H; g.K = kInPad; g.bias = f->p + ld.off_b1; g.C = Z1; g.ldc = H; g.Cb = A1;
+        g.ldcb = H; g.act = 1;
+        s = gemm(g, 1, st);
+        if (s != PS_OK) return s;
+        g = GemmArgs{};
+        g.A = A1; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W2; g.lbn = H; g.lbk = 1;
+        g.M = static_cast<int>(B); g.N = H; g.K = H; g.bias = f->p + ld.off_b2; g.C = Z2; g.ldc = H; g.Cb = A2;
+        g.ldcb = H; g.act = 1;
+        s = gemm(g, 1, st);
+        if (s != PS_OK) return s;
+        g = GemmArgs{};
+        g.A = A2; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W3; g.lbn = H; g.lbk = 1;
+        g.M = static_cast<int>(B); g.N = ld.Ppad; g.K = H; g.bias = f->p + ld.off_b3; g.C = P; g.ldc = f->max_batch;
+        g.trans_c = 1;
+        s = gemm(g, 1, st);
+        if (s != PS_OK) return s;
+    }
+    ps::count_launches(1);
+    return PS_OK;
+}
+
+// forward of all layers for a chunk of `B` events starting at event ev0; stores activations
+int forward(ps_flow f, int64_t B, uint64_t seed, uint64_t ev0, cudaStream_t st) {
+    const FlowDesc& fd = f->fd;
+    const int d = fd.d, T = 256;
+    k_init_z<<<blocks(B, T), T, 0, st>>>(B, d, seed, ev0, f->X);
+    cudaMemsetAsync(f->logdet, 0, B * sizeof(float), st);
+    for (int l = 0; l < fd.L; ++l) {
+        const LayerDesc& ld = fd.layer[l];
+        float* Xl = f->X + static_cast<int64_t>(l) * f->max_batch * d;
+        float* Xn = Xl + f->max_batch * d;
+        int s = mlp(f, l, B, Xl, st);
+        if (s != PS_OK) return s;
+        const float* P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
+        k_spline_forward<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xl, Xn, P, f->max_batch, ld, f->logdet);
+    }
+    ps::count_launches(1 + fd.L);
+    return fcheck(cudaGetLastError(), "flow forward");
+}
+
+// inverse of all layers for a chunk: X[L] (already loaded) -> X[0]; f->logdet receives log g
+int inverse(ps_flow f, int64_t B, cudaStream_t st) {
+    const FlowDesc& fd = f->fd;
+    const int d = fd.d, T = 256;
+    cudaMemsetAsync(f->logdet, 0, B * sizeof(float), st);
+    for (int l = fd.L - 1; l >= 0; --l) {
+        const LayerDesc& ld = fd.layer[l];
+        float* Xl = f->X + static_cast<int64_t>(l) * f->max_batch * d;
+        float* Xn = Xl + f->max_batch * d;
+        // the conditioning dims of x^(l+1) equal those of x^(l)
+        int s = mlp(f, l, B, Xn, st);
+        if (s != PS_OK) return s;
+        const float* P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
+        k_spline_inverse<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xn, Xl, P, f->max_batch, ld, f->logdet);
+    }
+    ps::count_launches(fd.L);
+    return fcheck(cudaGetLastError(), "flow inverse");
+}
+
+// backward sweep (layers 0 .. L-1) of the importance-weighted forward KL; accumulates f->grad
+int backward(ps_flow f, int64_t B, cudaStream_t st) {
+    const FlowDesc& fd = f->fd;
+    const int d = fd.d, H = fd.H, T = 256;
+    cudaMemsetAsync(f->gX, 0, B * d * sizeof(float), st);
+    cudaMemsetAsync(f->grad, 0, f->n_params * sizeof(float), st);
+    int launches = 0;
+    const int split = std::max(1, static_cast<int>(std::min<int64_t>(64, B / 2048)));
+    for (int l = 0; l < fd.L; ++l) {
+        const LayerDesc& ld = fd.layer[l];
+        float* Xl = f->X + static_cast<int64_t>(l) * f->max_batch * d;
+        bf16* In = f->In + static_cast<int64_t>(l) * f->max_batch * kInPad;
+        float* Z1 = f->Z1 + static_cast<int64_t>(l) * f->max_batch * H;
+        float* Z2 = f->Z2 + static_cast<int64_t>(l) * f->max_batch * H;
+        bf16* A1 = f->A1 + static_cast<int64_t>(l) * f->max_batch * H;
+        bf16* A2 = f->A2 + static_cast<int64_t>(l) * f->max_batch * H;
+        float* P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
+        const int64_t ldg = f->max_batch;  // G, Gb and Praw are parameter-major
+        k_spline_backward<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xl, P, ldg, ld, f->gX, f->wtot, f->scal, f->G,
+                                                        f->Gb, f->gXn, f->scal + 1);
+        // last linear layer: dW3 += G^T A2, db3 += colsum G, dA2 = G W3
+        GemmArgs g{};
+        g.A = f->Gb; g.lam = ldg; g.lak = 1; g.B = A2; g.lbn = 1; g.lbk = H;
+        g.M = ld.Ppad; g.N = H; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W3; g.ldc = H; g.atomic = 1;
+        int s = gemm(g, split, st);
+        if (s != PS_OK) return s;
+        k_rowsum<<<dim3(std::min<unsigned>(blocks(B, 256), 64), ld.Ppad), 256, 0, st>>>(B, ldg, f->G,
+                                                                                          f->grad + ld.off_b3);
+        g = GemmArgs{};
+        g.A = f->Gb; g.lam = 1; g.lak = ldg; g.B = f->pb + ld.off_W3; g.lbn = 1; g.lbk = H;
+        g.M = static_cast<int>(B); g.N = H; g.K = ld.Ppad; g.C = f->dA; g.ldc = H;
+        s = gemm(g, 1, st);
+        if (s != PS_OK) return s;
+        k_silu_backward<<<blocks(B * H, T), T, 0, st>>>(B * H, f->dA, Z2, f->dZ, f->dZb);
+        // middle layer
+        g = GemmArgs{};
+        g.A = f->dZb; g.lam = 1; g.lak = H; g.B = A1; g.lbn = 1; g.lbk = H;
+        g.M = H; g.N = H; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W2; g.ldc = H; g.atomic = 1;
+        s = gemm(g, split, st);
+        if (s != PS_OK) return s;
+        k_colsum<<<dim3(blocks(H, 64), 64), 64, 0, st>>>(B, H, f->dZ, f->grad + ld.off_b2);
+        g = GemmArgs{};
+        g.A = f->dZb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W2; g.lbn = 1; g.lbk = H;
+        g.M = static_cast<int>(B); g.N = H; g.K = H; g.C = f->dA; g.ldc = H;
+        s = gemm(g, 1, st);
+        if (s != PS_OK) return s;
+        k_silu_backward<<<blocks(B * H, T), T, 0, st>>>(B * H, f->dA, Z1, f->dZ, f->dZb);
+        // first layer
+        g = GemmArgs{};
+        g.A = f->dZb; g.lam = 1; g.lak = H; g.B = In; g.lbn = 1; g.lbk = kInPad;
+        g.M = H; g.N = kInPad; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W1; g.ldc = kInPad; g.atomic = 1;
+        s = gemm(g, split, st);
+        if (s != PS_OK) return s;
+        k_colsum<<<dim3(blocks(H, 64), 64), 64, 0, st>>>(B, H, f->dZ, f->grad + ld.off_b1);
+        g = GemmArgs{};
+        g.A = f->dZb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W1; g.lbn = 1; g.lbk = kInPad;
+        g.M = static_cast<int>(B); g.N = kInPad; g.K = H; g.C = f->dIn; g.ldc = kInPad;
+        s = gemm(g, 1, st);
+        if (s != PS_OK) return s;
+        k_scatter<<<blocks(B, T), T, 0, st>>>(B, d, ld, f->dIn, f->gXn);
+        std::swap(f->gX, f->gXn);
+        launches += 7;
+    }
+    ps::count_launches(launches);
+    return fcheck(cudaGetLastError(), "flow backward");
+}
+
+// padded device layout <-> logical layout (per layer W1[H][na], b1[H], W2[H][H], b2[H], W3[P][H], b3[P])
+int64_t logical_size(const FlowDesc& fd) {
+    int64_t n = 0;
+    for (int l = 0; l < fd.L; ++l) {
+        const LayerDesc& ld = fd.layer[l];
+        n += static_cast<int64_t>(fd.H) * ld.na + fd.H + static_cast<int64_t>(fd.H) * fd.H + fd.H +
+             static_cast<int64_t>(ld.P) * fd.H + ld.P;
+    }
+    return n;
+}
+
+void to_logical(const FlowDesc& fd, const std::vector<float>& dev, float* out) {
+    int64_t o = 0;
+    for (int l = 0; l < fd.L; ++l) {
+        const LayerDesc& ld = fd.layer[l];
+        const int H = fd.H;
+        for (int h = 0; h < H; ++h)
+            for (int i = 0; i < ld.na; ++i) out[o++] = dev[ld.off_W1 + h * kInPad + i];
+        for (int h = 0; h < H; ++h) out[o++] = dev[ld.off_b1 + h];
+        for (int h = 0; h < H * H; ++h) out[o++] = dev[ld.off_W2 + h];
+        for (int h = 0; h < H; ++h) out[o++] = dev[ld.off_b2 + h];
+        for (int p = 0; p < ld.P; ++p)
+            for (int h = 0; h < H; ++h) out[o++] = dev[ld.off_W3 + static_cast<int64_t>(p) * H + h];
+        for (int p = 0; p < ld.P; ++p) out[o++] = dev[ld.off_b3 + p];
+    }
+}
+
+void from_logical(const FlowDesc& fd, const float* in, std::vector<float>& dev) {
+    int64_t o = 0;
+    std::fill(dev.begin(), dev.end(), 0.0f);
+    for (int l = 0; l < fd.L; ++l) {
+        const LayerDesc& ld = fd.layer[l];
+        const int H = fd.H;
+        for (int h = 0; h < H; ++h)
+            for (int i = 0; i < ld.na; ++i) dev[ld.off_W1 + h * kInPad + i] = in[o++];
+        for (int h = 0; h < H; ++h) dev[ld.off_b1 + h] = in[o++];
+        for (int h = 0; h < H * H; ++h) dev[ld.off_W2 + h] = in[o++];
+        for (int h = 0; h < H; ++h) dev[ld.off_b2 + h] = in[o++];
+        for (int p = 0; p < ld.P; ++p)
+            for (int h = 0; h < H; ++h) dev[ld.off_W3 + static_cast<int64_t>(p) * H + h] = in[o++];
+        for (int p = 0; p < ld.P; ++p) dev[ld.off_b3 + p] = in[o++];
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ps_flow_last_error(void) { return f_err.c_str(); }
+
+int ps_flow_create(int dims, int n_layers, int bins, int hidden, int64_t max_batch, uint64_t init_seed, int device,
+                   ps_flow* out) {
+    if (!out || dims < 2 || dims > kMaxDims || n_layers < 1 || n_layers > kMaxLayers || bins < 1 ||
+        bins > kMaxBins || hidden < 16 || hidden % 16 != 0 || hidden > 512 || max_batch < 1 || max_batch > (1 << 24))
+        return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_create: bad arguments");
+    ps_flow f = new (std::nothrow) ps_flow_s;
+    if (!f) return ffail(PS_ERR_CAPACITY, "out of host memory");
+    FlowDesc& fd = f->fd;
+    fd.d = dims;
+    fd.L = n_layers;
+    fd.K = bins;
+    fd.H = hidden;
+    int nbits = 1;
+    while ((1 << nbits) < dims) ++nbits;
+    int64_t off = 0;
+    for (int l = 0; l < n_layers; ++l) {
+        LayerDesc& ld = fd.layer[l];
+        int b = l % nbits, flip = (l / nbits) % 2;
+        ld.nb = ld.na = 0;
+        for (int j = 0; j < dims; ++j) {
+            if (((j >> b) & 1) != flip) ld.tb[ld.nb++] = j;
+            else ld.ta[ld.na++] = j;
+        }
+        if (ld.nb == 0 || ld.na == 0 || ld.na > kInPad) { delete f; return ffail(PS_ERR_INVALID_ARGUMENT, "bad mask"); }
+        ld.P = ld.nb * (3 * bins + 1);
+        ld.Ppad = (ld.P + 15) / 16 * 16;
+        f->Pmax = std::max(f->Pmax, ld.Ppad);
+        ld.off_W1 = off; off += static_cast<int64_t>(hidden) * kInPad;
+        ld.off_b1 = off; off += hidden;
+        ld.off_W2 = off; off += static_cast<int64_t>(hidden) * hidden;
+        ld.off_b2 = off; off += hidden;
+        ld.off_W3 = off; off += static_cast<int64_t>(ld.Ppad) * hidden;
+        ld.off_b3 = off; off += ld.Ppad;
+        off = (off + 7) / 8 * 8;
+    }
+    f->n_params = off;
+    f->device = device;
+    f->max_batch = max_batch;
+    // initial parameters: hidden layers uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases;
+    // last layer zero with biases giving unit knot derivatives (the identity spline)
+    std::vector<float> h(off, 0.0f);
+    uint64_t s = init_seed;
+    auto unif = [&](float a) { return a * (2.0f * static_cast<float>((splitmix(s) >> 11) * 0x1p-53) - 1.0f); };
+    const float d_id = std::log(std::expm1(1.0 - kMinD));
+    for (int l = 0; l < n_layers; ++l) {
+        const LayerDesc& ld = fd.layer[l];
+        for (int r = 0; r < hidden; ++r)
+            for (int i = 0; i < ld.na; ++i) h[ld.off_W1 + r * kInPad + i] = unif(1.0f / std::sqrt(static_cast<float>(ld.na)));
+        for (int r = 0; r < hidden * hidden; ++r) h[ld.off_W2 + r] = unif(1.0f / std::sqrt(static_cast<float>(hidden)));
+        for (int q = 0; q < ld.nb; ++q)
+            for (int k = 0; k <= bins; ++k) h[ld.off_b3 + q * (3 * bins + 1) + 2 * bins + k] = d_id;
+    }
+    Guard g(device);
+    int st = PS_OK;
+    auto alloc = [&](void** q, size_t bytes) {
+        if (st == PS_OK) st = fcheck(cudaMalloc(q, std::max<size_t>(bytes, 256)), "cudaMalloc (flow)");
+    };
+    const int64_t B = max_batch, H = hidden, L = n_layers;
+    alloc(reinterpret_cast<void**>(&f->p), off * 4);
+    alloc(reinterpret_cast<void**>(&f->grad), off * 4);
+    alloc(reinterpret_cast<void**>(&f->m), off * 4);
+    alloc(reinterpret_cast<void**>(&f->v), off * 4);
+    alloc(reinterpret_cast<void**>(&f->pb), off * 2);
+    alloc(reinterpret_cast<void**>(&f->X), (L + 1) * B * dims * 4);
+    alloc(reinterpret_cast<void**>(&f->In), L * B * kInPad * 2);
+    alloc(reinterpret_cast<void**>(&f->Z1), L * B * H * 4);
+    alloc(reinterpret_cast<void**>(&f->Z2), L * B * H * 4);
+    alloc(reinterpret_cast<void**>(&f->A1), L * B * H * 2);
+    alloc(reinterpret_cast<void**>(&f->A2), L * B * H * 2);
+    alloc(reinterpret_cast<void**>(&f->Praw), L * B * f->Pmax * 4);
+    alloc(reinterpret_cast<void**>(&f->logdet), B * 4);
+    alloc(reinterpret_cast<void**>(&f->G), B * f->Pmax * 4);
+    alloc(reinterpret_cast<void**>(&f->Gb), B * f->Pmax * 2);
+    alloc(reinterpret_cast<void**>(&f->dA), B * H * 4);
+    alloc(reinterpret_cast<void**>(&f->dZ), B * H * 4);
+    alloc(reinterpret_cast<void**>(&f->dZb), B * H * 2);
+    alloc(reinterpret_cast<void**>(&f->dIn), B * kInPad * 4);
+    alloc(reinterpret_cast<void**>(&f->gX), B * dims * 4);
+    alloc(reinterpret_cast<void**>(&f->gXn), B * dims * 4);
+    alloc(reinterpret_cast<void**>(&f->wtot), B * 8);
+    alloc(reinterpret_cast<void**>(&f->scal), 2 * 8);
+    if (st == PS_OK) st = fcheck(cudaMemcpy(f->p, h.data(), off * 4, cudaMemcpyHostToDevice), "upload flow params");
+    if (st == PS_OK) st = fcheck(cudaMemset(f->m, 0, off * 4), "memset");
+    if (st == PS_OK) st = fcheck(cudaMemset(f->v, 0, off * 4), "memset");
+    if (st == PS_OK) {
+        k_to_bf16<<<blocks(off, 256), 256>>>(off, f->p, f->pb);
+        st = fcheck(cudaDeviceSynchronize(), "flow init");
+    }
+    if (st != PS_OK) { free_flow(f); delete f; return st; }
+    *out = f;
+    return PS_OK;
+}
+
+int ps_flow_free(ps_flow f) {
+    if (!f) return PS_OK;
+    {
+        Guard g(f->device);
+        free_flow(f);
+    }
+    delete f;
+    return PS_OK;
+}
+
+int ps_flow_info(ps_flow f, int* dims, int* n_layers, int* bins, int* hidden, int64_t* n_params) {
+    if (!f) return ffail(PS_ERR_INVALID_ARGUMENT, "null flow");
+    if (dims) *dims = f->fd.d;
+    if (n_layers) *n_layers = f->fd.L;
+    if (bins) *bins = f->fd.K;
+    if (hidden) *hidden = f->fd.H;
+    if (n_params) *n_params = logical_size(f->fd);
+    return PS_OK;
+}
+
+int ps_flow_mask(ps_flow f, int layer, int* transformed, int* n_transformed) {
+    if (!f || layer < 0 || layer >= f->fd.L || !transformed || !n_transformed)
+        return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_mask: bad arguments");
+    const LayerDesc& ld = f->fd.layer[layer];
+    for (int i = 0; i < ld.nb; ++i) transformed[i] = ld.tb[i];
+    *n_transformed = ld.nb;
+    return PS_OK;
+}
+
+int ps_flow_get_params(ps_flow f, float* host, int64_t n) {
+    if (!f || !host || n != logical_size(f->fd)) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_get_params: bad size");
+    Guard g(f->device);
+    std::vector<float> dev(f->n_params);
+    int st = fcheck(cudaMemcpy(dev.data(), f->p, f->n_params * 4, cudaMemcpyDeviceToHost), "download params");
+    if (st != PS_OK) return st;
+    to_logical(f->fd, dev, host);
+    return PS_OK;
+}
+
+int ps_flow_set_params(ps_flow f, const float* host, int64_t n) {
+    if (!f || !host || n != logical_size(f->fd)) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_set_params: bad size");
+    Guard g(f->device);
+    std::vector<float> dev(f->n_params);
+    from_logical(f->fd, host, dev);
+    int st = fcheck(cudaMemcpy(f->p, dev.data(), f->n_params * 4, cudaMemcpyHostToDevice), "upload params");
+    if (st != PS_OK) return st;
+    k_to_bf16<<<blocks(f->n_params, 256), 256>>>(f->n_params, f->p, f->pb);
+    return fcheck(cudaDeviceSynchronize(), "set params");
+}
+
+int ps_flow_sample(ps_flow f, int64_t batch, uint64_t seed, uint64_t event_offset, double* r, int64_t ld_r,
+                   double* logdet, double* z, void* stream) {
+    if (!f || batch < 0 || (batch > 0 && !r) || ld_r < batch) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_sample: bad arguments");
+    Guard g(f->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int64_t c0 = 0; c0 < batch; c0 += f->max_batch) {
+        int64_t B = std::min(f->max_batch, batch - c0);
+        int s = forward(f, B, seed, event_offset + static_cast<uint64_t>(c0), st);
+        if (s != PS_OK) return s;
+        const float* XL = f->X + static_cast<int64_t>(f->fd.L) * f->max_batch * f->fd.d;
+        k_store_r<<<blocks(B, 256), 256, 0, st>>>(B, f->fd.d, c0, ld_r, XL, f->X, f->logdet, r, logdet, z);
+        ps::count_launches(1);
+        f->batch = B;
+    }
+    if (batch > f->max_batch) f->batch = 0;  // intermediates of the last chunk only: no training step
+    return fcheck(cudaGetLastError(), "ps_flow_sample");
+}
+
+int ps_flow_inverse(ps_flow f, int64_t batch, const double* r, int64_t ld_r, double* z, double* logq,
+                    void* stream) {
+    if (!f || batch < 0 || (batch > 0 && (!r || !z)) || ld_r < batch)
+        return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_inverse: bad arguments");
+    Guard g(f->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int d = f->fd.d;
+    float* XL = f->X + static_cast<int64_t>(f->fd.L) * f->max_batch * d;
+    for (int64_t c0 = 0; c0 < batch; c0 += f->max_batch) {
+        int64_t B = std::min(f->max_batch, batch - c0);
+        k_load_r<<<blocks(B, 256), 256, 0, st>>>(B, d, c0, ld_r, r, XL);
+        int s = inverse(f, B, st);
+        if (s != PS_OK) return s;
+        // z = X[0]; logq from f->logdet
+        k_store_r<<<blocks(B, 256), 256, 0, st>>>(B, d, c0, ld_r, f->X, f->X, f->logdet, z, logq, nullptr);
+        ps::count_launches(2);
+    }
+    f->batch = 0;  // the stored activations are no longer those of a sampled batch
+    return fcheck(cudaGetLastError(), "ps_flow_inverse");
+}
+
+int ps_flow_weights(ps_flow f, int64_t batch, const double* w_map, const double* logdet, double* w, void* stream) {
+    if (!f || (batch > 0 && (!w_map || !logdet || !w))) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_weights: bad arguments");
+    Guard g(f->device);
+    if (batch > 0) {
+        k_combine<<<blocks(batch, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, w_map, logdet, w);
+        ps::count_launches(1);
+    }
+    return fcheck(cudaGetLastError(), "ps_flow_weights");
+}
+
+static int prepare_grads(ps_flow f, const double* w_map, cudaStream_t st) {
+    if (f->batch <= 0) return ffail(PS_ERR_INVALID_ARGUMENT, "no sampled batch to train on (sample <= max_batch first)");
+    const int64_t B = f->batch;
+    cudaMemsetAsync(f->scal, 0, 2 * sizeof(double), st);
+    k_weights<<<blocks(B, 256), 256, 0, st>>>(B, w_map, f->logdet, f->wtot, f->scal);
+    ps::count_launches(1);
+    return backward(f, B, st);
+}
+
+int ps_flow_gradients(ps_flow f, const double* w_map, float* host, int64_t n, double* loss, void* stream) {
+    if (!f || !w_map || !host || n != logical_size(f->fd)) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_gradients: bad arguments");
+    Guard g(f->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int s = prepare_grads(f, w_map, st);
+    if (s != PS_OK) return s;
+    std::vector<float> dev(f->n_params);
+    double sc[2];
+    s = fcheck(cudaMemcpyAsync(dev.data(), f->grad, f->n_params * 4, cudaMemcpyDeviceToHost, st), "download grads");
+    if (s == PS_OK) s = fcheck(cudaMemcpyAsync(sc, f->scal, sizeof sc, cudaMemcpyDeviceToHost, st), "download loss");
+    if (s == PS_OK) s = fcheck(cudaStreamSynchronize(st), "sync");
+    if (s != PS_OK) return s;
+    to_logical(f->fd, dev, host);
+    if (loss) *loss = sc[1];
+    return PS_OK;
+}
+
+int ps_flow_train_step(ps_flow f, const double* w_map, double lr, void* stream) {
+    if (!f || !w_map || !(lr > 0.0)) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_train_step: bad arguments");
+    Guard g(f->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int s = prepare_grads(f, w_map, st);
+    if (s != PS_OK) return s;
+    f->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    float c1 = 1.0f - std::pow(b1, static_cast<float>(f->step)), c2 = 1.0f - std::pow(b2, static_cast<float>(f->step));
+    k_adam<<<blocks(f->n_params, 256), 256, 0, st>>>(f->n_params, f->p, f->grad, f->m, f->v, f->pb,
+                                                     static_cast<float>(lr), b1, b2, 1e-8f, c1, c2);
+    ps::count_launches(1);
+    return fcheck(cudaGetLastError(), "ps_flow_train_step");
+}
+
+int ps_flow_loss(ps_flow f, double* loss, double* sum_w, void* stream) {
+    if (!f || !loss) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_loss: bad arguments");
+    Guard g(f->device);
+    double sc[2];
+    int s = fcheck(cudaMemcpyAsync(sc, f->scal, sizeof sc, cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream)), "loss");
+    if (s == PS_OK) s = fcheck(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "sync");
+    if (s != PS_OK) return s;
+    *loss = sc[1];
+    if (sum_w) *sum_w = sc[0];
+    return PS_OK;
+}
+
+}  // extern "C"

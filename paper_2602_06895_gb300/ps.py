@@ -107,6 +107,24 @@ _SIGS = {
     "ps_status_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ps_program_free": (C.c_int, [C.c_void_p]),
     "ps_launch_count": (C.c_int64, []),
+    "ps_flow_last_error": (C.c_char_p, []),
+    "ps_flow_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_uint64, C.c_int,
+                                 C.POINTER(C.c_void_p)]),
+    "ps_flow_free": (C.c_int, [C.c_void_p]),
+    "ps_flow_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "ps_flow_mask": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ps_flow_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
+    "ps_flow_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
+    "ps_flow_sample": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]),
+    "ps_flow_inverse": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "ps_flow_weights": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ps_flow_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    "ps_flow_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.c_int64,
+                                    C.POINTER(C.c_double), C.c_void_p]),
+    "ps_flow_loss": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
 }
 
 
@@ -464,3 +482,106 @@ def program_for(channels, block_threads=128, ctas_per_sm=0, device=0, precision=
     graphs = [build_channel(channels, c) for c in range(len(channels))]
     return Program(graphs, block_threads=block_threads, ctas_per_sm=ctas_per_sm, device=device,
                    precision=precision)
+
+
+# ------------------------------------------------------------------ coupling flow (ps_flow_*)
+def _fcheck(status, what=""):
+    if status != PS_OK:
+        msg = lib().ps_flow_last_error().decode(errors="replace")
+        raise PSError(f"{what} failed ({status}): {msg}")
+
+
+class Flow:
+    """Rational-quadratic-spline coupling flow on one device (ps_flow): the learned proposal
+    that feeds r into :meth:`Program.map`."""
+
+    def __init__(self, dims, n_layers=6, bins=16, hidden=128, max_batch=1 << 16, init_seed=1, device=0):
+        h = C.c_void_p()
+        _fcheck(lib().ps_flow_create(dims, n_layers, bins, hidden, max_batch, init_seed, device, C.byref(h)),
+                "ps_flow_create")
+        self.h, self.device, self.max_batch = h, device, max_batch
+        d, L, K, H, n = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int64()
+        _fcheck(lib().ps_flow_info(h, C.byref(d), C.byref(L), C.byref(K), C.byref(H), C.byref(n)), "ps_flow_info")
+        self.dims, self.n_layers, self.bins, self.hidden, self.n_params = d.value, L.value, K.value, H.value, n.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.ps_flow_free(self.h)
+            self.h = C.c_void_p()
+
+    def mask(self, layer):
+        arr, n = (C.c_int * self.dims)(), C.c_int()
+        _fcheck(lib().ps_flow_mask(self.h, layer, arr, C.byref(n)), "ps_flow_mask")
+        return list(arr[: n.value])
+
+    def get_params(self):
+        import numpy as np
+
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _fcheck(lib().ps_flow_get_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float)), self.n_params),
+                "ps_flow_get_params")
+        return p
+
+    def set_params(self, p):
+        import numpy as np
+
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _fcheck(lib().ps_flow_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
+                "ps_flow_set_params")
+
+    def sample(self, batch, seed, r, logdet=None, z=None, event_offset=0, stream=None):
+        """r (and z): float64 CUDA tensors [dims, >= batch] with unit stride along the events."""
+        if r.dim() != 2 or r.shape[0] != self.dims or r.shape[1] < batch or (r.shape[1] > 1 and r.stride(1) != 1):
+            raise PSError("r must be a [dims, batch] tensor with unit stride along the batch")
+        if z is not None and z.stride() != r.stride():
+            raise PSError("z must have the layout of r")
+        ld = r.stride(0)
+        _fcheck(lib().ps_flow_sample(self.h, batch, seed, event_offset, _ptr(r), ld, _ptr(logdet), _ptr(z),
+                                     _stream_ptr(stream)), "ps_flow_sample")
+
+    def inverse(self, r, z, logq=None, stream=None):
+        """z = flow^-1(r), logq = log g(r): float64 CUDA tensors [dims, batch] and [batch]."""
+        if r.dim() != 2 or r.shape[0] != self.dims or (r.shape[1] > 1 and r.stride(1) != 1) or z.stride() != r.stride():
+            raise PSError("r and z must be [dims, batch] tensors of one layout with unit stride along the batch")
+        _fcheck(lib().ps_flow_inverse(self.h, r.shape[1], _ptr(r), r.stride(0), _ptr(z), _ptr(logq),
+                                      _stream_ptr(stream)), "ps_flow_inverse")
+
+    def weights(self, w_map, logdet, w, stream=None):
+        _fcheck(lib().ps_flow_weights(self.h, w_map.numel(), _ptr(w_map), _ptr(logdet), _ptr(w),
+                                      _stream_ptr(stream)), "ps_flow_weights")
+
+    def train_step(self, w_map, lr, stream=None):
+        _fcheck(lib().ps_flow_train_step(self.h, _ptr(w_map), lr, _stream_ptr(stream)), "ps_flow_train_step")
+
+    def gradients(self, w_map, stream=None):
+        import numpy as np
+
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_double()
+        _fcheck(lib().ps_flow_gradients(self.h, _ptr(w_map), g.ctypes.data_as(C.POINTER(C.c_float)), self.n_params,
+                                        C.byref(loss), _stream_ptr(stream)), "ps_flow_gradients")
+        return loss.value, g
+
+    def loss(self, stream=None):
+        loss, sw = C.c_double(), C.c_double()
+        _fcheck(lib().ps_flow_loss(self.h, C.byref(loss), C.byref(sw), _stream_ptr(stream)), "ps_flow_loss")
+        return loss.value, sw.value
+
+
+def flow_param_layout(dims, n_layers, bins, hidden, masks):
+    """Logical parameter layout of a flow: list over layers of {name: (offset, shape)}."""
+    out, o = [], 0
+    for l in range(n_layers):
+        nb = len(masks[l])
+        na = dims - nb
+        P = nb * (3 * bins + 1)
+        lay = {}
+        for name, shape in (("W1", (hidden, na)), ("b1", (hidden,)), ("W2", (hidden, hidden)), ("b2", (hidden,)),
+                            ("W3", (P, hidden)), ("b3", (P,))):
+            n = 1
+            for x in shape:
+                n *= x
+            lay[name] = (o, shape)
+            o += n
+        out.append(lay)
+    return out, o
