@@ -59,12 +59,18 @@ struct GemmArgs {
     int64_t ldc;
     bf16* Cb;
     int64_t ldcb;
-    int act;      // 1: SiLU on the bf16 copy
+    int act;      // 1: SiLU on the bf16 copy; 2: C and its copy times SiLU'(Zs) (backward)
+    const float* Zs;  // pre-activations for act == 2, [M][ldc]
     int atomic;   // 1: atomicAdd into C
     int trans_c;  // 1: C(m, n) stored at C[n * ldc + m] (fp32 only)
+    int a_vec, b_vec;  // 1: the operand's base is 16-byte aligned (16-byte loads allowed)
 };
 
 __device__ __forceinline__ float silu(float x) { return x / (1.0f + __expf(-x)); }
+__device__ __forceinline__ float silu_grad(float x) {
+    const float s = 1.0f / (1.0f + __expf(-x));
+    return s * (1.0f + x * (1.0f - s));
+}
 
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
     asm volatile(
@@ -72,6 +78,58 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint
         "{%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One operand tile (64 rows x 32 k) moves through registers as 2 x 8 bf16 per thread: eight
+// consecutive elements along the operand's unit-stride dimension (k if lk == 1, else rows if
+// lr == 1), as one 16-byte load when they are in range and aligned, else element by element
+// (zero outside the operand).
+struct TileRegs {
+    uint4 v[2];
+};
+
+__device__ __forceinline__ bool along_k(int64_t lr, int64_t lk) { return lk == 1 || lr != 1; }
+
+__device__ __forceinline__ void fetch_tile(const bf16* X, int64_t lr, int64_t lk, int r0, int R, int k0, int kend,
+                                           bool vec, int tid, TileRegs& t) {
+    const bool ak = along_k(lr, lk);
+    const bf16 zero = __float2bfloat16(0.0f);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int v = tid + i * 128;
+        const int r = ak ? v >> 2 : (v & 7) * 8;
+        const int k = ak ? (v & 3) * 8 : v >> 3;
+        const int gr = r0 + r, gk = k0 + k;
+        const int64_t off = static_cast<int64_t>(gr) * lr + static_cast<int64_t>(gk) * lk;
+        const bool full = ak ? (lk == 1 && gr < R && gk + 8 <= kend) : (gk < kend && gr + 8 <= R);
+        if (vec && full && (off & 7) == 0) {
+            t.v[i] = *reinterpret_cast<const uint4*>(X + off);
+        } else {
+            __align__(16) bf16 e[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int rr = ak ? gr : gr + j, kk = ak ? gk + j : gk;
+                e[j] = (rr < R && kk < kend) ? X[static_cast<int64_t>(rr) * lr + static_cast<int64_t>(kk) * lk] : zero;
+            }
+            t.v[i] = *reinterpret_cast<const uint4*>(e);
+        }
+    }
+}
+
+__device__ __forceinline__ void store_tile(bf16 (*S)[40], int64_t lr, int64_t lk, int tid, const TileRegs& t) {
+    const bool ak = along_k(lr, lk);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int v = tid + i * 128;
+        if (ak) {
+            *reinterpret_cast<uint4*>(&S[v >> 2][(v & 3) * 8]) = t.v[i];
+        } else {
+            const bf16* e = reinterpret_cast<const bf16*>(&t.v[i]);
+            const int r = (v & 7) * 8, k = v >> 3;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) S[r + j][k] = e[j];
+        }
+    }
 }
 
 __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
@@ -90,20 +148,20 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-    const bf16 zero = __float2bfloat16(0.0f);
+    TileRegs ra, rb;
+    if (k_begin < k_end) {
+        fetch_tile(g.A, g.lam, g.lak, m0, g.M, k_begin, k_end, g.a_vec, tid, ra);
+        fetch_tile(g.B, g.lbn, g.lbk, n0, g.N, k_begin, k_end, g.b_vec, tid, rb);
+        store_tile(As, g.lam, g.lak, tid, ra);
+        store_tile(Bs, g.lbn, g.lbk, tid, rb);
+    }
+    __syncthreads();
     for (int k0 = k_begin; k0 < k_end; k0 += 32) {
-        for (int idx = tid; idx < 64 * 32; idx += 128) {
-            int m, k;
-            if (g.lak == 1) { m = idx >> 5; k = idx & 31; } else { m = idx & 63; k = idx >> 6; }
-            int gm = m0 + m, gk = k0 + k;
-            As[m][k] = (gm < g.M && gk < k_end) ? g.A[gm * g.lam + gk * g.lak] : zero;
-            int n;
-            if (g.lbk == 1) { n = idx >> 5; k = idx & 31; } else { n = idx & 63; k = idx >> 6; }
-            int gn = n0 + n;
-            gk = k0 + k;
-            Bs[n][k] = (gn < g.N && gk < k_end) ? g.B[gn * g.lbn + gk * g.lbk] : zero;
+        const bool more = k0 + 32 < k_end;
+        if (more) {  // next tile's global loads overlap this tile's MMAs
+            fetch_tile(g.A, g.lam, g.lak, m0, g.M, k0 + 32, k_end, g.a_vec, tid, ra);
+            fetch_tile(g.B, g.lbn, g.lbk, n0, g.N, k0 + 32, k_end, g.b_vec, tid, rb);
         }
-        __syncthreads();
 #pragma unroll
         for (int ks = 0; ks < 32; ks += 16) {
             uint32_t af[2][4], bfr[4][2];
@@ -127,6 +185,11 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
                 for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bfr[j]);
         }
         __syncthreads();
+        if (more) {
+            store_tile(As, g.lam, g.lak, tid, ra);
+            store_tile(Bs, g.lbn, g.lbk, tid, rb);
+        }
+        __syncthreads();
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -144,8 +207,9 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
                 } else if (g.trans_c) {
                     g.C[col * g.ldc + row] = v;
                 } else {
+                    if (g.act == 2) v *= silu_grad(g.Zs[row * g.ldc + col]);
                     if (g.C) g.C[row * g.ldc + col] = v;
-                    if (g.Cb) g.Cb[row * g.ldcb + col] = __float2bfloat16(g.act ? silu(v) : v);
+                    if (g.Cb) g.Cb[row * g.ldcb + col] = __float2bfloat16(g.act == 1 ? silu(v) : v);
                 }
             }
 }
@@ -460,17 +524,6 @@ __global__ void k_colsum(int64_t B, int n, const float* M, float* out) {
     atomicAdd(out + col, s);
 }
 
-// dZ = dA * SiLU'(Z) (fp32 -> bf16)
-__global__ void k_silu_backward(int64_t count, const float* dA, const float* Z, float* dZ, bf16* dZb) {
-    int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= count) return;
-    float z = Z[i];
-    float s = 1.0f / (1.0f + __expf(-z));
-    float v = dA[i] * s * (1.0f + z * (1.0f - s));
-    dZ[i] = v;
-    dZb[i] = __float2bfloat16(v);
-}
-
 __global__ void k_scatter(int64_t B, int d, const __grid_constant__ LayerDesc ld, const float* dIn, float* gXn) {
     int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (b >= B) return;
@@ -569,6 +622,7 @@ inline unsigned blocks(int64_t n, int t) { return static_cast<unsigned>((n + t -
 struct ps_flow_s {
     FlowDesc fd;
     int device = 0;
+    int sms = 1;
     int64_t max_batch = 0;
     int64_t n_params = 0;
     // parameters and optimiser state (device)
@@ -594,6 +648,7 @@ struct ps_flow_s {
     float* dA = nullptr;     // [max_batch][H]
     float* dZ = nullptr;
     bf16* dZb = nullptr;
+    bf16* dAb = nullptr;
     float* dIn = nullptr;    // [max_batch][16]
     float* gX = nullptr;     // [max_batch][d]
     float* gXn = nullptr;
@@ -610,7 +665,7 @@ void free_flow(ps_flow f) {
                     static_cast<void*>(f->In), static_cast<void*>(f->Z1), static_cast<void*>(f->Z2),
                     static_cast<void*>(f->A1), static_cast<void*>(f->A2), static_cast<void*>(f->Praw),
                     static_cast<void*>(f->logdet), static_cast<void*>(f->G), static_cast<void*>(f->Gb),
-                    static_cast<void*>(f->dA), static_cast<void*>(f->dZ), static_cast<void*>(f->dZb),
+                    static_cast<void*>(f->dA), static_cast<void*>(f->dZ), static_cast<void*>(f->dZb), static_cast<void*>(f->dAb),
                     static_cast<void*>(f->dIn), static_cast<void*>(f->gX), static_cast<void*>(f->gXn),
                     static_cast<void*>(f->wtot), static_cast<void*>(f->scal)})
         cudaFree(q);
@@ -626,6 +681,8 @@ uint64_t splitmix(uint64_t& s) {
 // launch one GEMM; kchunk = K unless split
 int gemm(const GemmArgs& a0, int splits, cudaStream_t st) {
     GemmArgs a = a0;
+    a.a_vec = (reinterpret_cast<uintptr_t>(a.A) & 15) == 0;
+    a.b_vec = (reinterpret_cast<uintptr_t>(a.B) & 15) == 0;
     splits = std::max(1, splits);
     a.kchunk = ((a.K + splits - 1) / splits + 31) / 32 * 32;
     int nz = (a.K + a.kchunk - 1) / a.kchunk;
@@ -717,7 +774,14 @@ int backward(ps_flow f, int64_t B, cudaStream_t st) {
     cudaMemsetAsync(f->gX, 0, B * d * sizeof(float), st);
     cudaMemsetAsync(f->grad, 0, f->n_params * sizeof(float), st);
     int launches = 0;
-    const int split = std::max(1, static_cast<int>(std::min<int64_t>(64, B / 2048)));
+    const unsigned colsum_rows = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(512, B / 64)));
+    // batch-long weight-gradient GEMMs: split the batch so that about two CTAs per SM run,
+    // with at least 256 events per split
+    auto split_for = [&](int M, int N) {
+        const int64_t tiles = static_cast<int64_t>((M + 63) / 64) * ((N + 63) / 64);
+        const int64_t want = (2 * f->sms + tiles - 1) / tiles;
+        return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, B / 256)));
+    };
     for (int l = 0; l < fd.L; ++l) {
         const LayerDesc& ld = fd.layer[l];
         float* Xl = f->X + static_cast<int64_t>(l) * f->max_batch * d;
@@ -734,44 +798,44 @@ int backward(ps_flow f, int64_t B, cudaStream_t st) {
         GemmArgs g{};
         g.A = f->Gb; g.lam = ldg; g.lak = 1; g.B = A2; g.lbn = 1; g.lbk = H;
         g.M = ld.Ppad; g.N = H; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W3; g.ldc = H; g.atomic = 1;
-        int s = gemm(g, split, st);
+        int s = gemm(g, split_for(ld.Ppad, H), st);
         if (s != PS_OK) return s;
         k_rowsum<<<dim3(std::min<unsigned>(blocks(B, 256), 64), ld.Ppad), 256, 0, st>>>(B, ldg, f->G,
                                                                                           f->grad + ld.off_b3);
         g = GemmArgs{};
         g.A = f->Gb; g.lam = 1; g.lak = ldg; g.B = f->pb + ld.off_W3; g.lbn = 1; g.lbk = H;
-        g.M = static_cast<int>(B); g.N = H; g.K = ld.Ppad; g.C = f->dA; g.ldc = H;
+        g.M = static_cast<int>(B); g.N = H; g.K = ld.Ppad; g.C = f->dZ; g.ldc = H; g.Cb = f->dZb; g.ldcb = H;
+        g.act = 2; g.Zs = Z2;
         s = gemm(g, 1, st);
         if (s != PS_OK) return s;
-        k_silu_backward<<<blocks(B * H, T), T, 0, st>>>(B * H, f->dA, Z2, f->dZ, f->dZb);
         // middle layer
         g = GemmArgs{};
         g.A = f->dZb; g.lam = 1; g.lak = H; g.B = A1; g.lbn = 1; g.lbk = H;
         g.M = H; g.N = H; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W2; g.ldc = H; g.atomic = 1;
-        s = gemm(g, split, st);
+        s = gemm(g, split_for(H, H), st);
         if (s != PS_OK) return s;
-        k_colsum<<<dim3(blocks(H, 64), 64), 64, 0, st>>>(B, H, f->dZ, f->grad + ld.off_b2);
+        k_colsum<<<dim3(blocks(H, 64), colsum_rows), 64, 0, st>>>(B, H, f->dZ, f->grad + ld.off_b2);
         g = GemmArgs{};
         g.A = f->dZb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W2; g.lbn = 1; g.lbk = H;
-        g.M = static_cast<int>(B); g.N = H; g.K = H; g.C = f->dA; g.ldc = H;
+        g.M = static_cast<int>(B); g.N = H; g.K = H; g.C = f->dA; g.ldc = H; g.Cb = f->dAb; g.ldcb = H;
+        g.act = 2; g.Zs = Z1;
         s = gemm(g, 1, st);
         if (s != PS_OK) return s;
-        k_silu_backward<<<blocks(B * H, T), T, 0, st>>>(B * H, f->dA, Z1, f->dZ, f->dZb);
         // first layer
         g = GemmArgs{};
-        g.A = f->dZb; g.lam = 1; g.lak = H; g.B = In; g.lbn = 1; g.lbk = kInPad;
+        g.A = f->dAb; g.lam = 1; g.lak = H; g.B = In; g.lbn = 1; g.lbk = kInPad;
         g.M = H; g.N = kInPad; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W1; g.ldc = kInPad; g.atomic = 1;
-        s = gemm(g, split, st);
+        s = gemm(g, split_for(H, kInPad), st);
         if (s != PS_OK) return s;
-        k_colsum<<<dim3(blocks(H, 64), 64), 64, 0, st>>>(B, H, f->dZ, f->grad + ld.off_b1);
+        k_colsum<<<dim3(blocks(H, 64), colsum_rows), 64, 0, st>>>(B, H, f->dA, f->grad + ld.off_b1);
         g = GemmArgs{};
-        g.A = f->dZb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W1; g.lbn = 1; g.lbk = kInPad;
+        g.A = f->dAb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W1; g.lbn = 1; g.lbk = kInPad;
         g.M = static_cast<int>(B); g.N = kInPad; g.K = H; g.C = f->dIn; g.ldc = kInPad;
         s = gemm(g, 1, st);
         if (s != PS_OK) return s;
         k_scatter<<<blocks(B, T), T, 0, st>>>(B, d, ld, f->dIn, f->gXn);
         std::swap(f->gX, f->gXn);
-        launches += 7;
+        launches += 5;
     }
     ps::count_launches(launches);
     return fcheck(cudaGetLastError(), "flow backward");
@@ -880,7 +944,7 @@ int ps_flow_create(int dims, int n_layers, int bins, int hidden, int64_t max_bat
             for (int k = 0; k <= bins; ++k) h[ld.off_b3 + q * (3 * bins + 1) + 2 * bins + k] = d_id;
     }
     Guard g(device);
-    int st = PS_OK;
+    int st = fcheck(cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, device), "SM count");
     auto alloc = [&](void** q, size_t bytes) {
         if (st == PS_OK) st = fcheck(cudaMalloc(q, std::max<size_t>(bytes, 256)), "cudaMalloc (flow)");
     };
@@ -903,6 +967,7 @@ int ps_flow_create(int dims, int n_layers, int bins, int hidden, int64_t max_bat
     alloc(reinterpret_cast<void**>(&f->dA), B * H * 4);
     alloc(reinterpret_cast<void**>(&f->dZ), B * H * 4);
     alloc(reinterpret_cast<void**>(&f->dZb), B * H * 2);
+    alloc(reinterpret_cast<void**>(&f->dAb), B * H * 2);
     alloc(reinterpret_cast<void**>(&f->dIn), B * kInPad * 4);
     alloc(reinterpret_cast<void**>(&f->gX), B * dims * 4);
     alloc(reinterpret_cast<void**>(&f->gXn), B * dims * 4);
