@@ -402,6 +402,36 @@ int ps_flow_gradients(ps_flow f, const double* w_map, float* host, int64_t n, do
 /* Loss and sum of w of the last train_step / gradients call.  Synchronises `stream`. */
 int ps_flow_loss(ps_flow f, double* loss, double* sum_w, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Unweighting (Sec. "Unweighting and file output"): the maximum weight is estimated allowing a
+ * given amount of over-weight events relative to the total cross section (0.1% in the paper's
+ * validation runs), and events are accepted against it.
+ *
+ *   w_max(eps) = the smallest t >= 0 with  sum_b max(0, w_b - t) <= eps * sum_b w_b
+ *
+ * (the share of the cross section above w_max is at most eps).  Event b is accepted iff
+ * u_b w_max < w_b, with u_b the first uniform of the generator's Philox point of event
+ * (event_offset + b) in stream 0x556E7700 (counter (event lo, event hi, 0x556E7700, 0), key
+ * (seed lo, seed hi), top 52 bits of words 1:0, (k + 1/2) 2^-52); an accepted event keeps the
+ * weight max(w_b, w_max), so the accepted weights estimate sum_b w_b without bias.
+ * Weights that are negative or not finite are counted and skipped (never accepted).
+ * All pointers are device pointers; the calls are asynchronous on `stream` and reproducible
+ * bit for bit for a given n.
+ * ------------------------------------------------------------------------------------------ */
+const char* ps_unweight_last_error(void);
+/* Bytes of workspace for n weights (the workspace must be 256-byte aligned). */
+int ps_unweight_workspace_size(int64_t n, size_t* bytes);
+/* result[5] (device doubles) <- { w_max, sum of valid w, max w, number of weights above w_max
+ * (the over-weight events), number of invalid weights }.  eps >= 0. */
+int ps_unweight_max(const double* w, int64_t n, double eps, double* result, void* workspace, size_t ws_bytes,
+                    void* stream);
+/* Accept against *w_max (device scalar, e.g. result[0] above): the indices of the accepted
+ * events in increasing order into idx[], their weights max(w, w_max) into w_out[] (both with
+ * room for n), and their number into *n_accepted (device int64). */
+int ps_unweight_select(const double* w, int64_t n, const double* w_max, uint64_t seed, uint64_t event_offset,
+                       int64_t* idx, double* w_out, int64_t* n_accepted, void* workspace, size_t ws_bytes,
+                       void* stream);
+
 /* Number of kernel launches issued by the library since load (all programs). */
 int64_t ps_launch_count(void);
 

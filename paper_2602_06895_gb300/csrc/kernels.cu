@@ -20,6 +20,7 @@
 #include <mutex>
 #include <string>
 
+#include "philox.cuh"
 #include "ps_internal.h"
 
 namespace ps {
@@ -75,27 +76,8 @@ __device__ __forceinline__ P4 boost_in(P4 p, P4 q, double mq) {
     return {(q.e * p.e - qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
 }
 
-// ---------------------------------------------------------------- Philox4x32-10
-// Salmon et al., SC'11: two 32x32 multiplies per round, Weyl key schedule.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// (k + 1/2) 2^-52 for the top 52 bits k of (hi:lo), exactly: the double 1 + k 2^-52 is
-// assembled from bits and (1 - 2^-53) subtracted, which is exact by Sterbenz's lemma.
-__device__ __forceinline__ double unit_from_bits(uint32_t hi, uint32_t lo) {
-    unsigned long long k = ((static_cast<unsigned long long>(hi) << 32) | lo) >> 12;
-    double one_plus = __longlong_as_double(0x3FF0000000000000ULL | k);
-    return one_plus - 0x1.fffffffffffffp-1;
-}
+using rng::philox4x32_10;
+using rng::unit_from_bits;
 
 // ---------------------------------------------------------------- invariant maps (Sec. 2.2.1)
 // Power law G_nu / log map, anchored at x_min for nu <= 1 and at m^2 for nu > 1, so that

@@ -18,5 +18,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// (k + 1/2) 2^-52 for the top 52 bits k of (hi:lo), exactly: the double 1 + k 2^-52 is
+// assembled from bits and (1 - 2^-53) subtracted, which is exact by Sterbenz's lemma.
+__device__ __forceinline__ double unit_from_bits(uint32_t hi, uint32_t lo) {
+    unsigned long long k = ((static_cast<unsigned long long>(hi) << 32) | lo) >> 12;
+    double one_plus = __longlong_as_double(0x3FF0000000000000ULL | k);
+    return one_plus - 0x1.fffffffffffffp-1;
+}
+
 }  // namespace rng
 }  // namespace ps

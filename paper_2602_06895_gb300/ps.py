@@ -107,6 +107,12 @@ _SIGS = {
     "ps_status_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ps_program_free": (C.c_int, [C.c_void_p]),
     "ps_launch_count": (C.c_int64, []),
+    "ps_unweight_last_error": (C.c_char_p, []),
+    "ps_unweight_workspace_size": (C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
+    "ps_unweight_max": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_size_t,
+                                  C.c_void_p]),
+    "ps_unweight_select": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "ps_flow_last_error": (C.c_char_p, []),
     "ps_flow_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_uint64, C.c_int,
                                  C.POINTER(C.c_void_p)]),
@@ -585,3 +591,49 @@ def flow_param_layout(dims, n_layers, bins, hidden, masks):
             o += n
         out.append(lay)
     return out, o
+
+
+# ------------------------------------------------------------------ unweighting (ps_unweight_*)
+def _ucheck(status, what=""):
+    if status != PS_OK:
+        msg = lib().ps_unweight_last_error().decode(errors="replace")
+        raise PSError(f"{what} failed ({status}): {msg}")
+
+
+class Unweighter:
+    """Maximum weight with a bounded over-weight share and accept/reject (ps_unweight_*) for
+    batches of up to `capacity` weights on one device."""
+
+    def __init__(self, capacity, device=0):
+        import torch
+
+        n = C.c_size_t()
+        _ucheck(lib().ps_unweight_workspace_size(capacity, C.byref(n)), "ps_unweight_workspace_size")
+        self.capacity = capacity
+        self._ws = torch.empty(n.value // 8 + 64, dtype=torch.float64, device=torch.device("cuda", device))
+        self.result = torch.zeros(5, dtype=torch.float64, device=self._ws.device)
+        self.n_accepted = torch.zeros(1, dtype=torch.int64, device=self._ws.device)
+
+    def _wsp(self):
+        base = self._ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        return C.c_void_p(aligned), self._ws.numel() * 8 - (aligned - base)
+
+    def max_weight(self, w, eps=1e-3, stream=None):
+        """Fills self.result = [w_max, sum w, max w, n over w_max, n invalid] (asynchronous)."""
+        if w.numel() > self.capacity:
+            raise PSError("more weights than the unweighter's capacity")
+        wp, wn = self._wsp()
+        _ucheck(lib().ps_unweight_max(_ptr(w), w.numel(), eps, _ptr(self.result), wp, wn, _stream_ptr(stream)),
+                "ps_unweight_max")
+        return self.result
+
+    def select(self, w, seed, idx, w_out, event_offset=0, w_max=None, stream=None):
+        """Accept against w_max (device scalar; default self.result[0]); fills idx, w_out and
+        self.n_accepted (asynchronous)."""
+        if w.numel() > self.capacity:
+            raise PSError("more weights than the unweighter's capacity")
+        wm = self.result[0:1] if w_max is None else w_max
+        wp, wn = self._wsp()
+        _ucheck(lib().ps_unweight_select(_ptr(w), w.numel(), _ptr(wm), seed, event_offset, _ptr(idx), _ptr(w_out),
+                                         _ptr(self.n_accepted), wp, wn, _stream_ptr(stream)), "ps_unweight_select")
