@@ -104,6 +104,7 @@ def lib():
                                              C.c_int]
             L.orc_inverse_batch.argtypes = [C.POINTER(Channel), C.c_void_p, C.c_int64, _D, _D, _D, C.c_int]
             L.orc_stats.argtypes = [_D, C.c_int64, _D]
+            L.orc_sde_weights.argtypes = [C.POINTER(Sde), C.c_int, C.c_int64, C.c_int, _D, _D]
             L.orc_max_threads.restype = C.c_int
             assert L.orc_sizeof_channel() == C.sizeof(Channel)
             assert L.orc_sizeof_sde() == C.sizeof(Sde)
@@ -276,6 +277,44 @@ def inverse(ch, mom, x, grid=None, threads=None):
     g, gp = _grid_arg(ch, grid)
     L.orc_inverse_batch(C.byref(c), gp, B, mom, x, r, _threads(threads))
     return r
+
+
+def sde_weights(channels, j, mom):
+    """P_j(p) of channel j of `channels` (the SDE propagator product) for momenta [B, n+2, 4]."""
+    sde = encode_sde(channels)
+    mom = np.ascontiguousarray(mom, dtype=np.float64)
+    out = np.zeros(mom.shape[0])
+    lib().orc_sde_weights(C.byref(sde), j, mom.shape[0], mom.shape[1] - 2, mom, out)
+    return out
+
+
+def global_weights(channels, alphas, mom, x, grids=None, threads=None):
+    """Global multichannel weights (Kleiss-Pittau, Eq. multi-channel-standard) of events given by
+    lab momenta [B, n+2, 4] and x [B, 2]:  w = f / sum_j alpha_j g_j,  g_j = 1/J_j(G_j^-1(p)) with
+    J_j the phase-space weight of channel j (integrand "none") at its inverse point, and
+    f = pdf(x1) pdf(x2) sum_j P_j(p) (the integrand whose SDE split the channels' own weights use).
+    Returns (w, J [M, B], P [M, B], r list)."""
+    M = len(channels)
+    grids = grids if grids is not None else [None] * M
+    J, P, rs = [], [], []
+    for j, ch in enumerate(channels):
+        r = inverse(ch, mom, x, grids[j], threads)
+        dens = dict(ch)
+        dens["integrand"] = "none"
+        J.append(forward(dens, r, grids[j], threads=threads)["w"])
+        P.append(sde_weights(channels, j, mom))
+        rs.append(r)
+    J, P = np.array(J), np.array(P)
+    ch0 = channels[0]
+    f = P.sum(axis=0)
+    if ch0["hadronic"]:
+        a, b = ch0["pdf"]
+        f = f * x[:, 0] ** a * (1 - x[:, 0]) ** b * x[:, 1] ** a * (1 - x[:, 1]) ** b
+    al = np.asarray(alphas, dtype=np.float64)[:, None]
+    inv = np.where(J > 0, 1.0 / np.where(J > 0, J, 1.0), 0.0)
+    g = np.sum(al * inv, axis=0)
+    w = np.where(g > 0, f / np.where(g > 0, g, 1.0), 0.0)
+    return w, J, P, rs
 
 
 def stats(w):

@@ -1153,6 +1153,13 @@ void orc_inverse_batch(const orc_channel* ch, const double* grid, int64_t B, con
     for (int64_t e = 0; e < B; ++e) inverse_event(ch, grid, mom + e * nm, x + 2 * e, r + e * d);
 }
 
+/* The SDE weight P_j of channel j (products of propagator denominators) for a batch of lab
+ * momenta [B][n+2][4]: the channel density numerator of the global multichannel integrand. */
+void orc_sde_weights(const orc_sde* sde, int j, int64_t B, int n, const double* mom, double* out)
+{
+    for (int64_t e = 0; e < B; ++e) out[e] = sde_from_momenta(sde, j, mom + e * (n + 2) * 4);
+}
+
 int orc_sizeof_channel(void) { return (int)sizeof(orc_channel); }
 int orc_sizeof_sde(void) { return (int)sizeof(orc_sde); }
 int orc_max_threads(void)
