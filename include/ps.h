@@ -403,6 +403,41 @@ int ps_flow_gradients(ps_flow f, const double* w_map, float* host, int64_t n, do
 int ps_flow_loss(ps_flow f, double* loss, double* sum_w, void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Inverse maps and global multichannel weights.
+ *
+ * Every mapping of the phase-space construction is invertible (Sec. 2), and the global
+ * multichannel method (Kleiss and Pittau; Eq. channel_densities and Eq. multi-channel-standard)
+ * weights an event x by w = f(x) / g(x) with g = sum_i alpha_i g_i, where g_i(x) =
+ * |d G_i^-1(x) / dx| is channel i's density at x.  g_i is 1/J_i(r_i), J_i the phase-space
+ * weight of channel i (integrand "none") at r_i = G_i^-1(x): the inverse below gives r_i, a
+ * program of the channels with integrand "none" gives J_i through ps_map, and
+ * ps_global_weights combines them.
+ * ------------------------------------------------------------------------------------------ */
+
+/* r = G^-1(x) of program channel `ch` for `batch` events, in FP64 on the device:
+ *   momenta  [4 (n+2)][ld_m] lab-frame event records [p_a, p_b, p_1..p_n] (row 4 i + mu), as
+ *            written by ps_generate / ps_map;  x1, x2 [batch] (hadronic channels; else null);
+ *   r        [n_random][ld_r] output, the random numbers the forward map takes to these momenta
+ *            (VEGAS inverted with the program's current grid);
+ *   P        [batch] output or null: the channel's SDE weight prod 1/|q^2 - M^2 + i M G|^2 of its
+ *            s-channel propagators in the SDE list and t-channel propagators, from the momenta.
+ * `desc` must describe program channel `ch` (same dimension count and VEGAS dimensions).
+ * Invariants come from the leaves in a collinear-safe form; the beam boost is undone on the
+ * light cone.  Asynchronous. */
+int ps_inverse_map(ps_program p, int ch, const ps_channel_desc* desc, int64_t batch, const double* momenta,
+                   int64_t ld_m, const double* x1, const double* x2, double* r, int64_t ld_r, double* P,
+                   void* stream);
+
+/* Global multichannel weights (device arrays):  w[b] = f_b / sum_j alpha[j] / J[j ld_j + b]
+ * (terms with J <= 0 contribute no density; w = 0 if none is left), where f_b = f[b] if f is
+ * given, else  pdf(x1) pdf(x2) sum_j P[j ld_p + b]  with pdf(x) = x^pdf_alpha (1-x)^pdf_beta
+ * (x1 = x2 = null: the PDF factor is 1).  alpha: host array of n_ch non-negative channel
+ * weights (normally summing to 1).  Asynchronous. */
+int ps_global_weights(int n_ch, int64_t batch, const double* J, int64_t ld_j, const double* P, int64_t ld_p,
+                      const double* alpha, const double* x1, const double* x2, double pdf_alpha, double pdf_beta,
+                      const double* f, double* w, void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Unweighting (Sec. "Unweighting and file output"): the maximum weight is estimated allowing a
  * given amount of over-weight events relative to the total cross section (0.1% in the paper's
  * validation runs), and events are accepted against it.

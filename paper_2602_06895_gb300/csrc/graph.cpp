@@ -877,6 +877,151 @@ void build(const ps_channel_desc* all, int n_ch, int which, ps_graph g) {
 
 }  // namespace
 
+namespace ps {
+// The inverse plan of a channel: the forward builder's dimension layout, s-order bounds recipe,
+// t-chain order and SDE propagators, flattened for the inverse kernel.
+int build_inverse_plan(const ps_channel_desc* d, InvPlan* plan, std::string* err) {
+    std::string why;
+    if (!validate_desc(d, &why)) {
+        *err = "channel description: " + why;
+        return PS_ERR_GRAPH;
+    }
+    InvPlan P{};
+    const ps_node_desc* nd = d->nodes;
+    std::vector<int> parent(d->n_nodes, -1);
+    for (int j = 0; j < d->n_nodes; ++j)
+        for (int k = 0; k < nd[j].n_children; ++k) parent[nd[j].children[k]] = j;
+    P.n = d->n_out;
+    P.n_nodes = d->n_nodes;
+    P.hadronic = d->hadronic;
+    P.lab_frame = d->lab_frame;
+    P.kappa = nd[0].kind == PS_NODE_TCHAIN ? nd[0].n_children - 1 : 0;
+    P.S = d->s_beam;
+    P.sqrt_s = d->sqrt_s;
+    P.a = d->a_shift;
+    P.shat_M = d->shat_mass;
+    P.shat_G = d->shat_width;
+    P.shat_nu = d->shat_nu;
+    P.t_nu = d->t_nu;
+    P.ts_nu = d->ts_nu;
+    P.vdims = d->vegas_dims;
+    P.vbins = d->vegas_bins;
+    double mleaf = 0.0;
+    for (int j = 0; j < d->n_nodes; ++j) {
+        InvNode& q = P.node[j];
+        q.kind = nd[j].kind;
+        q.nch = nd[j].n_children;
+        q.leaf = nd[j].leaf_index;
+        for (int k = 0; k < nd[j].n_children; ++k) q.child[k] = nd[j].children[k];
+        unsigned m = 0;
+        leaves_of(d, j, &m);
+        q.mask = m;
+        q.mass = nd[j].mass;
+        q.M = nd[j].prop_mass;
+        q.G = nd[j].prop_width;
+        q.nu = nd[j].nu;
+        if (nd[j].kind == PS_NODE_LEAF) mleaf += nd[j].mass;
+    }
+    P.mleaf = mleaf;
+    std::vector<int> pre;
+    preorder(d, 0, &pre);
+    P.n_pre = static_cast<int>(pre.size());
+    for (int i = 0; i < P.n_pre; ++i) P.pre[i] = pre[i];
+    P.n_sorder = d->n_sorder;
+    for (int i = 0; i < d->n_sorder; ++i) P.sorder[i] = d->sorder[i];
+    // dimension layout (as the forward builder)
+    for (int j = 0; j < kInvNodes; ++j) P.d_s[j] = P.d_dphi[j] = P.d_dth[j] = -1;
+    int idx = 0;
+    P.d_shat = P.d_x = -1;
+    if (d->hadronic) P.d_shat = idx++;
+    for (int i = 0; i < d->n_sorder; ++i) P.d_s[d->sorder[i]] = idx++;
+    for (int i = 1; i < P.kappa; ++i) P.d_ts[i] = idx++;
+    if (d->hadronic) P.d_x = idx++;
+    for (int i = 1; i <= P.kappa; ++i) {
+        P.d_tphi[i] = idx++;
+        P.d_tt[i] = idx++;
+    }
+    for (int j : pre) {
+        P.d_dphi[j] = idx++;
+        P.d_dth[j] = idx++;
+    }
+    P.d = idx;
+    // t-chain order (legs taken inwards from side A or B)
+    if (P.kappa > 0) {
+        int left = 0, right = P.kappa;
+        for (int i = 1; i < P.kappa; ++i) {
+            if (d->tside[i] == 0) {
+                P.order[i] = left++;
+                P.side[i] = 0;
+            } else {
+                P.order[i] = right--;
+                P.side[i] = 1;
+            }
+        }
+        P.order[P.kappa] = left;
+        P.order[P.kappa + 1] = right;
+    }
+    // s-order bounds recipe
+    std::vector<char> sampled(d->n_nodes, 0);
+    sampled[0] = 1;
+    int nid = 0;
+    auto push = [&](int id) {
+        if (nid >= kInvIds) throw PS_ERR_CAPACITY;
+        P.ids[nid++] = id;
+    };
+    std::function<void(int, double*)> min_mass = [&](int j, double* c) {
+        if (nd[j].kind == PS_NODE_LEAF) { *c += nd[j].mass; return; }
+        if (sampled[j]) {
+            if (j == 0 && !d->hadronic) *c += d->sqrt_s;
+            else push(j);
+            return;
+        }
+        for (int k = 0; k < nd[j].n_children; ++k) min_mass(nd[j].children[k], c);
+    };
+    try {
+        for (int i = 0; i < d->n_sorder; ++i) {
+            int j = d->sorder[i];
+            P.lo_beg[i] = nid;
+            P.lo_c[i] = 0.0;
+            min_mass(j, &P.lo_c[i]);
+            P.off_beg[i] = nid;
+            P.off_c[i] = 0.0;
+            int cur = j;
+            for (;;) {
+                int p = parent[cur];
+                for (int k = 0; k < nd[p].n_children; ++k)
+                    if (nd[p].children[k] != cur) min_mass(nd[p].children[k], &P.off_c[i]);
+                if (sampled[p]) {
+                    P.top[i] = p;
+                    break;
+                }
+                cur = p;
+            }
+            P.lo_beg[i + 1] = nid;  // the end of this step's off list
+            sampled[j] = 1;
+        }
+    } catch (int code) {
+        *err = "inverse plan: too many bound terms";
+        return code;
+    }
+    // SDE propagators
+    std::vector<Prop> props = sde_props(d);
+    if (static_cast<int>(props.size()) > kInvProps) {
+        *err = "inverse plan: too many propagators";
+        return PS_ERR_CAPACITY;
+    }
+    P.n_prop = static_cast<int>(props.size());
+    for (int k = 0; k < P.n_prop; ++k) {
+        P.pkind[k] = props[k].kind;
+        P.pmask[k] = props[k].mask;
+        P.pM[k] = props[k].M;
+        P.pG[k] = props[k].G;
+    }
+    *plan = P;
+    return PS_OK;
+}
+}  // namespace ps
+
 extern "C" int ps_channel_dims(const ps_channel_desc* ch, int* n_random) {
     if (!ch || !n_random) return fail(PS_ERR_INVALID_ARGUMENT, "ps_channel_dims: null argument");
     std::string why;
@@ -1342,6 +1487,44 @@ int ps_map(ps_program p, int ch, int64_t batch, const double* r, int64_t ld_r, c
     st = ps::launch_reduce(lp, p->d_stats + 5 * ch, stream, &err);
     if (st != PS_OK) return fail(st, err);
     return PS_OK;
+}
+
+int ps_inverse_map(ps_program p, int ch, const ps_channel_desc* desc, int64_t batch, const double* momenta,
+                   int64_t ld_m, const double* x1, const double* x2, double* r, int64_t ld_r, double* P,
+                   void* stream) {
+    if (!p || !desc || ch < 0 || ch >= p->n_ch || batch < 0 || ld_m < batch || ld_r < batch ||
+        (batch > 0 && (!momenta || !r)))
+        return fail(PS_ERR_INVALID_ARGUMENT, "ps_inverse_map: bad arguments");
+    ps::InvPlan plan;
+    std::string err;
+    int st = ps::build_inverse_plan(desc, &plan, &err);
+    if (st != PS_OK) return fail(st, err);
+    const ps::Compiled& C = p->ch[ch];
+    if (plan.d != C.n_random || plan.vdims != C.vegas_dims)
+        return fail(PS_ERR_INVALID_ARGUMENT, "ps_inverse_map: the description does not match the program's channel");
+    if (plan.hadronic && batch > 0 && (!x1 || !x2))
+        return fail(PS_ERR_INVALID_ARGUMENT, "ps_inverse_map: a hadronic channel needs x1 and x2");
+    if (plan.n + 2 > ps::kMaxOutMomenta + 2 || plan.n_nodes > ps::kInvNodes)
+        return fail(PS_ERR_CAPACITY, "ps_inverse_map: channel too large");
+    plan.vbins = C.vegas_dims > 0 ? (p->grid_off[ch + 1] - p->grid_off[ch]) / C.vegas_dims - 1 : 1;
+    DeviceGuard dg(p->device);
+    st = ps::launch_inverse(plan, batch, momenta, ld_m, x1, x2, p->d_grid + p->grid_off[ch], r, ld_r, P, stream,
+                            &err);
+    return st == PS_OK ? PS_OK : fail(st, err);
+}
+
+int ps_global_weights(int n_ch, int64_t batch, const double* J, int64_t ld_j, const double* P, int64_t ld_p,
+                      const double* alpha, const double* x1, const double* x2, double pdf_alpha, double pdf_beta,
+                      const double* f, double* w, void* stream) {
+    if (n_ch < 1 || n_ch > ps::kMaxChannels || batch < 0 || !alpha || ld_j < batch ||
+        (batch > 0 && (!J || !w || (!f && (!P || ld_p < batch)))) || ((x1 == nullptr) != (x2 == nullptr)))
+        return fail(PS_ERR_INVALID_ARGUMENT, "ps_global_weights: bad arguments");
+    for (int j = 0; j < n_ch; ++j)
+        if (!(alpha[j] >= 0.0)) return fail(PS_ERR_INVALID_ARGUMENT, "ps_global_weights: negative channel weight");
+    std::string err;
+    int st = ps::launch_global_weights(n_ch, batch, J, ld_j, P, ld_p, alpha, x1, x2, pdf_alpha, pdf_beta, f, w,
+                                       stream, &err);
+    return st == PS_OK ? PS_OK : fail(st, err);
 }
 
 int ps_stats(ps_program p, ps_channel_stats* host, int n_ch, void* stream) {

@@ -20,6 +20,7 @@
 #include <mutex>
 #include <string>
 
+#include "kin.cuh"
 #include "philox.cuh"
 #include "ps_internal.h"
 
@@ -28,53 +29,6 @@ namespace ps {
 static unsigned long long g_launches = 0;
 
 namespace dev {
-
-constexpr double kPi = 3.141592653589793238462643383279502884;
-
-struct P4 {
-    double e, x, y, z;
-};
-
-__device__ __forceinline__ P4 p4_add(P4 a, P4 b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ P4 p4_sub(P4 a, P4 b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ double p4_sq(P4 a) { return a.e * a.e - a.x * a.x - a.y * a.y - a.z * a.z; }
-
-// Kallen lambda(x, y, z) = (x - y - z)^2 - 4 y z (x >= 0), without cancellation:
-//   y, z >= 0: (x - (sqrt y + sqrt z)^2)(x - (sqrt y - sqrt z)^2)
-//   y, z <= 0: x^2 + 2x(|y| + |z|) + (|y| - |z|)^2  (space-like legs of a t-chain)
-//   mixed:     (x - y - z)^2 - 4 y z                (-4yz >= 0)
-// clamped at zero.
-__device__ __forceinline__ double kallen(double x, double y, double z) {
-    double l;
-    if (y >= 0.0 && z >= 0.0) {
-        double ry = sqrt(y), rz = sqrt(z);
-        double hi = ry + rz, lo = ry - rz;
-        l = (x - hi * hi) * (x - lo * lo);
-    } else if (y <= 0.0 && z <= 0.0) {
-        double d = z - y;
-        l = x * x - 2.0 * x * (y + z) + d * d;
-    } else {
-        double d = x - y - z;
-        l = d * d - 4.0 * y * z;
-    }
-    return fmax(l, 0.0);
-}
-
-// Pure boost of p from the rest frame of q (invariant mass mq) to the frame where q is given.
-__device__ __forceinline__ P4 boost_out(P4 p, P4 q, double mq) {
-    double qp = q.x * p.x + q.y * p.y + q.z * p.z;
-    double inv = 1.0 / mq;
-    double c = qp / (mq * (q.e + mq)) + p.e * inv;
-    return {(q.e * p.e + qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
-}
-
-// The inverse boost: p given in the frame of q -> rest frame of q.
-__device__ __forceinline__ P4 boost_in(P4 p, P4 q, double mq) {
-    double qp = q.x * p.x + q.y * p.y + q.z * p.z;
-    double inv = 1.0 / mq;
-    double c = qp / (mq * (q.e + mq)) - p.e * inv;
-    return {(q.e * p.e - qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
-}
 
 using rng::philox4x32_10;
 using rng::unit_from_bits;
@@ -153,24 +107,6 @@ __device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin
     x = fmin(fmax(x, xmin), xmax);
     if (!ok) { x = xmin; jac = 0.0; }
     return ok;
-}
-
-// t range of a 2->2 block (Eq. t_invariant_theta): t = A + B cos(theta); the root of larger
-// magnitude directly, the other from t+ t- =
-//   (m1^2 - mA^2)(m2^2 - mB^2) + (m1^2 mB^2 - m2^2 mA^2)(m1^2 - m2^2 - mA^2 + mB^2)/s.
-__device__ __forceinline__ void t_range(double s, double mA2, double mB2, double m1, double m2,
-                                        double& tabs_min, double& tabs_max, double& B) {
-    double m12 = m1 * m1, m22 = m2 * m2;
-    double inv2s = 0.5 / s;
-    double A = mA2 + m12 - (s + mA2 - mB2) * (s + m12 - m22) * inv2s;
-    B = sqrt(kallen(s, mA2, mB2) * kallen(s, m12, m22)) * inv2s;
-    double prod = (m12 - mA2) * (m22 - mB2) + (m12 * mB2 - m22 * mA2) * (m12 - m22 - mA2 + mB2) / s;
-    double big = (A <= 0.0) ? A - B : A + B;   // root without cancellation
-    double small = (big != 0.0) ? prod / big : 0.0;
-    double tplus = (A <= 0.0) ? small : big;  // closest to zero
-    double tminus = (A <= 0.0) ? big : small;
-    tabs_min = -tplus;
-    tabs_max = -tminus;
 }
 
 // 2->2 block in (phi, t), Sec. 2.2.4: the polar axis is the direction of pA in the rest

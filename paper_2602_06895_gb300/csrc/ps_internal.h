@@ -95,6 +95,37 @@ struct LaunchParams {
     ChannelLaunch ch[kMaxChannels];
 };
 
+// ---------------------------------------------------------------- inverse map plan
+// Everything the inverse kernel needs about one channel, flattened on the host from its
+// ps_channel_desc (the same layout, bounds recipe and propagators as the forward builder).
+constexpr int kInvNodes = 32, kInvLegs = 10, kInvIds = 512, kInvProps = 40;
+struct InvNode {
+    int32_t kind, nch, leaf;
+    int32_t child[kInvLegs];
+    uint32_t mask;       // leaf-index bit mask of the subtree
+    double mass, M, G, nu;
+};
+struct InvPlan {
+    int32_t n, n_nodes, hadronic, lab_frame, kappa, n_sorder, n_pre, d, vdims, vbins;
+    double S, sqrt_s, a, shat_M, shat_G, shat_nu, t_nu, ts_nu, mleaf;
+    int32_t sorder[kInvNodes], pre[kInvNodes];
+    int32_t d_shat, d_x, d_s[kInvNodes], d_ts[kInvLegs + 1], d_tt[kInvLegs + 1], d_tphi[kInvLegs + 1];
+    int32_t d_dphi[kInvNodes], d_dth[kInvNodes];
+    int32_t order[kInvLegs + 2], side[kInvLegs + 1];
+    // s-order step i: m_min = lo_c + sum sqrt(s_id) over ids[lo_beg[i] .. off_beg[i]),
+    // m_max = m_top - (off_c + sum sqrt(s_id) over ids[off_beg[i] .. lo_beg[i+1])),
+    // m_top = sqrt(s_top) (sqrt_s for the root at fixed energy)
+    double lo_c[kInvNodes], off_c[kInvNodes];
+    int32_t top[kInvNodes], lo_beg[kInvNodes + 1], off_beg[kInvNodes + 1];
+    int32_t ids[kInvIds];
+    // propagators of the channel's SDE weight P(p): kind 0 s-channel (mask, M, G), 1 t-channel
+    int32_t n_prop, pkind[kInvProps];
+    uint32_t pmask[kInvProps];
+    double pM[kInvProps], pG[kInvProps];
+    InvNode node[kInvNodes];
+};
+int build_inverse_plan(const ps_channel_desc* d, InvPlan* plan, std::string* err);
+
 // kernels.cu
 int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem_bytes, void* stream, std::string* err);
 int launch_reduce(const LaunchParams& lp, double* stats_dev, void* stream, std::string* err);
@@ -103,5 +134,13 @@ int max_ctas_per_sm(int block, size_t smem_bytes, int mixed, int* out, std::stri
 // Device address and size of the fixed scratch of ps_generate_noalloc on `device` (which must be
 // current); the first call on a device looks the address up.
 int noalloc_scratch(int device, void** ptr, size_t* bytes, std::string* err);
+
+// inverse.cu
+int launch_inverse(const InvPlan& plan, int64_t batch, const double* mom, int64_t ld_m, const double* x1,
+                   const double* x2, const double* grid, double* r, int64_t ld_r, double* P, void* stream,
+                   std::string* err);
+int launch_global_weights(int n_ch, int64_t batch, const double* J, int64_t ld_j, const double* P, int64_t ld_p,
+                          const double* alpha, const double* x1, const double* x2, double pdf_a, double pdf_b,
+                          const double* f, double* w, void* stream, std::string* err);
 
 }  // namespace ps

@@ -107,6 +107,11 @@ _SIGS = {
     "ps_status_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ps_program_free": (C.c_int, [C.c_void_p]),
     "ps_launch_count": (C.c_int64, []),
+    "ps_inverse_map": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ChannelDesc), C.c_int64, C.c_void_p, C.c_int64,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ps_global_weights": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                    C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_double, C.c_double,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "ps_unweight_last_error": (C.c_char_p, []),
     "ps_unweight_workspace_size": (C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
     "ps_unweight_max": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_size_t,
@@ -421,6 +426,29 @@ class Program:
 
     def status_reset(self, stream=None):
         _check(lib().ps_status_reset(self.h, _stream_ptr(stream)), "ps_status_reset")
+
+
+def inverse_map(prog, ch, channel, momenta, x1, x2, r, P=None, stream=None):
+    """r = G^-1(p) of program channel `ch` (workload dict `channel`): momenta [4 (n+2), B] and
+    r [n_random, B] float64 CUDA tensors with unit stride along the events; x1, x2 [B] for hadronic
+    channels; P [B] receives the channel's SDE weight (optional)."""
+    B = momenta.shape[1]
+    for t in (momenta, r):
+        if t.dim() != 2 or (B > 1 and t.stride(1) != 1) or t.shape[1] < B:
+            raise PSError("momenta and r must be [rows, batch] tensors with unit stride along the batch")
+    d = channel_desc(channel)
+    _check(lib().ps_inverse_map(prog.h, ch, C.byref(d), B, _ptr(momenta), momenta.stride(0), _ptr(x1), _ptr(x2),
+                                _ptr(r), r.stride(0), _ptr(P), _stream_ptr(stream)), "ps_inverse_map")
+
+
+def global_weights(J, alphas, w, P=None, x1=None, x2=None, pdf=(0.0, 0.0), f=None, stream=None):
+    """Kleiss-Pittau weights w = f / sum_j alpha_j / J_j (ps_global_weights): J [M, B] (and P [M, B])
+    float64 CUDA tensors; f defaults to pdf(x1) pdf(x2) sum_j P_j."""
+    M, B = J.shape
+    al = (C.c_double * M)(*[float(a) for a in alphas])
+    ldp = P.stride(0) if P is not None else B
+    _check(lib().ps_global_weights(M, B, _ptr(J), J.stride(0), _ptr(P), ldp, al, _ptr(x1), _ptr(x2), float(pdf[0]),
+                                   float(pdf[1]), _ptr(f), _ptr(w), _stream_ptr(stream)), "ps_global_weights")
 
 
 class Exec:
