@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-multichannel", action="store_true")
+    ap.add_argument("--no-flow", action="store_true")
+    ap.add_argument("--no-unweight", action="store_true")
+    ap.add_argument("--no-global", action="store_true")
+    ap.add_argument("--flow-steps", type=int, default=400)
     return ap.parse_args()
 
 
@@ -150,6 +154,142 @@ def adapted_grid(ps, W, torch):
         prog.vegas_adapt(0, alpha=1.5)
     torch.cuda.synchronize()
     return prog.get_vegas(0, 8)
+
+
+def timed(torch, fn, reps, stream):
+    """Mean CUDA-event time (ms) of fn() over reps calls after one warm-up call."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+FLOW_LAYERS, FLOW_BINS, FLOW_HIDDEN, FLOW_BATCH = 6, 16, 128, 1 << 16
+
+
+def flow_leg(args, ps, W, torch, grid, vegas_ess_per_event, vegas_ms_per_event, stream):
+    """The learned proposal on C2's integrand: a 6-layer RQ-spline coupling flow (16 bins, MLP
+    2 x 128, BF16 tensor-core GEMMs) trained on the method's own weights in batches of 2^16 on top
+    of the adapted VEGAS grid, then 1e7 events drawn from it (sample -> explicit-input map -> flow
+    weights), against VEGAS alone on the same integrand."""
+    ch = W.ww_hadronic()
+    d = W.n_random_dims(ch)
+    prog = ps.program_for([ch])
+    prog.set_vegas(0, grid)
+    fl = ps.Flow(d, FLOW_LAYERS, FLOW_BINS, FLOW_HIDDEN, max_batch=FLOW_BATCH, init_seed=1004)
+    B = FLOW_BATCH
+    r = torch.empty((d, B), dtype=torch.float64, device="cuda")
+    ld = torch.empty(B, dtype=torch.float64, device="cuda")
+    out, ws = prog.alloc([B], 6)
+    step = [0]
+
+    def train_step():
+        fl.sample(B, 1004, r, ld, event_offset=step[0] * B)
+        prog.map(0, r, out, ws)
+        fl.train_step(out["weight"], 1e-3)
+        step[0] += 1
+
+    for _ in range(args.flow_steps - 10):
+        train_step()
+    train_ms = timed(torch, train_step, 9, stream)
+    loss, _ = fl.loss()
+    N = EVENTS
+    ri = torch.empty((d, N), dtype=torch.float64, device="cuda")
+    ldi = torch.empty(N, dtype=torch.float64, device="cuda")
+    oi, wsi = prog.alloc([N], 6)
+    wi = torch.empty(N, dtype=torch.float64, device="cuda")
+
+    def infer():
+        fl.sample(N, 2004, ri, ldi)
+        prog.map(0, ri, oi, wsi)
+        fl.weights(oi["weight"], ldi, wi)
+
+    sample_ms = timed(torch, lambda: fl.sample(N, 2004, ri, ldi), 2, stream)
+    infer_ms = timed(torch, infer, 2, stream)
+    w = wi
+    s1, s2 = float(w.sum()), float((w * w).sum())
+    ess = s1 * s1 / s2
+    # forward GEMM FLOPs per event: 2 (16 H + H^2 + H P_l) per layer, P_l = n_B (3K + 1) padded
+    flops = 0.0
+    for l in range(FLOW_LAYERS):
+        nb = len(fl.mask(l))
+        P = (nb * (3 * FLOW_BINS + 1) + 15) // 16 * 16
+        flops += 2.0 * (16 * FLOW_HIDDEN + FLOW_HIDDEN * FLOW_HIDDEN + FLOW_HIDDEN * P)
+    return {"workload": "C2 integrand, flow refining the adapted VEGAS grid: 6 coupling layers, 16 bins, "
+                        f"MLP 2 x 128, BF16 operands / FP32 accumulation, batches of 2^16, {args.flow_steps} "
+                        "Adam steps (lr 1e-3), inference on 1e7 events",
+            "train_ms_per_step": train_ms, "train_steps": args.flow_steps, "final_loss": loss,
+            "sample_ms_per_1e7": sample_ms, "inference_ms_per_1e7": infer_ms,
+            "ess_fraction_flow": ess / N, "ess_fraction_vegas": vegas_ess_per_event,
+            "ess_per_s_flow": ess / (infer_ms / 1e3),
+            "ess_per_s_vegas": vegas_ess_per_event / vegas_ms_per_event * 1e3,
+            "integral_flow": s1 / N,
+            "tensor_gflop_per_event": flops / 1e9,
+            "tensor_tflops_over_sample": flops * N / (sample_ms / 1e3) / 1e12,
+            "note": "ESS = (sum w)^2 / sum w^2; ESS/s counts the whole generation time of each sampler "
+                    "(no matrix element: the flow's gain per integrand call is ess_fraction_flow / "
+                    "ess_fraction_vegas)"}
+
+
+def unweight_leg(ps, torch, weights, stream):
+    """Unweighting of one step's 1e7 C2 weights: maximum weight with 0.1% over-weight share of the
+    cross section, then accept/reject and compaction."""
+    N = weights.numel()
+    uw = ps.Unweighter(N)
+    idx = torch.empty(N, dtype=torch.int64, device="cuda")
+    wo = torch.empty(N, dtype=torch.float64, device="cuda")
+    mx_ms = timed(torch, lambda: uw.max_weight(weights, 1e-3), 5, stream)
+    sel_ms = timed(torch, lambda: uw.select(weights, 1005, idx, wo), 5, stream)
+    res = uw.result.cpu().tolist()
+    na = int(uw.n_accepted.item())
+    return {"events": N, "eps_overweight": 1e-3, "max_weight_ms": mx_ms, "select_ms": sel_ms,
+            "events_per_s": N / ((mx_ms + sel_ms) / 1e3), "w_max": res[0], "n_over_w_max": int(res[3]),
+            "unweighting_efficiency": na / N, "accepted": na}
+
+
+def global_leg(ps, W, torch, stream):
+    """Global (Kleiss-Pittau) multichannel weights for C3: events of one channel reweighted with
+    the densities of all six channels (six GPU inverses, six density maps, one combination)."""
+    import numpy as np
+
+    chans = W.multichannel_2to5()
+    dens = [dict(c, integrand="none") for c in chans]
+    M = len(chans)
+    N = 1_000_000
+    prog = ps.program_for(chans)
+    dprog = ps.program_for(dens)
+    n_ev = [0, N, 0, 0, 0, 0]
+    out, ws = prog.alloc(n_ev, 7, alpha=True)
+    prog.generate(n_ev, 1006, out, ws)
+    J = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    P = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    rs = [torch.empty((W.n_random_dims(c), N), dtype=torch.float64, device="cuda") for c in chans]
+    outs = []
+    for j in range(M):
+        e = [0] * M
+        e[j] = N
+        outs.append(dprog.alloc(e, 7, x=True))
+    w = torch.empty(N, dtype=torch.float64, device="cuda")
+    alphas = np.full(M, 1.0 / M)
+
+    def step():
+        for j in range(M):
+            ps.inverse_map(prog, j, chans[j], out["momenta"], out["x1"], out["x2"], rs[j], P[j])
+            dprog.map(j, rs[j], outs[j][0], outs[j][1])
+            J[j].copy_(outs[j][0]["weight"])
+        ps.global_weights(J, alphas, w, P=P, x1=out["x1"], x2=out["x2"], pdf=chans[0]["pdf"])
+
+    ms = timed(torch, step, 3, stream)
+    inv_ms = timed(torch, lambda: ps.inverse_map(prog, 1, chans[1], out["momenta"], out["x1"], out["x2"], rs[1],
+                                                 P[1]), 3, stream)
+    return {"workload": "C3, 1e6 events of channel 1 reweighted with all six channel densities (alpha = 1/6)",
+            "events_per_s": N / (ms / 1e3), "ms_per_1e6": ms, "inverse_ms_per_1e6_one_channel": inv_ms,
+            "mean_w": float(w.mean())}
 
 
 def run_reference(args, rank, world):
@@ -329,6 +469,17 @@ def main():
                  "integral": sum(c["sum_w"] for c in cst) / 1.0,
                  "per_channel_sum_w": [c["sum_w"] for c in cst]}
 
+    flow = None
+    if not args.no_flow and rank == 0:
+        flow = flow_leg(args, ps, W, torch, grid, ess / N, ms / N, stream)
+    unweight = None
+    if not args.no_unweight and rank == 0:
+        prog.generate([N], SEED, out, ws)
+        unweight = unweight_leg(ps, torch, out["weight"], stream)
+    glob = None
+    if not args.no_global and rank == 0:
+        glob = global_leg(ps, W, torch, stream)
+
     flop = FP64_FLOP_PER_EVENT
     achieved = None if flop is None else flop * N / (ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
@@ -353,7 +504,8 @@ def main():
                                                         "ess_per_step": ess, "events_for_0.5pct": n_half_pct},
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
-            "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi}
+            "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi, "flow": flow,
+            "unweighting": unweight, "global_multichannel": glob}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -994,8 +994,23 @@ static int cuda_fail(cudaError_t e, const char* what, std::string* err) {
 int max_ctas_per_sm(int block, size_t smem, int mixed, int* out, std::string* err) {
     const void* fn = mixed ? reinterpret_cast<const void*>(ps_map_kernel<true>)
                            : reinterpret_cast<const void*>(ps_map_kernel<false>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", err);
+    // The dynamic shared-memory limit is a per-kernel, per-device setting shared by every program:
+    // it only ever grows, so a program created later with a smaller slot file cannot lower the
+    // limit below what an earlier program launches with.
+    static std::mutex mu;
+    static int limit[kMaxDevices][2] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", err);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        int& cur = limit[dev < kMaxDevices ? dev : 0][mixed ? 1 : 0];
+        if (static_cast<int>(smem) > cur) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", err);
+            cur = static_cast<int>(smem);
+        }
+    }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, block, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor", err);
     return PS_OK;

@@ -68,3 +68,18 @@ def test_autotune_returns_valid_choice(torch_cuda):
     assert min(t["ms"] for t in table) == next(t["ms"] for t in table if
                                                t["block_threads"] == best["block_threads"] and
                                                t["ctas_per_sm"] == best["ctas_per_sm"])
+
+
+def test_programs_with_different_slot_files_coexist(torch_cuda):
+    """A program created after another one with a larger shared-memory slot file must not lower
+    the kernel's dynamic shared-memory limit below what the first one launches with."""
+    torch = torch_cuda
+    big = ps.program_for(W.multichannel_2to5(), block_threads=128)
+    small = ps.program_for([W.two_body_fixed()], block_threads=64)
+    n = [0, 1000, 0, 0, 0, 0]
+    out, ws = big.alloc(n, 7, alpha=True)
+    big.generate(n, 3, out, ws)
+    o2, w2 = small.alloc([1000], 4, x=False)
+    small.generate([1000], 3, o2, w2)
+    torch.cuda.synchronize()
+    assert big.stats()[1]["n"] == 1000 and small.stats()[0]["n"] == 1000
