@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-unweight", action="store_true")
     ap.add_argument("--no-global", action="store_true")
     ap.add_argument("--flow-steps", type=int, default=400)
+    ap.add_argument("--flow-infer-events", type=int, default=EVENTS)
+    ap.add_argument("--leg", default="all", choices=["all", "flow", "unweight", "global"],
+                    help="run one secondary leg alone (for profiling); prints its object only")
     return ap.parse_args()
 
 
@@ -194,22 +197,22 @@ def flow_leg(args, ps, W, torch, grid, vegas_ess_per_event, vegas_ms_per_event, 
         fl.train_step(out["weight"], 1e-3)
         step[0] += 1
 
-    for _ in range(args.flow_steps - 10):
+    for _ in range(max(args.flow_steps - 10, 0)):
         train_step()
-    train_ms = timed(torch, train_step, 9, stream)
+    train_ms = timed(torch, train_step, min(9, max(args.flow_steps - 1, 1)), stream)
     loss, _ = fl.loss()
-    N = EVENTS
+    N = args.flow_infer_events
     ri = torch.empty((d, N), dtype=torch.float64, device="cuda")
     ldi = torch.empty(N, dtype=torch.float64, device="cuda")
     oi, wsi = prog.alloc([N], 6)
     wi = torch.empty(N, dtype=torch.float64, device="cuda")
 
     def infer():
-        fl.sample(N, 2004, ri, ldi)
+        fl.generate(N, 2004, ri, ldi)
         prog.map(0, ri, oi, wsi)
         fl.weights(oi["weight"], ldi, wi)
 
-    sample_ms = timed(torch, lambda: fl.sample(N, 2004, ri, ldi), 2, stream)
+    sample_ms = timed(torch, lambda: fl.generate(N, 2004, ri, ldi), 2, stream)
     infer_ms = timed(torch, infer, 2, stream)
     w = wi
     s1, s2 = float(w.sum()), float((w * w).sum())
@@ -222,15 +225,16 @@ def flow_leg(args, ps, W, torch, grid, vegas_ess_per_event, vegas_ms_per_event, 
         flops += 2.0 * (16 * FLOW_HIDDEN + FLOW_HIDDEN * FLOW_HIDDEN + FLOW_HIDDEN * P)
     return {"workload": "C2 integrand, flow refining the adapted VEGAS grid: 6 coupling layers, 16 bins, "
                         f"MLP 2 x 128, BF16 operands / FP32 accumulation, batches of 2^16, {args.flow_steps} "
-                        "Adam steps (lr 1e-3), inference on 1e7 events",
+                        f"Adam steps (lr 1e-3), inference on {N} events",
             "train_ms_per_step": train_ms, "train_steps": args.flow_steps, "final_loss": loss,
-            "sample_ms_per_1e7": sample_ms, "inference_ms_per_1e7": infer_ms,
+            "inference_events": N, "sample_ms": sample_ms, "inference_ms": infer_ms,
             "ess_fraction_flow": ess / N, "ess_fraction_vegas": vegas_ess_per_event,
             "ess_per_s_flow": ess / (infer_ms / 1e3),
             "ess_per_s_vegas": vegas_ess_per_event / vegas_ms_per_event * 1e3,
             "integral_flow": s1 / N,
             "tensor_gflop_per_event": flops / 1e9,
             "tensor_tflops_over_sample": flops * N / (sample_ms / 1e3) / 1e12,
+            "sampling_path": "ps_flow_generate: one fused kernel per coupling layer",
             "note": "ESS = (sum w)^2 / sum w^2; ESS/s counts the whole generation time of each sampler "
                     "(no matrix element: the flow's gain per integrand call is ess_fraction_flow / "
                     "ess_fraction_vegas)"}
@@ -348,6 +352,23 @@ def main():
     N = args.events
 
     grid = adapted_grid(ps, W, torch)
+    if args.leg != "all":  # one secondary leg alone
+        stream = torch.cuda.current_stream()
+        ch = W.ww_hadronic()
+        prog = ps.program_for([ch], device=local)
+        prog.set_vegas(0, grid)
+        out, ws = prog.alloc([N], 6, device=local)
+        ms = timed(torch, lambda: prog.generate([N], SEED, out, ws), 1, stream)
+        st = prog.stats()[0]
+        ess = st["sum_w"] ** 2 / st["sum_w2"]
+        if args.leg == "flow":
+            res = flow_leg(args, ps, W, torch, grid, ess / N, ms / N, stream)
+        elif args.leg == "unweight":
+            res = unweight_leg(ps, torch, out["weight"], stream)
+        else:
+            res = global_leg(ps, W, torch, stream)
+        print(json.dumps({"leg": args.leg, args.leg: res}), flush=True)
+        return
     ch = W.ww_hadronic()
     prog = ps.program_for([ch], device=local)
     prog.set_vegas(0, grid)

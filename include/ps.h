@@ -386,9 +386,18 @@ int ps_flow_set_params(ps_flow f, const float* host, int64_t n);
  * (it uses the activations of this call).  Asynchronous. */
 int ps_flow_sample(ps_flow f, int64_t batch, uint64_t seed, uint64_t event_offset, double* r, int64_t ld_r,
                    double* logdet, double* z, void* stream);
+/* Sampling for inference (no training step can follow): the same draws and outputs as
+ * ps_flow_sample, any batch size.  With hidden = 128, bins <= 18 and at most 8 transformed dims
+ * per layer, each layer runs as one fused kernel (the three GEMMs with the hidden activations in
+ * registers, then the splines; weights in shared memory); otherwise the layer-by-layer path.
+ * Allocates its 2^20-event working buffers on first use.  Asynchronous. */
+int ps_flow_generate(ps_flow f, int64_t batch, uint64_t seed, uint64_t event_offset, double* r, int64_t ld_r,
+                     double* logdet, double* z, void* stream);
 /* The inverse map: z = flow^-1(r) and logq[b] = log g(r_b) = -log |dr/dz| for `batch` points r
- * (device, SoA [dims][ld_r], double); z has the layout of r; logq may be null.  Runs in chunks
- * of max_batch; discards the activations of the last sample.  Asynchronous. */
+ * (device, SoA [dims][ld_r], double); z has the layout of r; logq may be null.  Uses the fused
+ * layer kernels where ps_flow_generate does (leaving the activations of the last sample intact);
+ * otherwise runs layer by layer in chunks of max_batch and discards those activations.
+ * Asynchronous. */
 int ps_flow_inverse(ps_flow f, int64_t batch, const double* r, int64_t ld_r, double* z, double* logq,
                     void* stream);
 /* w[b] = w_map[b] exp(logdet[b]) (non-finite -> 0); device pointers.  Asynchronous. */

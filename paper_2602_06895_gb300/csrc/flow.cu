@@ -191,25 +191,44 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
         }
         __syncthreads();
     }
+    // epilogue: element pairs (row, col..col+1) as one 8-byte / 4-byte store where the row is
+    // complete and aligned, else element by element
+    const bool pair_ok = !g.atomic && !g.trans_c && (g.ldc % 2 == 0) && (g.ldcb % 2 == 0) &&
+                         (reinterpret_cast<uintptr_t>(g.C) & 7) == 0 && (reinterpret_cast<uintptr_t>(g.Cb) & 3) == 0;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                int row = m0 + wm + i * 16 + gq + (e >= 2 ? 8 : 0);
-                int col = n0 + wn + j * 8 + 2 * tq + (e & 1);
-                if (row >= g.M || col >= g.N) continue;
-                float v = acc[i][j][e];
-                if (g.bias && blockIdx.z == 0) v += g.bias[col];
-                if (g.atomic) {
-                    atomicAdd(g.C + row * g.ldc + col, v);
-                } else if (g.trans_c) {
-                    g.C[col * g.ldc + row] = v;
-                } else {
-                    if (g.act == 2) v *= silu_grad(g.Zs[row * g.ldc + col]);
-                    if (g.C) g.C[row * g.ldc + col] = v;
-                    if (g.Cb) g.Cb[row * g.ldcb + col] = __float2bfloat16(g.act == 1 ? silu(v) : v);
+            for (int h = 0; h < 2; ++h) {
+                const int row = m0 + wm + i * 16 + gq + 8 * h;
+                const int col = n0 + wn + j * 8 + 2 * tq;
+                if (row >= g.M) continue;
+                float v[2] = {acc[i][j][2 * h], acc[i][j][2 * h + 1]};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (g.bias && blockIdx.z == 0 && col + e < g.N) v[e] += g.bias[col + e];
+                    if (g.act == 2 && col + e < g.N) v[e] *= silu_grad(g.Zs[row * g.ldc + col + e]);
+                }
+                if (pair_ok && col + 1 < g.N) {
+                    if (g.C) *reinterpret_cast<float2*>(g.C + row * g.ldc + col) = make_float2(v[0], v[1]);
+                    if (g.Cb) {
+                        const float a0 = g.act == 1 ? silu(v[0]) : v[0], a1 = g.act == 1 ? silu(v[1]) : v[1];
+                        *reinterpret_cast<__nv_bfloat162*>(g.Cb + row * g.ldcb + col) = __floats2bfloat162_rn(a0, a1);
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (col + e >= g.N) continue;
+                    if (g.atomic) {
+                        atomicAdd(g.C + row * g.ldc + col + e, v[e]);
+                    } else if (g.trans_c) {
+                        g.C[(col + e) * g.ldc + row] = v[e];
+                    } else {
+                        if (g.C) g.C[row * g.ldc + col + e] = v[e];
+                        if (g.Cb) g.Cb[row * g.ldcb + col + e] = __float2bfloat16(g.act == 1 ? silu(v[e]) : v[e]);
+                    }
                 }
             }
 }
@@ -502,7 +521,8 @@ __global__ void k_spline_backward(int64_t B, int d, int K, const float* Xl, cons
 
 // row sums of an [n][ldm] fp32 matrix over its first B columns into out[n] (atomic; bias
 // gradients of the last layer)
-__global__ void k_rowsum(int64_t B, int64_t ldm, const float* M, float* out) {
+__global__ void __launch_bounds__(256) k_rowsum(int64_t B, int64_t ldm, const float* M, float* out) {
+    __shared__ float ws[8];
     const int row = blockIdx.y;
     float s = 0.0f;
     for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < B;
@@ -510,7 +530,13 @@ __global__ void k_rowsum(int64_t B, int64_t ldm, const float* M, float* out) {
         s += M[row * ldm + c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out + row, s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < 8; ++w) t += ws[w];
+        atomicAdd(out + row, t);
+    }
 }
 
 // column sums of a [B, n] fp32 matrix into out[n] (atomic; bias gradients)
@@ -542,6 +568,213 @@ __global__ void k_weights(int64_t B, const double* wmap, const float* logdet, do
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(wsum, w);
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused coupling layer for sampling and density evaluation (no training): one persistent CTA
+// per SM holds the layer's weights in shared memory; each warp takes 16 events, runs the three
+// GEMMs on the tensor cores with the hidden activations kept in registers (the accumulator
+// fragment of two adjacent 8-column tiles is the operand fragment of the next 16-wide k-step),
+// stages the raw spline parameters of two transformed dims at a time in shared memory and
+// evaluates their splines, and updates X in place (the conditioning dims are never written).
+constexpr int kFH = 128;             // hidden width of the fused path
+constexpr int kFWarps = 8;
+constexpr int kQRows = 56;           // raw rows per transformed dim, padded to 7 tiles of 8
+constexpr int kStage = 57;           // staging row stride (floats; odd: conflict-free rows)
+constexpr int kW2S = kFH + 8;        // shared row stride (bf16) of W2 and W3
+constexpr int kW1S = kInPad + 8;     // shared row stride (bf16) of W1
+constexpr int kMaxNb = 8;
+
+struct FusedSmem {
+    static constexpr size_t w1 = 0;
+    static constexpr size_t w2 = w1 + sizeof(bf16) * kFH * kW1S;
+    static constexpr size_t w3 = w2 + sizeof(bf16) * kFH * kW2S;
+    static constexpr size_t b1 = w3 + sizeof(bf16) * kMaxNb * kQRows * kW2S;
+    static constexpr size_t b2 = b1 + sizeof(float) * kFH;
+    static constexpr size_t b3 = b2 + sizeof(float) * kFH;
+    static constexpr size_t stage = b3 + sizeof(float) * kMaxNb * kQRows;
+    static constexpr size_t total = stage + sizeof(float) * kFWarps * 2 * 16 * kStage;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <bool kInverse>
+__global__ void __launch_bounds__(kFWarps * 32, 1)
+    k_layer_fused(int64_t B, int d, int K, float* X, float* logdet, const __grid_constant__ LayerDesc ld,
+                  const bf16* W1, const float* b1, const bf16* W2, const float* b2, const bf16* W3,
+                  const float* b3) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    bf16* w1s = reinterpret_cast<bf16*>(smem + FusedSmem::w1);
+    bf16* w2s = reinterpret_cast<bf16*>(smem + FusedSmem::w2);
+    bf16* w3s = reinterpret_cast<bf16*>(smem + FusedSmem::w3);
+    float* b1s = reinterpret_cast<float*>(smem + FusedSmem::b1);
+    float* b2s = reinterpret_cast<float*>(smem + FusedSmem::b2);
+    float* b3s = reinterpret_cast<float*>(smem + FusedSmem::b3);
+    float* stage = reinterpret_cast<float*>(smem + FusedSmem::stage);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int per_q = 3 * K + 1;
+    const bf16 zero = __float2bfloat16(0.0f);
+
+    // weights and biases of the layer into shared memory
+    for (int i = tid; i < kFH * kInPad; i += blockDim.x) w1s[(i / kInPad) * kW1S + i % kInPad] = W1[i];
+    for (int i = tid; i < kFH * kFH / 8; i += blockDim.x) {
+        const int r = i / (kFH / 8), c = (i % (kFH / 8)) * 8;
+        *reinterpret_cast<uint4*>(w2s + r * kW2S + c) = *reinterpret_cast<const uint4*>(W2 + r * kFH + c);
+    }
+    for (int i = tid; i < ld.nb * kQRows * (kFH / 8); i += blockDim.x) {
+        const int r = i / (kFH / 8), c = (i % (kFH / 8)) * 8;
+        const int q = r / kQRows, k = r % kQRows;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (k < per_q) v = *reinterpret_cast<const uint4*>(W3 + (q * per_q + k) * kFH + c);
+        *reinterpret_cast<uint4*>(w3s + r * kW2S + c) = v;
+    }
+    for (int i = tid; i < kFH; i += blockDim.x) {
+        b1s[i] = b1[i];
+        b2s[i] = b2[i];
+    }
+    for (int i = tid; i < ld.nb * kQRows; i += blockDim.x) {
+        const int q = i / kQRows, k = i % kQRows;
+        b3s[i] = k < per_q ? b3[q * per_q + k] : 0.0f;
+    }
+    __syncthreads();
+    (void)zero;
+
+    float* st0 = stage + warp * 2 * 16 * kStage;
+    const int64_t n_tiles = (B + 16 * kFWarps - 1) / (16 * kFWarps);
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t e0 = tile * (16 * kFWarps) + warp * 16;
+        const int64_t ea = e0 + gq, eb = e0 + gq + 8;
+        auto in = [&](int64_t ev, int k) -> float {
+            return (ev < B && k < ld.na) ? X[ev * d + ld.ta[k]] : 0.0f;
+        };
+        uint32_t a0[4];
+        a0[0] = pack_bf16(in(ea, 2 * tq), in(ea, 2 * tq + 1));
+        a0[1] = pack_bf16(in(eb, 2 * tq), in(eb, 2 * tq + 1));
+        a0[2] = pack_bf16(in(ea, 2 * tq + 8), in(ea, 2 * tq + 9));
+        a0[3] = pack_bf16(in(eb, 2 * tq + 8), in(eb, 2 * tq + 9));
+
+        // layer 1: 16 x 128, K = 16; SiLU; bf16 operand fragments of layer 2
+        uint32_t a1[8][4];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int n = (2 * kk + h) * 8;
+                uint32_t bf[2];
+                bf[0] = *reinterpret_cast<const uint32_t*>(w1s + (n + gq) * kW1S + 2 * tq);
+                bf[1] = *reinterpret_cast<const uint32_t*>(w1s + (n + gq) * kW1S + 2 * tq + 8);
+                float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                mma16816(c, a0, bf);
+                const float bb0 = b1s[n + 2 * tq], bb1 = b1s[n + 2 * tq + 1];
+                a1[kk][2 * h] = pack_bf16(silu(c[0] + bb0), silu(c[1] + bb1));
+                a1[kk][2 * h + 1] = pack_bf16(silu(c[2] + bb0), silu(c[3] + bb1));
+            }
+        }
+        // layer 2: 16 x 128, K = 128
+        uint32_t a2[8][4];
+#pragma unroll
+        for (int kk2 = 0; kk2 < 8; ++kk2) {
+            float c[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int n = (2 * kk2 + h) * 8;
+                    uint32_t bf[2];
+                    bf[0] = *reinterpret_cast<const uint32_t*>(w2s + (n + gq) * kW2S + 16 * kk + 2 * tq);
+                    bf[1] = *reinterpret_cast<const uint32_t*>(w2s + (n + gq) * kW2S + 16 * kk + 2 * tq + 8);
+                    mma16816(c[h], a1[kk], bf);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int n = (2 * kk2 + h) * 8;
+                const float bb0 = b2s[n + 2 * tq], bb1 = b2s[n + 2 * tq + 1];
+                a2[kk2][2 * h] = pack_bf16(silu(c[h][0] + bb0), silu(c[h][1] + bb1));
+                a2[kk2][2 * h + 1] = pack_bf16(silu(c[h][2] + bb0), silu(c[h][3] + bb1));
+            }
+        }
+        // layer 3 and the splines, two transformed dims at a time
+        float lsum = 0.0f;
+        for (int qp = 0; qp < ld.nb; qp += 2) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int q = qp + s;
+                if (q >= ld.nb) break;
+                float c[7][4];
+#pragma unroll
+                for (int t = 0; t < 7; ++t) c[t][0] = c[t][1] = c[t][2] = c[t][3] = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+                    for (int t = 0; t < 7; ++t) {
+                        const bf16* wr = w3s + (q * kQRows + t * 8 + gq) * kW2S + 16 * kk + 2 * tq;
+                        uint32_t bf[2];
+                        bf[0] = *reinterpret_cast<const uint32_t*>(wr);
+                        bf[1] = *reinterpret_cast<const uint32_t*>(wr + 8);
+                        mma16816(c[t], a2[kk], bf);
+                    }
+                }
+                float* sq = st0 + s * 16 * kStage;
+#pragma unroll
+                for (int t = 0; t < 7; ++t) {
+                    const int col = t * 8 + 2 * tq;
+                    const float bb0 = b3s[q * kQRows + col], bb1 = b3s[q * kQRows + col + 1];
+                    sq[gq * kStage + col] = c[t][0] + bb0;
+                    sq[gq * kStage + col + 1] = c[t][1] + bb1;
+                    sq[(gq + 8) * kStage + col] = c[t][2] + bb0;
+                    sq[(gq + 8) * kStage + col + 1] = c[t][3] + bb1;
+                }
+            }
+            __syncwarp();
+            {
+                const int s = lane >> 4, row = lane & 15;
+                const int q = qp + s;
+                const int64_t ev = e0 + row;
+                if (q < ld.nb && ev < B) {
+                    const float* raw = st0 + s * 16 * kStage + row * kStage;
+                    const int j = ld.tb[q];
+                    const float v = fminf(fmaxf(X[ev * d + j], 0.0f), 1.0f);
+                    Bin bn = locate(raw, 1, K, v, kInverse);
+                    float F, Fp;
+                    if (!kInverse) {
+                        bin_eval<float>(v, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
+                        X[ev * d + j] = fminf(fmaxf(F, 1e-7f), 1.0f - 1e-7f);
+                        lsum += logf(Fp);
+                    } else {
+                        const float sl = bn.h / bn.w, dy = v - bn.y0, e = bn.d1 + bn.d0 - 2.0f * sl;
+                        const float qa = bn.h * (sl - bn.d0) + dy * e, qb = bn.h * bn.d0 - dy * e, qc = -sl * dy;
+                        const float disc = fmaxf(qb * qb - 4.0f * qa * qc, 0.0f);
+                        const float den = -qb - sqrtf(disc);
+                        const float xi = den != 0.0f ? fminf(fmaxf(2.0f * qc / den, 0.0f), 1.0f) : 0.0f;
+                        const float x = bn.x0 + xi * bn.w;
+                        bin_eval<float>(x, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
+                        X[ev * d + j] = fminf(fmaxf(x, 0.0f), 1.0f);
+                        lsum -= logf(Fp);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        lsum += __shfl_down_sync(0xffffffffu, lsum, 16);
+        if (lane < 16 && e0 + lane < B) logdet[e0 + lane] += lsum;
+    }
+}
+
+// out[j ldr + col0 + b] <- X[b d + j] (event-major float -> SoA double)
+__global__ void k_store_cols(int64_t B, int d, int64_t col0, int64_t ldr, const float* X, double* out) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b >= B) return;
+    for (int j = 0; j < d; ++j) out[j * ldr + col0 + b] = static_cast<double>(X[b * d + j]);
+}
+
+__global__ void k_store_ld(int64_t B, int64_t col0, const float* ld, double* out) {
+    int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (b < B) out[col0 + b] = static_cast<double>(ld[b]);
 }
 
 // X[L] <- r (SoA double -> event-major float)
@@ -655,6 +888,10 @@ struct ps_flow_s {
     double* wtot = nullptr;  // [max_batch]
     double* scal = nullptr;  // [0] sum w, [1] loss
     int Pmax = 0;
+    // buffers of the fused sampling / density path (allocated on first use)
+    int64_t gen_cap = 0;
+    float* gen_X = nullptr;   // [gen_cap][d]
+    float* gen_ld = nullptr;  // [gen_cap]
 };
 
 namespace {
@@ -667,7 +904,8 @@ void free_flow(ps_flow f) {
                     static_cast<void*>(f->logdet), static_cast<void*>(f->G), static_cast<void*>(f->Gb),
                     static_cast<void*>(f->dA), static_cast<void*>(f->dZ), static_cast<void*>(f->dZb), static_cast<void*>(f->dAb),
                     static_cast<void*>(f->dIn), static_cast<void*>(f->gX), static_cast<void*>(f->gXn),
-                    static_cast<void*>(f->wtot), static_cast<void*>(f->scal)})
+                    static_cast<void*>(f->wtot), static_cast<void*>(f->scal),
+                    static_cast<void*>(f->gen_X), static_cast<void*>(f->gen_ld)})
         cudaFree(q);
 }
 
@@ -800,8 +1038,8 @@ int backward(ps_flow f, int64_t B, cudaStream_t st) {
         g.M = ld.Ppad; g.N = H; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W3; g.ldc = H; g.atomic = 1;
         int s = gemm(g, split_for(ld.Ppad, H), st);
         if (s != PS_OK) return s;
-        k_rowsum<<<dim3(std::min<unsigned>(blocks(B, 256), 64), ld.Ppad), 256, 0, st>>>(B, ldg, f->G,
-                                                                                          f->grad + ld.off_b3);
+        k_rowsum<<<dim3(std::min<unsigned>(blocks(B, 256), 4), ld.Ppad), 256, 0, st>>>(B, ldg, f->G,
+                                                                                         f->grad + ld.off_b3);
         g = GemmArgs{};
         g.A = f->Gb; g.lam = 1; g.lak = ldg; g.B = f->pb + ld.off_W3; g.lbn = 1; g.lbk = H;
         g.M = static_cast<int>(B); g.N = H; g.K = ld.Ppad; g.C = f->dZ; g.ldc = H; g.Cb = f->dZb; g.ldcb = H;
@@ -839,6 +1077,51 @@ int backward(ps_flow f, int64_t B, cudaStream_t st) {
     }
     ps::count_launches(launches);
     return fcheck(cudaGetLastError(), "flow backward");
+}
+
+// the fused path covers hidden width 128, at most 18 bins and 8 transformed dims per layer
+bool fused_ok(const FlowDesc& fd) {
+    if (fd.H != kFH || 3 * fd.K + 1 > kQRows) return false;
+    for (int l = 0; l < fd.L; ++l)
+        if (fd.layer[l].nb > kMaxNb) return false;
+    return true;
+}
+
+int ensure_gen(ps_flow f) {
+    if (f->gen_X) return PS_OK;
+    const int64_t cap = int64_t(1) << 20;
+    int s = fcheck(cudaMalloc(&f->gen_X, cap * f->fd.d * sizeof(float)), "cudaMalloc (flow sampling)");
+    if (s == PS_OK) s = fcheck(cudaMalloc(&f->gen_ld, cap * sizeof(float)), "cudaMalloc (flow sampling)");
+    if (s != PS_OK) return s;
+    f->gen_cap = cap;
+    // the dynamic shared memory of the fused kernel exceeds the default limit
+    s = fcheck(cudaFuncSetAttribute(k_layer_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(FusedSmem::total)), "cudaFuncSetAttribute");
+    if (s == PS_OK)
+        s = fcheck(cudaFuncSetAttribute(k_layer_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(FusedSmem::total)), "cudaFuncSetAttribute");
+    return s;
+}
+
+// all layers of the fused path on X [B][d] in place, log-determinant accumulated into ld
+int fused_layers(ps_flow f, int64_t B, float* X, float* ld, bool inverse, cudaStream_t st) {
+    const FlowDesc& fd = f->fd;
+    const int64_t tiles = (B + 16 * kFWarps - 1) / (16 * kFWarps);
+    const unsigned grid = static_cast<unsigned>(std::min<int64_t>(f->sms, tiles));
+    for (int k = 0; k < fd.L; ++k) {
+        const int l = inverse ? fd.L - 1 - k : k;
+        const LayerDesc& lay = fd.layer[l];
+        if (inverse)
+            k_layer_fused<true><<<grid, kFWarps * 32, FusedSmem::total, st>>>(
+                B, fd.d, fd.K, X, ld, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2,
+                f->p + lay.off_b2, f->pb + lay.off_W3, f->p + lay.off_b3);
+        else
+            k_layer_fused<false><<<grid, kFWarps * 32, FusedSmem::total, st>>>(
+                B, fd.d, fd.K, X, ld, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2,
+                f->p + lay.off_b2, f->pb + lay.off_W3, f->p + lay.off_b3);
+    }
+    ps::count_launches(fd.L);
+    return fcheck(cudaGetLastError(), "k_layer_fused");
 }
 
 // padded device layout <-> logical layout (per layer W1[H][na], b1[H], W2[H][H], b2[H], W3[P][H], b3[P])
@@ -1053,6 +1336,42 @@ int ps_flow_sample(ps_flow f, int64_t batch, uint64_t seed, uint64_t event_offse
     return fcheck(cudaGetLastError(), "ps_flow_sample");
 }
 
+int ps_flow_generate(ps_flow f, int64_t batch, uint64_t seed, uint64_t event_offset, double* r, int64_t ld_r,
+                     double* logdet, double* z, void* stream) {
+    if (!f || batch < 0 || (batch > 0 && !r) || ld_r < batch)
+        return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_generate: bad arguments");
+    Guard g(f->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!fused_ok(f->fd)) {  // the layer-by-layer path, chunk by chunk
+        int s = ps_flow_sample(f, batch, seed, event_offset, r, ld_r, logdet, z, stream);
+        f->batch = 0;
+        return s;
+    }
+    int s = ensure_gen(f);
+    if (s != PS_OK) return s;
+    const int d = f->fd.d;
+    for (int64_t c0 = 0; c0 < batch; c0 += f->gen_cap) {
+        const int64_t B = std::min(f->gen_cap, batch - c0);
+        k_init_z<<<blocks(B, 256), 256, 0, st>>>(B, d, seed, event_offset + static_cast<uint64_t>(c0), f->gen_X);
+        cudaMemsetAsync(f->gen_ld, 0, B * sizeof(float), st);
+        int n = 1;
+        if (z) {
+            k_store_cols<<<blocks(B, 256), 256, 0, st>>>(B, d, c0, ld_r, f->gen_X, z);
+            ++n;
+        }
+        s = fused_layers(f, B, f->gen_X, f->gen_ld, false, st);
+        if (s != PS_OK) return s;
+        k_store_cols<<<blocks(B, 256), 256, 0, st>>>(B, d, c0, ld_r, f->gen_X, r);
+        ++n;
+        if (logdet) {
+            k_store_ld<<<blocks(B, 256), 256, 0, st>>>(B, c0, f->gen_ld, logdet);
+            ++n;
+        }
+        ps::count_launches(n);
+    }
+    return fcheck(cudaGetLastError(), "ps_flow_generate");
+}
+
 int ps_flow_inverse(ps_flow f, int64_t batch, const double* r, int64_t ld_r, double* z, double* logq,
                     void* stream) {
     if (!f || batch < 0 || (batch > 0 && (!r || !z)) || ld_r < batch)
@@ -1060,6 +1379,25 @@ int ps_flow_inverse(ps_flow f, int64_t batch, const double* r, int64_t ld_r, dou
     Guard g(f->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int d = f->fd.d;
+    if (fused_ok(f->fd)) {
+        int s = ensure_gen(f);
+        if (s != PS_OK) return s;
+        for (int64_t c0 = 0; c0 < batch; c0 += f->gen_cap) {
+            const int64_t B = std::min(f->gen_cap, batch - c0);
+            k_load_r<<<blocks(B, 256), 256, 0, st>>>(B, d, c0, ld_r, r, f->gen_X);
+            cudaMemsetAsync(f->gen_ld, 0, B * sizeof(float), st);
+            s = fused_layers(f, B, f->gen_X, f->gen_ld, true, st);
+            if (s != PS_OK) return s;
+            k_store_cols<<<blocks(B, 256), 256, 0, st>>>(B, d, c0, ld_r, f->gen_X, z);
+            int n = 2;
+            if (logq) {
+                k_store_ld<<<blocks(B, 256), 256, 0, st>>>(B, c0, f->gen_ld, logq);
+                ++n;
+            }
+            ps::count_launches(n);
+        }
+        return fcheck(cudaGetLastError(), "ps_flow_inverse");
+    }
     float* XL = f->X + static_cast<int64_t>(f->fd.L) * f->max_batch * d;
     for (int64_t c0 = 0; c0 < batch; c0 += f->max_batch) {
         int64_t B = std::min(f->max_batch, batch - c0);

@@ -129,6 +129,8 @@ _SIGS = {
     "ps_flow_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
     "ps_flow_sample": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
+    "ps_flow_generate": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p, C.c_int64,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "ps_flow_inverse": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
     "ps_flow_weights": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -572,6 +574,15 @@ class Flow:
         ld = r.stride(0)
         _fcheck(lib().ps_flow_sample(self.h, batch, seed, event_offset, _ptr(r), ld, _ptr(logdet), _ptr(z),
                                      _stream_ptr(stream)), "ps_flow_sample")
+
+    def generate(self, batch, seed, r, logdet=None, z=None, event_offset=0, stream=None):
+        """Inference sampling (ps_flow_generate): same outputs as sample(), any batch size."""
+        if r.dim() != 2 or r.shape[0] != self.dims or r.shape[1] < batch or (r.shape[1] > 1 and r.stride(1) != 1):
+            raise PSError("r must be a [dims, batch] tensor with unit stride along the batch")
+        if z is not None and z.stride() != r.stride():
+            raise PSError("z must have the layout of r")
+        _fcheck(lib().ps_flow_generate(self.h, batch, seed, event_offset, _ptr(r), r.stride(0), _ptr(logdet),
+                                       _ptr(z), _stream_ptr(stream)), "ps_flow_generate")
 
     def inverse(self, r, z, logq=None, stream=None):
         """z = flow^-1(r), logq = log g(r): float64 CUDA tensors [dims, batch] and [batch]."""

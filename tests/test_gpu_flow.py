@@ -231,7 +231,7 @@ def test_training_beats_the_vegas_grid(torch_cuda):
     fl_eval = fl  # inference in chunks of max_batch
     r = torch.empty((d, n_eval), dtype=torch.float64, device="cuda")
     ld = torch.empty(n_eval, dtype=torch.float64, device="cuda")
-    fl_eval.sample(n_eval, 999, r, ld)
+    fl_eval.generate(n_eval, 999, r, ld)
     out_e, ws_e = prog.alloc([n_eval], 6)
     prog.map(0, r, out_e, ws_e)
     w = torch.empty(n_eval, dtype=torch.float64, device="cuda")
@@ -243,3 +243,53 @@ def test_training_beats_the_vegas_grid(torch_cuda):
     se = math.sqrt((var_vegas * mean_vegas ** 2 + var_flow * mean_flow ** 2) / n_eval)
     assert abs(mean_flow - mean_vegas) <= 5 * se, (mean_flow, mean_vegas, se)
     assert var_flow < var_vegas, (var_flow, var_vegas)
+
+
+@pytest.mark.parametrize("B", [1, 4099, 300_001])
+def test_fused_generate_matches_layer_by_layer_and_oracle(torch_cuda, B):
+    """ps_flow_generate (one fused kernel per layer) against ps_flow_sample (GEMM / spline
+    kernels per layer) on the same draws, and against the oracle on a sample of events."""
+    torch = torch_cuda
+    fl = ps.Flow(D, L, K, H, max_batch=4160)
+    p, orc, _ = random_params(fl, 15)
+    fl.set_params(p)
+    r = torch.empty((D, B), dtype=torch.float64, device="cuda")
+    ld = torch.empty(B, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    fl.generate(B, 8, r, ld, z, event_offset=3)
+    r2 = torch.empty_like(r)
+    ld2 = torch.empty_like(ld)
+    z2 = torch.empty_like(r)
+    fl.sample(B, 8, r2, ld2, z2, event_offset=3)
+    torch.cuda.synchronize()
+    assert torch.equal(z, z2)
+    assert torch.max(torch.abs(r - r2)).item() <= 1e-5, torch.max(torch.abs(r - r2)).item()
+    assert torch.max(torch.abs(ld - ld2)).item() <= 1e-3
+    idx = torch.arange(0, B, max(1, B // 4096), device="cuda")
+    r_o, ld_o = orc.forward(z[:, idx].T.cpu(), bf=True)
+    dr = np.abs(r[:, idx].T.cpu().numpy() - r_o.numpy())
+    dl = np.abs(ld[idx].cpu().numpy() - ld_o.numpy())
+    assert dr.max() <= 2e-3 and dr.mean() <= 1e-4, (dr.max(), dr.mean())
+    assert dl.max() <= 2e-2 and dl.mean() <= 1e-3, (dl.max(), dl.mean())
+
+
+def test_layer_by_layer_inverse_and_generate_fallback(torch_cuda):
+    """A flow outside the fused kernel's shape (hidden 64) inverts and generates layer by layer."""
+    torch = torch_cuda
+    fl = ps.Flow(D, 4, 8, 64, max_batch=2048)
+    p, orc, _ = random_params(fl, 16)
+    fl.set_params(p)
+    B = 3000
+    r = torch.empty((D, B), dtype=torch.float64, device="cuda")
+    ld = torch.empty(B, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    fl.generate(B, 9, r, ld, z)
+    zb = torch.empty_like(r)
+    lq = torch.empty_like(ld)
+    fl.inverse(r, zb, lq)
+    torch.cuda.synchronize()
+    r_o, ld_o = orc.forward(z.T.cpu(), bf=True)
+    assert np.abs(r.T.cpu().numpy() - r_o.numpy()).max() <= 2e-3
+    z_o, lq_o = orc.inverse(r.T.cpu(), bf=True)
+    assert np.abs(zb.T.cpu().numpy() - z_o.numpy()).max() <= 2e-3
+    assert np.abs(lq.cpu().numpy() - lq_o.numpy()).max() <= 2e-2
