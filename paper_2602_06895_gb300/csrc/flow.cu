@@ -66,9 +66,11 @@ struct GemmArgs {
     int a_vec, b_vec;  // 1: the operand's base is 16-byte aligned (16-byte loads allowed)
 };
 
-__device__ __forceinline__ float silu(float x) { return x / (1.0f + __expf(-x)); }
+// SiLU x sigma(x) with the hardware exponential and reciprocal (a few ulp in FP32, far below the
+// bfloat16 rounding that follows); for x -> -inf the denominator overflows and the result is 0.
+__device__ __forceinline__ float silu(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
 __device__ __forceinline__ float silu_grad(float x) {
-    const float s = 1.0f / (1.0f + __expf(-x));
+    const float s = __fdividef(1.0f, 1.0f + __expf(-x));
     return s * (1.0f + x * (1.0f - s));
 }
 
@@ -370,6 +372,76 @@ __device__ __forceinline__ Bin locate(const float* raw, int64_t ld, int K, float
     return b;
 }
 
+// locate() for a compile-time bin count and unit stride: the raw parameters are read once into
+// registers, each exponential is taken once and the bin search is unrolled into selects.  Same
+// operations in the same order as locate(), so the results agree bit for bit.
+template <int K>
+__device__ __forceinline__ Bin locate_fixed(const float* raw, int64_t ld, float v, bool by_height) {
+    float w[K], h[K];
+    float mw = -INFINITY, mh = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        w[i] = raw[i * ld];
+        h[i] = raw[(K + i) * ld];
+        mw = fmaxf(mw, w[i]);
+        mh = fmaxf(mh, h[i]);
+    }
+    float zw = 0.0f, zh = 0.0f;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        w[i] = __expf(w[i] - mw);
+        h[i] = __expf(h[i] - mh);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) zw += w[i];
+#pragma unroll
+    for (int i = 0; i < K; ++i) zh += h[i];
+    Bin b;
+    b.mw = mw;
+    b.mh = mh;
+    b.iw = 1.0f / zw;
+    b.ih = 1.0f / zh;
+    const float cw = 1.0f - K * kMinW, chh = 1.0f - K * kMinH;
+    float cx = 0.0f, cy = 0.0f, csx = 0.0f, csy = 0.0f;
+    bool found = false;
+    b.k = K - 1;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const float pw = w[i] * b.iw, ph = h[i] * b.ih;
+        const float ww = kMinW + cw * pw, hh = kMinH + chh * ph;
+        const bool hit = !found && (i == K - 1 || (by_height ? v < cy + hh : v < cx + ww));
+        if (hit) {
+            b.k = i;
+            b.x0 = cx;
+            b.y0 = cy;
+            b.sx = csx;
+            b.sy = csy;
+            b.w = ww;
+            b.h = hh;
+            b.pw = pw;
+            b.ph = ph;
+            found = true;
+        }
+        cx += ww;
+        cy += hh;
+        csx += pw;
+        csy += ph;
+    }
+    const float a0 = raw[(2 * K + b.k) * ld], a1 = raw[(2 * K + b.k + 1) * ld];
+    b.d0 = kMinD + softplus(a0);
+    b.d1 = kMinD + softplus(a1);
+    b.sg0 = sigmoid(a0);
+    b.sg1 = sigmoid(a1);
+    return b;
+}
+
+// locate() with the compile-time path when the bin count matches kK
+template <int kK>
+__device__ __forceinline__ Bin locate_k(const float* raw, int64_t ld, int K, float v, bool by_height) {
+    if constexpr (kK > 0) return locate_fixed<kK>(raw, ld, v, by_height);
+    else return locate(raw, ld, K, v, by_height);
+}
+
 // ------------------------------------------------------------------------------------------
 struct LayerDesc {
     int nb, na;             // transformed / conditioning dims
@@ -408,6 +480,7 @@ __global__ void k_gather(int64_t B, int d, const float* X, const __grid_constant
 
 // forward spline of one layer: Xout = Xin with the B dims through F; logdet += sum log F'.
 // Praw is parameter-major: raw parameter p of event b at Praw[p * ldp + b].
+template <int kK>
 __global__ void k_spline_forward(int64_t B, int d, int K, const float* Xin, float* Xout, const float* Praw,
                                  int64_t ldp, const __grid_constant__ LayerDesc ld, float* logdet) {
     int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -418,7 +491,7 @@ __global__ void k_spline_forward(int64_t B, int d, int K, const float* Xin, floa
         const float* raw = Praw + static_cast<int64_t>(q) * (3 * K + 1) * ldp + b;
         int j = ld.tb[q];
         float x = fminf(fmaxf(Xin[b * d + j], 0.0f), 1.0f);
-        Bin bn = locate(raw, ldp, K, x, false);
+        Bin bn = locate_k<kK>(raw, ldp, K, x, false);
         float F, Fp;
         bin_eval<float>(x, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
         Xout[b * d + j] = fminf(fmaxf(F, 1e-7f), 1.0f - 1e-7f);
@@ -428,6 +501,7 @@ __global__ void k_spline_forward(int64_t B, int d, int K, const float* Xin, floa
 }
 
 // inverse spline of one layer: Xout = Xin with the B dims through F^-1; logq -= sum log F'(x)
+template <int kK>
 __global__ void k_spline_inverse(int64_t B, int d, int K, const float* Xin, float* Xout, const float* Praw,
                                  int64_t ldp, const __grid_constant__ LayerDesc ld, float* logq) {
     int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -438,7 +512,7 @@ __global__ void k_spline_inverse(int64_t B, int d, int K, const float* Xin, floa
         const float* raw = Praw + static_cast<int64_t>(q) * (3 * K + 1) * ldp + b;
         int j = ld.tb[q];
         float y = fminf(fmaxf(Xin[b * d + j], 0.0f), 1.0f);
-        Bin bn = locate(raw, ldp, K, y, true);
+        Bin bn = locate_k<kK>(raw, ldp, K, y, true);
         // y - y_k = h [s xi^2 + d0 xi (1-xi)] / [s + (d1 + d0 - 2s) xi (1-xi)] is a quadratic in xi;
         // the root in [0,1] in the form free of cancellation: xi = 2c / (-b - sqrt(b^2 - 4ac))
         float s = bn.h / bn.w, dy = y - bn.y0, e = bn.d1 + bn.d0 - 2.0f * s;
@@ -459,6 +533,7 @@ __global__ void k_spline_inverse(int64_t B, int d, int K, const float* Xin, floa
 // and the event coefficient c_b = w_b / sum w; outputs the raw-parameter adjoint G (fp32 and
 // bf16, parameter-major like Praw, padding rows zeroed) and the adjoint of x^(l+1) in gXn (the
 // conditioning dims get the MLP part later).
+template <int kK>
 __global__ void k_spline_backward(int64_t B, int d, int K, const float* Xl, const float* Praw, int64_t ldp,
                                   const __grid_constant__ LayerDesc ld, const float* gX, const double* wtot,
                                   const double* wsum, float* G, bf16* Gb, float* gXn, double* loss) {
@@ -473,7 +548,7 @@ __global__ void k_spline_backward(int64_t B, int d, int K, const float* Xl, cons
             const float* raw = Praw + row0 * ldp + b;
             int j = ld.tb[q];
             float xv = fminf(fmaxf(Xl[b * d + j], 0.0f), 1.0f);
-            Bin bn = locate(raw, ldp, K, xv, false);
+            Bin bn = locate_k<kK>(raw, ldp, K, xv, false);
             Dual F, Fp;
             bin_eval<Dual>(dvar(xv, 0), dvar(bn.x0, 1), dvar(bn.w, 2), dvar(bn.y0, 3), dvar(bn.h, 4), dvar(bn.d0, 5),
                            dvar(bn.d1, 6), F, Fp);
@@ -596,12 +671,31 @@ struct FusedSmem {
     static constexpr size_t total = stage + sizeof(float) * kFWarps * 2 * 16 * kStage;
 };
 
+// B-operand fragments of two adjacent 8-column tiles (16 rows n0.., one 16-wide k step at k0) of
+// a [n][k] bf16 matrix in shared memory: ldmatrix.x4 of the four 8x8 blocks; r[0..1] belong to
+// the tile at n0, r[2..3] to the tile at n0 + 8.
+__device__ __forceinline__ void ldsm_b2(uint32_t (&r)[4], const bf16* base, int stride, int n0, int k0, int lane) {
+    const int mi = lane >> 3, row = lane & 7;
+    const bf16* p = base + (n0 + (mi >> 1) * 8 + row) * stride + k0 + (mi & 1) * 8;
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+// one 8-column tile
+__device__ __forceinline__ void ldsm_b1(uint32_t (&r)[2], const bf16* base, int stride, int n0, int k0, int lane) {
+    const int mi = (lane >> 3) & 1, row = lane & 7;
+    const bf16* p = base + (n0 + row) * stride + k0 + mi * 8;
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <bool kInverse>
+template <bool kInverse, int kK>  // kK: compile-time bin count, or 0 for the runtime K
 __global__ void __launch_bounds__(kFWarps * 32, 1)
     k_layer_fused(int64_t B, int d, int K, float* X, float* logdet, const __grid_constant__ LayerDesc ld,
                   const bf16* W1, const float* b1, const bf16* W2, const float* b2, const bf16* W3,
@@ -657,45 +751,53 @@ __global__ void __launch_bounds__(kFWarps * 32, 1)
         a0[2] = pack_bf16(in(ea, 2 * tq + 8), in(ea, 2 * tq + 9));
         a0[3] = pack_bf16(in(eb, 2 * tq + 8), in(eb, 2 * tq + 9));
 
-        // layer 1: 16 x 128, K = 16; SiLU; bf16 operand fragments of layer 2
+        // layer 1: 16 x 128, K = 16 (all 16 tiles issued before their epilogues); SiLU; the bf16
+        // operand fragments of layer 2
         uint32_t a1[8][4];
+        {
+            float c[16][4];
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+            for (int p2 = 0; p2 < 8; ++p2) {
+                uint32_t bq[4];
+                ldsm_b2(bq, w1s, kW1S, 16 * p2, 0, lane);
+                const uint32_t b0[2] = {bq[0], bq[1]}, b1v[2] = {bq[2], bq[3]};
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int n = (2 * kk + h) * 8;
-                uint32_t bf[2];
-                bf[0] = *reinterpret_cast<const uint32_t*>(w1s + (n + gq) * kW1S + 2 * tq);
-                bf[1] = *reinterpret_cast<const uint32_t*>(w1s + (n + gq) * kW1S + 2 * tq + 8);
-                float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                mma16816(c, a0, bf);
+                for (int e = 0; e < 4; ++e) c[2 * p2][e] = c[2 * p2 + 1][e] = 0.0f;
+                mma16816(c[2 * p2], a0, b0);
+                mma16816(c[2 * p2 + 1], a0, b1v);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt) {
+                const int n = nt * 8;
                 const float bb0 = b1s[n + 2 * tq], bb1 = b1s[n + 2 * tq + 1];
-                a1[kk][2 * h] = pack_bf16(silu(c[0] + bb0), silu(c[1] + bb1));
-                a1[kk][2 * h + 1] = pack_bf16(silu(c[2] + bb0), silu(c[3] + bb1));
+                a1[nt >> 1][2 * (nt & 1)] = pack_bf16(silu(c[nt][0] + bb0), silu(c[nt][1] + bb1));
+                a1[nt >> 1][2 * (nt & 1) + 1] = pack_bf16(silu(c[nt][2] + bb0), silu(c[nt][3] + bb1));
             }
         }
-        // layer 2: 16 x 128, K = 128
+        // layer 2: 16 x 128, K = 128, eight independent 8-column accumulators per half
         uint32_t a2[8][4];
 #pragma unroll
-        for (int kk2 = 0; kk2 < 8; ++kk2) {
-            float c[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+        for (int half = 0; half < 2; ++half) {
+            float c[8][4];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) c[t][0] = c[t][1] = c[t][2] = c[t][3] = 0.0f;
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int n = (2 * kk2 + h) * 8;
-                    uint32_t bf[2];
-                    bf[0] = *reinterpret_cast<const uint32_t*>(w2s + (n + gq) * kW2S + 16 * kk + 2 * tq);
-                    bf[1] = *reinterpret_cast<const uint32_t*>(w2s + (n + gq) * kW2S + 16 * kk + 2 * tq + 8);
-                    mma16816(c[h], a1[kk], bf);
+                for (int p2 = 0; p2 < 4; ++p2) {
+                    uint32_t bq[4];
+                    ldsm_b2(bq, w2s, kW2S, 64 * half + 16 * p2, 16 * kk, lane);
+                    const uint32_t b0[2] = {bq[0], bq[1]}, b1v[2] = {bq[2], bq[3]};
+                    mma16816(c[2 * p2], a1[kk], b0);
+                    mma16816(c[2 * p2 + 1], a1[kk], b1v);
                 }
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int n = (2 * kk2 + h) * 8;
+            for (int t = 0; t < 8; ++t) {
+                const int nt = 8 * half + t, n = nt * 8;
                 const float bb0 = b2s[n + 2 * tq], bb1 = b2s[n + 2 * tq + 1];
-                a2[kk2][2 * h] = pack_bf16(silu(c[h][0] + bb0), silu(c[h][1] + bb1));
-                a2[kk2][2 * h + 1] = pack_bf16(silu(c[h][2] + bb0), silu(c[h][3] + bb1));
+                a2[nt >> 1][2 * (nt & 1)] = pack_bf16(silu(c[t][0] + bb0), silu(c[t][1] + bb1));
+                a2[nt >> 1][2 * (nt & 1) + 1] = pack_bf16(silu(c[t][2] + bb0), silu(c[t][3] + bb1));
             }
         }
         // layer 3 and the splines, two transformed dims at a time
@@ -711,13 +813,16 @@ __global__ void __launch_bounds__(kFWarps * 32, 1)
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk) {
 #pragma unroll
-                    for (int t = 0; t < 7; ++t) {
-                        const bf16* wr = w3s + (q * kQRows + t * 8 + gq) * kW2S + 16 * kk + 2 * tq;
-                        uint32_t bf[2];
-                        bf[0] = *reinterpret_cast<const uint32_t*>(wr);
-                        bf[1] = *reinterpret_cast<const uint32_t*>(wr + 8);
-                        mma16816(c[t], a2[kk], bf);
+                    for (int p2 = 0; p2 < 3; ++p2) {
+                        uint32_t bq[4];
+                        ldsm_b2(bq, w3s, kW2S, q * kQRows + 16 * p2, 16 * kk, lane);
+                        const uint32_t b0[2] = {bq[0], bq[1]}, b1v[2] = {bq[2], bq[3]};
+                        mma16816(c[2 * p2], a2[kk], b0);
+                        mma16816(c[2 * p2 + 1], a2[kk], b1v);
                     }
+                    uint32_t bl[2];
+                    ldsm_b1(bl, w3s, kW2S, q * kQRows + 48, 16 * kk, lane);
+                    mma16816(c[6], a2[kk], bl);
                 }
                 float* sq = st0 + s * 16 * kStage;
 #pragma unroll
@@ -739,7 +844,7 @@ __global__ void __launch_bounds__(kFWarps * 32, 1)
                     const float* raw = st0 + s * 16 * kStage + row * kStage;
                     const int j = ld.tb[q];
                     const float v = fminf(fmaxf(X[ev * d + j], 0.0f), 1.0f);
-                    Bin bn = locate(raw, 1, K, v, kInverse);
+                    Bin bn = locate_k<kK>(raw, 1, K, v, kInverse);
                     float F, Fp;
                     if (!kInverse) {
                         bin_eval<float>(v, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
@@ -980,7 +1085,8 @@ int forward(ps_flow f, int64_t B, uint64_t seed, uint64_t ev0, cudaStream_t st) 
         int s = mlp(f, l, B, Xl, st);
         if (s != PS_OK) return s;
         const float* P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
-        k_spline_forward<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xl, Xn, P, f->max_batch, ld, f->logdet);
+        auto kf = fd.K == 16 ? k_spline_forward<16> : k_spline_forward<0>;
+        kf<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xl, Xn, P, f->max_batch, ld, f->logdet);
     }
     ps::count_launches(1 + fd.L);
     return fcheck(cudaGetLastError(), "flow forward");
@@ -999,7 +1105,8 @@ int inverse(ps_flow f, int64_t B, cudaStream_t st) {
         int s = mlp(f, l, B, Xn, st);
         if (s != PS_OK) return s;
         const float* P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
-        k_spline_inverse<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xn, Xl, P, f->max_batch, ld, f->logdet);
+        auto ki = fd.K == 16 ? k_spline_inverse<16> : k_spline_inverse<0>;
+        ki<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xn, Xl, P, f->max_batch, ld, f->logdet);
     }
     ps::count_launches(fd.L);
     return fcheck(cudaGetLastError(), "flow inverse");
@@ -1030,8 +1137,9 @@ int backward(ps_flow f, int64_t B, cudaStream_t st) {
         bf16* A2 = f->A2 + static_cast<int64_t>(l) * f->max_batch * H;
         float* P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
         const int64_t ldg = f->max_batch;  // G, Gb and Praw are parameter-major
-        k_spline_backward<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xl, P, ldg, ld, f->gX, f->wtot, f->scal, f->G,
-                                                        f->Gb, f->gXn, f->scal + 1);
+        auto kb = fd.K == 16 ? k_spline_backward<16> : k_spline_backward<0>;
+        kb<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xl, P, ldg, ld, f->gX, f->wtot, f->scal, f->G, f->Gb, f->gXn,
+                                       f->scal + 1);
         // last linear layer: dW3 += G^T A2, db3 += colsum G, dA2 = G W3
         GemmArgs g{};
         g.A = f->Gb; g.lam = ldg; g.lak = 1; g.B = A2; g.lbn = 1; g.lbk = H;
@@ -1095,11 +1203,12 @@ int ensure_gen(ps_flow f) {
     if (s != PS_OK) return s;
     f->gen_cap = cap;
     // the dynamic shared memory of the fused kernel exceeds the default limit
-    s = fcheck(cudaFuncSetAttribute(k_layer_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(FusedSmem::total)), "cudaFuncSetAttribute");
-    if (s == PS_OK)
-        s = fcheck(cudaFuncSetAttribute(k_layer_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        static_cast<int>(FusedSmem::total)), "cudaFuncSetAttribute");
+    for (auto kern : {k_layer_fused<false, 16>, k_layer_fused<false, 0>, k_layer_fused<true, 16>,
+                      k_layer_fused<true, 0>})
+        if (s == PS_OK)
+            s = fcheck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(FusedSmem::total)),
+                       "cudaFuncSetAttribute");
     return s;
 }
 
@@ -1111,14 +1220,11 @@ int fused_layers(ps_flow f, int64_t B, float* X, float* ld, bool inverse, cudaSt
     for (int k = 0; k < fd.L; ++k) {
         const int l = inverse ? fd.L - 1 - k : k;
         const LayerDesc& lay = fd.layer[l];
-        if (inverse)
-            k_layer_fused<true><<<grid, kFWarps * 32, FusedSmem::total, st>>>(
-                B, fd.d, fd.K, X, ld, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2,
-                f->p + lay.off_b2, f->pb + lay.off_W3, f->p + lay.off_b3);
-        else
-            k_layer_fused<false><<<grid, kFWarps * 32, FusedSmem::total, st>>>(
-                B, fd.d, fd.K, X, ld, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2,
-                f->p + lay.off_b2, f->pb + lay.off_W3, f->p + lay.off_b3);
+        auto kern = inverse ? (fd.K == 16 ? k_layer_fused<true, 16> : k_layer_fused<true, 0>)
+                            : (fd.K == 16 ? k_layer_fused<false, 16> : k_layer_fused<false, 0>);
+        kern<<<grid, kFWarps * 32, FusedSmem::total, st>>>(B, fd.d, fd.K, X, ld, lay, f->pb + lay.off_W1,
+                                                            f->p + lay.off_b1, f->pb + lay.off_W2, f->p + lay.off_b2,
+                                                            f->pb + lay.off_W3, f->p + lay.off_b3);
     }
     ps::count_launches(fd.L);
     return fcheck(cudaGetLastError(), "k_layer_fused");
