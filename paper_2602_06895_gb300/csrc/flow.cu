@@ -299,16 +299,23 @@ __device__ __forceinline__ Dual operator*(const Dual& a, float b) { return b * a
 
 // The bin formula: y = y_k + h [s xi^2 + d0 xi(1-xi)] / [s + (d1 + d0 - 2s) xi (1-xi)] and its
 // derivative F' = s^2 [d1 xi^2 + 2 s xi (1-xi) + d0 (1-xi)^2] / [..]^2, s = h/w, xi = (x-x_k)/w.
+// reciprocals of the bin formula: the hardware reciprocal in FP32 (w >= 1e-3, den > 0), exact
+// division for the dual numbers of the backward pass
+__device__ __forceinline__ float brcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ Dual brcp(const Dual& a) { return dconst(1.0f) / a; }
+
 template <typename T>
 __device__ __forceinline__ void bin_eval(const T& x, const T& x0, const T& w, const T& y0, const T& h, const T& d0,
                                          const T& d1, T& F, T& Fp) {
-    T xi = (x - x0) / w;
-    T s = h / w;
+    const T iw = brcp(w);
+    T xi = (x - x0) * iw;
+    T s = h * iw;
     T om = xi - xi * xi;
     T xm = xi - 1.0f;
     T den = s + (d1 + d0 - 2.0f * s) * om;
-    F = y0 + h * (s * xi * xi + d0 * om) / den;
-    Fp = s * s * (d1 * xi * xi + 2.0f * s * om + d0 * (xm * xm)) / (den * den);
+    const T iden = brcp(den);
+    F = y0 + h * (s * xi * xi + d0 * om) * iden;
+    Fp = s * s * (d1 * xi * xi + 2.0f * s * om + d0 * (xm * xm)) * (iden * iden);
 }
 
 __device__ __forceinline__ float softplus(float a) { return a > 20.0f ? a : log1pf(__expf(a)); }
@@ -495,7 +502,7 @@ __global__ void k_spline_forward(int64_t B, int d, int K, const float* Xin, floa
         float F, Fp;
         bin_eval<float>(x, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
         Xout[b * d + j] = fminf(fmaxf(F, 1e-7f), 1.0f - 1e-7f);
-        acc += logf(Fp);
+        acc += __logf(Fp);
     }
     logdet[b] += acc;
 }
@@ -524,7 +531,7 @@ __global__ void k_spline_inverse(int64_t B, int d, int K, const float* Xin, floa
         float F, Fp;
         bin_eval<float>(x, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
         Xout[b * d + j] = fminf(fmaxf(x, 0.0f), 1.0f);
-        acc += logf(Fp);
+        acc += __logf(Fp);
     }
     logq[b] -= acc;
 }
@@ -849,7 +856,7 @@ __global__ void __launch_bounds__(kFWarps * 32, 1)
                     if (!kInverse) {
                         bin_eval<float>(v, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
                         X[ev * d + j] = fminf(fmaxf(F, 1e-7f), 1.0f - 1e-7f);
-                        lsum += logf(Fp);
+                        lsum += __logf(Fp);
                     } else {
                         const float sl = bn.h / bn.w, dy = v - bn.y0, e = bn.d1 + bn.d0 - 2.0f * sl;
                         const float qa = bn.h * (sl - bn.d0) + dy * e, qb = bn.h * bn.d0 - dy * e, qc = -sl * dy;
@@ -859,7 +866,7 @@ __global__ void __launch_bounds__(kFWarps * 32, 1)
                         const float x = bn.x0 + xi * bn.w;
                         bin_eval<float>(x, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
                         X[ev * d + j] = fminf(fmaxf(x, 0.0f), 1.0f);
-                        lsum -= logf(Fp);
+                        lsum -= __logf(Fp);
                     }
                 }
             }
