@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libps.so")
 
 PS_OK = 0
+PS_ERR_INVALID_ARGUMENT, PS_ERR_GRAPH, PS_ERR_CUDA, PS_ERR_DEVICE_STATUS, PS_ERR_CAPACITY, PS_ERR_NO_DEVICE = -1, -2, -3, -4, -5, -6
 MAX_NODES, MAX_LEGS = 32, 10
 
 # opcodes (include/ps.h)

@@ -91,3 +91,34 @@ def test_program_without_device_fails_loudly(built):
     g = ps.build_channel([W.two_body_fixed()], 0)
     with pytest.raises(ps.PSError):
         ps.Program([g])
+
+
+def test_flow_unweight_inverse_argument_checks(built):
+    """The flow, unweighting, inverse and global-weight entry points reject bad arguments on the
+    host, before touching a device."""
+    import ctypes as C
+
+    L = built
+    h = C.c_void_p()
+    assert L.ps_flow_create(1, 6, 16, 128, 1024, 1, 0, C.byref(h)) == ps.PS_ERR_INVALID_ARGUMENT  # dims < 2
+    assert L.ps_flow_create(10, 9, 16, 128, 1024, 1, 0, C.byref(h)) == ps.PS_ERR_INVALID_ARGUMENT  # > 8 layers
+    assert L.ps_flow_create(10, 6, 16, 100, 1024, 1, 0, C.byref(h)) == ps.PS_ERR_INVALID_ARGUMENT  # hidden % 16
+    assert L.ps_flow_create(10, 6, 33, 128, 1024, 1, 0, C.byref(h)) == ps.PS_ERR_INVALID_ARGUMENT  # > 32 bins
+    assert L.ps_flow_sample(None, 10, 1, 0, None, 10, None, None, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_flow_generate(None, 10, 1, 0, None, 10, None, None, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_flow_train_step(None, None, 1e-3, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_flow_free(None) == 0
+    n = C.c_size_t()
+    assert L.ps_unweight_workspace_size(-1, C.byref(n)) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_unweight_workspace_size(10_000_000, C.byref(n)) == 0 and n.value > 8 * 10_000_000 // 2048
+    assert L.ps_unweight_max(None, 10, 1e-3, None, None, 0, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_unweight_max(None, 0, -1.0, None, None, 0, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_unweight_select(None, 10, None, 1, 0, None, None, None, None, 0, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_inverse_map(None, 0, None, 10, None, 10, None, None, None, 10, None, None) == \
+        ps.PS_ERR_INVALID_ARGUMENT
+    al = (C.c_double * 2)(0.5, -0.5)
+    assert L.ps_global_weights(2, 0, None, 0, None, 0, al, None, None, 0.0, 0.0, None, None, None) == \
+        ps.PS_ERR_INVALID_ARGUMENT  # negative channel weight
+    assert L.ps_global_weights(0, 0, None, 0, None, 0, al, None, None, 0.0, 0.0, None, None, None) == \
+        ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_flow_last_error().decode()  # the last failure left a message
