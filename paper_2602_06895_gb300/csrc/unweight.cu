@@ -3,17 +3,22 @@
 // Maximum weight with a bounded over-weight share: w_max(eps) is the smallest t >= 0 with
 //     sum_b max(0, w_b - t) <= eps * sum_b w_b.
 // The excess is continuous and decreasing in t.  Non-negative doubles order like their bit
-// patterns, so the root is located by a radix search over the bits of t: each pass splits the
-// current bit range [lo, hi) into 256 buckets, histograms count and sum of the weights per
-// bucket, and keeps the bucket in which the excess crosses eps S (the excess at a bucket's lower
-// edge T follows from the counts and sums of all weights >= T).  The search stops when the kept
-// bucket holds no weight (or is one bit pattern wide); then no weight lies strictly between the
-// root and the bucket's upper edge, and w_max = (A - eps S) / K in closed form, A and K the sum
-// and count of the weights above.  At most 8 passes (64 bits / 8 bits per pass).
+// patterns, so the root is located by a radix search over the bits of t, most significant byte
+// first: pass p splits the current range [lo, lo + 2^(64-8p)) into 256 buckets by the byte at
+// bits 56-8p, histograms count and sum of the weights per bucket, and keeps the bucket in which
+// the excess crosses eps S (the excess at a bucket's lower edge T follows from the counts and sums
+// of all weights >= T).  The search stops when the kept bucket holds no weight (or is one bit
+// pattern wide); then no weight lies strictly between the root and the bucket's upper edge, and
+// w_max = (A - eps S) / K in closed form, A and K the sum and count of the weights above.  At most
+// 8 passes.
 //
-// Every sum has a fixed order for a given batch size (per-block partials over a fixed grid,
-// warp-private histograms filled in lane order by owner lanes, blocks combined in index order),
-// so the result is reproducible bit for bit.
+// The bucket sums are exact integers: a weight m 2^(e-1075) (53-bit significand m, exponent
+// field e) enters its bucket as m 2^(e-E) in units of 2^(E-1075), E the exponent field of the
+// bucket's largest bit pattern, accumulated in 128 bits.  Integer addition does not depend on
+// order, so shared-memory atomics keep the result reproducible bit for bit; the truncation of the
+// low bits of weights below the bucket's top binade costs at most one unit of 2^(E-1075) per
+// weight (relative 2^-48 of a bucket sum spanning up to 16 binades).  The total sum and the
+// maximum are per-block partials over a fixed grid, combined in block order.
 //
 // Accept/reject: event b is kept iff u_b w_max < w_b, u_b the first uniform of the generator's
 // Philox point of event (event_offset + b) in stream 0x556E7700; kept events carry max(w_b, w_max)
@@ -33,7 +38,6 @@ namespace uw {
 
 constexpr int kGrid = 512;          // blocks of the reductions and histograms (fixed: reproducible sums)
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 constexpr int kBuckets = 256;
 constexpr int kPasses = 8;
 constexpr int kSelPerThread = 8;    // events per thread in the select kernels
@@ -42,6 +46,7 @@ constexpr uint32_t kStream = 0x556E7700u;
 
 struct State {
     unsigned long long lo, hi;          // current bit range of the root, [lo, hi)
+    int shift;                          // the bucket digit of the next pass: bits shift .. shift+7
     double S, target, wmax;
     double carry_sum;                   // sum and count of the weights >= hi
     unsigned long long carry_cnt;
@@ -50,7 +55,27 @@ struct State {
     int done;
 };
 
-__device__ __forceinline__ bool valid(double w) { return w >= 0.0 && w <= 1.7976931348623157e308; }
+// finite and non-negative, decided on the bit pattern (sign clear, exponent field not all ones)
+__device__ __forceinline__ bool valid_bits(unsigned long long u) { return (u >> 52) < 0x7FFULL; }
+__device__ __forceinline__ bool valid(double w) {
+    return valid_bits(static_cast<unsigned long long>(__double_as_longlong(w)));
+}
+
+// exponent field of the largest bit pattern of bucket j (the bucket's fixed-point unit)
+__device__ __forceinline__ int bucket_exp(unsigned long long lo, unsigned long long step, unsigned long long hi, int j) {
+    unsigned long long top = lo + static_cast<unsigned long long>(j + 1) * step;  // wraps to 0 only at 2^64
+    if (top == 0 || top > hi) top = hi;
+    return static_cast<int>((top - 1) >> 52);
+}
+
+// significand of a non-negative finite double scaled to units of 2^(E-1075)
+// (subnormals have the unit of exponent field 1; a bucket of subnormals only uses that unit)
+__device__ __forceinline__ unsigned long long fixed_units(unsigned long long u, int E) {
+    const int e = static_cast<int>(u >> 52);
+    const unsigned long long m = (u & 0xFFFFFFFFFFFFFULL) | (e > 0 ? (1ULL << 52) : 0ULL);
+    const int sh = (E > 0 ? E : 1) - (e > 0 ? e : 1);
+    return sh >= 64 ? 0ULL : (m >> sh);
+}
 
 // per-block partials of sum, max and the number of invalid (negative or non-finite) weights
 __global__ void __launch_bounds__(kThreads) k_partials(const double* w, int64_t n, double* part) {
@@ -103,6 +128,7 @@ __global__ void k_init(const double* part, double eps, State* st) {
     s.target = eps * S;
     s.lo = 0;
     s.hi = static_cast<unsigned long long>(__double_as_longlong(m)) + 1;
+    s.shift = 56;
     s.carry_sum = 0.0;
     s.carry_cnt = 0;
     s.done = 0;
@@ -116,74 +142,87 @@ __global__ void k_init(const double* part, double eps, State* st) {
     *st = s;
 }
 
-// one radix pass: per-block histogram of count and sum over the 256 buckets of [lo, hi)
-__global__ void __launch_bounds__(kThreads) k_hist(const double* w, int64_t n, const State* st, double* hsum,
+// one radix pass: per-block histogram of count and exact sum over the 256 buckets of [lo, hi)
+__global__ void __launch_bounds__(kThreads) k_hist(const double* w, int64_t n, const State* st,
+                                                   unsigned long long* hlo, unsigned long long* hhi,
                                                    unsigned int* hcnt) {
-    __shared__ double ws[kWarps][kBuckets];
-    __shared__ unsigned int wc[kWarps][kBuckets];
+    __shared__ unsigned long long slo[kBuckets], shi[kBuckets];
+    __shared__ unsigned int sc[kBuckets];
+    __shared__ int sexp[kBuckets];
     if (st->done) return;
     const unsigned long long lo = st->lo, hi = st->hi;
-    const unsigned long long step = (hi - lo + kBuckets - 1) / kBuckets;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = lane; j < kBuckets; j += 32) {
-        ws[warp][j] = 0.0;
-        wc[warp][j] = 0;
+    const int shift = st->shift;
+    const unsigned long long step = 1ULL << shift;
+    for (int j = threadIdx.x; j < kBuckets; j += kThreads) {
+        slo[j] = 0;
+        shi[j] = 0;
+        sc[j] = 0;
+        sexp[j] = bucket_exp(lo, step, hi, j);
     }
-    __syncwarp();
+    __syncthreads();
     const int64_t chunk = (n + kGrid - 1) / kGrid;
     const int64_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
-    for (int64_t base = b0 + warp * 32; base < b1; base += kThreads) {
-        const int64_t i = base + lane;
-        double v = 0.0;
-        int bk = -1;
-        if (i < b1) {
-            v = w[i];
-            if (valid(v)) {
-                unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v));
-                if (u >= lo && u < hi) bk = static_cast<int>((u - lo) / step);
-            }
-        }
-        // lane order, each bucket updated only by its owner lane (bucket mod 32)
-        for (int src = 0; src < 32; ++src) {
-            const double sv = __shfl_sync(0xffffffffu, v, src);
-            const int sb = __shfl_sync(0xffffffffu, bk, src);
-            if (sb >= 0 && (sb & 31) == lane) {
-                ws[warp][sb] += sv;
-                wc[warp][sb] += 1;
-            }
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = b0; base < b1; base += kThreads) {  // block-uniform trip count (warp collectives)
+        const int64_t i = base + threadIdx.x;
+        const unsigned long long u = i < b1 ? static_cast<unsigned long long>(__double_as_longlong(w[i])) : ~0ULL;
+        const bool in = valid_bits(u) && u >= lo && u < hi;
+        const int bk = in ? static_cast<int>((u - lo) >> shift) : -1;
+        const unsigned long long v = in ? fixed_units(u, sexp[bk]) : 0ULL;
+        // lanes of one bucket combine first: exact 21-bit limb sums, one leader per bucket
+        const unsigned grp = __match_any_sync(0xffffffffu, bk);
+        const unsigned l0 = __reduce_add_sync(grp, static_cast<unsigned>(v & 0x1FFFFF));
+        const unsigned l1 = __reduce_add_sync(grp, static_cast<unsigned>((v >> 21) & 0x1FFFFF));
+        const unsigned l2 = __reduce_add_sync(grp, static_cast<unsigned>(v >> 42));
+        if (in && lane == __ffs(grp) - 1) {
+            // sum = l0 + l1 2^21 + l2 2^42 < 2^64 * 2^5: low 64 bits and the carry out
+            const unsigned long long t1 = static_cast<unsigned long long>(l1) << 21;
+            const unsigned long long t2 = static_cast<unsigned long long>(l2) << 42;
+            unsigned long long sum = static_cast<unsigned long long>(l0) + t1;
+            unsigned long long carry = 0;
+            const unsigned long long s2 = sum + t2;
+            if (s2 < sum) ++carry;
+            carry += static_cast<unsigned long long>(l2) >> 22;  // bits of l2 2^42 above 2^64
+            sum = s2;
+            const unsigned long long old = atomicAdd(&slo[bk], sum);
+            if (old + sum < old) ++carry;
+            if (carry) atomicAdd(&shi[bk], carry);
+            atomicAdd(&sc[bk], static_cast<unsigned>(__popc(grp)));
         }
     }
     __syncthreads();
     for (int j = threadIdx.x; j < kBuckets; j += kThreads) {
-        double s = 0.0;
-        unsigned int c = 0;
-        for (int k = 0; k < kWarps; ++k) {
-            s += ws[k][j];
-            c += wc[k][j];
-        }
-        hsum[blockIdx.x * kBuckets + j] = s;
-        hcnt[blockIdx.x * kBuckets + j] = c;
+        hlo[blockIdx.x * kBuckets + j] = slo[j];
+        hhi[blockIdx.x * kBuckets + j] = shi[j];
+        hcnt[blockIdx.x * kBuckets + j] = sc[j];
     }
 }
 
-// combine the block histograms in block order and choose the bucket holding the root
-__global__ void __launch_bounds__(kBuckets) k_decide(const double* hsum, const unsigned int* hcnt, State* st) {
+// combine the block histograms (exact 128-bit sums) and choose the bucket holding the root
+__global__ void __launch_bounds__(kBuckets) k_decide(const unsigned long long* hlo, const unsigned long long* hhi,
+                                                     const unsigned int* hcnt, State* st) {
     __shared__ double bs[kBuckets];
     __shared__ unsigned long long bc[kBuckets];
     if (st->done) return;
     const int j = threadIdx.x;
-    double s = 0.0;
-    unsigned long long c = 0;
+    const unsigned long long step0 = 1ULL << st->shift;
+    unsigned long long slo = 0, shi = 0, c = 0;
     for (int b = 0; b < kGrid; ++b) {
-        s += hsum[b * kBuckets + j];
+        const unsigned long long v = hlo[b * kBuckets + j];
+        slo += v;
+        if (slo < v) ++shi;
+        shi += hhi[b * kBuckets + j];
         c += hcnt[b * kBuckets + j];
     }
-    bs[j] = s;
+    // value = (shi 2^64 + slo) 2^(E - 1075)
+    const int E = bucket_exp(st->lo, step0, st->hi, j);
+    const int scale = (E > 0 ? E : 1) - 1075;
+    bs[j] = ldexp(static_cast<double>(shi) * 18446744073709551616.0 + static_cast<double>(slo), scale);
     bc[j] = c;
     __syncthreads();
     if (j != 0) return;
     State x = *st;
-    const unsigned long long step = (x.hi - x.lo + kBuckets - 1) / kBuckets;
+    const unsigned long long step = 1ULL << x.shift;
     double cum_s = x.carry_sum;
     unsigned long long cum_c = x.carry_cnt;
     int sel = 0;
@@ -211,6 +250,7 @@ __global__ void __launch_bounds__(kBuckets) k_decide(const double* hsum, const u
     x.hi = new_hi;
     x.carry_sum = cum_s;
     x.carry_cnt = cum_c;
+    x.shift -= 8;
     if (bc[sel] == 0 || step == 1) {
         // no weight strictly inside (lo, hi): excess(t) = A - t K on [lo, hi]
         double t = cum_c > 0 ? (cum_s - x.target) / static_cast<double>(cum_c) : 0.0;
@@ -335,7 +375,7 @@ int ucheck(cudaError_t e, const char* what) {
 }
 constexpr size_t kStateBytes = 256;
 constexpr size_t kPartBytes = sizeof(double) * 3 * kGrid;
-constexpr size_t kHistBytes = (sizeof(double) + sizeof(unsigned int)) * kGrid * kBuckets;
+constexpr size_t kHistBytes = (2 * sizeof(unsigned long long) + sizeof(unsigned int)) * kGrid * kBuckets;
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 int64_t sel_blocks(int64_t n) { return (n + kSelBlock - 1) / kSelBlock; }
 }  // namespace
@@ -362,13 +402,14 @@ int ps_unweight_max(const double* w, int64_t n, double eps, double* result, void
     char* base = static_cast<char*>(workspace);
     State* state = reinterpret_cast<State*>(base);
     double* part = reinterpret_cast<double*>(base + kStateBytes);
-    double* hsum = reinterpret_cast<double*>(base + kStateBytes + align256(kPartBytes));
-    unsigned int* hcnt = reinterpret_cast<unsigned int*>(hsum + static_cast<size_t>(kGrid) * kBuckets);
+    unsigned long long* hlo = reinterpret_cast<unsigned long long*>(base + kStateBytes + align256(kPartBytes));
+    unsigned long long* hhi = hlo + static_cast<size_t>(kGrid) * kBuckets;
+    unsigned int* hcnt = reinterpret_cast<unsigned int*>(hhi + static_cast<size_t>(kGrid) * kBuckets);
     k_partials<<<kGrid, kThreads, 0, st>>>(w, n, part);
     k_init<<<1, 32, 0, st>>>(part, eps, state);
     for (int p = 0; p < kPasses; ++p) {
-        k_hist<<<kGrid, kThreads, 0, st>>>(w, n, state, hsum, hcnt);
-        k_decide<<<1, kBuckets, 0, st>>>(hsum, hcnt, state);
+        k_hist<<<kGrid, kThreads, 0, st>>>(w, n, state, hlo, hhi, hcnt);
+        k_decide<<<1, kBuckets, 0, st>>>(hlo, hhi, hcnt, state);
     }
     k_result<<<1, 32, 0, st>>>(state, result);
     ps::count_launches(3 + 2 * kPasses);
