@@ -388,8 +388,10 @@ int ps_flow_sample(ps_flow f, int64_t batch, uint64_t seed, uint64_t event_offse
                    double* logdet, double* z, void* stream);
 /* Sampling for inference (no training step can follow): the same draws and outputs as
  * ps_flow_sample, any batch size.  With hidden = 128, bins <= 18 and at most 8 transformed dims
- * per layer, each layer runs as one fused kernel (the three GEMMs with the hidden activations in
- * registers, then the splines; weights in shared memory); otherwise the layer-by-layer path.
+ * per layer, each layer runs as one fused kernel (the three GEMMs, then the splines; weights in
+ * shared memory): with 16 bins on the tcgen05 tensor cores (FP32 accumulators in TMEM, one event
+ * per TMEM lane), otherwise with warp-level MMAs and the hidden activations in registers.  Other
+ * shapes run layer by layer.
  * Allocates its 2^20-event working buffers on first use.  Asynchronous. */
 int ps_flow_generate(ps_flow f, int64_t batch, uint64_t seed, uint64_t event_offset, double* r, int64_t ld_r,
                      double* logdet, double* z, void* stream);
@@ -408,6 +410,9 @@ int ps_flow_train_step(ps_flow f, const double* w_map, double lr, void* stream);
 /* The loss gradient of the last sampled batch in the logical layout (host, n = n_params) and
  * the loss value, without updating parameters.  Synchronises `stream`. */
 int ps_flow_gradients(ps_flow f, const double* w_map, float* host, int64_t n, double* loss, void* stream);
+/* Number of tensor-core completion waits of the fused sampling kernels that ran out (each wait
+ * is bounded; a timeout leaves that tile's outputs invalid).  0 in a healthy run.  Synchronous. */
+int ps_flow_status(ps_flow f, int64_t* timeouts);
 /* Loss and sum of w of the last train_step / gradients call.  Synchronises `stream`. */
 int ps_flow_loss(ps_flow f, double* loss, double* sum_w, void* stream);
 

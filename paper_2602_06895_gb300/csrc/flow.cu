@@ -877,6 +877,358 @@ __global__ void __launch_bounds__(kFWarps * 32, 1)
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Fused coupling layer on the 5th-generation tensor cores (tcgen05), for sampling and density
+// evaluation with hidden width 128 and 16 bins.  A CTA takes 128 events per tile, one event per
+// TMEM lane: the three GEMMs are single-thread tcgen05.mma issues (M = 128; operands in shared
+// memory in the K-major canonical layout of 8-row x 16-byte core matrices; FP32 accumulators in
+// TMEM), and each epilogue thread reads its own event's row back with tcgen05.ld -- the SiLU of
+// the hidden layers writes the next operand tile, and the raw spline parameters of a transformed
+// dim arrive in that thread's registers, so the spline needs no staging.  8 warps: warpgroup g
+// takes columns 64g..64g+63 of the hidden layers and the dim 2p+g of each pair p of transformed
+// dims.  Every wait on the tensor cores is bounded; on a timeout the kernel records it in the
+// status word, still frees its TMEM and returns.
+namespace umma {
+
+constexpr int kTile = 128;        // events per tile (TMEM lanes)
+constexpr int kThreads = 256;
+constexpr int kPairRows = 128;    // B rows of one pair of transformed dims: 49 + 15 zero rows each
+constexpr int kTmemCols = 256;    // [0,128) hidden accumulators, [128,256) raw parameters
+
+struct Smem {
+    static constexpr size_t w1 = 0;                                    // 128 x 16 bf16
+    static constexpr size_t w2 = w1 + 128 * kInPad * 2;                // 128 x 128
+    static constexpr size_t w3 = w2 + 128 * 128 * 2;                   // up to 4 pairs x 128 x 128
+    static constexpr size_t in = w3 + 4 * kPairRows * 128 * 2;         // 128 x 16 operand tile
+    static constexpr size_t act = in + kTile * kInPad * 2;             // 128 x 128 operand tile
+    static constexpr size_t b1 = act + kTile * 128 * 2;
+    static constexpr size_t b2 = b1 + 128 * 4;
+    static constexpr size_t b3 = b2 + 128 * 4;                         // 8 x 56 floats
+    static constexpr size_t ld = b3 + 8 * 56 * 4;                      // 128 floats: log-det exchange
+    static constexpr size_t total = ld + kTile * 4;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// element offset of (row, k) in a [rows][K] K-major canonical tile
+__device__ __forceinline__ int coff(int row, int k, int K) {
+    return (((row >> 3) * (K >> 3) + (k >> 3)) * 8 + (row & 7)) * 8 + (k & 7);
+}
+
+// shared-memory matrix descriptor: start, leading (K-direction) and stride (row-direction)
+// byte offsets between core matrices, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return static_cast<uint64_t>((addr >> 4) & 0x3FFF) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32) | (static_cast<uint64_t>(1) << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128
+__device__ __forceinline__ uint32_t idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+}
+
+// D[tmem] (+)= A[128 x K] B[n x K]^T over K in steps of 16 (one thread)
+__device__ __forceinline__ void mma_chain(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, int K, int n) {
+    const uint32_t sbo = (K / 8) * 128, id = idesc(n);
+    for (int s = 0; s < K / 16; ++s) {
+        const uint64_t ad = sdesc(a_addr + s * 256, 128, sbo), bd = sdesc(b_addr + s * 256, 128, sbo);
+        const uint32_t acc = s > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(id), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(mbar)));
+}
+
+// bounded wait for the given phase of the mbarrier; false on timeout
+__device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t phase) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(su32(mbar)), "r"(phase));
+        if (done) return true;
+    }
+    return false;
+}
+
+#define PS_TMEM_LD32(v, addr)                                                                                   \
+    asm volatile(                                                                                               \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"                                    \
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),       \
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), \
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),            \
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),            \
+          "=r"(v[30]), "=r"(v[31])                                                                            \
+        : "r"(addr))
+#define PS_TMEM_LD16(v, addr)                                                                                   \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, " \
+                 "[%16];\n"                                                                                     \
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), \
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),      \
+                   "=r"(v[15])                                                                                  \
+                 : "r"(addr))
+#define PS_TMEM_LD8(v, addr)                                                                                    \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"                     \
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]) \
+                 : "r"(addr))
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 64 hidden columns of this thread's event: + bias, SiLU, bf16 into the operand tile
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, bf16* act, int row, int c0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        PS_TMEM_LD32(v, taddr + c0 + 32 * h);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+            __align__(16) bf16 o[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int c = c0 + 32 * h + j + e;
+                o[e] = __float2bfloat16(silu(__uint_as_float(v[j + e]) + bias[c]));
+            }
+            *reinterpret_cast<uint4*>(act + coff(row, c0 + 32 * h + j, 128)) = *reinterpret_cast<const uint4*>(o);
+        }
+    }
+}
+
+// the bin of v from raw parameters held in registers (compile-time indices only)
+template <int K>
+__device__ __forceinline__ Bin locate_regs(const float (&raw)[3 * K + 1], float v, bool by_height) {
+    float w[K], h[K];
+    float mw = -INFINITY, mh = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        w[i] = raw[i];
+        h[i] = raw[K + i];
+        mw = fmaxf(mw, w[i]);
+        mh = fmaxf(mh, h[i]);
+    }
+    float zw = 0.0f, zh = 0.0f;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        w[i] = __expf(w[i] - mw);
+        h[i] = __expf(h[i] - mh);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) zw += w[i];
+#pragma unroll
+    for (int i = 0; i < K; ++i) zh += h[i];
+    Bin b;
+    b.mw = mw;
+    b.mh = mh;
+    b.iw = 1.0f / zw;
+    b.ih = 1.0f / zh;
+    const float cw = 1.0f - K * kMinW, chh = 1.0f - K * kMinH;
+    float cx = 0.0f, cy = 0.0f, csx = 0.0f, csy = 0.0f, a0 = 0.0f, a1 = 0.0f;
+    bool found = false;
+    b.k = K - 1;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const float pw = w[i] * b.iw, ph = h[i] * b.ih;
+        const float ww = kMinW + cw * pw, hh = kMinH + chh * ph;
+        const bool hit = !found && (i == K - 1 || (by_height ? v < cy + hh : v < cx + ww));
+        if (hit) {
+            b.k = i;
+            b.x0 = cx;
+            b.y0 = cy;
+            b.sx = csx;
+            b.sy = csy;
+            b.w = ww;
+            b.h = hh;
+            b.pw = pw;
+            b.ph = ph;
+            a0 = raw[2 * K + i];
+            a1 = raw[2 * K + i + 1];
+            found = true;
+        }
+        cx += ww;
+        cy += hh;
+        csx += pw;
+        csy += ph;
+    }
+    b.d0 = kMinD + softplus(a0);
+    b.d1 = kMinD + softplus(a1);
+    b.sg0 = sigmoid(a0);
+    b.sg1 = sigmoid(a1);
+    return b;
+}
+
+template <bool kInverse>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_layer_umma(int64_t B, int d, float* X, float* logdet, const __grid_constant__ LayerDesc ld, const bf16* W1,
+                 const float* b1, const bf16* W2, const float* b2, const bf16* W3, const float* b3,
+                 unsigned long long* status) {
+    constexpr int K = 16, PQ = 3 * K + 1;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    bf16* w1s = reinterpret_cast<bf16*>(smem + Smem::w1);
+    bf16* w2s = reinterpret_cast<bf16*>(smem + Smem::w2);
+    bf16* w3s = reinterpret_cast<bf16*>(smem + Smem::w3);
+    bf16* ins = reinterpret_cast<bf16*>(smem + Smem::in);
+    bf16* act = reinterpret_cast<bf16*>(smem + Smem::act);
+    float* b1s = reinterpret_cast<float*>(smem + Smem::b1);
+    float* b2s = reinterpret_cast<float*>(smem + Smem::b2);
+    float* b3s = reinterpret_cast<float*>(smem + Smem::b3);
+    float* lds = reinterpret_cast<float*>(smem + Smem::ld);
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = warp >> 2;                     // warpgroup: column half / dim of a pair
+    const int row = 32 * (warp & 3) + lane;      // this thread's event in the tile (TMEM lane)
+    const int npairs = (ld.nb + 1) / 2;
+
+    // weights into the canonical layout, biases
+    for (int i = tid; i < 128 * kInPad; i += kThreads) w1s[coff(i / kInPad, i % kInPad, kInPad)] = W1[i];
+    for (int i = tid; i < 128 * 128; i += kThreads) w2s[coff(i >> 7, i & 127, 128)] = W2[i];
+    for (int i = tid; i < npairs * kPairRows * 128; i += kThreads) {
+        const int r = i >> 7, k = i & 127;
+        const int p = r / kPairRows, rr = r % kPairRows, q = 2 * p + rr / 64, j = rr % 64;
+        const bf16 v = (q < ld.nb && j < PQ) ? W3[(q * PQ + j) * 128 + k] : __float2bfloat16(0.0f);
+        w3s[p * kPairRows * 128 + coff(rr, k, 128)] = v;
+    }
+    for (int i = tid; i < 128; i += kThreads) {
+        b1s[i] = b1[i];
+        b2s[i] = b2[i];
+    }
+    for (int i = tid; i < 8 * 56; i += kThreads) {
+        const int q = i / 56, j = i % 56;
+        b3s[i] = (q < ld.nb && j < PQ) ? b3[q * PQ + j] : 0.0f;
+    }
+    if (tid == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_holder)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_holder;
+    const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);  // this warp's TMEM lanes
+    uint32_t phase = 0;
+
+    const int64_t n_tiles = (B + kTile - 1) / kTile;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t ev = tile * kTile + row;
+        const bool valid = ev < B;
+        // operand tile of the conditioning dims (warpgroup g writes k = 8g .. 8g+7)
+        {
+            __align__(16) bf16 o[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = 8 * g + e;
+                o[e] = __float2bfloat16((valid && k < ld.na) ? X[ev * d + ld.ta[k]] : 0.0f);
+            }
+            *reinterpret_cast<uint4*>(ins + coff(row, 8 * g, kInPad)) = *reinterpret_cast<const uint4*>(o);
+        }
+        // layer 1
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            mma_chain(tmem, su32(ins), su32(w1s), kInPad, 128);
+            commit(&mbar);
+        }
+        if (!wait_phase(&mbar, phase)) failed = 1;
+        phase ^= 1;
+        fence_after();
+        hidden_epilogue(tlane, b1s, act, row, 64 * g);
+        // layer 2
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            mma_chain(tmem, su32(act), su32(w2s), 128, 128);
+            commit(&mbar);
+        }
+        if (!wait_phase(&mbar, phase)) failed = 1;
+        phase ^= 1;
+        fence_after();
+        hidden_epilogue(tlane, b2s, act, row, 64 * g);  // layer-2 reads of act are complete
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        // layer 3 and the splines, one pair of transformed dims per MMA chain
+        float lsum = 0.0f;
+        for (int p = 0; p < npairs; ++p) {
+            if (tid == 0) {
+                fence_after();
+                mma_chain(tmem + 128, su32(act), su32(w3s + p * kPairRows * 128), 128, kPairRows);
+                commit(&mbar);
+            }
+            if (!wait_phase(&mbar, phase)) failed = 1;
+            phase ^= 1;
+            fence_after();
+            const int q = 2 * p + g;
+            float raw[PQ];
+            {
+                uint32_t v[56];
+                const uint32_t a = tlane + 128 + 64 * g;  // column-aligned loads
+                PS_TMEM_LD32(v, a);
+                uint32_t* v2 = v + 32;
+                PS_TMEM_LD16(v2, a + 32);
+                uint32_t* v3 = v + 48;
+                PS_TMEM_LD8(v3, a + 48);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < PQ; ++j) raw[j] = __uint_as_float(v[j]) + b3s[q < 8 ? q * 56 + j : j];
+            }
+            if (valid && q < ld.nb) {
+                const int jd = ld.tb[q];
+                const float xv = fminf(fmaxf(X[ev * d + jd], 0.0f), 1.0f);
+                const Bin bn = locate_regs<K>(raw, xv, kInverse);
+                float F, Fp;
+                if (!kInverse) {
+                    bin_eval<float>(xv, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
+                    X[ev * d + jd] = fminf(fmaxf(F, 1e-7f), 1.0f - 1e-7f);
+                    lsum += __logf(Fp);
+                } else {
+                    const float sl = bn.h / bn.w, dy = xv - bn.y0, e = bn.d1 + bn.d0 - 2.0f * sl;
+                    const float qa = bn.h * (sl - bn.d0) + dy * e, qb = bn.h * bn.d0 - dy * e, qc = -sl * dy;
+                    const float disc = fmaxf(qb * qb - 4.0f * qa * qc, 0.0f);
+                    const float den = -qb - sqrtf(disc);
+                    const float xi = den != 0.0f ? fminf(fmaxf(2.0f * qc / den, 0.0f), 1.0f) : 0.0f;
+                    const float x = bn.x0 + xi * bn.w;
+                    bin_eval<float>(x, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
+                    X[ev * d + jd] = fminf(fmaxf(x, 0.0f), 1.0f);
+                    lsum -= __logf(Fp);
+                }
+            }
+            fence_before();
+            __syncthreads();  // every thread's reads of the raw columns precede the next chain
+        }
+        if (g == 1) lds[row] = lsum;
+        __syncthreads();
+        if (g == 0 && valid) logdet[ev] += lsum + lds[row];
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+    if (tid == 0 && failed) atomicAdd(status, 1ULL);
+}
+
+}  // namespace umma
+
 // out[j ldr + col0 + b] <- X[b d + j] (event-major float -> SoA double)
 __global__ void k_store_cols(int64_t B, int d, int64_t col0, int64_t ldr, const float* X, double* out) {
     int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -1004,6 +1356,7 @@ struct ps_flow_s {
     int64_t gen_cap = 0;
     float* gen_X = nullptr;   // [gen_cap][d]
     float* gen_ld = nullptr;  // [gen_cap]
+    unsigned long long* gen_status = nullptr;  // tensor-core waits that timed out
 };
 
 namespace {
@@ -1017,7 +1370,8 @@ void free_flow(ps_flow f) {
                     static_cast<void*>(f->dA), static_cast<void*>(f->dZ), static_cast<void*>(f->dZb), static_cast<void*>(f->dAb),
                     static_cast<void*>(f->dIn), static_cast<void*>(f->gX), static_cast<void*>(f->gXn),
                     static_cast<void*>(f->wtot), static_cast<void*>(f->scal),
-                    static_cast<void*>(f->gen_X), static_cast<void*>(f->gen_ld)})
+                    static_cast<void*>(f->gen_X), static_cast<void*>(f->gen_ld),
+                    static_cast<void*>(f->gen_status)})
         cudaFree(q);
 }
 
@@ -1207,6 +1561,8 @@ int ensure_gen(ps_flow f) {
     const int64_t cap = int64_t(1) << 20;
     int s = fcheck(cudaMalloc(&f->gen_X, cap * f->fd.d * sizeof(float)), "cudaMalloc (flow sampling)");
     if (s == PS_OK) s = fcheck(cudaMalloc(&f->gen_ld, cap * sizeof(float)), "cudaMalloc (flow sampling)");
+    if (s == PS_OK) s = fcheck(cudaMalloc(&f->gen_status, sizeof(unsigned long long)), "cudaMalloc (flow sampling)");
+    if (s == PS_OK) s = fcheck(cudaMemset(f->gen_status, 0, sizeof(unsigned long long)), "cudaMemset");
     if (s != PS_OK) return s;
     f->gen_cap = cap;
     // the dynamic shared memory of the fused kernel exceeds the default limit
@@ -1216,12 +1572,31 @@ int ensure_gen(ps_flow f) {
             s = fcheck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             static_cast<int>(FusedSmem::total)),
                        "cudaFuncSetAttribute");
+    for (auto kern : {umma::k_layer_umma<false>, umma::k_layer_umma<true>})
+        if (s == PS_OK)
+            s = fcheck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(umma::Smem::total)),
+                       "cudaFuncSetAttribute");
     return s;
 }
 
 // all layers of the fused path on X [B][d] in place, log-determinant accumulated into ld
 int fused_layers(ps_flow f, int64_t B, float* X, float* ld, bool inverse, cudaStream_t st) {
     const FlowDesc& fd = f->fd;
+    if (fd.K == 16) {  // the tcgen05 form: 128 events per tile, one persistent CTA per SM
+        const int64_t tiles = (B + umma::kTile - 1) / umma::kTile;
+        const unsigned grid = static_cast<unsigned>(std::min<int64_t>(f->sms, tiles));
+        for (int k = 0; k < fd.L; ++k) {
+            const int l = inverse ? fd.L - 1 - k : k;
+            const LayerDesc& lay = fd.layer[l];
+            auto kern = inverse ? umma::k_layer_umma<true> : umma::k_layer_umma<false>;
+            kern<<<grid, umma::kThreads, umma::Smem::total, st>>>(
+                B, fd.d, X, ld, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2, f->p + lay.off_b2,
+                f->pb + lay.off_W3, f->p + lay.off_b3, f->gen_status);
+        }
+        ps::count_launches(fd.L);
+        return fcheck(cudaGetLastError(), "k_layer_umma");
+    }
     const int64_t tiles = (B + 16 * kFWarps - 1) / (16 * kFWarps);
     const unsigned grid = static_cast<unsigned>(std::min<int64_t>(f->sms, tiles));
     for (int k = 0; k < fd.L; ++k) {
@@ -1574,6 +1949,18 @@ int ps_flow_train_step(ps_flow f, const double* w_map, double lr, void* stream) 
                                                      static_cast<float>(lr), b1, b2, 1e-8f, c1, c2);
     ps::count_launches(1);
     return fcheck(cudaGetLastError(), "ps_flow_train_step");
+}
+
+int ps_flow_status(ps_flow f, int64_t* timeouts) {
+    if (!f || !timeouts) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_status: bad arguments");
+    *timeouts = 0;
+    if (!f->gen_status) return PS_OK;
+    Guard g(f->device);
+    unsigned long long v = 0;
+    int s = fcheck(cudaMemcpy(&v, f->gen_status, sizeof v, cudaMemcpyDeviceToHost), "ps_flow_status");
+    if (s != PS_OK) return s;
+    *timeouts = static_cast<int64_t>(v);
+    return PS_OK;
 }
 
 int ps_flow_loss(ps_flow f, double* loss, double* sum_w, void* stream) {

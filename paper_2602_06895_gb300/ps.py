@@ -139,6 +139,7 @@ _SIGS = {
     "ps_flow_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.c_int64,
                                     C.POINTER(C.c_double), C.c_void_p]),
     "ps_flow_loss": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
+    "ps_flow_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
 }
 
 
@@ -607,6 +608,12 @@ class Flow:
         _fcheck(lib().ps_flow_gradients(self.h, _ptr(w_map), g.ctypes.data_as(C.POINTER(C.c_float)), self.n_params,
                                         C.byref(loss), _stream_ptr(stream)), "ps_flow_gradients")
         return loss.value, g
+
+    def status(self):
+        """Tensor-core waits of the fused sampling kernels that ran out (0 in a healthy run)."""
+        v = C.c_int64()
+        _fcheck(lib().ps_flow_status(self.h, C.byref(v)), "ps_flow_status")
+        return v.value
 
     def loss(self, stream=None):
         loss, sw = C.c_double(), C.c_double()

@@ -149,6 +149,7 @@ def test_inverse_matches_oracle_and_round_trips(torch_cuda):
     lq = torch.empty(B, dtype=torch.float64, device="cuda")
     fl.inverse(r, zb, lq)
     torch.cuda.synchronize()
+    assert fl.status() == 0
     z_o, lq_o = orc.inverse(r.T.cpu(), bf=True)
     dz = np.abs(zb.T.cpu().numpy() - z_o.numpy())
     assert dz.max() <= 2e-3 and dz.mean() <= 1e-4, (dz.max(), dz.mean())
@@ -271,6 +272,32 @@ def test_fused_generate_matches_layer_by_layer_and_oracle(torch_cuda, B):
     dl = np.abs(ld[idx].cpu().numpy() - ld_o.numpy())
     assert dr.max() <= 2e-3 and dr.mean() <= 1e-4, (dr.max(), dr.mean())
     assert dl.max() <= 2e-2 and dl.mean() <= 1e-3, (dl.max(), dl.mean())
+    assert fl.status() == 0
+
+
+def test_warp_mma_fused_path(torch_cuda):
+    """12 bins: the fused layer with warp-level MMAs (the tcgen05 form takes 16 bins), generate and
+    inverse against the oracle."""
+    torch = torch_cuda
+    fl = ps.Flow(D, L, 12, H, max_batch=2048)
+    p, orc, _ = random_params(fl, 17)
+    fl.set_params(p)
+    B = 4099
+    r = torch.empty((D, B), dtype=torch.float64, device="cuda")
+    ld = torch.empty(B, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    fl.generate(B, 10, r, ld, z)
+    zb = torch.empty_like(r)
+    lq = torch.empty_like(ld)
+    fl.inverse(r, zb, lq)
+    torch.cuda.synchronize()
+    r_o, ld_o = orc.forward(z.T.cpu(), bf=True)
+    dr = np.abs(r.T.cpu().numpy() - r_o.numpy())
+    assert dr.max() <= 2e-3 and dr.mean() <= 1e-4, (dr.max(), dr.mean())
+    assert np.abs(ld.cpu().numpy() - ld_o.numpy()).max() <= 2e-2
+    z_o, lq_o = orc.inverse(r.T.cpu(), bf=True)
+    assert np.abs(zb.T.cpu().numpy() - z_o.numpy()).max() <= 2e-3
+    assert np.abs(lq.cpu().numpy() - lq_o.numpy()).max() <= 2e-2
 
 
 def test_layer_by_layer_inverse_and_generate_fallback(torch_cuda):
