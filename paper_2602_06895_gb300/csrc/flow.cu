@@ -1091,13 +1091,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int npairs = (ld.nb + 1) / 2;
 
     // weights into the canonical layout, biases
-    for (int i = tid; i < 128 * kInPad; i += kThreads) w1s[coff(i / kInPad, i % kInPad, kInPad)] = W1[i];
-    for (int i = tid; i < 128 * 128; i += kThreads) w2s[coff(i >> 7, i & 127, 128)] = W2[i];
-    for (int i = tid; i < npairs * kPairRows * 128; i += kThreads) {
-        const int r = i >> 7, k = i & 127;
+    // weights into the canonical layout, 8 consecutive k (one core-matrix row) per 16-byte copy
+    for (int i = tid; i < 128 * kInPad / 8; i += kThreads) {
+        const int r = i / (kInPad / 8), k = (i % (kInPad / 8)) * 8;
+        *reinterpret_cast<uint4*>(w1s + coff(r, k, kInPad)) = *reinterpret_cast<const uint4*>(W1 + r * kInPad + k);
+    }
+    for (int i = tid; i < 128 * 16; i += kThreads) {
+        const int r = i >> 4, k = (i & 15) * 8;
+        *reinterpret_cast<uint4*>(w2s + coff(r, k, 128)) = *reinterpret_cast<const uint4*>(W2 + r * 128 + k);
+    }
+    for (int i = tid; i < npairs * kPairRows * 16; i += kThreads) {
+        const int r = i >> 4, k = (i & 15) * 8;
         const int p = r / kPairRows, rr = r % kPairRows, q = 2 * p + rr / 64, j = rr % 64;
-        const bf16 v = (q < ld.nb && j < PQ) ? W3[(q * PQ + j) * 128 + k] : __float2bfloat16(0.0f);
-        w3s[p * kPairRows * 128 + coff(rr, k, 128)] = v;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (q < ld.nb && j < PQ) v = *reinterpret_cast<const uint4*>(W3 + (q * PQ + j) * 128 + k);
+        *reinterpret_cast<uint4*>(w3s + p * kPairRows * 128 + coff(rr, k, 128)) = v;
     }
     for (int i = tid; i < 128; i += kThreads) {
         b1s[i] = b1[i];
@@ -1168,14 +1176,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_async_smem();
         fence_before();
         __syncthreads();
-        // layer 3 and the splines, one pair of transformed dims per MMA chain
+        // layer 3 and the splines, one pair of transformed dims per MMA chain; the raw columns of
+        // pair p land in TMEM columns 128 (p even) or 0 (p odd), so the chain of pair p+1 runs
+        // while the splines of pair p are evaluated
         float lsum = 0.0f;
+        if (tid == 0) {
+            fence_after();
+            mma_chain(tmem + 128, su32(act), su32(w3s), 128, kPairRows);
+            commit(&mbar);
+        }
         for (int p = 0; p < npairs; ++p) {
-            if (tid == 0) {
-                fence_after();
-                mma_chain(tmem + 128, su32(act), su32(w3s + p * kPairRows * 128), 128, kPairRows);
-                commit(&mbar);
-            }
             if (!wait_phase(&mbar, phase)) failed = 1;
             phase ^= 1;
             fence_after();
@@ -1183,7 +1193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             float raw[PQ];
             {
                 uint32_t v[56];
-                const uint32_t a = tlane + 128 + 64 * g;  // column-aligned loads
+                const uint32_t a = tlane + ((p & 1) ? 0 : 128) + 64 * g;  // column-aligned loads
                 PS_TMEM_LD32(v, a);
                 uint32_t* v2 = v + 32;
                 PS_TMEM_LD16(v2, a + 32);
@@ -1192,6 +1202,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < PQ; ++j) raw[j] = __uint_as_float(v[j]) + b3s[q < 8 ? q * 56 + j : j];
+            }
+            // the other column block was read completely before the previous iteration's barrier
+            if (tid == 0 && p + 1 < npairs) {
+                fence_after();
+                mma_chain(tmem + ((p & 1) ? 128 : 0), su32(act), su32(w3s + (p + 1) * kPairRows * 128), 128,
+                          kPairRows);
+                commit(&mbar);
             }
             if (valid && q < ld.nb) {
                 const int jd = ld.tb[q];
@@ -1215,7 +1232,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             fence_before();
-            __syncthreads();  // every thread's reads of the raw columns precede the next chain
+            __syncthreads();  // every thread's reads of this column block precede the chain of pair p+2
         }
         if (g == 1) lds[row] = lsum;
         __syncthreads();
