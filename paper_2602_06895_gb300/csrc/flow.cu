@@ -891,21 +891,22 @@ __global__ void __launch_bounds__(kFWarps * 32, 1)
 namespace umma {
 
 constexpr int kTile = 128;        // events per tile (TMEM lanes)
-constexpr int kThreads = 256;
-constexpr int kPairRows = 128;    // B rows of one pair of transformed dims: 49 + 15 zero rows each
-constexpr int kTmemCols = 256;    // [0,128) hidden accumulators, [128,256) raw parameters
+constexpr int kGroups = 4;        // warpgroups: hidden columns 32g.., transformed dim 4 s + g of set s
+constexpr int kThreads = 128 * kGroups;
+constexpr int kSetRows = 64 * kGroups;  // B rows of one set of transformed dims: 49 + 15 zero rows each
+constexpr int kTmemCols = 512;    // two blocks of 256: raw parameters of alternate sets; [0,128) hidden
 
 struct Smem {
     static constexpr size_t w1 = 0;                                    // 128 x 16 bf16
     static constexpr size_t w2 = w1 + 128 * kInPad * 2;                // 128 x 128
-    static constexpr size_t w3 = w2 + 128 * 128 * 2;                   // up to 4 pairs x 128 x 128
-    static constexpr size_t in = w3 + 4 * kPairRows * 128 * 2;         // 128 x 16 operand tile
+    static constexpr size_t w3 = w2 + 128 * 128 * 2;                   // up to 8 dims x 64 rows x 128
+    static constexpr size_t in = w3 + 8 * 64 * 128 * 2;                // 128 x 16 operand tile
     static constexpr size_t act = in + kTile * kInPad * 2;             // 128 x 128 operand tile
     static constexpr size_t b1 = act + kTile * 128 * 2;
     static constexpr size_t b2 = b1 + 128 * 4;
     static constexpr size_t b3 = b2 + 128 * 4;                         // 8 x 56 floats
-    static constexpr size_t ld = b3 + 8 * 56 * 4;                      // 128 floats: log-det exchange
-    static constexpr size_t total = ld + kTile * 4;
+    static constexpr size_t ld = b3 + 8 * 56 * 4;                      // log-det exchange [kGroups-1][128]
+    static constexpr size_t total = ld + (kGroups - 1) * kTile * 4;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -984,10 +985,10 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// 64 hidden columns of this thread's event: + bias, SiLU, bf16 into the operand tile
+// 32 hidden columns of this thread's event: + bias, SiLU, bf16 into the operand tile
 __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, bf16* act, int row, int c0) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 1; ++h) {
         uint32_t v[32];
         PS_TMEM_LD32(v, taddr + c0 + 32 * h);
         tmem_wait_ld();
@@ -1086,9 +1087,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ uint32_t tmem_holder;
     __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = warp >> 2;                     // warpgroup: column half / dim of a pair
+    const int g = warp >> 2;                     // warpgroup: hidden column block / dim of a set
     const int row = 32 * (warp & 3) + lane;      // this thread's event in the tile (TMEM lane)
-    const int npairs = (ld.nb + 1) / 2;
+    const int nsets = (ld.nb + kGroups - 1) / kGroups;
 
     // weights into the canonical layout, biases
     // weights into the canonical layout, 8 consecutive k (one core-matrix row) per 16-byte copy
@@ -1100,12 +1101,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int r = i >> 4, k = (i & 15) * 8;
         *reinterpret_cast<uint4*>(w2s + coff(r, k, 128)) = *reinterpret_cast<const uint4*>(W2 + r * 128 + k);
     }
-    for (int i = tid; i < npairs * kPairRows * 16; i += kThreads) {
+    for (int i = tid; i < nsets * kSetRows * 16; i += kThreads) {
         const int r = i >> 4, k = (i & 15) * 8;
-        const int p = r / kPairRows, rr = r % kPairRows, q = 2 * p + rr / 64, j = rr % 64;
+        const int p = r / kSetRows, rr = r % kSetRows, q = kGroups * p + rr / 64, j = rr % 64;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (q < ld.nb && j < PQ) v = *reinterpret_cast<const uint4*>(W3 + (q * PQ + j) * 128 + k);
-        *reinterpret_cast<uint4*>(w3s + p * kPairRows * 128 + coff(rr, k, 128)) = v;
+        *reinterpret_cast<uint4*>(w3s + p * kSetRows * 128 + coff(rr, k, 128)) = v;
     }
     for (int i = tid; i < 128; i += kThreads) {
         b1s[i] = b1[i];
@@ -1137,15 +1138,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t ev = tile * kTile + row;
         const bool valid = ev < B;
-        // operand tile of the conditioning dims (warpgroup g writes k = 8g .. 8g+7)
+        // operand tile of the conditioning dims (warpgroup g writes k = 4g .. 4g+3)
         {
-            __align__(16) bf16 o[8];
+            __align__(8) bf16 o[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = 8 * g + e;
+            for (int e = 0; e < 4; ++e) {
+                const int k = 4 * g + e;
                 o[e] = __float2bfloat16((valid && k < ld.na) ? X[ev * d + ld.ta[k]] : 0.0f);
             }
-            *reinterpret_cast<uint4*>(ins + coff(row, 8 * g, kInPad)) = *reinterpret_cast<const uint4*>(o);
+            *reinterpret_cast<uint2*>(ins + coff(row, 4 * g, kInPad)) = *reinterpret_cast<const uint2*>(o);
         }
         // layer 1
         fence_async_smem();
@@ -1159,7 +1160,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!wait_phase(&mbar, phase)) failed = 1;
         phase ^= 1;
         fence_after();
-        hidden_epilogue(tlane, b1s, act, row, 64 * g);
+        hidden_epilogue(tlane, b1s, act, row, 32 * g);
         // layer 2
         fence_async_smem();
         fence_before();
@@ -1172,28 +1173,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!wait_phase(&mbar, phase)) failed = 1;
         phase ^= 1;
         fence_after();
-        hidden_epilogue(tlane, b2s, act, row, 64 * g);  // layer-2 reads of act are complete
+        hidden_epilogue(tlane, b2s, act, row, 32 * g);  // layer-2 reads of act are complete
         fence_async_smem();
         fence_before();
         __syncthreads();
-        // layer 3 and the splines, one pair of transformed dims per MMA chain; the raw columns of
-        // pair p land in TMEM columns 128 (p even) or 0 (p odd), so the chain of pair p+1 runs
-        // while the splines of pair p are evaluated
+        // layer 3 and the splines, one set of kGroups transformed dims per MMA chain (N = 256); the
+        // raw columns of set p land in TMEM block 256 (p even) or 0 (p odd), so the chain of set
+        // p+1 runs while the splines of set p are evaluated
         float lsum = 0.0f;
         if (tid == 0) {
             fence_after();
-            mma_chain(tmem + 128, su32(act), su32(w3s), 128, kPairRows);
+            mma_chain(tmem + 256, su32(act), su32(w3s), 128, kSetRows);
             commit(&mbar);
         }
-        for (int p = 0; p < npairs; ++p) {
+        for (int p = 0; p < nsets; ++p) {
             if (!wait_phase(&mbar, phase)) failed = 1;
             phase ^= 1;
             fence_after();
-            const int q = 2 * p + g;
+            const int q = kGroups * p + g;
             float raw[PQ];
             {
                 uint32_t v[56];
-                const uint32_t a = tlane + ((p & 1) ? 0 : 128) + 64 * g;  // column-aligned loads
+                const uint32_t a = tlane + ((p & 1) ? 0 : 256) + 64 * g;  // column-aligned loads
                 PS_TMEM_LD32(v, a);
                 uint32_t* v2 = v + 32;
                 PS_TMEM_LD16(v2, a + 32);
@@ -1204,10 +1205,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int j = 0; j < PQ; ++j) raw[j] = __uint_as_float(v[j]) + b3s[q < 8 ? q * 56 + j : j];
             }
             // the other column block was read completely before the previous iteration's barrier
-            if (tid == 0 && p + 1 < npairs) {
+            if (tid == 0 && p + 1 < nsets) {
                 fence_after();
-                mma_chain(tmem + ((p & 1) ? 128 : 0), su32(act), su32(w3s + (p + 1) * kPairRows * 128), 128,
-                          kPairRows);
+                mma_chain(tmem + ((p & 1) ? 256 : 0), su32(act), su32(w3s + (p + 1) * kSetRows * 128), 128,
+                          kSetRows);
                 commit(&mbar);
             }
             if (valid && q < ld.nb) {
@@ -1232,11 +1233,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             fence_before();
-            __syncthreads();  // every thread's reads of this column block precede the chain of pair p+2
+            __syncthreads();  // every thread's reads of this column block precede the chain of set p+2
         }
-        if (g == 1) lds[row] = lsum;
+        if (g > 0) lds[(g - 1) * kTile + row] = lsum;
         __syncthreads();
-        if (g == 0 && valid) logdet[ev] += lsum + lds[row];
+        if (g == 0 && valid) {
+            float t = lsum;
+#pragma unroll
+            for (int k = 0; k < kGroups - 1; ++k) t += lds[k * kTile + row];
+            logdet[ev] += t;
+        }
     }
     fence_before();
     __syncthreads();
