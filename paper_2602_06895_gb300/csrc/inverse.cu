@@ -110,23 +110,34 @@ __global__ void __launch_bounds__(128) ps_inverse_kernel(const __grid_constant__
         }
     }
 
-    // node momenta and invariants
+    // node momenta, and the invariants of the non-root decay nodes (the root's is shat; leaves
+    // carry their masses): the leaf directions are needed only if such a node exists
     double ap[kMaxLeg], nx[kMaxLeg], ny[kMaxLeg], nz[kMaxLeg], ml[kMaxLeg];
+    bool any_decay = false;
+    for (int j = 1; j < P.n_nodes; ++j) any_decay |= P.node[j].kind == PS_NODE_DECAY;
     for (int j = 0; j < P.n_nodes; ++j)
         if (P.node[j].kind == PS_NODE_LEAF) {
             const int i = P.node[j].leaf;
-            const P4 p = q[2 + i];
-            const double a = sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
-            ap[i] = a;
-            nx[i] = p.x / a;
-            ny[i] = p.y / a;
-            nz[i] = p.z / a;
             ml[i] = P.node[j].mass;
+            if (any_decay) {
+                const P4 p = q[2 + i];
+                const double a = sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
+                ap[i] = a;
+                nx[i] = p.x / a;
+                ny[i] = p.y / a;
+                nz[i] = p.z / a;
+            }
         }
     P4 pn[kInvNodes];
     double s[kInvNodes];
-    for (int j = 0; j < P.n_nodes; ++j) {
-        const uint32_t mask = P.node[j].mask;
+    for (int j = 1; j < P.n_nodes; ++j) {
+        const InvNode& nd = P.node[j];
+        if (nd.kind == PS_NODE_LEAF) {
+            pn[j] = q[2 + nd.leaf];
+            s[j] = nd.mass * nd.mass;
+            continue;
+        }
+        const uint32_t mask = nd.mask;
         P4 acc{0.0, 0.0, 0.0, 0.0};
         double s2 = 0.0;
         for (int i = 0; i < n; ++i) {
