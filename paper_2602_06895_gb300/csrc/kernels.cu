@@ -67,7 +67,7 @@ __device__ __forceinline__ bool map_nu(double r, double m, double nu, double xmi
         x = m2 + xm;
         jac = -xm * rho / (w * (1.0 + z));
     }
-    x = fmin(fmax(x, xmin), xmax);  // the map lands in [x_min, x_max] (rounding at the ends)
+    x = clamp_nonneg(x, xmin, xmax);  // the map lands in [x_min, x_max] (rounding at the ends)
     if (!ok) { x = xmin; jac = 0.0; }
     return ok;
 }
@@ -104,7 +104,7 @@ __device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin
         sec2 = 1.0 + T * T;
     }
     jac = D * mg * sec2;
-    x = fmin(fmax(x, xmin), xmax);
+    x = clamp_nonneg(x, xmin, xmax);
     if (!ok) { x = xmin; jac = 0.0; }
     return ok;
 }
@@ -201,7 +201,6 @@ __device__ __forceinline__ void stp(const Frame& f, int slot, P4 p) {
     q[3 * f.block] = p.z;
 }
 
-__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
 // Executes one channel's instruction list for the calling thread's event.
 __device__ void run_code(const int32_t* code, int len, const Frame& f, const double* grid, int vbins,
@@ -311,10 +310,10 @@ __device__ void run_code(const int32_t* code, int len, const Frame& f, const dou
             }
             case PS_OP_CUT_UNPHYSICAL: {
                 double w = ld(f, a[0]), x1 = ld(f, a[1]), x2 = ld(f, a[2]);
-                bool bad = !finite(w) || !(x1 > 0.0 && x1 <= 1.0 && x2 > 0.0 && x2 <= 1.0);
+                bool bad = !finite_bits(w) || !(in_unit_bits(x1) && in_unit_bits(x2));
                 for (int k = 3; k < na; ++k) {
                     P4 p = ldp(f, a[k]);
-                    bad |= !(finite(p.e) && finite(p.x) && finite(p.y) && finite(p.z));
+                    bad |= !(finite_bits(p.e) && finite_bits(p.x) && finite_bits(p.y) && finite_bits(p.z));
                 }
                 if (bad && active) atomicAdd(cut_count, 1ULL);
                 st(f, o[0], bad ? 0.0 : w);
@@ -488,7 +487,7 @@ __device__ __forceinline__ void map_nu(float r, double m, double nu, double xmin
         x = m2 + xm;
         jac = -xm * static_cast<double>(rho / (w * (1.0f + z)));
     }
-    x = fmin(fmax(x, xmin), xmax);
+    x = clamp_nonneg(x, xmin, xmax);
     if (!ok) { x = xmin; jac = 0.0; }
 }
 
@@ -519,7 +518,7 @@ __device__ __forceinline__ void map_bw(float r, double M, double G, double xmin,
         sec2 = 1.0f + T * T;
     }
     jac = static_cast<double>(D * mgf * sec2);
-    x = fmin(fmax(x, xmin), xmax);
+    x = clamp_nonneg(x, xmin, xmax);
     if (!ok) { x = xmin; jac = 0.0; }
 }
 
@@ -709,7 +708,7 @@ __device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, con
             }
             case PS_OP_CUT_UNPHYSICAL: {
                 double w = ld(f, a[0]), x1 = ld(f, a[1]), x2 = ld(f, a[2]);
-                bool bad = !isfinite(w) || !(x1 > 0.0 && x1 <= 1.0 && x2 > 0.0 && x2 <= 1.0);
+                bool bad = !finite_bits(w) || !(in_unit_bits(x1) && in_unit_bits(x2));
                 for (int k = 3; k < na; ++k) {
                     F4 p = mx::ldp(f, a[k]);
                     bad |= !(isfinite(p.e) && isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
@@ -887,7 +886,7 @@ __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ Lau
             }
         }
         if (!active) w = 0.0;
-        if (active && !isfinite(w)) atomicAdd(lp.status + 0, 1ULL);
+        if (active && !dev::finite_bits(w)) atomicAdd(lp.status + 0, 1ULL);
 
         // VEGAS training: sum of w^2 per (dimension, bin of the unmapped r)
         if (lp.hist != nullptr && C.vdims > 0 && active) {

@@ -9,6 +9,25 @@ namespace dev {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
+// Decisions on doubles taken on their bit patterns in the integer ALU, which leaves the FP64
+// pipe (1/64 of the FP32 rate) to arithmetic: IEEE doubles of one sign order like their bit
+// patterns read as signed integers.
+constexpr long long kInfBits = 0x7FF0000000000000LL;
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+// isfinite(v)
+__device__ __forceinline__ bool finite_bits(double v) { return (dbits(v) & kInfBits) != kInfBits; }
+// 0 < v <= 1 (false for NaN)
+__device__ __forceinline__ bool in_unit_bits(double v) {
+    const long long b = dbits(v);
+    return b > 0 && b <= 0x3FF0000000000000LL;
+}
+// fmin(fmax(x, lo), hi) for 0 <= lo <= hi: NaN and values below lo give lo, +inf gives hi
+__device__ __forceinline__ double clamp_nonneg(double x, double lo, double hi) {
+    const long long b = dbits(x);
+    if (b < dbits(lo) || b > kInfBits) return lo;
+    return b > dbits(hi) ? hi : x;
+}
+
 struct P4 {
     double e, x, y, z;
 };
