@@ -42,16 +42,16 @@ using rng::unit_from_bits;
 //   nu >  1: z = (1-r) expm1(-w L), x - m^2 = hi exp(log1p(z)/w), J = -(x - m^2) rho'/(w (1+z))
 __device__ __forceinline__ bool map_nu(double r, double m, double nu, double xmin, double xmax, double a,
                                        double& x, double& jac) {
-    double m2 = (m > 0.0) ? m * m : -a;
+    double m2 = pos_bits(m) ? m * m : -a;
     double lo = xmin - m2, hi = xmax - m2;
-    bool ok = (lo > 0.0) && (hi >= lo);
+    bool ok = pos_bits(lo) && ge_pos_bits(hi, lo);
     double L = log1p((xmax - xmin) / lo);
-    if (nu == 1.0) {
+    if (dbits(nu) == dbits(1.0)) {
         double e = expm1(r * L);
         double xm = fma(lo, e, lo);
         x = fma(lo, e, xmin);
         jac = xm * L;
-    } else if (nu < 1.0) {
+    } else if (dbits(nu) < dbits(1.0)) {  // nu < 1 (nu is never NaN)
         double w = 1.0 - nu;
         double rho = expm1(w * L);
         double z = r * rho;
@@ -80,12 +80,12 @@ __device__ __forceinline__ bool map_nu(double r, double m, double nu, double xmi
 __device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin, double xmax,
                                        double& x, double& jac) {
     double mg = M * G, m2 = M * M;
-    bool ok = (mg > 0.0) && (xmax >= xmin);
+    bool ok = pos_bits(mg) && ge_pos_bits(xmax, xmin);  // x_min >= 0 here (a squared mass)
     double inv_mg = 1.0 / mg;
     double a = (xmin - m2) * inv_mg, b = (xmax - m2) * inv_mg;
     double D = atan2((xmax - xmin) * inv_mg, fma(a, b, 1.0));
     double u = atan(a) + D * r;
-    bool low = u < -0.25 * kPi, high = u > 0.25 * kPi;
+    bool low = below_neg_bits(u, 0.25 * kPi), high = above_pos_bits(u, 0.25 * kPi);
     double arg = low ? D * r : (high ? D * (1.0 - r) : u);
     double T = tan(arg);
     double sec2;
@@ -460,17 +460,17 @@ __device__ __forceinline__ F4 boost_in(F4 p, F4 q, float mq) {
 // power law / log map: transcendentals in float, x = x_min + lo e assembled in FP64
 __device__ __forceinline__ void map_nu(float r, double m, double nu, double xmin, double xmax, double a,
                                        double& x, double& jac) {
-    double m2 = (m > 0.0) ? m * m : -a;
+    double m2 = pos_bits(m) ? m * m : -a;
     double lo = xmin - m2, hi = xmax - m2;
-    bool ok = (lo > 0.0) && (hi >= lo);
+    bool ok = pos_bits(lo) && ge_pos_bits(hi, lo);
     float L = log1pf(static_cast<float>(xmax - xmin) / static_cast<float>(lo));
     float e, jf;
-    if (nu == 1.0) {
+    if (dbits(nu) == dbits(1.0)) {
         e = expm1f(r * L);
         jf = (1.0f + e) * L;
         x = fma(lo, static_cast<double>(e), xmin);
         jac = lo * static_cast<double>(jf);
-    } else if (nu < 1.0) {
+    } else if (dbits(nu) < dbits(1.0)) {  // nu < 1 (nu is never NaN)
         float w = static_cast<float>(1.0 - nu);
         float rho = expm1f(w * L);
         float z = r * rho;
@@ -495,7 +495,7 @@ __device__ __forceinline__ void map_nu(float r, double m, double nu, double xmin
 // s - m^2 and the assembly of x in FP64
 __device__ __forceinline__ void map_bw(float r, double M, double G, double xmin, double xmax, double& x, double& jac) {
     double mg = M * G, m2 = M * M;
-    bool ok = (mg > 0.0) && (xmax >= xmin);
+    bool ok = pos_bits(mg) && ge_pos_bits(xmax, xmin);  // x_min >= 0 here (a squared mass)
     float mgf = static_cast<float>(mg);
     float imgf = 1.0f / mgf;
     float a = static_cast<float>(xmin - m2) * imgf, b = static_cast<float>(xmax - m2) * imgf;

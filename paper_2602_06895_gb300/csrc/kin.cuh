@@ -21,6 +21,22 @@ __device__ __forceinline__ bool in_unit_bits(double v) {
     const long long b = dbits(v);
     return b > 0 && b <= 0x3FF0000000000000LL;
 }
+// v > 0 (false for NaN and -0)
+__device__ __forceinline__ bool pos_bits(double v) {
+    const long long b = dbits(v);
+    return b > 0 && b <= kInfBits;
+}
+// a >= b for b >= +0 (false for NaN a)
+__device__ __forceinline__ bool ge_pos_bits(double a, double b) {
+    const long long x = dbits(a);
+    return x >= dbits(b) && x <= kInfBits;
+}
+// v < -c and v > c for a constant c > 0 and finite v
+__device__ __forceinline__ bool below_neg_bits(double v, double c) {
+    const long long b = dbits(v);
+    return b < 0 && (b & 0x7FFFFFFFFFFFFFFFLL) > dbits(c);
+}
+__device__ __forceinline__ bool above_pos_bits(double v, double c) { return dbits(v) > dbits(c); }
 // fmin(fmax(x, lo), hi) for 0 <= lo <= hi: NaN and values below lo give lo, +inf gives hi
 __device__ __forceinline__ double clamp_nonneg(double x, double lo, double hi) {
     const long long b = dbits(x);
