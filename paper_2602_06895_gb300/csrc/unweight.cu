@@ -15,7 +15,7 @@
 // The bucket sums are exact integers: a weight m 2^(e-1075) (53-bit significand m, exponent
 // field e) enters its bucket as m 2^(e-E) in units of 2^(E-1075), E the exponent field of the
 // bucket's largest bit pattern, accumulated in 128 bits.  Integer addition does not depend on
-// order, so shared-memory atomics keep the result reproducible bit for bit; the truncation of the
+// order, so the result is reproducible bit for bit; the truncation of the
 // low bits of weights below the bucket's top binade costs at most one unit of 2^(E-1075) per
 // weight (relative 2^-48 of a bucket sum spanning up to 16 binades).  The total sum and the
 // maximum are per-block partials over a fixed grid, combined in block order.
@@ -113,14 +113,24 @@ __global__ void __launch_bounds__(kThreads) k_partials(const double* w, int64_t 
     }
 }
 
-__global__ void k_init(const double* part, double eps, State* st) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double S = 0.0, m = 0.0, bad = 0.0;
-    for (int b = 0; b < kGrid; ++b) {
-        S += part[3 * b];
-        m = fmax(m, part[3 * b + 1]);
-        bad += part[3 * b + 2];
+// combine the block partials: a fixed-order tree over kGrid entries (kGrid threads)
+__global__ void __launch_bounds__(kGrid) k_init(const double* part, double eps, State* st) {
+    __shared__ double ss[kGrid], sm[kGrid], sb[kGrid];
+    const int t = threadIdx.x;
+    ss[t] = part[3 * t];
+    sm[t] = part[3 * t + 1];
+    sb[t] = part[3 * t + 2];
+    __syncthreads();
+    for (int o = kGrid / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            ss[t] += ss[t + o];
+            sm[t] = fmax(sm[t], sm[t + o]);
+            sb[t] += sb[t + o];
+        }
+        __syncthreads();
     }
+    if (t != 0) return;
+    const double S = ss[0], m = sm[0], bad = sb[0];
     State s{};
     s.S = S;
     s.wmax = m;
@@ -146,23 +156,24 @@ __global__ void k_init(const double* part, double eps, State* st) {
 __global__ void __launch_bounds__(kThreads) k_hist(const double* w, int64_t n, const State* st,
                                                    unsigned long long* hlo, unsigned long long* hhi,
                                                    unsigned int* hcnt) {
-    __shared__ unsigned long long slo[kBuckets], shi[kBuckets];
-    __shared__ unsigned int sc[kBuckets];
+    // warp-private histograms: no contention between warps on a crowded bucket
+    __shared__ unsigned long long slo[kThreads / 32][kBuckets], shi[kThreads / 32][kBuckets];
+    __shared__ unsigned int sc[kThreads / 32][kBuckets];
     __shared__ int sexp[kBuckets];
     if (st->done) return;
     const unsigned long long lo = st->lo, hi = st->hi;
     const int shift = st->shift;
     const unsigned long long step = 1ULL << shift;
-    for (int j = threadIdx.x; j < kBuckets; j += kThreads) {
-        slo[j] = 0;
-        shi[j] = 0;
-        sc[j] = 0;
-        sexp[j] = bucket_exp(lo, step, hi, j);
+    for (int j = threadIdx.x; j < kBuckets; j += kThreads) sexp[j] = bucket_exp(lo, step, hi, j);
+    for (int j = threadIdx.x; j < (kThreads / 32) * kBuckets; j += kThreads) {
+        slo[j / kBuckets][j % kBuckets] = 0;
+        shi[j / kBuckets][j % kBuckets] = 0;
+        sc[j / kBuckets][j % kBuckets] = 0;
     }
     __syncthreads();
     const int64_t chunk = (n + kGrid - 1) / kGrid;
     const int64_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t base = b0; base < b1; base += kThreads) {  // block-uniform trip count (warp collectives)
         const int64_t i = base + threadIdx.x;
         const unsigned long long u = i < b1 ? static_cast<unsigned long long>(__double_as_longlong(w[i])) : ~0ULL;
@@ -184,42 +195,73 @@ __global__ void __launch_bounds__(kThreads) k_hist(const double* w, int64_t n, c
             if (s2 < sum) ++carry;
             carry += static_cast<unsigned long long>(l2) >> 22;  // bits of l2 2^42 above 2^64
             sum = s2;
-            const unsigned long long old = atomicAdd(&slo[bk], sum);
+            // one leader per bucket in this warp and the histogram private to the warp: plain
+            // read-modify-write, no atomics
+            const unsigned long long old = slo[warp][bk];
+            slo[warp][bk] = old + sum;
             if (old + sum < old) ++carry;
-            if (carry) atomicAdd(&shi[bk], carry);
-            atomicAdd(&sc[bk], static_cast<unsigned>(__popc(grp)));
+            shi[warp][bk] += carry;
+            sc[warp][bk] += static_cast<unsigned>(__popc(grp));
         }
     }
     __syncthreads();
     for (int j = threadIdx.x; j < kBuckets; j += kThreads) {
-        hlo[blockIdx.x * kBuckets + j] = slo[j];
-        hhi[blockIdx.x * kBuckets + j] = shi[j];
-        hcnt[blockIdx.x * kBuckets + j] = sc[j];
+        unsigned long long l = 0, h = 0;
+        unsigned int c = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const unsigned long long v = slo[w][j];
+            l += v;
+            if (l < v) ++h;
+            h += shi[w][j];
+            c += sc[w][j];
+        }
+        hlo[blockIdx.x * kBuckets + j] = l;
+        hhi[blockIdx.x * kBuckets + j] = h;
+        hcnt[blockIdx.x * kBuckets + j] = c;
     }
 }
 
 // combine the block histograms (exact 128-bit sums) and choose the bucket holding the root
-__global__ void __launch_bounds__(kBuckets) k_decide(const unsigned long long* hlo, const unsigned long long* hhi,
-                                                     const unsigned int* hcnt, State* st) {
+constexpr int kDecideSplit = 4;  // threads per bucket when combining the block histograms
+
+__global__ void __launch_bounds__(kBuckets * kDecideSplit) k_decide(const unsigned long long* hlo,
+                                                                   const unsigned long long* hhi,
+                                                                   const unsigned int* hcnt, State* st) {
     __shared__ double bs[kBuckets];
     __shared__ unsigned long long bc[kBuckets];
+    __shared__ unsigned long long plo[kDecideSplit][kBuckets], phi[kDecideSplit][kBuckets], pc[kDecideSplit][kBuckets];
     if (st->done) return;
-    const int j = threadIdx.x;
+    const int j = threadIdx.x % kBuckets, part = threadIdx.x / kBuckets;
     const unsigned long long step0 = 1ULL << st->shift;
+    {
+        unsigned long long l = 0, h = 0, c = 0;
+        for (int b = part; b < kGrid; b += kDecideSplit) {
+            const unsigned long long v = hlo[b * kBuckets + j];
+            l += v;
+            if (l < v) ++h;
+            h += hhi[b * kBuckets + j];
+            c += hcnt[b * kBuckets + j];
+        }
+        plo[part][j] = l;
+        phi[part][j] = h;
+        pc[part][j] = c;
+    }
+    __syncthreads();
+    if (part != 0) return;
     unsigned long long slo = 0, shi = 0, c = 0;
-    for (int b = 0; b < kGrid; ++b) {
-        const unsigned long long v = hlo[b * kBuckets + j];
+    for (int k = 0; k < kDecideSplit; ++k) {
+        const unsigned long long v = plo[k][j];
         slo += v;
         if (slo < v) ++shi;
-        shi += hhi[b * kBuckets + j];
-        c += hcnt[b * kBuckets + j];
+        shi += phi[k][j];
+        c += pc[k][j];
     }
     // value = (shi 2^64 + slo) 2^(E - 1075)
     const int E = bucket_exp(st->lo, step0, st->hi, j);
     const int scale = (E > 0 ? E : 1) - 1075;
     bs[j] = ldexp(static_cast<double>(shi) * 18446744073709551616.0 + static_cast<double>(slo), scale);
     bc[j] = c;
-    __syncthreads();
+    asm volatile("bar.sync 1, %0;\n" ::"r"(kBuckets));  // the kBuckets threads of part 0
     if (j != 0) return;
     State x = *st;
     const unsigned long long step = 1ULL << x.shift;
@@ -406,10 +448,10 @@ int ps_unweight_max(const double* w, int64_t n, double eps, double* result, void
     unsigned long long* hhi = hlo + static_cast<size_t>(kGrid) * kBuckets;
     unsigned int* hcnt = reinterpret_cast<unsigned int*>(hhi + static_cast<size_t>(kGrid) * kBuckets);
     k_partials<<<kGrid, kThreads, 0, st>>>(w, n, part);
-    k_init<<<1, 32, 0, st>>>(part, eps, state);
+    k_init<<<1, kGrid, 0, st>>>(part, eps, state);
     for (int p = 0; p < kPasses; ++p) {
         k_hist<<<kGrid, kThreads, 0, st>>>(w, n, state, hlo, hhi, hcnt);
-        k_decide<<<1, kBuckets, 0, st>>>(hlo, hhi, hcnt, state);
+        k_decide<<<1, kBuckets * kDecideSplit, 0, st>>>(hlo, hhi, hcnt, state);
     }
     k_result<<<1, 32, 0, st>>>(state, result);
     ps::count_launches(3 + 2 * kPasses);
