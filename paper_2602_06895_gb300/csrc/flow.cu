@@ -318,8 +318,11 @@ __device__ __forceinline__ void bin_eval(const T& x, const T& x0, const T& w, co
     Fp = s * s * (d1 * xi * xi + 2.0f * s * om + d0 * (xm * xm)) * (iden * iden);
 }
 
-__device__ __forceinline__ float softplus(float a) { return a > 20.0f ? a : log1pf(__expf(a)); }
-__device__ __forceinline__ float sigmoid(float a) { return 1.0f / (1.0f + __expf(-a)); }
+// softplus and sigmoid with the hardware exponential and logarithm; for a << 0 softplus(a) ~ e^a
+// falls below the 1e-3 floor added to the knot derivatives, so log(1 + e^a) rounding to 0 there
+// is harmless
+__device__ __forceinline__ float softplus(float a) { return a > 20.0f ? a : __logf(1.0f + __expf(a)); }
+__device__ __forceinline__ float sigmoid(float a) { return __fdividef(1.0f, 1.0f + __expf(-a)); }
 
 // Raw MLP outputs of one transformed dim are read as raw[i * ld] (parameter-major layout: the
 // events of a warp read one parameter row, coalesced): widths 0..K-1, heights K..2K-1, knot
@@ -994,13 +997,15 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bia
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 32; j += 8) {
-            __align__(16) bf16 o[8];
+            const float4 b0 = *reinterpret_cast<const float4*>(bias + c0 + 32 * h + j);
+            const float4 b1v = *reinterpret_cast<const float4*>(bias + c0 + 32 * h + j + 4);
+            const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1v.x, b1v.y, b1v.z, b1v.w};
+            uint4 o;
+            uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int c = c0 + 32 * h + j + e;
-                o[e] = __float2bfloat16(silu(__uint_as_float(v[j + e]) + bias[c]));
-            }
-            *reinterpret_cast<uint4*>(act + coff(row, c0 + 32 * h + j, 128)) = *reinterpret_cast<const uint4*>(o);
+            for (int e = 0; e < 8; e += 2)
+                ow[e / 2] = pack_bf16(silu(__uint_as_float(v[j + e]) + bb[e]), silu(__uint_as_float(v[j + e + 1]) + bb[e + 1]));
+            *reinterpret_cast<uint4*>(act + coff(row, c0 + 32 * h + j, 128)) = o;
         }
     }
 }
