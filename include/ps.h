@@ -410,9 +410,20 @@ int ps_flow_train_step(ps_flow f, const double* w_map, double lr, void* stream);
 /* The loss gradient of the last sampled batch in the logical layout (host, n = n_params) and
  * the loss value, without updating parameters.  Synchronises `stream`. */
 int ps_flow_gradients(ps_flow f, const double* w_map, float* host, int64_t n, double* loss, void* stream);
-/* Number of tensor-core completion waits of the fused sampling kernels that ran out (each wait
- * is bounded; a timeout leaves that tile's outputs invalid).  0 in a healthy run.  Synchronous. */
+/* Number of tensor-core completion waits of the fused sampling kernels that ran out since the
+ * last call (the count is cleared).  Each wait is bounded; a timeout leaves that tile's outputs
+ * invalid, and the kernel still drains its MMAs and frees its TMEM before it returns, so the
+ * context stays usable.  0 in a healthy run.  Synchronises the device. */
 int ps_flow_status(ps_flow f, int64_t* timeouts);
+/* Bound of every completion wait of the fused sampling kernels, in polls of the mbarrier
+ * (default 2^24; polls <= 0 restores it).  A small bound makes the waits run out: the failure
+ * path of ps_flow_status can be exercised without faulting or hanging the device. */
+int ps_flow_set_wait_limit(ps_flow f, int polls);
+/* Test flags of the fused tcgen05 sampling kernels (0 = none, the default).  Bit 0: each CTA
+ * withholds the completion signal of its first MMA chain, so that the bounded wait on it runs
+ * out (use with a small ps_flow_set_wait_limit); the outputs of that run are invalid, the
+ * timeouts appear in ps_flow_status, and nothing faults or hangs.  Tests only. */
+int ps_flow_set_debug(ps_flow f, int flags);
 /* Loss and sum of w of the last train_step / gradients call.  Synchronises `stream`. */
 int ps_flow_loss(ps_flow f, double* loss, double* sum_w, void* stream);
 

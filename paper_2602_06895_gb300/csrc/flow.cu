@@ -948,9 +948,11 @@ __device__ __forceinline__ void commit(uint64_t* mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(mbar)));
 }
 
+constexpr int kWaitPolls = 1 << 24;  // default bound of a completion wait (polls of try_wait)
+
 // bounded wait for the given phase of the mbarrier; false on timeout
-__device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t phase) {
-    for (int it = 0; it < (1 << 24); ++it) {
+__device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t phase, int limit) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -1076,7 +1078,7 @@ template <bool kInverse>
 __global__ void __launch_bounds__(kThreads, 1)
     k_layer_umma(int64_t B, int d, float* X, float* logdet, const __grid_constant__ LayerDesc ld, const bf16* W1,
                  const float* b1, const bf16* W2, const float* b2, const bf16* W3, const float* b3,
-                 unsigned long long* status) {
+                 unsigned long long* status, int wait_limit, int debug_flags) {
     constexpr int K = 16, PQ = 3 * K + 1;
     extern __shared__ __align__(1024) unsigned char smem[];
     bf16* w1s = reinterpret_cast<bf16*>(smem + Smem::w1);
@@ -1089,6 +1091,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* b3s = reinterpret_cast<float*>(smem + Smem::b3);
     float* lds = reinterpret_cast<float*>(smem + Smem::ld);
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t drain;  // end-of-kernel completion of every MMA issued
     __shared__ uint32_t tmem_holder;
     __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1124,6 +1127,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         failed = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&drain)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -1160,9 +1164,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tid == 0) {
             fence_after();
             mma_chain(tmem, su32(ins), su32(w1s), kInPad, 128);
-            commit(&mbar);
+            // test flag: withhold the first completion signal, so that the wait runs out
+            if (!((debug_flags & 1) && tile == blockIdx.x)) commit(&mbar);
         }
-        if (!wait_phase(&mbar, phase)) failed = 1;
+        if (!wait_phase(&mbar, phase, wait_limit)) failed = 1;
         phase ^= 1;
         fence_after();
         hidden_epilogue(tlane, b1s, act, row, 32 * g);
@@ -1175,7 +1180,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_chain(tmem, su32(act), su32(w2s), 128, 128);
             commit(&mbar);
         }
-        if (!wait_phase(&mbar, phase)) failed = 1;
+        if (!wait_phase(&mbar, phase, wait_limit)) failed = 1;
         phase ^= 1;
         fence_after();
         hidden_epilogue(tlane, b2s, act, row, 32 * g);  // layer-2 reads of act are complete
@@ -1192,7 +1197,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             commit(&mbar);
         }
         for (int p = 0; p < nsets; ++p) {
-            if (!wait_phase(&mbar, phase)) failed = 1;
+            if (!wait_phase(&mbar, phase, wait_limit)) failed = 1;
             phase ^= 1;
             fence_after();
             const int q = kGroups * p + g;
@@ -1249,6 +1254,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             logdet[ev] += t;
         }
     }
+    // drain: after a wait that ran out, MMAs may still be in flight; the TMEM is freed only after
+    // a commit issued behind all of them has arrived (default bound)
+    if (tid == 0) commit(&drain);
+    if (!wait_phase(&drain, 0, kWaitPolls)) failed = 1;
+    fence_after();
     fence_before();
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
@@ -1385,6 +1395,8 @@ struct ps_flow_s {
     float* gen_X = nullptr;   // [gen_cap][d]
     float* gen_ld = nullptr;  // [gen_cap]
     unsigned long long* gen_status = nullptr;  // tensor-core waits that timed out
+    int wait_limit = umma::kWaitPolls;         // bound of every completion wait (polls)
+    int debug_flags = 0;                       // tests only (ps_flow_set_debug)
 };
 
 namespace {
@@ -1620,7 +1632,7 @@ int fused_layers(ps_flow f, int64_t B, float* X, float* ld, bool inverse, cudaSt
             auto kern = inverse ? umma::k_layer_umma<true> : umma::k_layer_umma<false>;
             kern<<<grid, umma::kThreads, umma::Smem::total, st>>>(
                 B, fd.d, X, ld, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2, f->p + lay.off_b2,
-                f->pb + lay.off_W3, f->p + lay.off_b3, f->gen_status);
+                f->pb + lay.off_W3, f->p + lay.off_b3, f->gen_status, f->wait_limit, f->debug_flags);
         }
         ps::count_launches(fd.L);
         return fcheck(cudaGetLastError(), "k_layer_umma");
@@ -1985,9 +1997,23 @@ int ps_flow_status(ps_flow f, int64_t* timeouts) {
     if (!f->gen_status) return PS_OK;
     Guard g(f->device);
     unsigned long long v = 0;
-    int s = fcheck(cudaMemcpy(&v, f->gen_status, sizeof v, cudaMemcpyDeviceToHost), "ps_flow_status");
+    int s = fcheck(cudaDeviceSynchronize(), "ps_flow_status");
+    if (s == PS_OK) s = fcheck(cudaMemcpy(&v, f->gen_status, sizeof v, cudaMemcpyDeviceToHost), "ps_flow_status");
+    if (s == PS_OK) s = fcheck(cudaMemset(f->gen_status, 0, sizeof v), "ps_flow_status");
     if (s != PS_OK) return s;
     *timeouts = static_cast<int64_t>(v);
+    return PS_OK;
+}
+
+int ps_flow_set_wait_limit(ps_flow f, int polls) {
+    if (!f) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_set_wait_limit: null flow");
+    f->wait_limit = polls > 0 ? polls : umma::kWaitPolls;
+    return PS_OK;
+}
+
+int ps_flow_set_debug(ps_flow f, int flags) {
+    if (!f || flags < 0 || flags > 1) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_set_debug: bad arguments");
+    f->debug_flags = flags;
     return PS_OK;
 }
 

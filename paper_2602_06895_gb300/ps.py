@@ -140,6 +140,8 @@ _SIGS = {
                                     C.POINTER(C.c_double), C.c_void_p]),
     "ps_flow_loss": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "ps_flow_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "ps_flow_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int]),
+    "ps_flow_set_debug": (C.c_int, [C.c_void_p, C.c_int]),
 }
 
 
@@ -610,10 +612,19 @@ class Flow:
         return loss.value, g
 
     def status(self):
-        """Tensor-core waits of the fused sampling kernels that ran out (0 in a healthy run)."""
+        """Tensor-core waits of the fused sampling kernels that ran out since the last call
+        (0 in a healthy run); clears the count."""
         v = C.c_int64()
         _fcheck(lib().ps_flow_status(self.h, C.byref(v)), "ps_flow_status")
         return v.value
+
+    def set_wait_limit(self, polls):
+        """Bound of the fused kernels' completion waits in polls (<= 0: the default)."""
+        _fcheck(lib().ps_flow_set_wait_limit(self.h, int(polls)), "ps_flow_set_wait_limit")
+
+    def set_debug(self, flags):
+        """Test flags of the fused kernels (bit 0: withhold the first completion signal)."""
+        _fcheck(lib().ps_flow_set_debug(self.h, int(flags)), "ps_flow_set_debug")
 
     def loss(self, stream=None):
         loss, sw = C.c_double(), C.c_double()

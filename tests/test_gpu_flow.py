@@ -320,3 +320,30 @@ def test_layer_by_layer_inverse_and_generate_fallback(torch_cuda):
     z_o, lq_o = orc.inverse(r.T.cpu(), bf=True)
     assert np.abs(zb.T.cpu().numpy() - z_o.numpy()).max() <= 2e-3
     assert np.abs(lq.cpu().numpy() - lq_o.numpy()).max() <= 2e-2
+
+
+def test_bounded_waits_report_timeouts_and_recover(torch_cuda):
+    """A completion signal that never arrives (the test flag withholds it) and a 4-poll bound make
+    a tcgen05 completion wait run out: the kernel counts the timeout in the status word, drains
+    its MMAs and frees its TMEM, and the next run with the defaults is correct again (no device
+    fault, no hang)."""
+    torch = torch_cuda
+    fl = ps.Flow(D, L, K, H, max_batch=1024)
+    p, orc, _ = random_params(fl, 18)
+    fl.set_params(p)
+    B = 20_000
+    r = torch.empty((D, B), dtype=torch.float64, device="cuda")
+    ld = torch.empty(B, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    assert fl.status() == 0
+    fl.set_wait_limit(4)
+    fl.set_debug(1)
+    fl.generate(B, 12, r, ld, z)
+    assert fl.status() > 0
+    fl.set_debug(0)
+    fl.set_wait_limit(0)
+    fl.generate(B, 12, r, ld, z)
+    assert fl.status() == 0
+    r_o, ld_o = orc.forward(z[:, :3000].T.cpu(), bf=True)
+    dr = np.abs(r[:, :3000].T.cpu().numpy() - r_o.numpy())
+    assert dr.max() <= 2e-3 and dr.mean() <= 1e-4, (dr.max(), dr.mean())
