@@ -163,6 +163,48 @@ def multichannel_2to5():
 
 MULTICHANNEL_EVENTS = [100_000, 4_000_000, 4_000_000, 4_000_000, 4_000_000, 3_900_000]
 
+C5_MASSES = [0.0] * 6 + [M_T, M_T]   # 2->8: six massless and two top-mass final-state particles
+C5_EVENTS = 100_000_000               # streamed in chunks of C5_CHUNK
+C5_CHUNK = 1 << 22
+
+
+def channels_2to8(n_channels=24, seed=1005):
+    """Channels of the hadronic 2->8 process (six massless particles, two of mass 173 GeV), mixing
+    t-chains and pure s-channel trees, drawn deterministically from `seed`: every third channel is
+    one binary s-channel tree of all eight particles; the others are t-chains of 3-6 clusters,
+    each cluster of two or more particles a binary decay tree.  An internal node is a resonance
+    (W, Z, H or top, Breit-Wigner, in the SDE weights) with probability 1/2, else a massless
+    power-law node; the t-chain legs are taken from side A or B at random.  Integrand: PDFs times
+    the SDE channel sum, as in the 2->5 workload."""
+    rng = np.random.default_rng(seed)
+    res = [(M_W, G_W), (M_Z, G_Z), (M_H, G_H), (M_T, G_T)]
+
+    def tree(parts):
+        if len(parts) == 1:
+            return leaf(int(parts[0]), C5_MASSES[int(parts[0])])
+        cut = int(rng.integers(1, len(parts)))
+        left, right = tree(parts[:cut]), tree(parts[cut:])
+        if rng.random() < 0.5:
+            M, G = res[int(rng.integers(len(res)))]
+            return decay(M, G, left, right)
+        return decay(0.0, 0.0, left, right, sde=False)
+
+    chans = []
+    for c in range(n_channels):
+        legs = [int(x) for x in rng.permutation(8)]
+        if c % 3 == 2:
+            root = tree(legs)
+            root = ("decay", 0.0, 0.0, NU_DEFAULT, False, root[5], root[6]) if root[0] == "decay" else root
+            tside = None
+        else:
+            m = int(rng.integers(3, 7))
+            cuts = sorted(int(x) for x in rng.choice(np.arange(1, 8), m - 1, replace=False))
+            groups = [legs[a:b] for a, b in zip([0] + cuts, cuts + [8])]
+            root = tchain(*[tree(gr) for gr in groups])
+            tside = [int(x) for x in rng.integers(0, 2, m - 2)]
+        chans.append(make_channel(root, 8, integrand="pdf_sde", tside=tside, name=f"c5_{c:02d}"))
+    return chans
+
 
 def volume_topologies(n=4, sqrt_s=1000.0, nu=0.3):
     """Massless 2->n at fixed energy with every invariant on the power law with
