@@ -21,20 +21,30 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ps_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_PROBE = os.path.join(_HERE, "rounding_probe.h")
+_RLIB = os.path.join(_HERE, "liboracle_rounding.so")
 _lock = threading.Lock()
 _lib = None
+_rlib = None
 
 MAXN, MAXK, MAXP, MAXC, NAUX = 32, 10, 16, 32, 10
 AUX = {"shat": 0, "w_ps": 1, "f": 2, "jac_vegas": 3, "p_own": 4, "cut": 5, "fail": 6, "p_own_momenta": 7, "cond": 8, "cond_p": 9}
 
 
 def build(force=False):
-    """Compile ps_oracle.c into liboracle.so (gcc, -O2 -ffp-contract=off, OpenMP)."""
+    """Compile ps_oracle.c into liboracle.so (gcc, -O2 -ffp-contract=off, OpenMP), and the
+    rounding-probe copy liboracle_rounding.so (rounding_probe.h force-included, no OpenMP)."""
+    src_time = max(os.path.getmtime(_SRC), os.path.getmtime(_PROBE))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
                "-o", _LIB + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
+    if force or not os.path.exists(_RLIB) or os.path.getmtime(_RLIB) < src_time:
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-include", _PROBE,
+               "-o", _RLIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_RLIB + ".tmp", _RLIB)
     return _LIB
 
 
@@ -65,51 +75,66 @@ class Sde(C.Structure):
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 
+def _setup(L):
+    L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+    L.orc_bits_to_unit.restype = C.c_double
+    L.orc_bits_to_unit.argtypes = [C.c_uint64]
+    L.orc_random_batch.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int, _D, C.c_int]
+    L.orc_kallen.restype = C.c_double
+    L.orc_kallen.argtypes = [C.c_double] * 3
+    L.orc_map_nu.argtypes = [C.c_double] * 6 + [C.POINTER(C.c_double)] * 2
+    L.orc_map_bw.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)] * 2
+    L.orc_inv_nu.restype = C.c_double
+    L.orc_inv_nu.argtypes = [C.c_double] * 6
+    L.orc_inv_bw.restype = C.c_double
+    L.orc_inv_bw.argtypes = [C.c_double] * 5
+    L.orc_r_to_x1x2.argtypes = [C.c_double] * 3 + [C.POINTER(C.c_double)] * 3
+    L.orc_two_body_decay.restype = C.c_double
+    L.orc_two_body_decay.argtypes = [C.c_double] * 5 + [C.c_void_p, _D, _D]
+    L.orc_t_min_max.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)] * 2
+    L.orc_two_to_two.restype = C.c_double
+    L.orc_two_to_two.argtypes = [C.c_double, _D, _D] + [C.c_double] * 6 + [_D, _D]
+    L.orc_vegas_map.restype = C.c_double
+    L.orc_vegas_map.argtypes = [C.c_double, _D, C.c_int, C.POINTER(C.c_double)]
+    L.orc_vegas_inv.restype = C.c_double
+    L.orc_vegas_inv.argtypes = [C.c_double, _D, C.c_int]
+    L.orc_vegas_accumulate.argtypes = [_D, C.c_int, _D, C.c_int64, C.c_int, C.c_int, _D]
+    L.orc_vegas_rebin.argtypes = [_D, _D, _D, C.c_int, C.c_double]
+    L.orc_channel_dims.restype = C.c_int
+    L.orc_channel_dims.argtypes = [C.POINTER(Channel)]
+    L.orc_forward_batch.argtypes = [C.POINTER(Channel), C.POINTER(Sde), C.c_int, C.c_void_p, C.c_int64,
+                                    _D, _D, _D, _D, _D, C.c_void_p, C.c_int]
+    L.orc_generate_batch.argtypes = [C.POINTER(Channel), C.POINTER(Sde), C.c_int, C.c_void_p, C.c_uint64,
+                                     C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p, _D, C.c_void_p,
+                                     C.c_int]
+    L.orc_inverse_batch.argtypes = [C.POINTER(Channel), C.c_void_p, C.c_int64, _D, _D, _D, C.c_int]
+    L.orc_stats.argtypes = [_D, C.c_int64, _D]
+    L.orc_sde_weights.argtypes = [C.POINTER(Sde), C.c_int, C.c_int64, C.c_int, _D, _D]
+    L.orc_max_threads.restype = C.c_int
+    assert L.orc_sizeof_channel() == C.sizeof(Channel)
+    assert L.orc_sizeof_sde() == C.sizeof(Sde)
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(_LIB)
-            L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
-            L.orc_bits_to_unit.restype = C.c_double
-            L.orc_bits_to_unit.argtypes = [C.c_uint64]
-            L.orc_random_batch.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int, _D, C.c_int]
-            L.orc_kallen.restype = C.c_double
-            L.orc_kallen.argtypes = [C.c_double] * 3
-            L.orc_map_nu.argtypes = [C.c_double] * 6 + [C.POINTER(C.c_double)] * 2
-            L.orc_map_bw.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)] * 2
-            L.orc_inv_nu.restype = C.c_double
-            L.orc_inv_nu.argtypes = [C.c_double] * 6
-            L.orc_inv_bw.restype = C.c_double
-            L.orc_inv_bw.argtypes = [C.c_double] * 5
-            L.orc_r_to_x1x2.argtypes = [C.c_double] * 3 + [C.POINTER(C.c_double)] * 3
-            L.orc_two_body_decay.restype = C.c_double
-            L.orc_two_body_decay.argtypes = [C.c_double] * 5 + [C.c_void_p, _D, _D]
-            L.orc_t_min_max.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)] * 2
-            L.orc_two_to_two.restype = C.c_double
-            L.orc_two_to_two.argtypes = [C.c_double, _D, _D] + [C.c_double] * 6 + [_D, _D]
-            L.orc_vegas_map.restype = C.c_double
-            L.orc_vegas_map.argtypes = [C.c_double, _D, C.c_int, C.POINTER(C.c_double)]
-            L.orc_vegas_inv.restype = C.c_double
-            L.orc_vegas_inv.argtypes = [C.c_double, _D, C.c_int]
-            L.orc_vegas_accumulate.argtypes = [_D, C.c_int, _D, C.c_int64, C.c_int, C.c_int, _D]
-            L.orc_vegas_rebin.argtypes = [_D, _D, _D, C.c_int, C.c_double]
-            L.orc_channel_dims.restype = C.c_int
-            L.orc_channel_dims.argtypes = [C.POINTER(Channel)]
-            L.orc_forward_batch.argtypes = [C.POINTER(Channel), C.POINTER(Sde), C.c_int, C.c_void_p, C.c_int64,
-                                            _D, _D, _D, _D, _D, C.c_void_p, C.c_int]
-            L.orc_generate_batch.argtypes = [C.POINTER(Channel), C.POINTER(Sde), C.c_int, C.c_void_p, C.c_uint64,
-                                             C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p, _D, C.c_void_p,
-                                             C.c_int]
-            L.orc_inverse_batch.argtypes = [C.POINTER(Channel), C.c_void_p, C.c_int64, _D, _D, _D, C.c_int]
-            L.orc_stats.argtypes = [_D, C.c_int64, _D]
-            L.orc_sde_weights.argtypes = [C.POINTER(Sde), C.c_int, C.c_int64, C.c_int, _D, _D]
-            L.orc_max_threads.restype = C.c_int
-            assert L.orc_sizeof_channel() == C.sizeof(Channel)
-            assert L.orc_sizeof_sde() == C.sizeof(Sde)
-            _lib = L
+            _lib = _setup(C.CDLL(_LIB))
     return _lib
+
+
+def rounding_lib():
+    """The rounding-probe copy of the oracle (see rounding_probe.h)."""
+    global _rlib
+    with _lock:
+        if _rlib is None:
+            build()
+            L = _setup(C.CDLL(_RLIB))
+            L.orc_rounding_seed.argtypes = [C.c_uint64]
+            _rlib = L
+    return _rlib
 
 
 def max_threads():
@@ -223,7 +248,41 @@ def _threads(threads):
 
 def forward(ch, r, grid=None, channels=None, chan=0, threads=None, aux=False):
     """Forward map of a batch: r [B, d] -> dict(mom [B, n+2, 4], x [B, 2], w [B], alpha [B], aux)."""
-    L = lib()
+    return _forward(lib(), ch, r, grid, channels, chan, threads, aux)
+
+
+def rounding_spread(ch, r, grid=None, channels=None, chan=0, runs=8, base=None):
+    """Rounding sensitivity of the forward map by stochastic arithmetic (see rounding_probe.h):
+    the oracle re-run `runs` times with every elementary-function result moved by a random
+    whole number of ulps in [-2, 2].  Per event: "w" the largest relative change of a nonzero
+    weight, "alpha" that of the multichannel weight, "mom" the largest change of a momentum
+    component over the event's largest energy, "flip" whether some run changed w == 0."""
+    if base is None:
+        base = forward(ch, r, grid, channels, chan)
+    L = rounding_lib()
+    B = base["w"].shape[0]
+    scale = np.max(np.abs(base["mom"][:, :, 0]), axis=1)
+    scale = np.where(scale > 0, scale, 1.0)
+    nz = base["w"] != 0
+    out = {"w": np.zeros(B), "alpha": np.zeros(B), "mom": np.zeros(B), "flip": np.zeros(B, bool)}
+    for k in range(runs):
+        L.orc_rounding_seed(k + 1)
+        o = _forward(L, ch, r, grid, channels, chan, 1, False)
+        both = nz & (o["w"] != 0)
+        out["flip"] |= (o["w"] != 0) != nz
+        rel = np.zeros(B)
+        rel[both] = np.abs(o["w"][both] / base["w"][both] - 1.0)
+        out["w"] = np.maximum(out["w"], rel)
+        ra = np.zeros(B)
+        ab = both & (base["alpha"] != 0)
+        ra[ab] = np.abs(o["alpha"][ab] / base["alpha"][ab] - 1.0)
+        out["alpha"] = np.maximum(out["alpha"], ra)
+        dm = np.max(np.abs(o["mom"] - base["mom"]), axis=(1, 2)) / scale
+        out["mom"] = np.maximum(out["mom"], np.where(both, dm, 0.0))
+    return out
+
+
+def _forward(L, ch, r, grid, channels, chan, threads, aux):
     c = encode_channel(ch)
     sde = encode_sde(channels if channels is not None else [ch])
     r = np.ascontiguousarray(r, dtype=np.float64)

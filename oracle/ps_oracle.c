@@ -797,6 +797,12 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
             orc_t_min_max(scur, mA2, mB2, mt1, mt2, &tlo, &thi);
             if (tlo < 0.0) tlo = 0.0;
             if (thi < tlo) { fail = 1; thi = tlo; }
+            {   /* condition number of the |t| range width: both bounds carry rounding relative to |t|_max,
+                 * and the Jacobian of the |t| map is proportional to |t|_max - |t|_min; spacelike
+                 * incoming legs of a light block make the range a sliver of a large |t| */
+                double k = thi > tlo ? thi / (thi - tlo) : 1e300;
+                if (k > cond) cond = k;
+            }
             fail |= orc_map_nu(r[L.d_tt[i]], 0.0, ch->t_nu, tlo, thi, ch->a, &tabs, &jt);
             double q1[4], q2[4];
             double j22 = orc_two_to_two(r[L.d_tphi[i]], pA, pB, tabs, mt1, mt2, scur, mA2, mB2, q1, q2);

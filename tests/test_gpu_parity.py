@@ -16,9 +16,18 @@ Tolerances (stated per quantity; the derivation is in the design notes):
   alpha     relative 1e-12, or the conditioning bound of a propagator evaluated from
             momenta (see _alpha_tolerance)
   integers  (cut decisions, counts, VEGAS bin indices, Philox bits) bit-exact
-In addition, at least 95% of the events whose random numbers are not pushed to within 1e-8 of
-0 or 1 meet the flat 1e-12 bar on momenta and weights (the conditioning-aware bounds only cover
-the ill-conditioned tail; t-chains through light clusters are the bulk of it).
+  spread    the analytic kappa assumes inputs good to an ulp; nested sliver ranges compound the
+            libm differences of earlier invariants (a range spanning many decades gives its top
+            end ~|exponent| ulps, which the next sliver range amplifies).  The oracle's own
+            rounding sensitivity is therefore also measured by stochastic arithmetic
+            (oracle.rounding_spread: 8 re-runs with every elementary-function result moved by up
+            to 2 ulps -- CUDA's double functions are within 1-2 ulps of the exact value, glibc's
+            within about 1) and every per-event bound above is at least 4x that spread; a zero
+            weight may differ where a perturbed run of the oracle also changes it.
+In addition, at least 99% of the events whose random numbers are not pushed to within 1e-8 of
+0 or 1 meet the bounds without their safety factors -- max(1e-12, 4 eps kappa, spread) on
+weights and momenta: the bulk must agree as closely as two roundings of the oracle do, and
+only a tail may use the factor 32 and the factor 4 on the spread.
 """
 import math
 
@@ -35,12 +44,14 @@ RTOL = 1e-12
 EPS = 2.0 ** -52
 
 
-def weight_tol(orc):
-    return np.maximum(RTOL, 32.0 * EPS * orc["aux"][:, O.AUX["cond"]])
+def weight_tol(orc, spread=None):
+    t = np.maximum(RTOL, 32.0 * EPS * orc["aux"][:, O.AUX["cond"]])
+    return t if spread is None else np.maximum(t, 4.0 * spread["w"])
 
 
-def momentum_tol(orc):
-    return np.maximum(RTOL, 32.0 * EPS * orc["aux"][:, O.AUX["cond_p"]])
+def momentum_tol(orc, spread=None):
+    t = np.maximum(RTOL, 32.0 * EPS * orc["aux"][:, O.AUX["cond_p"]])
+    return t if spread is None else np.maximum(t, 4.0 * spread["mom"])
 
 
 @pytest.fixture(scope="module")
@@ -79,25 +90,38 @@ def run_map(torch, channels, which, r, grid=None, block=128):
     return res
 
 
-def compare(gpu, orc, ch, label, alpha_tol=None, r=None):
+def compare(gpu, orc, ch, label, alpha_tol=None, r=None, spread=None):
     mom_g, mom_o = gpu["mom"], orc["mom"]
     scale = np.max(np.abs(mom_o[:, :, 0]), axis=1)
     # zero weights (cuts, empty ranges) are integer outcomes and must agree -- except at an exact
-    # threshold, where the weight itself is undetermined (its bound 32 eps kappa reaches 1)
+    # threshold, where the weight itself is undetermined (its bound reaches 1, or a perturbed
+    # rounding of the oracle changes it too)
     bad = np.flatnonzero((gpu["w"] == 0) != (orc["w"] == 0))
     n_threshold = 0
     if "aux" in orc:
-        n_threshold = int(np.sum(weight_tol(orc)[bad] >= 1.0))
-        bad = bad[weight_tol(orc)[bad] < 1.0]
+        undetermined = weight_tol(orc, spread) >= 1.0
+        if spread is not None:
+            undetermined |= spread["flip"]
+        n_threshold = int(np.sum(undetermined[bad]))
+        bad = bad[~undetermined[bad]]
     assert bad.size == 0, (label, "zero weights differ", bad[:5].tolist(), gpu["w"][bad[:5]].tolist(),
                            orc["w"][bad[:5]].tolist(), orc["aux"][bad[:5]].tolist() if "aux" in orc else None)
     ok = (orc["w"] != 0) & (gpu["w"] != 0)
     dm = np.max(np.abs(mom_g - mom_o), axis=(1, 2))
-    ptol = momentum_tol(orc)[ok] if "aux" in orc else RTOL
-    flat_ok = (dm[ok] <= RTOL * scale[ok]) & (np.abs(gpu["w"][ok] / orc["w"][ok] - 1.0) <= RTOL)
+    ptol = momentum_tol(orc, spread)[ok] if "aux" in orc else RTOL
+    # the bulk: the per-event bounds without their safety factors (spread x1, kappa x4)
+    bulk_w, bulk_p, need = RTOL, RTOL, 0.95
+    if "aux" in orc:
+        bulk_w = np.maximum(RTOL, 4.0 * EPS * orc["aux"][ok, O.AUX["cond"]])
+        bulk_p = np.maximum(RTOL, 4.0 * EPS * orc["aux"][ok, O.AUX["cond_p"]])
+        need = 0.99
+        if spread is not None:
+            bulk_w = np.maximum(bulk_w, spread["w"][ok])
+            bulk_p = np.maximum(bulk_p, spread["mom"][ok])
+    bulk_ok = (dm[ok] <= bulk_p * scale[ok]) & (np.abs(gpu["w"][ok] / orc["w"][ok] - 1.0) <= bulk_w)
     interior = np.ones(ok.sum(), bool) if r is None else np.all((r[ok] > 1e-8) & (r[ok] < 1 - 1e-8), axis=1)
-    frac = float(flat_ok[interior].mean()) if interior.any() else 1.0
-    assert frac >= 0.95, (label, "fraction of interior events within the flat 1e-12 bar", frac)
+    frac = float(bulk_ok[interior].mean()) if interior.any() else 1.0
+    assert frac >= need, (label, "fraction of interior events within the bulk bar", frac)
     ratio = dm[ok] / (ptol * scale[ok])
     worst = int(np.flatnonzero(ok)[np.argmax(ratio)])
     assert np.all(ratio <= 1.0), (label, "momenta", "worst event", worst, "rel err", dm[worst] / scale[worst],
@@ -106,7 +130,7 @@ def compare(gpu, orc, ch, label, alpha_tol=None, r=None):
         rx = np.abs(gpu["x"] / orc["x"] - 1.0)
         assert np.all(rx[ok] <= RTOL), (label, "x", rx[ok].max())
     rw = np.abs(gpu["w"][ok] / orc["w"][ok] - 1.0)
-    tol = weight_tol(orc)[ok]
+    tol = weight_tol(orc, spread)[ok]
     assert np.all(rw <= tol), (label, "weight", "worst event", int(np.flatnonzero(ok)[np.argmax(rw / tol)]),
                                float(np.max(rw / tol)), rw.max(), int(np.sum(rw > RTOL)))
     if alpha_tol is not None:
@@ -130,10 +154,13 @@ def parity_channels():
     multi = W.multichannel_2to5()
     for i in range(len(multi)):
         out.append((multi[i]["name"], multi, i, None))
+    c5 = W.channels_2to8()
+    for i in range(len(c5)):
+        out.append((c5[i]["name"], c5, i, None))
     return out
 
 
-def _alpha_tolerance(orc):
+def _alpha_tolerance(orc, spread=None):
     # alpha_c = P_c / sum_j P_j with the other channels' P_j from momenta.  A propagator
     # 1/((s-M^2)^2 + M^2 G^2) evaluated from momenta inherits the rounding of s = (sum p)^2:
     # the momenta agree to 32 eps kappa_p E (E the event's energy scale), so s to ~4 of that
@@ -143,7 +170,8 @@ def _alpha_tolerance(orc):
     e = np.max(np.abs(orc["mom"][:, :, 0]), axis=1)
     kp = np.maximum(1.0, orc["aux"][:, O.AUX["cond_p"]])
     rel_s = 4.0 * 32.0 * EPS * kp * e * e / 0.5
-    return np.maximum(RTOL, np.minimum(1.0, rel_s) * (1.0 - a))
+    t = np.maximum(RTOL, np.minimum(1.0, rel_s) * (1.0 - a))
+    return t if spread is None else np.maximum(t, 4.0 * spread["alpha"])
 
 
 @pytest.mark.parametrize("case", parity_channels(), ids=lambda c: c[0])
@@ -155,13 +183,14 @@ def test_explicit_input_parity(torch_cuda, case):
     r = W.uniform_r(4242 + which, 4999, d, edge_fraction=0.02)
     gpu = run_map(torch_cuda, chans, which, r, grid=grid)
     orc = O.forward(ch, r, grid=grid, channels=chans, chan=which, aux=True)
-    at = _alpha_tolerance(orc) if ch["integrand"] == "pdf_sde" else None
-    n_thr = compare(gpu, orc, ch, name, alpha_tol=at, r=r)
+    spread = O.rounding_spread(ch, r, grid=grid, channels=chans, chan=which, base=orc)
+    at = _alpha_tolerance(orc, spread) if ch["integrand"] == "pdf_sde" else None
+    n_thr = compare(gpu, orc, ch, name, alpha_tol=at, r=r, spread=spread)
     st = O.stats(orc["w"])
     s = gpu["stats"]
     assert s["n"] == st["n"] and abs(s["n_nonzero"] - st["n_nonzero"]) <= n_thr
     for k in ("sum_w", "sum_w2", "max_w"):
-        assert abs(s[k] - st[k]) <= max(RTOL, float(np.max(weight_tol(orc)))) * abs(st[k]), (name, k)
+        assert abs(s[k] - st[k]) <= max(RTOL, float(np.max(weight_tol(orc, spread)))) * abs(st[k]), (name, k)
 
 
 @pytest.mark.parametrize("B", [0, 1, 31, 33, 127, 128, 129, 1000])
