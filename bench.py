@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--no-flow", action="store_true")
     ap.add_argument("--no-unweight", action="store_true")
     ap.add_argument("--no-global", action="store_true")
+    ap.add_argument("--no-streamed", action="store_true")
     ap.add_argument("--flow-steps", type=int, default=400)
     ap.add_argument("--flow-infer-events", type=int, default=EVENTS)
-    ap.add_argument("--leg", default="all", choices=["all", "flow", "unweight", "global"],
+    ap.add_argument("--leg", default="all", choices=["all", "flow", "unweight", "global", "streamed"],
                     help="run one secondary leg alone (for profiling); prints its object only")
     return ap.parse_args()
 
@@ -173,6 +174,109 @@ def timed(torch, fn, reps, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best=None, host_copy=False):
+    """The 2->8 workload (six massless partons and two 173 GeV particles, 24 channels, SDE weights
+    in-kernel) streamed: 1e8 events in chunks of 2^22, each chunk one persistent launch for all 24
+    channels (CUDA graph, tiles and schedule from the autotuner) into one of two output buffers, its
+    per-channel sums added on the device (streaming statistics, read once at the end).  With
+    host_copy the record of each chunk also goes to pinned host memory on a second stream while
+    the next chunk is generated."""
+    import numpy as np
+
+    from paper_2602_06895_gb300 import distributed as D
+
+    chans = W.channels_2to8()
+    nc, chunk, total = len(chans), W.C5_CHUNK, W.C5_EVENTS
+    split = lambda n: [n // nc + (1 if c < n % nc else 0) for c in range(nc)]
+    n_full, tail = divmod(total, chunk)
+    table = None
+    if best is None:
+        best, table = ps.autotune(chans, split(chunk // 4), precision=precision, blocks=(64, 128, 256),
+                                  ctas=(1, 2, 3, 4), reps=2, device=local)
+    prog = ps.program_for(chans, device=local, precision=precision, **best)
+    n_mom = chans[0]["n"] + 2
+    bufs = [prog.alloc(split(chunk), n_mom, alpha=True, device=local) for _ in range(2)]
+    execs = [prog.exec_create(split(chunk), o, w) for o, w in bufs]
+    plan = [(execs[k % 2], k % 2, chunk) for k in range(n_full)]
+    if tail:
+        b = n_full % 2
+        plan.append((prog.exec_create(split(tail), *bufs[b]), b, tail))
+    seed = 1005
+    # warm-up: one chunk per buffer
+    for b in range(2):
+        execs[b].launch(seed, D.step_offset(rank, world, chunk, len(plan) + b), stream)
+    torch.cuda.synchronize()
+
+    copy_stream = host = None
+    if host_copy:
+        copy_stream = torch.cuda.Stream(device=local)
+        host = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()} for o, _ in bufs]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    d2h = 0
+    prog.stats_accumulate(True, stream)  # per-channel sums of all chunks add up on the device
+    l0 = ps.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for k, (ex, b, n) in enumerate(plan):
+        if host_copy and k >= 2:
+            stream.wait_event(copied[b])  # the copy of the chunk that last used this buffer is done
+        ex.launch(seed, D.step_offset(rank, world, chunk, k), stream)
+        if host_copy:
+            gen = torch.cuda.Event()
+            gen.record(stream)
+            copy_stream.wait_event(gen)
+            with torch.cuda.stream(copy_stream):
+                for key, v in bufs[b][0].items():
+                    cols = v[:, :n] if v.dim() == 2 else v[:n]
+                    dst = host[b][key][:, :n] if v.dim() == 2 else host[b][key][:n]
+                    dst.copy_(cols, non_blocking=True)
+                    d2h += cols.numel() * cols.element_size()
+            copied[b].record(copy_stream)
+    st = prog.stats(stream)  # the running per-channel sums of all chunks, read once
+    e1.record(stream)
+    if host_copy:
+        copy_stream.synchronize()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    prog.stats_accumulate(False, stream)
+    acc = np.array([(sc["n"], sc["n_nonzero"], sc["sum_w"], sc["sum_w2"]) for sc in st])
+    max_w = max(sc["max_w"] for sc in st)
+    launches = ps.launch_count() - l0
+    if world > 1:
+        t = torch.tensor([ms, wall], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, wall = float(t[0]), float(t[1])
+        a = torch.tensor(acc, device="cuda")
+        torch.distributed.all_reduce(a)
+        acc = a.cpu().numpy()
+    n_ev = acc[:, 0].sum()
+    # equal counts per channel: the integral is nc x the mean pooled weight, Kish ESS of the pool
+    integral = nc * acc[:, 2].sum() / n_ev
+    ess = acc[:, 2].sum() ** 2 / acc[:, 3].sum()
+    var_mean = (acc[:, 3].sum() / n_ev - (acc[:, 2].sum() / n_ev) ** 2) / n_ev
+    res = {"workload": "2->8 at sqrt(S)=13 TeV: 6 massless + 2 x 173 GeV, 24 channels (t-chains of 3-6 "
+                       "clusters with W/Z/H/top resonances, s-channel trees), SDE multichannel weights "
+                       "in-kernel, f(x)=x^-1.1(1-x)^3, uniform r (no VEGAS)",
+           "events": int(n_ev), "chunk": chunk, "chunks": len(plan), "precision": precision,
+           "value": world * total / (ms / 1e3), "unit": "streamed events/s", "ms_total": ms,
+           "wall_s": wall, "map_launches_per_chunk": 1, "gpu_launches": int(launches), "cuda_graph": True,
+           "autotuned": best, "integral": integral, "rel_err": math.sqrt(var_mean) * nc / integral,
+           "ess": ess, "effective_events_per_s": ess / (ms / 1e3), "max_w": max_w,
+           "nonzero_fraction": acc[:, 1].sum() / n_ev}
+    if table is not None:
+        res["autotune_table"] = table
+    if host_copy:
+        res["e2e"] = {"value": world * total / wall, "unit": "streamed events/s", "h2d_bytes_per_chunk": 16,
+                      "d2h_bytes_per_chunk": int(d2h / len(plan)) + 40 * nc,
+                      "note": "event records of every chunk copied to pinned host memory on a second stream, "
+                              "double-buffered; timed on the host clock"}
+    del execs, plan, bufs
+    return res
 
 
 FLOW_LAYERS, FLOW_BINS, FLOW_HIDDEN, FLOW_BATCH = 6, 16, 128, 1 << 16
@@ -366,6 +470,8 @@ def main():
         ess = st["sum_w"] ** 2 / st["sum_w2"]
         if args.leg == "flow":
             res = flow_leg(args, ps, W, torch, grid, ess / N, ms / N, stream)
+        elif args.leg == "streamed":
+            res = streamed_leg(ps, W, torch, stream, rank, world, local)
         elif args.leg == "unweight":
             res = unweight_leg(ps, torch, out["weight"], stream)
         else:
@@ -493,6 +599,17 @@ def main():
                  "integral": sum(c["sum_w"] for c in cst) / 1.0,
                  "per_channel_sum_w": [c["sum_w"] for c in cst]}
 
+    # 2->8, 24 channels, 1e8 events streamed in 2^22-event chunks: FP64 (device-resident and with the
+    # records copied to the host) and the mixed-precision form on the same events
+    streamed = None
+    if not args.no_streamed:
+        streamed = streamed_leg(ps, W, torch, stream, rank, world, local, host_copy=not args.no_e2e)
+        sm = streamed_leg(ps, W, torch, stream, rank, world, local, precision="mixed")
+        streamed["mixed_precision"] = {k: sm[k] for k in ("value", "ms_total", "integral", "rel_err", "ess",
+                                                          "effective_events_per_s", "autotuned")}
+        streamed["mixed_precision"]["integral_rel_diff_vs_fp64_same_events"] = sm["integral"] / streamed["integral"] - 1
+        streamed["mixed_precision"]["speedup_vs_fp64"] = streamed["ms_total"] / sm["ms_total"]
+
     flow = None
     if not args.no_flow and rank == 0:
         flow = flow_leg(args, ps, W, torch, grid, ess / N, ms / N, stream)
@@ -528,8 +645,8 @@ def main():
                                                         "ess_per_step": ess, "events_for_0.5pct": n_half_pct},
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
-            "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi, "flow": flow,
-            "unweighting": unweight, "global_multichannel": glob}
+            "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi, "streamed_2to8": streamed,
+            "flow": flow, "unweighting": unweight, "global_multichannel": glob}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -310,8 +310,19 @@ typedef struct {
     double max_w;
 } ps_channel_stats;
 
-/* Copy the statistics of the last ps_generate / ps_map (synchronises `stream`). */
+/* Copy the statistics of the last ps_generate / ps_map (synchronises `stream`); in
+ * streaming mode (ps_stats_accumulate) the running statistics of every launch since the
+ * mode was enabled. */
 int ps_stats(ps_program p, ps_channel_stats* host_out, int n_ch, void* stream);
+
+/* Streaming mode for event samples generated in chunks (the integral over all chunks,
+ * Sec. 2 Monte Carlo estimate from the per-channel sums).  enable != 0 zeroes the program's
+ * statistics and makes every later reduction, including those of captured ps_exec graphs,
+ * add its per-channel sums to them (n, n_nonzero, sum_w, sum_w2; max_w by maximum) in stream
+ * order, so a stream of chunks needs one ps_stats read at its end.  enable == 0 restores
+ * per-launch statistics.  Enqueued on `stream` (asynchronous); the mode applies to launches
+ * ordered after it.  Errors: PS_ERR_INVALID_ARGUMENT for a null program, PS_ERR_CUDA. */
+int ps_stats_accumulate(ps_program p, int enable, void* stream);
 
 /* VEGAS training: while enabled, ps_generate also accumulates, per channel, mapped
  * dimension j and bin k, the sum of w^2 over events whose r_j falls in bin k. */

@@ -1070,6 +1070,7 @@ struct ps_program_s {
     double* d_stats = nullptr;
     double* d_hist = nullptr;
     unsigned long long* d_status = nullptr;
+    int32_t* d_stats_mode = nullptr;  // nonzero: reductions add into d_stats (ps_stats_accumulate)
     size_t hist_total = 0;
     bool training = false;
 };
@@ -1099,6 +1100,7 @@ void free_device(ps_program p) {
     cudaFree(p->d_stats);
     cudaFree(p->d_hist);
     cudaFree(p->d_status);
+    cudaFree(p->d_stats_mode);
 }
 
 int64_t tiles_of(int64_t n, int block) { return (n + block - 1) / block; }
@@ -1147,6 +1149,7 @@ int fill_launch(ps_program p, const int* chans, const int64_t* counts, int n, co
         return fail(PS_ERR_INVALID_ARGUMENT, "workspace must be 256-byte aligned");
     lp->tile_partials = static_cast<double*>(workspace);
     lp->status = p->d_status;
+    lp->stats_mode = p->d_stats_mode;
     lp->mixed = p->opt.precision == PS_PRECISION_MIXED ? 1 : 0;
     lp->hist = p->training ? p->d_hist : nullptr;
     if (out) {
@@ -1253,12 +1256,14 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
     if (st == PS_OK) st = cuda_check(cudaMalloc(&p->d_stats, 5 * n_ch * sizeof(double)), "cudaMalloc stats");
     if (st == PS_OK) st = cuda_check(cudaMalloc(&p->d_hist, std::max<size_t>(p->hist_total, 1) * sizeof(double)), "cudaMalloc hist");
     if (st == PS_OK) st = cuda_check(cudaMalloc(&p->d_status, 4 * sizeof(unsigned long long)), "cudaMalloc status");
+    if (st == PS_OK) st = cuda_check(cudaMalloc(&p->d_stats_mode, sizeof(int32_t)), "cudaMalloc stats mode");
     if (st == PS_OK) st = cuda_check(cudaMemcpy(p->d_code, code.data(), code.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "upload code");
     if (st == PS_OK) st = cuda_check(cudaMemcpy(p->d_imm, imm.data(), imm.size() * sizeof(double), cudaMemcpyHostToDevice), "upload imm");
     if (st == PS_OK) st = cuda_check(cudaMemcpy(p->d_grid, p->h_grid.data(), p->h_grid.size() * sizeof(double), cudaMemcpyHostToDevice), "upload grid");
     if (st == PS_OK) st = cuda_check(cudaMemset(p->d_stats, 0, 5 * n_ch * sizeof(double)), "memset stats");
     if (st == PS_OK) st = cuda_check(cudaMemset(p->d_hist, 0, std::max<size_t>(p->hist_total, 1) * sizeof(double)), "memset hist");
     if (st == PS_OK) st = cuda_check(cudaMemset(p->d_status, 0, 4 * sizeof(unsigned long long)), "memset status");
+    if (st == PS_OK) st = cuda_check(cudaMemset(p->d_stats_mode, 0, sizeof(int32_t)), "memset stats mode");
     if (st != PS_OK) { free_device(p); delete p; return st; }
 
     ps::LaunchParams lp;
@@ -1543,6 +1548,16 @@ int ps_stats(ps_program p, ps_channel_stats* host, int n_ch, void* stream) {
         host[c].max_w = h[5 * c + 4];
     }
     return PS_OK;
+}
+
+int ps_stats_accumulate(ps_program p, int enable, void* stream) {
+    if (!p) return fail(PS_ERR_INVALID_ARGUMENT, "ps_stats_accumulate: null program");
+    DeviceGuard dg(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int st = PS_OK;
+    if (enable) st = cuda_check(cudaMemsetAsync(p->d_stats, 0, 5 * p->n_ch * sizeof(double), s), "zero stats");
+    if (st == PS_OK) st = cuda_check(cudaMemsetAsync(p->d_stats_mode, enable ? 1 : 0, sizeof(int32_t), s), "stats mode");
+    return st;
 }
 
 int ps_vegas_training(ps_program p, int enable) {

@@ -940,7 +940,8 @@ __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ Lau
     }
 }
 
-// One CTA per channel sums the channel's tile partials in a fixed order (deterministic).
+// One CTA per channel sums the channel's tile partials in a fixed order (deterministic); in
+// streaming mode the launch's sums are added to the statistics of the earlier launches.
 __global__ void __launch_bounds__(256) ps_reduce_kernel(const __grid_constant__ LaunchParams lp, double* stats) {
     const int c = blockIdx.x;
     const ChannelLaunch& C = lp.ch[c];
@@ -971,11 +972,19 @@ __global__ void __launch_bounds__(256) ps_reduce_kernel(const __grid_constant__ 
     }
     if (threadIdx.x == 0) {
         double* o = stats + 5 * c;
-        o[0] = static_cast<double>(C.n_events);
-        o[1] = red[0][0];
-        o[2] = red[1][0];
-        o[3] = red[2][0];
-        o[4] = red[3][0];
+        if (lp.stats_mode && *lp.stats_mode != 0) {  // streaming: add this launch to the running sums
+            o[0] += static_cast<double>(C.n_events);
+            o[1] += red[0][0];
+            o[2] += red[1][0];
+            o[3] += red[2][0];
+            o[4] = fmax(o[4], red[3][0]);
+        } else {
+            o[0] = static_cast<double>(C.n_events);
+            o[1] = red[0][0];
+            o[2] = red[1][0];
+            o[3] = red[2][0];
+            o[4] = red[3][0];
+        }
     }
 }
 

@@ -92,6 +92,7 @@ struct LaunchParams {
     double* tile_partials;         // [n_tiles][4]
     double* hist;                  // VEGAS histograms (program-owned), or nullptr
     unsigned long long* status;    // [4]
+    const int32_t* stats_mode;     // device flag: nonzero adds each launch's sums into the statistics
     ChannelLaunch ch[kMaxChannels];
 };
 

@@ -101,6 +101,7 @@ _SIGS = {
     "ps_exec_launch": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p]),
     "ps_exec_free": (C.c_int, [C.c_void_p]),
     "ps_stats": (C.c_int, [C.c_void_p, C.POINTER(ChannelStats), C.c_int, C.c_void_p]),
+    "ps_stats_accumulate": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "ps_vegas_training": (C.c_int, [C.c_void_p, C.c_int]),
     "ps_vegas_histogram": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "ps_vegas_adapt": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
@@ -424,6 +425,11 @@ class Program:
         _check(lib().ps_stats(self.h, arr, self.n_ch, _stream_ptr(stream)), "ps_stats")
         return [{"n": s.n, "n_nonzero": s.n_nonzero, "sum_w": s.sum_w, "sum_w2": s.sum_w2, "max_w": s.max_w}
                 for s in arr]
+
+    def stats_accumulate(self, enable, stream=None):
+        """Streaming mode (ps_stats_accumulate): zero the statistics and let every later launch add
+        its per-channel sums; stats() then returns the running totals."""
+        _check(lib().ps_stats_accumulate(self.h, 1 if enable else 0, _stream_ptr(stream)), "ps_stats_accumulate")
 
     def status(self, stream=None):
         arr = (C.c_int64 * 4)()

@@ -83,3 +83,34 @@ def test_programs_with_different_slot_files_coexist(torch_cuda):
     small.generate([1000], 3, o2, w2)
     torch.cuda.synchronize()
     assert big.stats()[1]["n"] == 1000 and small.stats()[0]["n"] == 1000
+
+
+def test_stats_accumulate_adds_launches_in_order(torch_cuda):
+    """Streaming statistics: generate and CUDA-graph launches add their per-channel sums, in stream
+    order, to the running totals; turning the mode off restores per-launch statistics."""
+    chans = W.multichannel_2to5()
+    counts = [1000, 5000, 0, 3000, 2000, 777]
+    prog = ps.program_for(chans)
+    out, ws = prog.alloc(counts, 7, alpha=True)
+    per = []
+    for k in range(3):
+        prog.generate(counts, 11, out, ws, event_offset=k * 10_000)
+        per.append(prog.stats())
+    prog.stats_accumulate(True)
+    ex = prog.exec_create(counts, out, ws)
+    for k in range(3):
+        if k == 1:
+            ex.launch(11, k * 10_000)
+        else:
+            prog.generate(counts, 11, out, ws, event_offset=k * 10_000)
+    acc = prog.stats()
+    prog.stats_accumulate(False)
+    for c in range(len(chans)):
+        for key in ("n", "n_nonzero", "sum_w", "sum_w2"):
+            expect = 0.0
+            for k in range(3):
+                expect += per[k][c][key]
+            assert acc[c][key] == expect, (c, key)
+        assert acc[c]["max_w"] == max(per[k][c]["max_w"] for k in range(3))
+    prog.generate(counts, 11, out, ws, event_offset=0)
+    assert prog.stats() == per[0]
