@@ -63,9 +63,14 @@ def parse():
     ap.add_argument("--no-unweight", action="store_true")
     ap.add_argument("--no-global", action="store_true")
     ap.add_argument("--no-streamed", action="store_true")
+    ap.add_argument("--no-c5-importance", action="store_true")
+    ap.add_argument("--stream-events", type=int, default=None, help="streamed leg: total events (default 1e8)")
+    ap.add_argument("--stream-chunk", type=int, default=None, help="streamed leg: events per chunk (default 2^22)")
+    ap.add_argument("--stream-config", default=None, help="streamed leg: 'threads,ctas_per_sm' instead of autotuning")
+    ap.add_argument("--stream-precision", default="f64", choices=["f64", "mixed"])
     ap.add_argument("--flow-steps", type=int, default=400)
     ap.add_argument("--flow-infer-events", type=int, default=EVENTS)
-    ap.add_argument("--leg", default="all", choices=["all", "flow", "unweight", "global", "streamed"],
+    ap.add_argument("--leg", default="all", choices=["all", "flow", "unweight", "global", "streamed", "c5_importance"],
                     help="run one secondary leg alone (for profiling); prints its object only")
     return ap.parse_args()
 
@@ -176,7 +181,8 @@ def timed(torch, fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
-def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best=None, host_copy=False):
+def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best=None, host_copy=False,
+                 total=None, chunk=None):
     """The 2->8 workload (six massless partons and two 173 GeV particles, 24 channels, SDE weights
     in-kernel) streamed: 1e8 events in chunks of 2^22, each chunk one persistent launch for all 24
     channels (CUDA graph, tiles and schedule from the autotuner) into one of two output buffers, its
@@ -188,7 +194,9 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
     from paper_2602_06895_gb300 import distributed as D
 
     chans = W.channels_2to8()
-    nc, chunk, total = len(chans), W.C5_CHUNK, W.C5_EVENTS
+    nc = len(chans)
+    chunk = chunk or W.C5_CHUNK
+    total = total or W.C5_EVENTS
     split = lambda n: [n // nc + (1 if c < n % nc else 0) for c in range(nc)]
     n_full, tail = divmod(total, chunk)
     table = None
@@ -278,6 +286,151 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
     del execs, plan, bufs
     return res
 
+
+def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=1 << 21, flow_steps=150,
+                      flow_batch=1 << 14, eval_events=1 << 22):
+    """Importance sampling on the 2->8 workload (24 channels, d = 22): uniform r, a VEGAS grid per
+    channel (22 dims x 64 bins, adapted in one multichannel launch per iteration), the same grids
+    in the mixed-precision program, and one RQ-spline flow per channel trained on top of its grid.
+
+    Each sampler first draws eval_events events with equal counts per channel (pilot), then
+    eval_events events with the variance-optimal counts n_c ~ sigma_c of its own pilot (the
+    multichannel estimate I = sum_c mean_c has Var = sum_c sigma_c^2 / n_c).  Figure of merit:
+    N_eff = I^2 / Var (unit-weight-equivalent events) per second of generation; the integrals
+    must agree.  The median per-channel Kish ESS fraction shows the sampler quality alone."""
+    import numpy as np
+
+    chans = W.channels_2to8()
+    nc, d = len(chans), W.n_random_dims(chans[0])
+    n_mom = chans[0]["n"] + 2
+    equal = [eval_events // nc + (1 if c < eval_events % nc else 0) for c in range(nc)]
+    res = {"workload": "2->8, 24 channels (the streamed workload), " + str(eval_events) + " events per sampler"}
+
+    def optimal(stats):
+        sig = np.array([math.sqrt(max(s2 / n - (s1 / n) ** 2, 0.0)) if n else 0.0 for n, s1, s2 in stats])
+        share = np.maximum(sig / max(sig.sum(), 1e-300), 0.002)  # every channel keeps a few events
+        n = np.floor(share / share.sum() * eval_events).astype(np.int64)
+        n[np.argmax(n)] += eval_events - int(n.sum())
+        return [int(x) for x in n]
+
+    def measure(name, run):
+        """run(counts) -> per-channel (n, sum w, sum w^2) of the events it drew (after the timing)."""
+        pilot = run(equal, timed_run=False)
+        counts = optimal(pilot)
+        run(counts, timed_run=False)  # warm-up at the final counts
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = run(counts, timed_run=True, events=(e0, e1))
+        ms = e0.elapsed_time(e1)
+        mean = [s1 / n for n, s1, _ in st]
+        var = sum((s2 / n - (s1 / n) ** 2) / n for n, s1, s2 in st)
+        I = sum(mean)
+        neff = I * I / var
+        kish = [s1 * s1 / s2 / n for n, s1, s2 in st if s2 > 0]
+        res[name] = {"ms": ms, "events_per_s": eval_events / (ms / 1e3), "integral": I,
+                     "rel_err": math.sqrt(var) / I, "n_eff": neff, "n_eff_fraction": neff / eval_events,
+                     "n_eff_per_s": neff / (ms / 1e3), "events_for_0.5pct": var / (I * 0.005) ** 2 * eval_events,
+                     "median_channel_kish_ess_fraction": float(np.median(kish)),
+                     "pilot_kish_ess_fraction_equal_counts": sum(x[1] for x in pilot) ** 2 /
+                     sum(x[2] for x in pilot) / eval_events}
+        return res[name]
+
+    def program_runner(prog, out_ws, seed):
+        def run(counts, timed_run, events=None):
+            # one generate call draws every channel's events into one record
+            if "full" not in out_ws or out_ws["full"][0] != counts:
+                out_ws["full"] = (counts, prog.alloc(counts, n_mom, alpha=True, device=local))
+            out, ws = out_ws["full"][1]
+            prog.generate(counts, seed, out, ws)
+            if events is not None:
+                events[1].record(stream)
+            return [(sc["n"], sc["sum_w"], sc["sum_w2"]) for sc in prog.stats(stream)]
+        return run
+
+    prog_u = ps.program_for(chans, device=local, block_threads=64, ctas_per_sm=3)
+    measure("uniform_fp64", program_runner(prog_u, {}, 51))
+    del prog_u
+
+    # VEGAS per channel, adapted on the GPU (untimed)
+    vchans = [dict(ch, vegas_dims=d) for ch in chans]
+    prog_v = ps.program_for(vchans, device=local, block_threads=64, ctas_per_sm=3)
+    vc = [vegas_events // nc] * nc
+    out_v, ws_v = prog_v.alloc(vc, n_mom, alpha=True, device=local)
+    prog_v.vegas_training(True)
+    for it in range(vegas_iters):
+        prog_v.generate(vc, 61 + it, out_v, ws_v)
+        for c in range(nc):
+            prog_v.vegas_adapt(c, alpha=1.5)
+    prog_v.vegas_training(False)
+    grids = [prog_v.get_vegas(c, d) for c in range(nc)]
+    del out_v, ws_v
+    vegas = measure("vegas_fp64", program_runner(prog_v, {}, 52))
+    res["vegas_fp64"]["adaptation"] = f"{vegas_iters} iterations x {vegas_events} events, alpha 1.5"
+
+    prog_m = ps.program_for(vchans, device=local, block_threads=64, ctas_per_sm=3, precision="mixed")
+    for c in range(nc):
+        prog_m.set_vegas(c, grids[c])
+    measure("vegas_mixed", program_runner(prog_m, {}, 52))
+
+    # one flow per channel on top of its VEGAS grid, trained on the method's own weights
+    flows = [ps.Flow(d, FLOW_LAYERS, FLOW_BINS, FLOW_HIDDEN, max_batch=flow_batch, init_seed=3000 + c)
+             for c in range(nc)]
+    r = torch.empty((d, flow_batch), dtype=torch.float64, device="cuda")
+    ld = torch.empty(flow_batch, dtype=torch.float64, device="cuda")
+    out_t, ws_t = prog_v.alloc([flow_batch] + [0] * (nc - 1), n_mom, alpha=True, device=local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(flow_steps):
+        for c in range(nc):
+            flows[c].sample(flow_batch, 4000 + c, r, ld, event_offset=k * flow_batch)
+            prog_v.map(c, r, out_t, ws_t)
+            flows[c].train_step(out_t["weight"], 1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del out_t, ws_t, r, ld
+
+    def flow_runner(prog):
+        buf = {}
+
+        def run_f(counts, timed_run, events=None):
+            nmax = max(counts)
+            if buf.get("n") != nmax:
+                buf.clear()
+                buf["n"] = nmax
+                buf["r"] = torch.empty((d, nmax), dtype=torch.float64, device="cuda")
+                buf["ld"] = torch.empty(nmax, dtype=torch.float64, device="cuda")
+                buf["o"] = prog.alloc([nmax] + [0] * (nc - 1), n_mom, alpha=True, device=local)
+                buf["w"] = torch.empty(eval_events, dtype=torch.float64, device="cuda")
+            ri, ldi, (oi, wsi), wf = buf["r"], buf["ld"], buf["o"], buf["w"]
+            col = 0
+            for c in range(nc):
+                n = counts[c]
+                flows[c].generate(n, 5000 + c, ri[:, :n], ldi[:n])
+                prog.map(c, ri[:, :n], oi, wsi)
+                flows[c].weights(oi["weight"][:n], ldi[:n], wf[col:col + n])
+                col += n
+            if events is not None:
+                events[1].record(stream)
+            out, col = [], 0
+            for c in range(nc):
+                w = wf[col:col + counts[c]]
+                out.append((counts[c], float(w.sum()), float((w * w).sum())))
+                col += counts[c]
+            return out
+        return run_f
+
+    flow = measure("flow_on_vegas", flow_runner(prog_v))
+    res["flow_on_vegas"]["training"] = {"steps_per_channel": flow_steps, "batch": flow_batch, "seconds": train_s,
+                                        "flows": nc, "layers": FLOW_LAYERS, "bins": FLOW_BINS,
+                                        "hidden": FLOW_HIDDEN, "lr": 1e-3, "map": "fp64"}
+    flow_m = measure("flow_on_vegas_mixed_map", flow_runner(prog_m))
+    res["flow_on_vegas_mixed_map"]["note"] = "the same trained flows; events mapped by the mixed-precision program"
+    res["flow_n_eff_per_s_over_vegas_fp64"] = flow["n_eff_per_s"] / vegas["n_eff_per_s"]
+    res["flow_mixed_map_n_eff_per_s_over_vegas_fp64"] = flow_m["n_eff_per_s"] / vegas["n_eff_per_s"]
+    res["mixed_n_eff_per_s_over_vegas_fp64"] = res["vegas_mixed"]["n_eff_per_s"] / vegas["n_eff_per_s"]
+    del flows, prog_m
+    return res
 
 FLOW_LAYERS, FLOW_BINS, FLOW_HIDDEN, FLOW_BATCH = 6, 16, 128, 1 << 16
 
@@ -471,7 +624,14 @@ def main():
         if args.leg == "flow":
             res = flow_leg(args, ps, W, torch, grid, ess / N, ms / N, stream)
         elif args.leg == "streamed":
-            res = streamed_leg(ps, W, torch, stream, rank, world, local)
+            cfg = None
+            if args.stream_config:
+                b, k = (int(x) for x in args.stream_config.split(","))
+                cfg = {"block_threads": b, "ctas_per_sm": k}
+            res = streamed_leg(ps, W, torch, stream, rank, world, local, precision=args.stream_precision, best=cfg,
+                               total=args.stream_events, chunk=args.stream_chunk)
+        elif args.leg == "c5_importance":
+            res = c5_importance_leg(ps, W, torch, stream, local)
         elif args.leg == "unweight":
             res = unweight_leg(ps, torch, out["weight"], stream)
         else:

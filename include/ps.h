@@ -348,7 +348,9 @@ int ps_program_free(ps_program p);
  * w = w_map |dr/dz|  (the flow density in r is |dz/dr|).
  *
  * Coupling layer l transforms the dims whose index has bit (l mod nbits) different from
- * ((l div nbits) mod 2), nbits = ceil(log2 d), conditioned on the other dims through the MLP
+ * ((l div nbits) mod 2), nbits = ceil(log2 d), for d <= 16, and the dims j with
+ * j mod 3 == l mod 3 for 16 < d <= 24 (at most 8 transformed and 16 conditioning dims, the
+ * shape of the fused tensor-core layer), conditioned on the other dims through the MLP
  *     A -> Linear(hidden) -> SiLU -> Linear(hidden) -> SiLU -> Linear(n_B (3 bins + 1)),
  * giving per transformed dim `bins` width logits, `bins` height logits and bins+1 derivative
  * pre-activations:  widths/heights = 1e-3 + (1 - bins 1e-3) softmax(.), knot derivatives =
@@ -371,7 +373,7 @@ typedef struct ps_flow_s* ps_flow;
 /* Message of the last failed flow call on this thread. */
 const char* ps_flow_last_error(void);
 
-/* Create a flow on `device`: 2 <= dims <= 16, 1 <= n_layers <= 8, 1 <= bins <= 32,
+/* Create a flow on `device`: 2 <= dims <= 24, 1 <= n_layers <= 8, 1 <= bins <= 32,
  * hidden a multiple of 16 in [16, 512], 1 <= max_batch <= 2^24 events per sample chunk.
  * Allocates the parameters, Adam state and the activations of max_batch events
  * (about (L (10 hidden + 4 P) + 4 P + 20 hidden) bytes per event).  Synchronises. */

@@ -28,7 +28,11 @@ MIN_D = 1e-3
 
 
 def masks(d, n_layers):
-    """Transformed dims of each layer: bit (l mod nbits) of the dim index, flipped every nbits layers."""
+    """Transformed dims of each layer: up to 16 dims, bit (l mod nbits) of the dim index, flipped
+    every nbits layers; above 16 dims, the group j mod 3 == l mod 3 (at most 8 transformed and 16
+    conditioning dims per layer for d <= 24)."""
+    if d > 16:
+        return [[j for j in range(d) if j % 3 == l % 3] for l in range(n_layers)]
     nb = max(1, math.ceil(math.log2(d)))
     out = []
     for l in range(n_layers):

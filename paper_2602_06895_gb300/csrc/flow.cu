@@ -33,7 +33,7 @@ namespace ps {
 void count_launches(int n);
 namespace flow {
 
-constexpr int kMaxDims = 16;
+constexpr int kMaxDims = 24;
 constexpr int kMaxLayers = 8;
 constexpr int kMaxBins = 32;
 constexpr float kMinW = 1e-3f, kMinH = 1e-3f, kMinD = 1e-3f;
@@ -1722,7 +1722,11 @@ int ps_flow_create(int dims, int n_layers, int bins, int hidden, int64_t max_bat
         int b = l % nbits, flip = (l / nbits) % 2;
         ld.nb = ld.na = 0;
         for (int j = 0; j < dims; ++j) {
-            if (((j >> b) & 1) != flip) ld.tb[ld.nb++] = j;
+            // up to 16 dims: bit (l mod nbits) of the index, flipped every nbits layers; above 16, three
+            // interleaved groups (j mod 3 == l mod 3), so that a layer transforms at most 8 dims and
+            // conditions on at most 16
+            const bool transformed = dims > 16 ? (j % 3 == l % 3) : (((j >> b) & 1) != flip);
+            if (transformed) ld.tb[ld.nb++] = j;
             else ld.ta[ld.na++] = j;
         }
         if (ld.nb == 0 || ld.na == 0 || ld.na > kInPad) { delete f; return ffail(PS_ERR_INVALID_ARGUMENT, "bad mask"); }

@@ -354,21 +354,29 @@ __device__ void run_code(const int32_t* code, int len, const Frame& f, const dou
                 break;
             }
             case PS_OP_CHANNEL_WEIGHT: {
-                const int k = static_cast<int>(ld(f, a[0]));
-                P4 pa = ldp(f, a[1]);
-                double P = 1.0;
+                // P_j = 1 / prod(denominators): one division per channel; kind and mask decoded
+                // from their bits, the momentum sum over the set bits of the mask only
+                const int k = small_int(ld(f, a[0]));
+                const P4 pa = ldp(f, a[1]);
+                double den = 1.0, P = 1.0;
                 for (int j = 2 + k; j + 3 < na; j += 4) {
-                    int kind = static_cast<int>(ld(f, a[j]));
-                    int mask = static_cast<int>(ld(f, a[j + 1]));
-                    double M = ld(f, a[j + 2]), G = ld(f, a[j + 3]);
+                    const int kind = small_int(ld(f, a[j]));
+                    int mask = small_int(ld(f, a[j + 1]));
+                    const double M = ld(f, a[j + 2]), G = ld(f, a[j + 3]);
                     P4 q = (kind == 1) ? pa : P4{0.0, 0.0, 0.0, 0.0};
-                    for (int i = 0; i < k; ++i)
-                        if (mask & (1 << i)) q = (kind == 1) ? p4_sub(q, ldp(f, a[2 + i])) : p4_add(q, ldp(f, a[2 + i]));
-                    double inv = p4_sq(q);
-                    double d = inv - M * M;
-                    P *= (kind == 1) ? 1.0 / (d * d) : 1.0 / (d * d + M * M * G * G);
+                    while (mask) {
+                        const int i = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        q = (kind == 1) ? p4_sub(q, ldp(f, a[2 + i])) : p4_add(q, ldp(f, a[2 + i]));
+                    }
+                    const double d = p4_sq(q) - M * M, mg = M * G;
+                    den *= (kind == 1) ? d * d : fma(d, d, mg * mg);
+                    if (above_pos_bits(den, 1e200)) {  // keep the running product in range
+                        P /= den;
+                        den = 1.0;
+                    }
                 }
-                st(f, o[0], P);
+                st(f, o[0], P / den);
                 break;
             }
             default: break;
@@ -754,25 +762,35 @@ __device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, con
                 break;
             }
             case PS_OP_CHANNEL_WEIGHT: {
-                const int k = static_cast<int>(ld(f, a[0]));
-                F4 paf = mx::ldp(f, a[1]);
-                P4 pa = {paf.e, paf.x, paf.y, paf.z};
-                double P = 1.0;
+                // FP32 throughout, as the momenta it starts from: momentum sums, invariants and
+                // denominators; the product of the denominators is kept as an FP32 mantissa in
+                // [1, 2) and an integer exponent (no FP64 work per propagator), and P_j becomes a
+                // double once per channel
+                const int k = small_int(ld(f, a[0]));
+                const F4 pa = mx::ldp(f, a[1]);
+                float acc = 1.0f;
+                int ex = 0;
                 for (int j = 2 + k; j + 3 < na; j += 4) {
-                    int kind = static_cast<int>(ld(f, a[j]));
-                    int mask = static_cast<int>(ld(f, a[j + 1]));
-                    double M = ld(f, a[j + 2]), G = ld(f, a[j + 3]);
-                    P4 q = (kind == 1) ? pa : P4{0.0, 0.0, 0.0, 0.0};
-                    for (int i = 0; i < k; ++i)
-                        if (mask & (1 << i)) {
-                            F4 qf = mx::ldp(f, a[2 + i]);
-                            P4 qi = {qf.e, qf.x, qf.y, qf.z};
-                            q = (kind == 1) ? p4_sub(q, qi) : p4_add(q, qi);
-                        }
-                    double d = p4_sq(q) - M * M;
-                    P *= (kind == 1) ? 1.0 / (d * d) : 1.0 / (d * d + M * M * G * G);
+                    const int kind = small_int(ld(f, a[j]));
+                    int mask = small_int(ld(f, a[j + 1]));
+                    const float M = static_cast<float>(ld(f, a[j + 2]));
+                    const float G = static_cast<float>(ld(f, a[j + 3]));
+                    F4 q = (kind == 1) ? pa : F4{0.0f, 0.0f, 0.0f, 0.0f};
+                    while (mask) {
+                        const int i = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        q = (kind == 1) ? mx::f4_sub(q, mx::ldp(f, a[2 + i])) : mx::f4_add(q, mx::ldp(f, a[2 + i]));
+                    }
+                    const float s = fmaf(q.e, q.e, -fmaf(q.x, q.x, fmaf(q.y, q.y, q.z * q.z)));
+                    const float d = s - M * M, mg = M * G;
+                    acc *= (kind == 1) ? d * d : fmaf(d, d, mg * mg);
+                    const int bits = __float_as_int(acc);  // acc = 1.m 2^e with e moved into ex
+                    ex += ((bits >> 23) & 0xFF) - 127;
+                    acc = __int_as_float((bits & 0x807FFFFF) | 0x3F800000);
                 }
-                st(f, o[0], P);
+                // 1 / (acc 2^ex) with 2^-ex built from its bits (|ex| stays far below 1022 here)
+                const double scale = __longlong_as_double(static_cast<long long>(1023 - ex) << 52);
+                st(f, o[0], static_cast<double>(1.0f / acc) * scale);
                 break;
             }
             default: break;

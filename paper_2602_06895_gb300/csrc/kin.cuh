@@ -37,6 +37,14 @@ __device__ __forceinline__ bool below_neg_bits(double v, double c) {
     return b < 0 && (b & 0x7FFFFFFFFFFFFFFFLL) > dbits(c);
 }
 __device__ __forceinline__ bool above_pos_bits(double v, double c) { return dbits(v) > dbits(c); }
+// an integer 0 <= v < 2^31 held in a double (byte-code immediates), decoded from its bits:
+// v = 1.m 2^e gives (1m) >> (52 - e)
+__device__ __forceinline__ int small_int(double v) {
+    const unsigned long long b = static_cast<unsigned long long>(dbits(v));
+    const int e = static_cast<int>((b >> 52) & 0x7FF) - 1023;
+    if (e < 0) return 0;
+    return static_cast<int>(((b & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL) >> (52 - e));
+}
 // fmin(fmax(x, lo), hi) for 0 <= lo <= hi: NaN and values below lo give lo, +inf gives hi
 __device__ __forceinline__ double clamp_nonneg(double x, double lo, double hi) {
     const long long b = dbits(x);

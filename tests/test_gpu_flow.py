@@ -80,7 +80,7 @@ def sample(torch, fl, B, seed, offset=0):
 
 
 def test_masks_match_oracle(torch_cuda):
-    for d in (2, 5, 10, 16):
+    for d in (2, 5, 10, 16, 17, 22, 24):
         fl = ps.Flow(d, 6, 4, 32, max_batch=64)
         assert [fl.mask(l) for l in range(6)] == OF.masks(d, 6)
 
@@ -347,3 +347,57 @@ def test_bounded_waits_report_timeouts_and_recover(torch_cuda):
     r_o, ld_o = orc.forward(z[:, :3000].T.cpu(), bf=True)
     dr = np.abs(r[:, :3000].T.cpu().numpy() - r_o.numpy())
     assert dr.max() <= 2e-3 and dr.mean() <= 1e-4, (dr.max(), dr.mean())
+
+
+def test_22_dims_fused_inverse_and_gradients(torch_cuda):
+    """d = 22 (the 2->8 channels: six massless and two massive particles): three interleaved
+    coupling groups, at most 8 transformed dims per layer, so the fused tensor-core layer runs;
+    fused generate against the layer-by-layer path and the oracle, the inverse, and the
+    gradients of the training loss."""
+    torch = torch_cuda
+    d, B = 22, 3001
+    fl = ps.Flow(d, L, K, H, max_batch=4096)
+    assert [fl.mask(l) for l in range(L)] == OF.masks(d, L)
+    assert max(len(fl.mask(l)) for l in range(L)) <= 8
+    p, orc, layout = random_params(fl, 16)
+    fl.set_params(p)
+    r = torch.empty((d, B), dtype=torch.float64, device="cuda")
+    ld = torch.empty(B, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    fl.generate(B, 41, r, ld, z)
+    r2, ld2, z2 = torch.empty_like(r), torch.empty_like(ld), torch.empty_like(r)
+    fl.sample(B, 41, r2, ld2, z2)
+    torch.cuda.synchronize()
+    assert torch.equal(z, z2)
+    assert torch.max(torch.abs(r - r2)).item() <= 1e-5
+    assert torch.max(torch.abs(ld - ld2)).item() <= 1e-3
+    r_o, ld_o = orc.forward(z.T.cpu(), bf=True)
+    dr = np.abs(r.T.cpu().numpy() - r_o.numpy())
+    dl = np.abs(ld.cpu().numpy() - ld_o.numpy())
+    assert dr.max() <= 2e-3 and dr.mean() <= 1e-4, (dr.max(), dr.mean())
+    assert dl.max() <= 2e-2 and dl.mean() <= 1e-3, (dl.max(), dl.mean())
+    assert np.abs(r_o.numpy() - z.T.cpu().numpy()).mean() > 1e-2
+    zb = torch.empty_like(r)
+    lq = torch.empty(B, dtype=torch.float64, device="cuda")
+    fl.inverse(r, zb, lq)
+    torch.cuda.synchronize()
+    z_o, lq_o = orc.inverse(r.T.cpu(), bf=True)
+    dz = np.abs(zb.T.cpu().numpy() - z_o.numpy())
+    assert dz.max() <= 2e-3 and dz.mean() <= 1e-4, (dz.max(), dz.mean())
+    x = r.T
+    w_map = (torch.exp(-((x[:, 0] - x[:, 13]) ** 2) / 0.02) * (1.0 + 4.0 * x[:, 2] * x[:, 21]) + 0.05).contiguous()
+    fl.sample(B, 41, r2, ld2, z2)  # the training batch is the last sampled one
+    loss, g = fl.gradients(w_map)
+    w = (w_map * torch.exp(ld2)).cpu()
+    loss_o, grads_o = orc.loss_and_grads(r2.T.cpu(), w, bf=True)
+    assert abs(loss - loss_o) <= 1e-3 * max(1.0, abs(loss_o)), (loss, loss_o)
+    for l, lay in enumerate(layout):
+        for name, (o, shape) in lay.items():
+            ref = grads_o[l][name].numpy().ravel()
+            got = g[o:o + ref.size].astype(np.float64)
+            nrm = np.linalg.norm(ref)
+            if nrm == 0:
+                assert np.all(got == 0)
+                continue
+            assert np.linalg.norm(got - ref) / nrm <= 5e-2, (l, name)
+    assert fl.status() == 0
