@@ -763,12 +763,19 @@ def main():
     # records copied to the host) and the mixed-precision form on the same events
     streamed = None
     if not args.no_streamed:
-        streamed = streamed_leg(ps, W, torch, stream, rank, world, local, host_copy=not args.no_e2e)
+        streamed = streamed_leg(ps, W, torch, stream, rank, world, local)
+        if not args.no_e2e:
+            streamed["e2e"] = streamed_leg(ps, W, torch, stream, rank, world, local, best=streamed["autotuned"],
+                                           host_copy=True)["e2e"]
         sm = streamed_leg(ps, W, torch, stream, rank, world, local, precision="mixed")
         streamed["mixed_precision"] = {k: sm[k] for k in ("value", "ms_total", "integral", "rel_err", "ess",
                                                           "effective_events_per_s", "autotuned")}
         streamed["mixed_precision"]["integral_rel_diff_vs_fp64_same_events"] = sm["integral"] / streamed["integral"] - 1
         streamed["mixed_precision"]["speedup_vs_fp64"] = streamed["ms_total"] / sm["ms_total"]
+
+    c5imp = None
+    if not args.no_c5_importance and rank == 0:
+        c5imp = c5_importance_leg(ps, W, torch, stream, local)
 
     flow = None
     if not args.no_flow and rank == 0:
@@ -806,7 +813,7 @@ def main():
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
             "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi, "streamed_2to8": streamed,
-            "flow": flow, "unweighting": unweight, "global_multichannel": glob}
+            "importance_2to8": c5imp, "flow": flow, "unweighting": unweight, "global_multichannel": glob}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
