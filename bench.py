@@ -758,6 +758,28 @@ def main():
                  "autotuned": best, "autotune_table": table,
                  "integral": sum(c["sum_w"] for c in cst) / 1.0,
                  "per_channel_sum_w": [c["sum_w"] for c in cst]}
+        # the mixed-precision form of the same step on the same events
+        mbest, _ = ps.autotune(chans, [c // 8 for c in counts], precision="mixed", blocks=(64, 128, 256),
+                               ctas=(1, 2, 3, 4), reps=2, device=local)
+        xprog = ps.program_for(chans, device=local, precision="mixed", **mbest)
+        xout, xws = xprog.alloc(counts, 7, alpha=True, device=local)
+        xex = xprog.exec_create(counts, xout, xws)
+        for k in range(args.warmup):
+            xex.launch(1003, D.step_offset(rank, world, sum(counts), k))
+        torch.cuda.synchronize()
+        xev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        xev[0].record(stream)
+        for k in range(args.steps):
+            xex.launch(1003, D.step_offset(rank, world, sum(counts), args.warmup + k), stream)
+        xev[1].record(stream)
+        torch.cuda.synchronize()
+        xms = xev[0].elapsed_time(xev[1]) / args.steps
+        xst = xprog.stats()  # the last step drew the same events as the last FP64 step
+        multi["mixed_precision"] = {"value": world * sum(counts) / (xms / 1e3), "ms_per_step": xms,
+                                    "speedup_vs_fp64": cms / xms, "autotuned": mbest,
+                                    "integral_rel_diff_vs_fp64_same_events":
+                                        sum(c["sum_w"] for c in xst) / multi["integral"] - 1.0}
+        del xex, xprog, xout, xws
 
     # 2->8, 24 channels, 1e8 events streamed in 2^22-event chunks: FP64 (device-resident and with the
     # records copied to the host) and the mixed-precision form on the same events
