@@ -149,7 +149,10 @@ def cpu_baseline(events, grid, seconds_target=12.0):
         O.generate(ch, SEED, k * events, events, grid=grid, keep_momenta=True, threads=threads)
     dt = time.perf_counter() - t0
     n = steps * events
-    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    t1 = time.perf_counter()
+    O.generate(ch, SEED, 0, 200_000, grid=grid, keep_momenta=True, threads=1)
+    single = 200_000 / (time.perf_counter() - t1)
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "single_core_value": single,
             "sample": f"{steps} consecutive steps of {events} events (seed {SEED}, events 0..{n - 1}) of the "
                       f"workload, full event record kept, {dt:.2f} s wall ({dt * threads:.0f} core-s) on "
                       f"{threads} OpenMP threads"}
@@ -179,6 +182,27 @@ def timed(torch, fn, reps, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def c1_leg(ps, W, torch, stream, local, events=100_000, reps=20):
+    """2->2 at fixed sqrt(s) = 1000 GeV (two_body_decay of p0 = (1000, 0, 0, 0)): the phase-space
+    volume (every weight is 1/(8 pi)) and the integral of 1 + cos^2(theta) (closed form 1/(6 pi)),
+    1e5 events per launch (the size is launch-bound: the rate is that of a 1e5-event batch)."""
+    res = {}
+    for name, integrand, exact in (("volume", "none", 1.0 / (8.0 * math.pi)),
+                                   ("one_plus_cos2", "one_plus_cos2", 1.0 / (6.0 * math.pi))):
+        ch = W.two_body_fixed(integrand=integrand)
+        prog = ps.program_for([ch], device=local)
+        out, ws = prog.alloc([events], 4, x=False)
+        ms = timed(torch, lambda: prog.generate([events], 1001, out, ws), reps, stream)
+        st = prog.stats()[0]
+        mean = st["sum_w"] / st["n"]
+        sigma = math.sqrt(max(st["sum_w2"] / st["n"] - mean * mean, 0.0) / st["n"])
+        res[name] = {"integral": mean, "sigma": sigma, "exact": exact, "rel_diff": mean / exact - 1.0,
+                     "pulls": (mean - exact) / sigma if sigma > 1e-12 * mean else None,
+                     "events_per_s": events / (ms / 1e3), "ms_per_launch": ms}
+    res["workload"] = "2->2 massless at sqrt(s) = 1000 GeV, 1e5 events per launch (seed 1001)"
+    return res
 
 
 def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best=None, host_copy=False,
@@ -757,6 +781,9 @@ def main():
                  "gpu_launches": int(ps.launch_count() - l0), "cuda_graph": True,
                  "autotuned": best, "autotune_table": table,
                  "integral": sum(c["sum_w"] for c in cst) / 1.0,
+                 "integral_mean": sum(c["sum_w"] / c["n"] for c in cst if c["n"]),
+                 "integral_sigma": math.sqrt(sum((c["sum_w2"] / c["n"] - (c["sum_w"] / c["n"]) ** 2) / c["n"]
+                                                 for c in cst if c["n"])),
                  "per_channel_sum_w": [c["sum_w"] for c in cst]}
         # the mixed-precision form of the same step on the same events
         mbest, _ = ps.autotune(chans, [c // 8 for c in counts], precision="mixed", blocks=(64, 128, 256),
@@ -794,6 +821,8 @@ def main():
                                                           "effective_events_per_s", "autotuned")}
         streamed["mixed_precision"]["integral_rel_diff_vs_fp64_same_events"] = sm["integral"] / streamed["integral"] - 1
         streamed["mixed_precision"]["speedup_vs_fp64"] = streamed["ms_total"] / sm["ms_total"]
+
+    c1 = c1_leg(ps, W, torch, stream, local) if rank == 0 else None
 
     c5imp = None
     if not args.no_c5_importance and rank == 0:
@@ -835,7 +864,7 @@ def main():
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
             "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi, "streamed_2to8": streamed,
-            "importance_2to8": c5imp, "flow": flow, "unweighting": unweight, "global_multichannel": glob}
+            "importance_2to8": c5imp, "fixed_2to2": c1, "flow": flow, "unweighting": unweight, "global_multichannel": glob}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
