@@ -266,8 +266,25 @@ int compile_graph(const Graph& g, Compiled* out, std::string* err) {
         out->code.push_back(static_cast<int32_t>(in.args.size()));
         out->code.push_back(static_cast<int32_t>(in.outs.size()));
         for (auto& a : in.args) out->code.push_back(a.kind == PS_ARG_VALUE ? slot[a.id] : ~imm(a.imm));
-        for (int id : in.outs) {
-            slot[id] = alloc(width(id));
+        // In place: vegas and boost_beam read argument k before they write output k and touch no
+        // other argument after that, so output k may take the slot of argument k when that
+        // argument dies here (it halves the peak of the slot file at the beam boost).
+        const bool in_place = in.op == PS_OP_VEGAS || in.op == PS_OP_BOOST_BEAM;
+        for (size_t k = 0; k < in.outs.size(); ++k) {
+            const int id = in.outs[k];
+            int from = -1;
+            if (in_place && k < in.args.size() && in.args[k].kind == PS_ARG_VALUE && last[in.args[k].id] == i &&
+                width(in.args[k].id) == width(id)) {
+                int uses = 0;
+                for (auto& a : in.args) uses += (a.kind == PS_ARG_VALUE && a.id == in.args[k].id) ? 1 : 0;
+                if (uses == 1) from = in.args[k].id;
+            }
+            if (from >= 0) {
+                slot[id] = slot[from];
+                last[from] = -2;  // its slot now belongs to the output
+            } else {
+                slot[id] = alloc(width(id));
+            }
             out->code.push_back(slot[id]);
         }
         for (auto& a : in.args)
