@@ -79,10 +79,12 @@ enum {
      * auxiliary mass m^2 = -a; nu = 1 is the logarithmic map.  J = dx/dr. */
     PS_OP_INVARIANT_NU = 2,
     /* Breit-Wigner map G_BW, Eq. prop_massive (Sec. 2.2.1):
-     * (s r, i M, i Gamma, s|i x_min, s|i x_max) -> (s x, s J). */
+     * (s r, i M, i Gamma, s|i x_min, s|i x_max [, i u1]) -> (s x, s J).  The optional u1 is
+     * atan((x_min - M^2)/(M Gamma)), the lower angle, when x_min is a constant. */
     PS_OP_INVARIANT_BW = 3,
     /* r_to_x1x2, Eq. pdf_sampling (Sec. 2.2.2): (s r, s shat, i S) -> (s x1, s x2, s J),
-     * J = -log(shat/S)/S. */
+     * J = -log(shat/S)/S.  With a fourth immediate argument (any value) it also returns
+     * (s log x1, s log x2) = (r, 1 - r) log(shat/S). */
     PS_OP_R_TO_X1X2 = 4,
     /* com_p_in (Sec. 3.2): (s sqrt_shat) -> (p p_a, p p_b) along +-z. */
     PS_OP_COM_P_IN = 5,
@@ -120,7 +122,8 @@ enum {
     PS_OP_MAX = 19,    /* (s|i a, s|i b) -> (s max(a,b)) */
     PS_OP_MOM_ADD = 20, /* (p a, p b) -> (p a + b)      */
     PS_OP_MOM_SUB = 21, /* (p a, p b) -> (p a - b)      */
-    /* synthetic parton density (x^alpha (1-x)^beta): (s x, i alpha, i beta) -> (s f). */
+    /* synthetic parton density (x^alpha (1-x)^beta): (s x, i alpha, i beta [, s log x]) -> (s f);
+     * a given log x replaces the logarithm of x. */
     PS_OP_PDF_POWER = 22,
     /* propagator denominator 1/((s - M^2)^2 + M^2 Gamma^2): (s s, i M, i Gamma) -> (s P). */
     PS_OP_PROPAGATOR = 23,

@@ -109,11 +109,16 @@ int signature(const Graph& g, int op, const std::vector<Arg>& a, std::vector<int
             if (!expect({S, SI, I, SI, SI, I})) return 0;
             *outs = {sc, sc};
             return 1;
-        case PS_OP_INVARIANT_BW:
-            if (!expect({S, I, I, SI, SI})) return 0;
+        case PS_OP_INVARIANT_BW:  // optional 6th: the immediate atan((x_min - M^2)/(M Gamma))
+            if (a.size() == 6 ? !expect({S, I, I, SI, SI, I}) : !expect({S, I, I, SI, SI})) return 0;
             *outs = {sc, sc};
             return 1;
-        case PS_OP_R_TO_X1X2:
+        case PS_OP_R_TO_X1X2:  // optional 4th immediate (any value): also return log x1, log x2
+            if (a.size() == 4) {
+                if (!expect({S, S, I, I})) return 0;
+                *outs = {sc, sc, sc, sc, sc};
+                return 1;
+            }
             if (!expect({S, S, I})) return 0;
             *outs = {sc, sc, sc};
             return 1;
@@ -177,7 +182,11 @@ int signature(const Graph& g, int op, const std::vector<Arg>& a, std::vector<int
             if (!expect({P, P})) return 0;
             *outs = {mo};
             return 1;
-        case PS_OP_PDF_POWER: case PS_OP_PROPAGATOR:
+        case PS_OP_PDF_POWER:  // optional 4th: log x
+            if (a.size() == 4 ? !expect({S, I, I, S}) : !expect({S, I, I})) return 0;
+            *outs = {sc};
+            return 1;
+        case PS_OP_PROPAGATOR:
             if (!expect({S, I, I})) return 0;
             *outs = {sc};
             return 1;
@@ -595,6 +604,14 @@ void build(const ps_channel_desc* all, int n_ch, int which, ps_graph g) {
         jac.push_back(B::V(o[d->vegas_dims]));
     }
 
+    // Breit-Wigner arguments; with an immediate x_min the lower angle atan((x_min - M^2)/(M Gamma))
+    // is a constant of the channel and goes in as a sixth immediate
+    auto bw_args = [&](ps_arg rr, double M, double G, ps_arg smin, ps_arg smax) {
+        std::vector<ps_arg> a = {rr, B::C(M), B::C(G), smin, smax};
+        if (smin.kind == PS_ARG_IMM) a.push_back(B::C(std::atan((smin.imm - M * M) / (M * G))));
+        return a;
+    };
+
     // ---- shat (Sec. 2.2.2)
     std::vector<int> sid(d->n_nodes, -1), sqrt_id(d->n_nodes, -1);
     std::vector<char> sampled(d->n_nodes, 0);
@@ -604,8 +621,8 @@ void build(const ps_channel_desc* all, int n_ch, int which, ps_graph g) {
         for (int j = 0; j < d->n_nodes; ++j) if (nd[j].kind == PS_NODE_LEAF) mleaf += nd[j].mass;
         std::vector<int> o;
         if (d->shat_width > 0.0)
-            b.emit(PS_OP_INVARIANT_BW, {B::V(r[d_shat]), B::C(d->shat_mass), B::C(d->shat_width), B::C(mleaf * mleaf),
-                                        B::C(d->s_beam)}, 2, &o);
+            b.emit(PS_OP_INVARIANT_BW, bw_args(B::V(r[d_shat]), d->shat_mass, d->shat_width, B::C(mleaf * mleaf),
+                                               B::C(d->s_beam)), 2, &o);
         else
             b.emit(PS_OP_INVARIANT_NU, {B::V(r[d_shat]), B::C(d->shat_mass), B::C(d->shat_nu), B::C(mleaf * mleaf),
                                         B::C(d->s_beam), B::C(d->a_shift)}, 2, &o);
@@ -672,7 +689,7 @@ void build(const ps_channel_desc* all, int n_ch, int which, ps_graph g) {
         }
         std::vector<int> o;
         if (nd[j].prop_width > 0.0)
-            b.emit(PS_OP_INVARIANT_BW, {B::V(r[d_s[j]]), B::C(nd[j].prop_mass), B::C(nd[j].prop_width), smin, smax}, 2, &o);
+            b.emit(PS_OP_INVARIANT_BW, bw_args(B::V(r[d_s[j]]), nd[j].prop_mass, nd[j].prop_width, smin, smax), 2, &o);
         else
             b.emit(PS_OP_INVARIANT_NU, {B::V(r[d_s[j]]), B::C(nd[j].prop_mass), B::C(nd[j].nu), smin, smax,
                                         B::C(d->a_shift)}, 2, &o);
@@ -729,10 +746,17 @@ void build(const ps_channel_desc* all, int n_ch, int which, ps_graph g) {
     }
 
     // ---- x1, x2 (Sec. 2.2.2)
-    int x1 = -1, x2 = -1;
+    int x1 = -1, x2 = -1, lx1 = -1, lx2 = -1;
     if (d->hadronic) {
         std::vector<int> o;
-        b.emit(PS_OP_R_TO_X1X2, {B::V(r[d_x]), B::V(shat), B::C(d->s_beam)}, 3, &o);
+        const bool want_logs = d->integrand == PS_INTEGRAND_PDF_PROPS || d->integrand == PS_INTEGRAND_PDF_SDE;
+        if (want_logs) {  // log x = r log tau is known: the parton densities need no logarithm
+            b.emit(PS_OP_R_TO_X1X2, {B::V(r[d_x]), B::V(shat), B::C(d->s_beam), B::C(1.0)}, 5, &o);
+            lx1 = o[3];
+            lx2 = o[4];
+        } else {
+            b.emit(PS_OP_R_TO_X1X2, {B::V(r[d_x]), B::V(shat), B::C(d->s_beam)}, 3, &o);
+        }
         x1 = o[0];
         x2 = o[1];
         jac.push_back(B::V(o[2]));
@@ -835,8 +859,14 @@ void build(const ps_channel_desc* all, int n_ch, int which, ps_graph g) {
     ps_arg f = B::C(1.0);
     int alpha = -1;
     auto pdfs = [&]() -> int {
-        int f1 = b.emit(PS_OP_PDF_POWER, {B::V(x1), B::C(d->pdf_alpha), B::C(d->pdf_beta)}, 1);
-        int f2 = b.emit(PS_OP_PDF_POWER, {B::V(x2), B::C(d->pdf_alpha), B::C(d->pdf_beta)}, 1);
+        std::vector<ps_arg> a1 = {B::V(x1), B::C(d->pdf_alpha), B::C(d->pdf_beta)}, a2 = a1;
+        a2[0] = B::V(x2);
+        if (lx1 >= 0) {
+            a1.push_back(B::V(lx1));
+            a2.push_back(B::V(lx2));
+        }
+        int f1 = b.emit(PS_OP_PDF_POWER, a1, 1);
+        int f2 = b.emit(PS_OP_PDF_POWER, a2, 1);
         return b.emit(PS_OP_MUL, {B::V(f1), B::V(f2)}, 1);
     };
     if (d->integrand == PS_INTEGRAND_ONE_PLUS_COS2) {

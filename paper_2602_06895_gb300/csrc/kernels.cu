@@ -77,14 +77,15 @@ __device__ __forceinline__ bool map_nu(double r, double m, double nu, double xmi
 //   u < -pi/4: T = tan(D r),     x = x_min + mG T(1+a^2)/(1-aT), 1+tan^2u = (1+a^2)(1+T^2)/(1-aT)^2
 //   u >  pi/4: T = tan(D (1-r)), tan u = (b-T)/(1+bT), 1+tan^2u = (1+b^2)(1+T^2)/(1+bT)^2
 //   otherwise: T = tan(u).        J = D mG (1 + tan^2 u)
+// u1 = atan(a) may come in as the channel's constant (x_min immediate); have_u1 selects it.
 __device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin, double xmax,
-                                       double& x, double& jac) {
+                                       double& x, double& jac, bool have_u1 = false, double u1 = 0.0) {
     double mg = M * G, m2 = M * M;
     bool ok = pos_bits(mg) && ge_pos_bits(xmax, xmin);  // x_min >= 0 here (a squared mass)
     double inv_mg = 1.0 / mg;
     double a = (xmin - m2) * inv_mg, b = (xmax - m2) * inv_mg;
     double D = atan2((xmax - xmin) * inv_mg, fma(a, b, 1.0));
-    double u = atan(a) + D * r;
+    double u = (have_u1 ? u1 : atan(a)) + D * r;
     bool low = below_neg_bits(u, 0.25 * kPi), high = above_pos_bits(u, 0.25 * kPi);
     double arg = low ? D * r : (high ? D * (1.0 - r) : u);
     double T = tan(arg);
@@ -236,7 +237,8 @@ __device__ void run_code(const int32_t* code, int len, const Frame& f, const dou
             }
             case PS_OP_INVARIANT_BW: {
                 double x, j;
-                map_bw(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), x, j);
+                map_bw(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), x, j, na > 5,
+                       na > 5 ? ld(f, a[5]) : 0.0);
                 st(f, o[0], x);
                 st(f, o[1], j);
                 break;
@@ -244,9 +246,14 @@ __device__ void run_code(const int32_t* code, int len, const Frame& f, const dou
             case PS_OP_R_TO_X1X2: {
                 double r = ld(f, a[0]), shat = ld(f, a[1]), S = ld(f, a[2]);
                 double L = log(shat / S);
-                st(f, o[0], exp(r * L));
-                st(f, o[1], exp((1.0 - r) * L));
+                const double l1 = r * L, l2 = (1.0 - r) * L;  // log x1, log x2
+                st(f, o[0], exp(l1));
+                st(f, o[1], exp(l2));
                 st(f, o[2], -L / S);
+                if (no > 3) {
+                    st(f, o[3], l1);
+                    st(f, o[4], l2);
+                }
                 break;
             }
             case PS_OP_COM_P_IN: {
@@ -330,7 +337,7 @@ __device__ void run_code(const int32_t* code, int len, const Frame& f, const dou
             case PS_OP_MOM_SUB: stp(f, o[0], p4_sub(ldp(f, a[0]), ldp(f, a[1]))); break;
             case PS_OP_PDF_POWER: {
                 double x = ld(f, a[0]), al = ld(f, a[1]), be = ld(f, a[2]);
-                double fx = exp(al * log(x));
+                double fx = exp(al * (na > 3 ? ld(f, a[3]) : log(x)));
                 double y = 1.0 - x;
                 double fy;
                 if (be == 3.0) fy = y * y * y;
@@ -501,14 +508,15 @@ __device__ __forceinline__ void map_nu(float r, double m, double nu, double xmin
 
 // Breit-Wigner: angles and tan in float (same endpoint-relative branches as the FP64 form),
 // s - m^2 and the assembly of x in FP64
-__device__ __forceinline__ void map_bw(float r, double M, double G, double xmin, double xmax, double& x, double& jac) {
+__device__ __forceinline__ void map_bw(float r, double M, double G, double xmin, double xmax, double& x, double& jac,
+                                       bool have_u1 = false, double u1 = 0.0) {
     double mg = M * G, m2 = M * M;
     bool ok = pos_bits(mg) && ge_pos_bits(xmax, xmin);  // x_min >= 0 here (a squared mass)
     float mgf = static_cast<float>(mg);
     float imgf = 1.0f / mgf;
     float a = static_cast<float>(xmin - m2) * imgf, b = static_cast<float>(xmax - m2) * imgf;
     float D = atan2f(static_cast<float>(xmax - xmin) * imgf, fmaf(a, b, 1.0f));
-    float u = atanf(a) + D * r;
+    float u = (have_u1 ? static_cast<float>(u1) : atanf(a)) + D * r;
     bool low = u < -0.785398163f, high = u > 0.785398163f;
     float arg = low ? D * r : (high ? D * (1.0f - r) : u);
     float T = tanf(arg);
@@ -643,7 +651,8 @@ __device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, con
             }
             case PS_OP_INVARIANT_BW: {
                 double x, j;
-                mx::map_bw(mx::ldf(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), x, j);
+                mx::map_bw(mx::ldf(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), x, j, na > 5,
+                           na > 5 ? ld(f, a[5]) : 0.0);
                 st(f, o[0], x);
                 st(f, o[1], j);
                 break;
@@ -652,9 +661,14 @@ __device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, con
                 float r = mx::ldf(f, a[0]);
                 float S = mx::ldf(f, a[2]);
                 float L = logf(mx::ldf(f, a[1]) / S);
-                st(f, o[0], static_cast<double>(fminf(expf(r * L), 1.0f)));
-                st(f, o[1], static_cast<double>(fminf(expf((1.0f - r) * L), 1.0f)));
+                const float l1 = r * L, l2 = (1.0f - r) * L;  // log x1, log x2
+                st(f, o[0], static_cast<double>(fminf(expf(l1), 1.0f)));
+                st(f, o[1], static_cast<double>(fminf(expf(l2), 1.0f)));
                 st(f, o[2], static_cast<double>(-L / S));
+                if (no > 3) {
+                    st(f, o[3], static_cast<double>(fminf(l1, 0.0f)));
+                    st(f, o[4], static_cast<double>(fminf(l2, 0.0f)));
+                }
                 break;
             }
             case PS_OP_COM_P_IN: {
@@ -737,7 +751,7 @@ __device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, con
             case PS_OP_PDF_POWER: {
                 double xd = ld(f, a[0]);
                 float x = static_cast<float>(xd), al = mx::ldf(f, a[1]), be = mx::ldf(f, a[2]);
-                float fx = expf(al * logf(x));
+                float fx = expf(al * (na > 3 ? static_cast<float>(ld(f, a[3])) : logf(x)));
                 float y = static_cast<float>(1.0 - xd);
                 float fy;
                 if (be == 3.0f) fy = y * y * y;
