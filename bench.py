@@ -38,11 +38,11 @@ WORKLOAD = ("hadronic 2->4 W W at sqrt(S)=13 TeV: 1/tau shat map, r_to_x1x2, 2 B
 # Algorithmic output bytes of one event: 6 momenta x 4 x 8 + x1 + x2 + w.
 BYTES_PER_EVENT = 6 * 4 * 8 + 8 + 8 + 8
 # FP64 floating-point operations executed per event by the map kernel (DFMA = 2, DADD/DMUL = 1):
-# 2 x 613.1 + 172.6 + 261.6 from the ncu instruction counters of this kernel on this workload
+# 2 x 537.4 + 152.7 + 249.8 from the ncu instruction counters of this kernel on this workload
 # (profiles/ps_map_kernel_ww_2to4.md).
-FP64_FLOP_PER_EVENT = 1660.5
+FP64_FLOP_PER_EVENT = 1477.3
 # DRAM traffic per event from the same capture (read + write, 2e6-event launch), scaled to a launch.
-DRAM_BYTES_PER_EVENT = 186.5
+DRAM_BYTES_PER_EVENT = 185.7
 # FP64 peak of a GB300: 1.25 TFLOP/s nominal (152 SMs x 2 DFMA/clk x ~2.07 GHz) -- the ALU peak
 # derived from the unit counts and clocks; no measured FP64 peak is provided.
 FP64_PEAK_GFLOPS = 1250.0
@@ -845,7 +845,7 @@ def main():
                 "frac": None if achieved is None else achieved / FP64_PEAK_GFLOPS,
                 "traffic": DRAM_BYTES_PER_EVENT * N,
                 "peak_source": "derived: 1.25 TFLOP/s FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                "fp64_pipe_active_ncu": 0.853,
+                "fp64_pipe_active_ncu": 0.859,
                 "hbm_gbs": BYTES_PER_EVENT * N / (ms / 1e3) / 1e9}
 
     cpu = None
