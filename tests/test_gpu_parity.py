@@ -360,3 +360,50 @@ def test_full_size_sampled(torch_cuda):
     assert abs(s["max_w"] / full["w"][k] - 1.0) <= weight_tol(orc_k)[0]
     assert np.array_equal(w == 0, full["w"] == 0)
     assert prog.status()["nonfinite"] == 0
+
+
+def _multichannel_full_size(torch, chans, counts, seed, offset, block, ctas, per_channel, label):
+    """One CUDA-graph launch of a multichannel program in the benchmark's configuration; sampled
+    events of every channel against the oracle one by one (their Philox draws recomputed by the
+    oracle), with the rounding-spread bounds."""
+    prog = ps.program_for(chans, block_threads=block, ctas_per_sm=ctas)
+    n_mom = chans[0]["n"] + 2
+    out, ws = prog.alloc(counts, n_mom, alpha=True)
+    ex = prog.exec_create(counts, out, ws)
+    ex.launch(seed, offset)
+    torch.cuda.synchronize()
+    st = prog.stats()
+    assert [s["n"] for s in st] == counts
+    assert prog.status()["nonfinite"] == 0
+    rng = np.random.default_rng(seed)
+    col = 0
+    for c, n in enumerate(counts):
+        ch = chans[c]
+        d = O.dims(ch)
+        loc = np.sort(rng.choice(n, min(per_channel, n), replace=False))
+        loc = np.unique(np.concatenate([loc, [0, n - 1]]))
+        cols = torch.from_numpy(col + loc).cuda()
+        mom = out["momenta"][:, cols].cpu().numpy().reshape(n_mom, 4, loc.size).transpose(2, 0, 1)
+        gpu = {"mom": mom, "w": out["weight"][cols].cpu().numpy(), "alpha": out["alpha"][cols].cpu().numpy(),
+               "x": np.stack([out["x1"][cols].cpu().numpy(), out["x2"][cols].cpu().numpy()], axis=1)}
+        r = np.vstack([O.random(seed, c, offset + int(j), 1, d) for j in loc])
+        orc = O.forward(ch, r, channels=chans, chan=c, aux=True)
+        sp = O.rounding_spread(ch, r, channels=chans, chan=c, base=orc)
+        compare(gpu, orc, ch, f"{label} {ch['name']}", alpha_tol=_alpha_tolerance(orc, sp), spread=sp)
+        col += n
+
+
+def test_full_size_multichannel_2to5(torch_cuda):
+    """2e7 events in six 2->5 channels with the benchmark's uneven counts, one persistent launch
+    replayed from its CUDA graph (128 threads x 3 CTAs per SM, the autotuner's choice)."""
+    _multichannel_full_size(torch_cuda, W.multichannel_2to5(), list(W.MULTICHANNEL_EVENTS), 1003, 0, 128, 3, 400,
+                            "2->5 full size")
+
+
+def test_full_size_streamed_chunk_2to8(torch_cuda):
+    """One 2^22-event chunk of the streamed 2->8 workload (24 channels, the chunk of the third
+    step of the stream) in the benchmark's launch configuration (64 threads x 4 CTAs per SM)."""
+    chans = W.channels_2to8()
+    chunk = W.C5_CHUNK
+    counts = [chunk // 24 + (1 if c < chunk % 24 else 0) for c in range(24)]
+    _multichannel_full_size(torch_cuda, chans, counts, 1005, 2 * chunk, 64, 4, 120, "2->8 chunk")
