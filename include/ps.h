@@ -313,7 +313,8 @@ typedef struct {
     double max_w;
 } ps_channel_stats;
 
-/* Copy the statistics of the last ps_generate / ps_map (synchronises `stream`); in
+/* Copy the statistics of the last ps_generate / ps_map (synchronises `stream`; the copy is a
+ * one-block kernel into host-mapped memory, so it does not wait for copy-engine traffic); in
  * streaming mode (ps_stats_accumulate) the running statistics of every launch since the
  * mode was enabled. */
 int ps_stats(ps_program p, ps_channel_stats* host_out, int n_ch, void* stream);

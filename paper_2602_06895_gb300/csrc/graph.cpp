@@ -1118,6 +1118,8 @@ struct ps_program_s {
     double* d_hist = nullptr;
     unsigned long long* d_status = nullptr;
     int32_t* d_stats_mode = nullptr;  // nonzero: reductions add into d_stats (ps_stats_accumulate)
+    double* h_stats = nullptr;        // host-mapped pinned copy of d_stats (read-back of ps_stats)
+    double* h_stats_dev = nullptr;    // its device address
     size_t hist_total = 0;
     bool training = false;
 };
@@ -1148,6 +1150,7 @@ void free_device(ps_program p) {
     cudaFree(p->d_hist);
     cudaFree(p->d_status);
     cudaFree(p->d_stats_mode);
+    if (p->h_stats) cudaFreeHost(p->h_stats);
 }
 
 int64_t tiles_of(int64_t n, int block) { return (n + block - 1) / block; }
@@ -1304,6 +1307,9 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
     if (st == PS_OK) st = cuda_check(cudaMalloc(&p->d_hist, std::max<size_t>(p->hist_total, 1) * sizeof(double)), "cudaMalloc hist");
     if (st == PS_OK) st = cuda_check(cudaMalloc(&p->d_status, 4 * sizeof(unsigned long long)), "cudaMalloc status");
     if (st == PS_OK) st = cuda_check(cudaMalloc(&p->d_stats_mode, sizeof(int32_t)), "cudaMalloc stats mode");
+    if (st == PS_OK)
+        st = cuda_check(cudaHostAlloc(&p->h_stats, 5 * n_ch * sizeof(double), cudaHostAllocMapped), "cudaHostAlloc stats");
+    if (st == PS_OK) st = cuda_check(cudaHostGetDevicePointer(&p->h_stats_dev, p->h_stats, 0), "mapped stats");
     if (st == PS_OK) st = cuda_check(cudaMemcpy(p->d_code, code.data(), code.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "upload code");
     if (st == PS_OK) st = cuda_check(cudaMemcpy(p->d_imm, imm.data(), imm.size() * sizeof(double), cudaMemcpyHostToDevice), "upload imm");
     if (st == PS_OK) st = cuda_check(cudaMemcpy(p->d_grid, p->h_grid.data(), p->h_grid.size() * sizeof(double), cudaMemcpyHostToDevice), "upload grid");
@@ -1582,11 +1588,12 @@ int ps_global_weights(int n_ch, int64_t batch, const double* J, int64_t ld_j, co
 int ps_stats(ps_program p, ps_channel_stats* host, int n_ch, void* stream) {
     if (!p || !host || n_ch < 1 || n_ch > p->n_ch) return fail(PS_ERR_INVALID_ARGUMENT, "ps_stats: bad arguments");
     DeviceGuard dg(p->device);
-    std::vector<double> h(5 * n_ch);
-    int st = cuda_check(cudaMemcpyAsync(h.data(), p->d_stats, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                        static_cast<cudaStream_t>(stream)), "copy stats");
-    if (st == PS_OK) st = cuda_check(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "stream sync");
+    std::string err;
+    int st = ps::launch_copy(p->h_stats_dev, p->d_stats, 5 * n_ch, stream, &err);
+    if (st != PS_OK) return fail(st, err);
+    st = cuda_check(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "stream sync");
     if (st != PS_OK) return st;
+    const double* h = p->h_stats;
     for (int c = 0; c < n_ch; ++c) {
         host[c].n = h[5 * c];
         host[c].n_nonzero = h[5 * c + 1];

@@ -1074,6 +1074,22 @@ int launch_reduce(const LaunchParams& lp, double* stats, void* stream, std::stri
     return PS_OK;
 }
 
+// Copies the statistics into host-mapped pinned memory: the read-back of ps_stats uses no copy
+// engine, so it does not queue behind large device-to-host copies of event records.
+__global__ void __launch_bounds__(256) ps_copy_kernel(double* dst, const double* src, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i];
+}
+
+int launch_copy(double* dst, const double* src, int n, void* stream, std::string* err) {
+    if (n <= 0) return PS_OK;
+    ps_copy_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(dst, src, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ps_copy_kernel launch", err);
+    __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+    return PS_OK;
+}
+
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 void count_launches(int n) { __atomic_add_fetch(&g_launches, static_cast<unsigned long long>(n), __ATOMIC_RELAXED); }
 bool is_map_kernel(const void* func) {

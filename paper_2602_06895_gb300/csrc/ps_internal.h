@@ -130,6 +130,7 @@ int build_inverse_plan(const ps_channel_desc* d, InvPlan* plan, std::string* err
 // kernels.cu
 int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem_bytes, void* stream, std::string* err);
 int launch_reduce(const LaunchParams& lp, double* stats_dev, void* stream, std::string* err);
+int launch_copy(double* dst, const double* src, int n, void* stream, std::string* err);
 size_t smem_bytes_for(const LaunchParams& lp);
 int max_ctas_per_sm(int block, size_t smem_bytes, int mixed, int* out, std::string* err);
 // Device address and size of the fixed scratch of ps_generate_noalloc on `device` (which must be

@@ -34,8 +34,8 @@ def test_exec_replay_matches_generate(torch_cuda):
     for seed, off in [(1003, 0), (1003, 200_000), (42, 7)]:
         launches = ps.launch_count()
         ex.launch(seed, off)
-        ex_stats = prog.stats()
         assert ps.launch_count() - launches == 2
+        ex_stats = prog.stats()
         prog.generate(counts, seed, ref, ws_ref, event_offset=off)
         ref_stats = prog.stats()
         torch_cuda.cuda.synchronize()
