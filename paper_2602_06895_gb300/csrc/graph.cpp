@@ -1326,6 +1326,7 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
     lp.smem_imm = p->max_imm;
     lp.smem_grid = p->max_grid;
     lp.smem_slots = p->max_slots;
+    lp.mixed = p->opt.precision == PS_PRECISION_MIXED ? 1 : 0;  // the mixed kernel also stages float immediates
     p->smem = ps::smem_bytes_for(lp);
     if (p->smem > static_cast<size_t>(prop.sharedMemPerBlockOptin)) {
         free_device(p);

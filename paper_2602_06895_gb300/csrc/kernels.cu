@@ -186,6 +186,7 @@ struct Frame {
     double* S;            // slot file base for this thread: slot k at S[k * block]
     const double* imm;    // channel immediates (shared memory)
     int block;
+    const float* immf;    // the immediates rounded to float (mixed kernel only)
 };
 
 __device__ __forceinline__ double ld(const Frame& f, int a) { return a >= 0 ? f.S[a * f.block] : f.imm[~a]; }
@@ -422,7 +423,10 @@ __device__ __forceinline__ void stp(const Frame& f, int slot, F4 p) {
     q[2 * st] = p.y;
     q[3 * st] = p.z;
 }
-__device__ __forceinline__ float ldf(const Frame& f, int a) { return static_cast<float>(ld(f, a)); }
+// immediates come from their float copy: no FP64-pipe conversion per read
+__device__ __forceinline__ float ldf(const Frame& f, int a) {
+    return a >= 0 ? static_cast<float>(f.S[a * f.block]) : f.immf[~a];
+}
 
 // sqrt in FP64 from a float reciprocal-square-root seed and one Newton step in FP64:
 // s = x r, e = x - s^2, s += e r/2 (relative error ~ 1.5 delta^2 for a seed error delta).
@@ -787,8 +791,7 @@ __device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, con
                 for (int j = 2 + k; j + 3 < na; j += 4) {
                     const int kind = small_int(ld(f, a[j]));
                     int mask = small_int(ld(f, a[j + 1]));
-                    const float M = static_cast<float>(ld(f, a[j + 2]));
-                    const float G = static_cast<float>(ld(f, a[j + 3]));
+                    const float M = mx::ldf(f, a[j + 2]), G = mx::ldf(f, a[j + 3]);
                     F4 q = (kind == 1) ? pa : F4{0.0f, 0.0f, 0.0f, 0.0f};
                     while (mask) {
                         const int i = __ffs(mask) - 1;
@@ -833,8 +836,9 @@ __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ Lau
     double* s_red = s_slots + static_cast<size_t>(lp.smem_slots) * B;
     int32_t* s_code = reinterpret_cast<int32_t*>(s_red + 4 * (B / 32));
     float* s_gridf = reinterpret_cast<float*>(s_grid);  // mixed mode: the grid staged as float
+    float* s_immf = reinterpret_cast<float*>(s_code + lp.smem_code_ints);  // mixed mode: float immediates
 
-    dev::Frame f{s_slots + tid, s_imm, B};
+    dev::Frame f{s_slots + tid, s_imm, B, s_immf};
     int cur = -1;
     int out_pc = 0;
     for (int64_t tile = blockIdx.x; tile < lp.n_tiles; tile += gridDim.x) {
@@ -845,6 +849,8 @@ __global__ void __launch_bounds__(256) ps_map_kernel(const __grid_constant__ Lau
             __syncthreads();
             for (int i = tid; i < C.code_len; i += B) s_code[i] = lp.code[C.code_off + i];
             for (int i = tid; i < C.imm_len; i += B) s_imm[i] = lp.imm[C.imm_off + i];
+            if (kMix)
+                for (int i = tid; i < C.imm_len; i += B) s_immf[i] = static_cast<float>(lp.imm[C.imm_off + i]);
             const int ng = C.vdims * (C.vbins + 1);
             if (kMix) {
                 for (int i = tid; i < ng; i += B) s_gridf[i] = static_cast<float>(lp.grid[C.grid_off + i]);
@@ -1023,7 +1029,8 @@ __global__ void __launch_bounds__(256) ps_reduce_kernel(const __grid_constant__ 
 size_t smem_bytes_for(const LaunchParams& lp) {
     size_t doubles = static_cast<size_t>(lp.smem_imm) + lp.smem_grid + static_cast<size_t>(lp.smem_slots) * lp.block +
                      4 * (lp.block / 32);
-    return doubles * sizeof(double) + static_cast<size_t>(lp.smem_code_ints) * sizeof(int32_t);
+    return doubles * sizeof(double) + static_cast<size_t>(lp.smem_code_ints) * sizeof(int32_t) +
+           (lp.mixed ? static_cast<size_t>(lp.smem_imm) * sizeof(float) : 0);
 }
 
 static int cuda_fail(cudaError_t e, const char* what, std::string* err) {
