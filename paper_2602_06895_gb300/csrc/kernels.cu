@@ -117,8 +117,10 @@ __device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin
 __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double tabs, double m1, double m2,
                                              double s, double mA2, double mB2, P4& p1, P4& p2) {
     P4 p0 = p4_add(pA, pB);
+    const double inv_s = 1.0 / s;
     double m0 = sqrt(s);
-    P4 a = boost_in(pA, p0, m0);
+    const BoostFrame bf = boost_frame(p0, m0, m0 * inv_s);  // 1/m0 = m0/s
+    P4 a = boost_in(pA, bf);
     double pt2 = a.x * a.x + a.y * a.y;
     double pt = sqrt(pt2);
     double rp = rsqrt(pt2 + a.z * a.z);
@@ -141,7 +143,7 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
     sincospi(2.0 * rphi, &sph, &cph);
 
     double m12 = m1 * m1, m22 = m2 * m2;
-    double i2m0 = 0.5 / m0;
+    double i2m0 = 0.5 * bf.inv_m;
     double pabs = sqrt(kallen(s, m12, m22)) * i2m0;
     double e1 = (s + m12 - m22) * i2m0, e2 = (s + m22 - m12) * i2m0;
     double vx = pabs * sth * cph, vy = pabs * sth * sph, vz = pabs * cth;
@@ -149,8 +151,8 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
     double rx = ca * vx + sa * vz, rz = -sa * vx + ca * vz;
     P4 q1 = {e1, cpa * rx - spa * vy, spa * rx + cpa * vy, rz};
     P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
-    p1 = boost_out(q1, p0, m0);
-    p2 = boost_out(q2, p0, m0);
+    p1 = boost_out(q1, bf);
+    p2 = boost_out(q2, bf);
     return 0.5 * kPi / sqrt(kallen(s, mA2, mB2));
 }
 
@@ -160,9 +162,12 @@ template <bool kBoost>
 __device__ __forceinline__ double two_body(double rphi, double rth, double s0, double m1, double m2, P4 p0,
                                            P4& p1, P4& p2) {
     double m0 = sqrt(s0);
+    const double inv_s0 = 1.0 / s0;
+    const double inv_m0 = m0 * inv_s0;  // 1/m0 = m0/s0: one division per decay
     double m12 = m1 * m1, m22 = m2 * m2;
-    double sl = sqrt(kallen(s0, m12, m22));
-    double i2m0 = 0.5 / m0;
+    // sqrt(lambda) = s0 exactly for two massless daughters
+    double sl = (zero_bits(m12) && zero_bits(m22)) ? s0 : sqrt(kallen(s0, m12, m22));
+    double i2m0 = 0.5 * inv_m0;
     double pabs = sl * i2m0;
     double e1 = (s0 + m12 - m22) * i2m0, e2 = (s0 + m22 - m12) * i2m0;
     double cth = 2.0 * rth - 1.0;
@@ -172,13 +177,14 @@ __device__ __forceinline__ double two_body(double rphi, double rth, double s0, d
     P4 q1 = {e1, pabs * sth * cph, pabs * sth * sph, pabs * cth};
     P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
     if (kBoost) {
-        p1 = boost_out(q1, p0, m0);
-        p2 = boost_out(q2, p0, m0);
+        const BoostFrame bf = boost_frame(p0, m0, inv_m0);
+        p1 = boost_out(q1, bf);
+        p2 = boost_out(q2, bf);
     } else {
         p1 = q1;
         p2 = q2;
     }
-    return 0.5 * kPi * sl / s0;
+    return 0.5 * kPi * sl * inv_s0;
 }
 
 // ---------------------------------------------------------------- interpreter
@@ -431,7 +437,7 @@ __device__ __forceinline__ float ldf(const Frame& f, int a) {
 // sqrt in FP64 from a float reciprocal-square-root seed and one Newton step in FP64:
 // s = x r, e = x - s^2, s += e r/2 (relative error ~ 1.5 delta^2 for a seed error delta).
 __device__ __forceinline__ double sqrt64(double x) {
-    if (!(x > 0.0)) return 0.0;
+    if (!pos_bits(x)) return 0.0;
     double r = static_cast<double>(rsqrtf(static_cast<float>(x)));
     double s = x * r;
     double e = fma(-s, s, x);
@@ -447,20 +453,20 @@ __device__ __forceinline__ double rcp64(double x) {
 
 __device__ __forceinline__ double kallen64(double x, double y, double z) {
     double l;
-    if (y == 0.0 && z == 0.0) {
+    if (zero_bits(y) && zero_bits(z)) {
         l = x * x;
-    } else if (y >= 0.0 && z >= 0.0) {
+    } else if (nonneg_bits(y) && nonneg_bits(z)) {
         double ry = sqrt64(y), rz = sqrt64(z);
         double hi = ry + rz, lo = ry - rz;
         l = (x - hi * hi) * (x - lo * lo);
-    } else if (y <= 0.0 && z <= 0.0) {
+    } else if (nonpos_bits(y) && nonpos_bits(z)) {
         double d = z - y;
         l = x * x - 2.0 * x * (y + z) + d * d;
     } else {
         double d = x - y - z;
         l = d * d - 4.0 * y * z;
     }
-    return fmax(l, 0.0);
+    return pos_bits(l) ? l : 0.0;
 }
 
 __device__ __forceinline__ F4 boost_out(F4 p, F4 q, float mq) {

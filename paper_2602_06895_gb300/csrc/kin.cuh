@@ -65,20 +65,46 @@ __device__ __forceinline__ double p4_sq(P4 a) { return a.e * a.e - a.x * a.x - a
 //   y, z <= 0: x^2 + 2x(|y| + |z|) + (|y| - |z|)^2  (space-like legs of a t-chain)
 //   mixed:     (x - y - z)^2 - 4 y z                (-4yz >= 0)
 // clamped at zero.
+// The branches are taken on the bit patterns (integer ALU); y = z = 0 (two massless legs) is x^2.
+__device__ __forceinline__ bool zero_bits(double v) { return (dbits(v) << 1) == 0; }       // +-0
+__device__ __forceinline__ bool nonneg_bits(double v) { return dbits(v) >= 0 || zero_bits(v); }
+__device__ __forceinline__ bool nonpos_bits(double v) { return dbits(v) <= 0; }            // includes -0
 __device__ __forceinline__ double kallen(double x, double y, double z) {
     double l;
-    if (y >= 0.0 && z >= 0.0) {
+    if (zero_bits(y) && zero_bits(z)) {
+        l = x * x;
+    } else if (nonneg_bits(y) && nonneg_bits(z)) {
         double ry = sqrt(y), rz = sqrt(z);
         double hi = ry + rz, lo = ry - rz;
         l = (x - hi * hi) * (x - lo * lo);
-    } else if (y <= 0.0 && z <= 0.0) {
+    } else if (nonpos_bits(y) && nonpos_bits(z)) {
         double d = z - y;
         l = x * x - 2.0 * x * (y + z) + d * d;
     } else {
         double d = x - y - z;
         l = d * d - 4.0 * y * z;
     }
-    return fmax(l, 0.0);
+    return pos_bits(l) ? l : 0.0;  // clamped at zero (NaN -> 0)
+}
+
+// Pure boosts out of the rest frame of q (mass mq) sharing their reciprocals: 1/mq and
+// 1/(mq (E_q + mq)) are taken once per frame, for every momentum boosted with it.
+struct BoostFrame {
+    double e, x, y, z;  // q
+    double inv_m, k;    // 1/mq, 1/(mq (E_q + mq))
+};
+__device__ __forceinline__ BoostFrame boost_frame(const P4& q, double mq, double inv_m) {
+    return {q.e, q.x, q.y, q.z, inv_m, 1.0 / (mq * (q.e + mq))};
+}
+__device__ __forceinline__ P4 boost_out(const P4& p, const BoostFrame& b) {
+    double qp = b.x * p.x + b.y * p.y + b.z * p.z;
+    double c = fma(qp, b.k, p.e * b.inv_m);
+    return {(b.e * p.e + qp) * b.inv_m, p.x + b.x * c, p.y + b.y * c, p.z + b.z * c};
+}
+__device__ __forceinline__ P4 boost_in(const P4& p, const BoostFrame& b) {
+    double qp = b.x * p.x + b.y * p.y + b.z * p.z;
+    double c = fma(qp, b.k, -p.e * b.inv_m);
+    return {(b.e * p.e - qp) * b.inv_m, p.x + b.x * c, p.y + b.y * c, p.z + b.z * c};
 }
 
 // Pure boost of p from the rest frame of q (invariant mass mq) to the frame where q is given.
