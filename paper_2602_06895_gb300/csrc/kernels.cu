@@ -122,11 +122,11 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
     const BoostFrame bf = boost_frame(p0, m0, m0 * inv_s);  // 1/m0 = m0/s
     P4 a = boost_in(pA, bf);
     double pt2 = a.x * a.x + a.y * a.y;
-    double pt = sqrt(pt2);
+    bool has_pt = pos_bits(pt2);
+    double ipt = has_pt ? rsqrt(pt2) : 0.0;
+    double pt = pt2 * ipt;
     double rp = rsqrt(pt2 + a.z * a.z);
     double ca = a.z * rp, sa = pt * rp;
-    bool has_pt = pt > 0.0;
-    double ipt = has_pt ? 1.0 / pt : 0.0;
     double cpa = has_pt ? a.x * ipt : 1.0, spa = has_pt ? a.y * ipt : 0.0;
 
     double tlo, thi, B;
@@ -153,7 +153,7 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
     P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
     p1 = boost_out(q1, bf);
     p2 = boost_out(q2, bf);
-    return 0.5 * kPi / sqrt(kallen(s, mA2, mB2));
+    return 0.5 * kPi * rsqrt(kallen(s, mA2, mB2));
 }
 
 // 1->2 decay in (phi, theta), Sec. 2.2.3: cos = 2 r_theta - 1, sin = 2 sqrt(r_theta (1 - r_theta)),
@@ -307,8 +307,9 @@ __device__ void run_code(const int32_t* code, int len, const Frame& f, const dou
                 // light-cone form of the longitudinal boost: E+p_z scales by rho = sqrt(x1/x2),
                 // E-p_z by 1/rho (no cancellation for extreme boosts)
                 double x1 = ld(f, a[na - 2]), x2 = ld(f, a[na - 1]);
-                double rho = sqrt(x1 / x2);
-                double irho = 1.0 / rho;
+                const double t = rsqrt(x1 * x2);  // rho = sqrt(x1/x2) = x1 t, 1/rho = x2 t
+                double rho = x1 * t;
+                double irho = x2 * t;
                 for (int k = 0; k < na - 2; ++k) {
                     P4 p = ldp(f, a[k]);
                     double plus = rho * (p.e + p.z), minus = (p.e - p.z) * irho;
