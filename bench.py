@@ -38,18 +38,18 @@ WORKLOAD = ("hadronic 2->4 W W at sqrt(S)=13 TeV: 1/tau shat map, r_to_x1x2, 2 B
 # Algorithmic output bytes of one event: 6 momenta x 4 x 8 + x1 + x2 + w.
 BYTES_PER_EVENT = 6 * 4 * 8 + 8 + 8 + 8
 # FP64 floating-point operations executed per event by the map kernel (DFMA = 2, DADD/DMUL = 1):
-# 2 x 537.4 + 152.7 + 249.8 from the ncu instruction counters of this kernel on this workload
+# 2 x 438.2 + 140.6 + 233.7 from the ncu instruction counters of this kernel on this workload
 # (profiles/ps_map_kernel_ww_2to4.md).
-FP64_FLOP_PER_EVENT = 1477.3
+FP64_FLOP_PER_EVENT = 1250.7
 # DRAM traffic per event from the same capture (read + write, 2e6-event launch), scaled to a launch.
-DRAM_BYTES_PER_EVENT = 185.7
+DRAM_BYTES_PER_EVENT = 186.0
 # FP64 peak of a GB300: 1.25 TFLOP/s nominal (152 SMs x 2 DFMA/clk x ~2.07 GHz) -- the ALU peak
 # derived from the unit counts and clocks; no measured FP64 peak is provided.
 FP64_PEAK_GFLOPS = 1250.0
 # The binding resource is the FP64 pipe: 2 FP64 instructions per clock per SM, whether DFMA, DADD
 # or DMUL, i.e. 152 x 2 x 2.07 GHz = 629.3 G instructions/s.  FP64 arithmetic instructions per
-# event of the map kernel from the same ncu capture: DFMA + DADD + DMUL = 537.4 + 152.7 + 249.8.
-FP64_INSTR_PER_EVENT = 939.9
+# event of the map kernel from the same ncu capture: DFMA + DADD + DMUL = 438.2 + 140.6 + 233.7.
+FP64_INSTR_PER_EVENT = 812.5
 FP64_PEAK_GINSTR = 152 * 2 * 2.07
 
 
@@ -867,7 +867,7 @@ def main():
                 "unit": "G FP64-pipe instructions/s", "frac": achieved / FP64_PEAK_GINSTR,
                 "traffic": DRAM_BYTES_PER_EVENT * N,
                 "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz",
-                "fp64_pipe_active_ncu": 0.859,
+                "fp64_pipe_active_ncu": 0.854,
                 "flops": {"achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                           "frac": gflops / FP64_PEAK_GFLOPS,
                           "peak_source": "derived: 1.25 TFLOP/s FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)"},
