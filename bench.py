@@ -51,6 +51,12 @@ FP64_PEAK_GFLOPS = 1250.0
 # event of the map kernel from the same ncu capture: DFMA + DADD + DMUL = 438.2 + 140.6 + 233.7.
 FP64_INSTR_PER_EVENT = 812.5
 FP64_PEAK_GINSTR = 152 * 2 * 2.07
+# The same counters for the compiled program's kernel (ps_jit_map) on this workload, from its own
+# ncu capture (profiles/ps_jit_map_ww_2to4.md): DFMA 405.6 + DADD 113.6 + DMUL 197.6 = 716.8 FP64
+# arithmetic instructions (1122.4 flops) and 185.9 DRAM bytes per event; FP64 pipe 85.4 % active.
+COMPILED_COUNTERS = {"instr": 716.8, "flops": 1122.4, "dram": 185.9, "pipe": 0.854}
+INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
+                        "pipe": 0.854}
 
 
 def parse():
@@ -69,6 +75,8 @@ def parse():
     ap.add_argument("--no-global", action="store_true")
     ap.add_argument("--no-streamed", action="store_true")
     ap.add_argument("--no-c5-importance", action="store_true")
+    ap.add_argument("--no-jit", action="store_true",
+                    help="run the 2->4 and 2->5 steps on the interpreter instead of compiled programs")
     ap.add_argument("--stream-events", type=int, default=None, help="streamed leg: total events (default 1e8)")
     ap.add_argument("--stream-chunk", type=int, default=None, help="streamed leg: events per chunk (default 2^22)")
     ap.add_argument("--stream-config", default=None, help="streamed leg: 'threads,ctas_per_sm' instead of autotuning")
@@ -668,7 +676,8 @@ def main():
         print(json.dumps({"leg": args.leg, args.leg: res}), flush=True)
         return
     ch = W.ww_hadronic()
-    prog = ps.program_for([ch], device=local)
+    jit = not args.no_jit
+    prog = ps.program_for([ch], device=local, jit=jit)  # compiled program (NVRTC) unless --no-jit
     prog.set_vegas(0, grid)
     out, ws = prog.alloc([N], 6, device=local)
     stream = torch.cuda.current_stream()
@@ -712,6 +721,24 @@ def main():
     eff = ess / (ms / 1e3)  # effective (unit-weight-equivalent) events per second of the last step
     n_half_pct = var / (mean * mean * 0.005 ** 2)
 
+    # the same steps on the interpreter kernel, for comparison (outside the timed region)
+    interpreter = None
+    if jit:
+        iprog = ps.program_for([ch], device=local)
+        iprog.set_vegas(0, grid)
+        for k in range(args.warmup):
+            iprog.generate([N], SEED, out, ws, event_offset=off(k))
+        iev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        iev[0].record(stream)
+        for k in range(args.steps):
+            iprog.generate([N], SEED, out, ws, event_offset=off(args.warmup + k))
+        iev[1].record(stream)
+        torch.cuda.synchronize()
+        ims = iev[0].elapsed_time(iev[1]) / args.steps
+        interpreter = {"value": world * N / (ims / 1e3), "ms_per_step": ims, "kernel": "ps_map_kernel<0>"}
+        del iprog
+
     # end to end: same call, event record read back to pinned host memory every step
     e2e = None
     if not args.no_e2e:
@@ -748,7 +775,7 @@ def main():
     # mixed precision (FP32 bulk, FP64 islands) on the same events: same step, same grid
     mixed = None
     if not args.no_mixed:
-        mprog = ps.program_for([ch], device=local, precision="mixed")
+        mprog = ps.program_for([ch], device=local, precision="mixed", jit=jit)
         mprog.set_vegas(0, grid)
         mout, mws = mprog.alloc([N], 6, device=local)
         for k in range(args.warmup):
@@ -777,9 +804,10 @@ def main():
     if not args.no_multichannel:
         chans = W.multichannel_2to5()
         counts = list(W.MULTICHANNEL_EVENTS)
-        best, table = ps.autotune(chans, [c // 8 for c in counts], blocks=(64, 128, 256), ctas=(1, 2, 3, 4),
-                                  reps=2, device=local)
-        mprog = ps.program_for(chans, device=local, **best)
+        # compiled programs: one block size (one compilation, the kernel cache serves the rest)
+        best, table = ps.autotune(chans, [c // 8 for c in counts], blocks=(128,) if jit else (64, 128, 256),
+                                  ctas=(2, 3, 4, 5, 6) if jit else (1, 2, 3, 4), reps=2, device=local, jit=jit)
+        mprog = ps.program_for(chans, device=local, jit=jit, **best)
         mout, mws = mprog.alloc(counts, 7, alpha=True, device=local)
         ex = mprog.exec_create(counts, mout, mws)
         for k in range(args.warmup):
@@ -797,7 +825,7 @@ def main():
         multi = {"workload": "2->5 massless at sqrt(S)=13 TeV, 6 channels (t-chains with Z/H/T resonances, "
                              "pure s), SDE multichannel weights in-kernel, events " + str(counts),
                  "value": world * sum(counts) / (cms / 1e3), "unit": UNIT, "ms_per_step": cms,
-                 "precision": "fp64", "map_launches_per_step": 1,
+                 "precision": "fp64", "map_launches_per_step": 1, "compiled": jit,
                  "gpu_launches": int(ps.launch_count() - l0), "cuda_graph": True,
                  "autotuned": best, "autotune_table": table,
                  "integral": sum(c["sum_w"] for c in cst) / 1.0,
@@ -806,9 +834,10 @@ def main():
                                                  for c in cst if c["n"])),
                  "per_channel_sum_w": [c["sum_w"] for c in cst]}
         # the mixed-precision form of the same step on the same events
-        mbest, _ = ps.autotune(chans, [c // 8 for c in counts], precision="mixed", blocks=(64, 128, 256),
-                               ctas=(1, 2, 3, 4), reps=2, device=local)
-        xprog = ps.program_for(chans, device=local, precision="mixed", **mbest)
+        mbest, _ = ps.autotune(chans, [c // 8 for c in counts], precision="mixed",
+                               blocks=(128,) if jit else (64, 128, 256), ctas=(2, 3, 4, 5, 6) if jit else (1, 2, 3, 4),
+                               reps=2, device=local, jit=jit)
+        xprog = ps.program_for(chans, device=local, precision="mixed", jit=jit, **mbest)
         xout, xws = xprog.alloc(counts, 7, alpha=True, device=local)
         xex = xprog.exec_create(counts, xout, xws)
         for k in range(args.warmup):
@@ -861,15 +890,17 @@ def main():
 
     # the FP64-pipe roofline: FP64 arithmetic instructions issued per second against the pipe's
     # issue rate (a DADD or DMUL takes a slot exactly like a DFMA); the flop form beside it
-    achieved = FP64_INSTR_PER_EVENT * N / (ms / 1e3) / 1e9
-    gflops = FP64_FLOP_PER_EVENT * N / (ms / 1e3) / 1e9
+    kc = COMPILED_COUNTERS if jit else INTERPRETER_COUNTERS
+    achieved = None if kc["instr"] is None else kc["instr"] * N / (ms / 1e3) / 1e9
+    gflops = None if kc["flops"] is None else kc["flops"] * N / (ms / 1e3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GINSTR,
-                "unit": "G FP64-pipe instructions/s", "frac": achieved / FP64_PEAK_GINSTR,
-                "traffic": DRAM_BYTES_PER_EVENT * N,
+                "unit": "G FP64-pipe instructions/s", "frac": None if achieved is None else achieved / FP64_PEAK_GINSTR,
+                "traffic": None if kc["dram"] is None else kc["dram"] * N,
+                "kernel": "ps_jit_map (compiled program)" if jit else "ps_map_kernel<0> (interpreter)",
                 "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz",
-                "fp64_pipe_active_ncu": 0.854,
+                "fp64_pipe_active_ncu": kc["pipe"],
                 "flops": {"achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                          "frac": gflops / FP64_PEAK_GFLOPS,
+                          "frac": None if gflops is None else gflops / FP64_PEAK_GFLOPS,
                           "peak_source": "derived: 1.25 TFLOP/s FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)"},
                 "hbm_gbs": BYTES_PER_EVENT * N / (ms / 1e3) / 1e9}
 
@@ -883,7 +914,9 @@ def main():
             "config": {"workload": WORKLOAD, "events_per_step": N, "global_events_per_step": world * N,
                        "parallelism": f"replicas x{world} (independent event ranges)",
                        "l2": "no flush: every step writes a 2.16 GB event record (> 129 MB L2)",
-                       "precision": "fp64", "block_threads": 128},
+                       "precision": "fp64", "block_threads": 128,
+                       "kernel": "compiled program (NVRTC, slots in registers)" if jit else "interpreter"},
+            "interpreter": interpreter,
             "effective_events_per_s": eff, "integral": {"mean_w": mean, "rel_err_per_step": math.sqrt(var / st["n"]) / mean,
                                                         "ess_per_step": ess, "events_for_0.5pct": n_half_pct},
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),

@@ -234,8 +234,19 @@ typedef struct {
     int32_t block_threads; /* events per tile = threads per CTA (multiple of 32; 0 = default 128) */
     int32_t ctas_per_sm;   /* resident CTAs requested per SM (0 = as many as fit, up to 4)      */
     int32_t precision;     /* PS_PRECISION_*                                                  */
-    int32_t reserved;
+    int32_t flags;         /* PS_PROGRAM_* bits                                               */
 } ps_options;
+
+/* Compile the program's instruction lists into one kernel at creation (NVRTC, sm_103a): the
+ * slot file in registers, the byte-code's slots and immediates as constants.  Same results as
+ * the interpreter up to the rounding of fused multiply-adds across op boundaries.  Creation
+ * fails (PS_ERR_GRAPH with the compiler's message, PS_ERR_CUDA) if the kernel cannot be built;
+ * kernels are cached per device and source. */
+#define PS_PROGRAM_JIT 1
+
+/* Generate and compile (NVRTC, no device needed) the kernel a program with these graphs and
+ * options would use under PS_PROGRAM_JIT; the compiler log goes to log[log_bytes]. */
+int ps_jit_check(const ps_graph* graphs, int n_ch, const ps_options* opt, char* log, size_t log_bytes);
 
 /* Compile n_ch graphs (channel c = graphs[c]) for `device`.  Every channel must declare
  * the same outputs.  Allocates the program's device constants on that device. */

@@ -18,7 +18,10 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libps.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "graph.cpp", "flow.cu", "unweight.cu", "inverse.cu"]
+SOURCES = ["kernels.cu", "graph.cpp", "flow.cu", "unweight.cu", "inverse.cu", "jit.cpp"]
+# device headers that compiled programs (jit.cpp) hand to NVRTC, embedded as text
+JIT_HEADERS = [("map_device.cuh", CSRC), ("kin.cuh", CSRC), ("philox.cuh", CSRC), ("launch_params.h", CSRC),
+               ("ps.h", INCLUDE)]
 
 
 def nvcc():
@@ -36,12 +39,42 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+def cuda_lib_dir():
+    """lib64 of the toolkit whose nvcc builds the library (libnvrtc is found there at run time)."""
+    path = nvcc()
+    if os.path.sep not in path:
+        from shutil import which
+        path = which(path) or path
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(path))), "lib64")
+
+
+def write_jit_sources(path):
+    """The device headers as C++ raw strings (kJitHeaderNames/Texts/Count) for jit.cpp."""
+    out = []
+    names = []
+    for k, (name, d) in enumerate(JIT_HEADERS):
+        text = open(os.path.join(d, name)).read()
+        assert ")PSJIT" not in text
+        out.append(f'const char* const kJitHeader{k} = R"PSJIT({text})PSJIT";')
+        names.append(f'"{name}"')
+    out.append("const char* const kJitHeaderNames[] = {" + ", ".join(names) + "};")
+    out.append("const char* const kJitHeaderTexts[] = {" +
+               ", ".join(f"kJitHeader{k}" for k in range(len(JIT_HEADERS))) + "};")
+    out.append(f"const int kJitHeaderCount = {len(JIT_HEADERS)};")
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        f.write("\n".join(out) + "\n")
+    os.replace(tmp, path)
+
+
 def build(force=False, verbose=False, ptxas_verbose=False):
     """Compile the library if any source is newer than libps.so; returns its path."""
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
-    common = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    write_jit_sources(os.path.join(BUILD_DIR, "jit_sources.inc"))
+    common = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+              "-I", BUILD_DIR]
     if ptxas_verbose:
         common += ["-Xptxas", "-v"]
 
@@ -60,7 +93,9 @@ def build(force=False, verbose=False, ptxas_verbose=False):
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    libdir = cuda_lib_dir()
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-L", libdir, "-lnvrtc", "-ldl",
+           "-Xlinker", "-rpath", "-Xlinker", libdir]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

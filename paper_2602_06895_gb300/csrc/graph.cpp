@@ -19,7 +19,7 @@
 namespace ps {
 unsigned long long launch_count();
 void count_launches(int n);
-bool is_map_kernel(const void* func);
+bool is_reduce_kernel(const void* func);
 }
 
 using ps::Arg;
@@ -1122,6 +1122,9 @@ struct ps_program_s {
     double* h_stats_dev = nullptr;    // its device address
     size_t hist_total = 0;
     bool training = false;
+    void* jit_fn = nullptr;  // the compiled kernel (PS_PROGRAM_JIT), else the interpreter runs
+    size_t jit_smem = 0;
+    int jit_grid = 0;
 };
 
 namespace {
@@ -1155,6 +1158,16 @@ void free_device(ps_program p) {
 
 int64_t tiles_of(int64_t n, int block) { return (n + block - 1) / block; }
 
+// The map launch of a program: its compiled kernel, else the interpreter.
+int launch_program_map(ps_program p, const ps::LaunchParams& lp, void* stream, std::string* err) {
+    if (p->jit_fn) {
+        const int grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>(lp.n_tiles, 1), p->jit_grid));
+        return ps::jit_launch(p->jit_fn, lp, grid, p->jit_smem, stream, err);
+    }
+    const int grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>(lp.n_tiles, 1), p->grid_ctas));
+    return ps::launch_map(lp, grid, p->smem, stream, err);
+}
+
 // Fills the launch description shared by ps_generate and ps_map.
 int fill_launch(ps_program p, const int* chans, const int64_t* counts, int n, const ps_out_buffers* out,
                 void* workspace, size_t ws_bytes, ps::LaunchParams* lp) {
@@ -1184,6 +1197,7 @@ int fill_launch(ps_program p, const int* chans, const int64_t* counts, int n, co
         L.n_slots = C.n_slots;
         L.n_random = C.n_random;
         L.hist_off = p->hist_off[c];
+        L.channel = c;
         L.n_events = counts[k];
         L.col_off = cols;
         L.tile_begin = tiles;
@@ -1343,6 +1357,19 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
     }
     int want = p->opt.ctas_per_sm > 0 ? p->opt.ctas_per_sm : 4;
     p->grid_ctas = p->sm_count * std::min(per_sm, want);
+    if (p->opt.flags & PS_PROGRAM_JIT) {  // the compiled kernel: VEGAS grid and reduction scratch in shared memory
+        st = ps::jit_prepare(p->ch, p->block, p->opt.precision == PS_PRECISION_MIXED, device, &p->jit_fn, &err);
+        int jit_per_sm = 0;
+        p->jit_smem = (static_cast<size_t>(p->max_grid) + 4 * (p->block / 32)) * sizeof(double);
+        if (st == PS_OK) st = ps::jit_occupancy(p->jit_fn, p->block, p->jit_smem, &jit_per_sm);
+        if (st != PS_OK || jit_per_sm < 1) {
+            free_device(p);
+            delete p;
+            return fail(st != PS_OK ? st : PS_ERR_CAPACITY, st != PS_OK ? err : "compiled kernel does not fit on an SM");
+        }
+        const int jit_want = p->opt.ctas_per_sm > 0 ? p->opt.ctas_per_sm : 16;
+        p->jit_grid = p->sm_count * std::min(jit_per_sm, jit_want);
+    }
     *out = p;
     return PS_OK;
 }
@@ -1398,9 +1425,8 @@ int ps_generate(ps_program p, const int64_t* events, uint64_t seed, uint64_t eve
     lp.seed = seed;
     DeviceGuard dg(p->device);
     std::string err;
-    int grid = static_cast<int>(std::min<int64_t>(lp.n_tiles, p->grid_ctas));
     if (lp.n_tiles > 0) {
-        st = ps::launch_map(lp, grid, p->smem, stream, &err);
+        st = launch_program_map(p, lp, stream, &err);
         if (st != PS_OK) return fail(st, err);
     }
     st = ps::launch_reduce(lp, p->d_stats, stream, &err);
@@ -1434,14 +1460,15 @@ int ps_exec_create(ps_program p, const int64_t* events, const ps_out_buffers* ou
     if (st != PS_OK) { delete e; return st; }
     e->lp.r = nullptr;
     e->stats = p->d_stats;
-    e->grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>(e->lp.n_tiles, 1), p->grid_ctas));
+    e->grid = static_cast<int>(
+        std::min<int64_t>(std::max<int64_t>(e->lp.n_tiles, 1), p->jit_fn ? p->jit_grid : p->grid_ctas));
     DeviceGuard dg(p->device);
     cudaStream_t cs;
     st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
     if (st != PS_OK) { delete e; return st; }
     std::string err;
     st = cuda_check(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    if (st == PS_OK && e->lp.n_tiles > 0) st = ps::launch_map(e->lp, e->grid, p->smem, cs, &err);
+    if (st == PS_OK && e->lp.n_tiles > 0) st = launch_program_map(p, e->lp, cs, &err);
     if (st == PS_OK) st = ps::launch_reduce(e->lp, e->stats, cs, &err);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &g);
@@ -1458,10 +1485,17 @@ int ps_exec_create(ps_program p, const int64_t* events, const ps_out_buffers* ou
         cudaGraphNodeType t;
         cudaGraphNodeGetType(nodes[k], &t);
         if (t != cudaGraphNodeTypeKernel) continue;
+        if (p->jit_fn && ps::jit_node_runs(nodes[k], p->jit_fn)) {
+            e->map_node = nodes[k];  // a compiled program's kernel, launched through the driver
+            continue;
+        }
         cudaKernelNodeParams kp;
-        if (cudaGraphKernelNodeGetParams(nodes[k], &kp) != cudaSuccess) continue;
-        if (ps::is_map_kernel(kp.func)) e->map_node = nodes[k];
-        else e->reduce_node = nodes[k];
+        if (cudaGraphKernelNodeGetParams(nodes[k], &kp) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (ps::is_reduce_kernel(kp.func)) e->reduce_node = nodes[k];
+        else if (!p->jit_fn) e->map_node = nodes[k];
     }
     if (e->lp.n_tiles > 0 && !e->map_node) {
         cudaGraphDestroy(g);
@@ -1479,7 +1513,11 @@ int ps_exec_launch(ps_exec e, uint64_t seed, uint64_t event_offset, void* stream
     e->lp.seed = seed;
     for (int c = 0; c < e->lp.n_ch; ++c) e->lp.ch[c].ev_offset = static_cast<int64_t>(event_offset);
     DeviceGuard dg(e->p->device);
-    if (e->map_node) {
+    if (e->map_node && e->p->jit_fn) {
+        std::string err;
+        int st = ps::jit_node_set(e->exec, e->map_node, e->p->jit_fn, e->lp, e->grid, e->p->jit_smem, &err);
+        if (st != PS_OK) return fail(st, err);
+    } else if (e->map_node) {
         cudaKernelNodeParams kp;
         int st = cuda_check(cudaGraphKernelNodeGetParams(e->map_node, &kp), "cudaGraphKernelNodeGetParams");
         if (st != PS_OK) return st;
@@ -1538,9 +1576,8 @@ int ps_map(ps_program p, int ch, int64_t batch, const double* r, int64_t ld_r, c
     lp.ld_r = ld_r;
     DeviceGuard dg(p->device);
     std::string err;
-    int grid = static_cast<int>(std::min<int64_t>(lp.n_tiles, p->grid_ctas));
     if (lp.n_tiles > 0) {
-        st = ps::launch_map(lp, grid, p->smem, stream, &err);
+        st = launch_program_map(p, lp, stream, &err);
         if (st != PS_OK) return fail(st, err);
     }
     st = ps::launch_reduce(lp, p->d_stats + 5 * ch, stream, &err);
@@ -1602,6 +1639,28 @@ int ps_stats(ps_program p, ps_channel_stats* host, int n_ch, void* stream) {
         host[c].sum_w2 = h[5 * c + 3];
         host[c].max_w = h[5 * c + 4];
     }
+    return PS_OK;
+}
+
+int ps_jit_check(const ps_graph* graphs, int n_ch, const ps_options* opt, char* log, size_t log_bytes) {
+    if (!graphs || n_ch < 1 || n_ch > ps::kMaxChannels || (log_bytes > 0 && !log))
+        return fail(PS_ERR_INVALID_ARGUMENT, "ps_jit_check: bad arguments");
+    const bool mixed = opt && opt->precision == PS_PRECISION_MIXED;
+    const int block = (opt && opt->block_threads > 0) ? opt->block_threads : 128;
+    std::vector<Compiled> ch(n_ch);
+    std::string err;
+    for (int c = 0; c < n_ch; ++c) {
+        if (!graphs[c]) return fail(PS_ERR_INVALID_ARGUMENT, "ps_jit_check: null graph");
+        int st = ps::compile_graph(graphs[c]->g, &ch[c], &err);
+        if (st != PS_OK) return fail(st, "channel " + std::to_string(c) + ": " + err);
+    }
+    std::vector<char> cubin;
+    std::string lg;
+    int st = ps::jit_compile(ps::jit_source(ch, block, mixed), &cubin, &lg);
+    if (log_bytes > 0) {
+        std::snprintf(log, log_bytes, "%s", lg.c_str());
+    }
+    if (st != PS_OK) return fail(st, "NVRTC: " + lg);
     return PS_OK;
 }
 

@@ -1,0 +1,352 @@
+// jit.cpp -- compiled programs: every channel's instruction list (the paper's compute graph,
+// Sec. 3.1) written out as straight-line CUDA and compiled at run time with NVRTC for sm_103a.
+//
+// The generated kernel runs the same op implementations as the interpreter (map_device.cuh),
+// instantiated on a register frame: the slot file lives in registers, the byte-code's slot
+// indices and immediates become compile-time constants, and the compiler can fold constant
+// sub-expressions (M^2, M Gamma, 1/(M Gamma) ...), fuse multiply-adds across op boundaries and
+// cancel the float<->double round trips of the mixed form.  The tile loop, inputs, outputs and
+// per-tile sums are the interpreter's (map_tiles).  Modules are cached per device and source.
+//
+// The driver API (module load, launch, occupancy) is opened with dlopen at first use, so the
+// library also loads on machines without a GPU driver.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cinttypes>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ps_internal.h"
+
+namespace ps {
+namespace {
+
+// Header texts for NVRTC, embedded at build time: kJitHeaderNames[], kJitHeaderTexts[], kJitHeaderCount.
+#include "jit_sources.inc"
+
+// Stand-ins for the standard headers that the device headers include; NVRTC has the CUDA math
+// functions built in.
+const char* kStdInt =
+    "#pragma once\n"
+    "typedef signed char int8_t; typedef short int16_t; typedef int int32_t; typedef long long int64_t;\n"
+    "typedef unsigned char uint8_t; typedef unsigned short uint16_t; typedef unsigned int uint32_t;\n"
+    "typedef unsigned long long uint64_t;\n"
+    "namespace std { using ::int8_t; using ::int16_t; using ::int32_t; using ::int64_t; using ::uint8_t;\n"
+    "using ::uint16_t; using ::uint32_t; using ::uint64_t; }\n";
+const char* kStdIntC =
+    "#pragma once\n"
+    "typedef signed char int8_t; typedef short int16_t; typedef int int32_t; typedef long long int64_t;\n"
+    "typedef unsigned char uint8_t; typedef unsigned short uint16_t; typedef unsigned int uint32_t;\n"
+    "typedef unsigned long long uint64_t;\n";
+const char* kStdDef = "#pragma once\n";
+const char* kCmath = "#pragma once\n";
+
+std::string hexlit(double v) {
+    char b[64];
+    std::snprintf(b, sizeof b, "%a", v);
+    return b;
+}
+
+std::string ints(const int32_t* p, int n) {
+    std::string s;
+    for (int i = 0; i < n; ++i) {
+        if (i) s += ", ";
+        s += std::to_string(p[i]);
+    }
+    return s;
+}
+
+bool all_finite(const std::vector<double>& v) {
+    for (double x : v)
+        if (!(x == x) || x > 1.7e308 || x < -1.7e308) return false;
+    return true;
+}
+
+// The SDE weight of another channel (PS_OP_CHANNEL_WEIGHT: k, p_a, q_1..q_k, (kind, mask, M,
+// Gamma)...) as straight-line code: the momentum sums over each mask written out, the
+// propagator arithmetic from the interpreter's sde_factor.
+std::string channel_weight_source(const Compiled& C, const int32_t* a, int na, bool mixed) {
+    auto imm = [&](int32_t arg) { return C.imm[~arg]; };
+    const int k = static_cast<int>(imm(a[0]));
+    const int32_t out = a[na];
+    std::string s = "                {";
+    if (mixed) s += " const dev::mx::F4 pa = dev::mx::ldp(f, " + std::to_string(a[1]) + "); float acc = 1.0f; int ex = 0;\n";
+    else s += " const dev::P4 pa = dev::ldp(f, " + std::to_string(a[1]) + "); double den = 1.0, P = 1.0;\n";
+    for (int j = 2 + k; j + 3 < na; j += 4) {
+        const int kind = static_cast<int>(imm(a[j]));
+        const int mask = static_cast<int>(imm(a[j + 1]));
+        const double M = imm(a[j + 2]), G = imm(a[j + 3]);
+        s += mixed ? "                  { dev::mx::F4 q = " : "                  { dev::P4 q = ";
+        s += kind == 1 ? "pa;" : (mixed ? "dev::mx::F4{0.0f, 0.0f, 0.0f, 0.0f};" : "dev::P4{0.0, 0.0, 0.0, 0.0};");
+        for (int i = 0; i < k; ++i) {
+            if (!((mask >> i) & 1)) continue;
+            const std::string ld = (mixed ? "dev::mx::ldp(f, " : "dev::ldp(f, ") + std::to_string(a[2 + i]) + ")";
+            if (mixed) s += std::string(" q = dev::mx::") + (kind == 1 ? "f4_sub" : "f4_add") + "(q, " + ld + ");";
+            else s += std::string(" q = dev::") + (kind == 1 ? "p4_sub" : "p4_add") + "(q, " + ld + ");";
+        }
+        if (mixed)
+            s += " dev::mx::sde_factor(acc, ex, q, " + std::to_string(kind) + ", static_cast<float>(" + hexlit(M) +
+                 "), static_cast<float>(" + hexlit(G) + ")); }\n";
+        else
+            s += " dev::sde_factor(den, P, q, " + std::to_string(kind) + ", " + hexlit(M) + ", " + hexlit(G) + "); }\n";
+    }
+    s += mixed ? "                  dev::st(f, " + std::to_string(out) + ", dev::mx::sde_weight(acc, ex)); }\n"
+               : "                  dev::st(f, " + std::to_string(out) + ", P / den); }\n";
+    return s;
+}
+
+}  // namespace
+
+// The CUDA source of a compiled program (all channels, one precision, one block size).
+std::string jit_source(const std::vector<Compiled>& ch, int block, bool mixed) {
+    std::string s;
+    s += "#include \"map_device.cuh\"\n\nnamespace psjit {\nusing namespace ps;\n";
+    s += mixed ? "constexpr bool kMix = true;\n" : "constexpr bool kMix = false;\n";
+    // immediates as constexpr functions of their index: a constant index folds to a literal (an
+    // array would be a device variable, whose loads the compiler cannot fold)
+    for (size_t c = 0; c < ch.size(); ++c) {
+        const Compiled& C = ch[c];
+        s += "struct I" + std::to_string(c) + " {\n    static __forceinline__ constexpr double v(int i) {\n        switch (i) {\n";
+        for (size_t i = 0; i < C.imm.size(); ++i)
+            s += "            case " + std::to_string(i) + ": return " + hexlit(C.imm[i]) + ";\n";
+        s += "            default: return 0.0;\n        }\n    }\n"
+             "    static __forceinline__ constexpr float f(int i) { return static_cast<float>(v(i)); }\n};\n";
+    }
+    s += "struct Events {\n"
+         "    static __device__ __forceinline__ double run(int c, const LaunchParams& lp, const ChannelLaunch& C,\n"
+         "                                                 int64_t ev, int64_t local, bool active, double* s_grid,\n"
+         "                                                 unsigned long long* cut) {\n"
+         "        switch (C.channel) {\n";
+    for (size_t c = 0; c < ch.size(); ++c) {
+        const Compiled& C = ch[c];
+        const std::string cs = std::to_string(c);
+        s += "            case " + cs + ": {\n";
+        s += "                const dev::RegFrame<" + std::to_string(std::max(C.n_slots, 1)) + ", I" + cs + "> f{};\n";
+        s += "                dev::load_inputs(f, lp, " + cs + ", " + std::to_string(C.n_random) + ", ev, local, active);\n";
+        size_t pc = 0;
+        while (pc < C.code.size() && C.code[pc] != kOpOutput) {
+            const int op = C.code[pc], na = C.code[pc + 1], no = C.code[pc + 2];
+            const int32_t* a = C.code.data() + pc + 3;
+            if (op == PS_OP_CHANNEL_WEIGHT) {  // unrolled here: counts, kinds and masks are known now
+                s += channel_weight_source(C, a, na, mixed);
+                pc += 3 + na + no;
+                continue;
+            }
+            s += "                {";
+            s += na ? " constexpr int32_t a[] = {" + ints(a, na) + "};" : " const int32_t* a = nullptr;";
+            s += no ? " constexpr int32_t o[] = {" + ints(a + na, no) + "};" : " const int32_t* o = nullptr;";
+            if (mixed)
+                s += " dev::exec_op_mixed(" + std::to_string(op) + ", a, o, " + std::to_string(na) + ", " +
+                     std::to_string(no) + ", f, reinterpret_cast<const float*>(s_grid), C.vbins, cut, active); }\n";
+            else
+                s += " dev::exec_op(" + std::to_string(op) + ", a, o, " + std::to_string(na) + ", " + std::to_string(no) +
+                     ", f, s_grid, C.vbins, cut, active); }\n";
+            pc += 3 + na + no;
+        }
+        const int n_out = pc + 1 < C.code.size() ? C.code[pc + 1] : 0;
+        s += "                constexpr int32_t od[] = {" + (n_out ? ints(C.code.data() + pc + 3, 2 * n_out) : std::string("0, 0")) + "};\n";
+        s += "                return dev::store_outputs<kMix>(f, od, " + std::to_string(n_out) + ", lp, C, local, active);\n";
+        s += "            }\n";
+    }
+    s += "        }\n        return 0.0;\n    }\n};\n}  // namespace psjit\n\n";
+    s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(block) +
+         ") ps_jit_map(const __grid_constant__ ps::LaunchParams lp) {\n"
+         "    extern __shared__ __align__(16) double smem[];\n"
+         "    ps::dev::CompiledPolicy<psjit::kMix, psjit::Events> pol{lp, smem};\n"
+         "    ps::dev::map_tiles(lp, pol, smem + lp.smem_grid);\n"
+         "}\n";
+    return s;
+}
+
+// NVRTC: source -> cubin for sm_103a (host only, no device needed).
+int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* log) {
+    if (const char* dump = std::getenv("PS_JIT_DUMP")) {  // diagnostic: the generated source
+        if (FILE* fp = std::fopen(dump, "w")) {
+            std::fputs(src.c_str(), fp);
+            std::fclose(fp);
+        }
+    }
+    std::vector<const char*> names, texts;
+    for (int i = 0; i < kJitHeaderCount; ++i) {
+        names.push_back(kJitHeaderNames[i]);
+        texts.push_back(kJitHeaderTexts[i]);
+    }
+    const char* extra_names[] = {"cstdint", "stdint.h", "stddef.h", "cmath"};
+    const char* extra_texts[] = {kStdInt, kStdIntC, kStdDef, kCmath};
+    for (int i = 0; i < 4; ++i) {
+        names.push_back(extra_names[i]);
+        texts.push_back(extra_texts[i]);
+    }
+    nvrtcProgram prog;
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "ps_jit.cu", static_cast<int>(names.size()), texts.data(),
+                                       names.data());
+    if (r != NVRTC_SUCCESS) {
+        *log = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r);
+        return PS_ERR_CUDA;
+    }
+    std::vector<const char*> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
+    if (std::getenv("PS_JIT_PTXAS_VERBOSE")) opts.push_back("--ptxas-options=-v");  // register and spill report in the log
+    r = nvrtcCompileProgram(prog, static_cast<int>(opts.size()), opts.data());
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string lg(n, '\0');
+    if (n) nvrtcGetProgramLog(prog, &lg[0]);
+    *log = lg;
+    if (r != NVRTC_SUCCESS) {
+        nvrtcDestroyProgram(&prog);
+        return PS_ERR_GRAPH;
+    }
+    size_t cn = 0;
+    nvrtcGetCUBINSize(prog, &cn);
+    cubin->resize(cn);
+    nvrtcGetCUBIN(prog, cubin->data());
+    nvrtcDestroyProgram(&prog);
+    return PS_OK;
+}
+
+namespace {
+// ---------------------------------------------------------------- driver API, opened at first use
+typedef int CUresult_t;
+typedef void* CUmodule_t;
+typedef void* CUfunction_t;
+struct Driver {
+    bool ok = false;
+    std::string why;
+    CUresult_t (*moduleLoadData)(CUmodule_t*, const void*) = nullptr;
+    CUresult_t (*moduleGetFunction)(CUfunction_t*, CUmodule_t, const char*) = nullptr;
+    CUresult_t (*launchKernel)(CUfunction_t, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                               void*, void**, void**) = nullptr;
+    CUresult_t (*occupancy)(int*, CUfunction_t, int, size_t) = nullptr;
+    // kernel nodes of a captured graph: the runtime cannot read back a node whose kernel came
+    // from a module loaded through the driver, so the executor reads and updates those here
+    CUresult_t (*nodeGetParams)(void*, CUDA_KERNEL_NODE_PARAMS*) = nullptr;
+    CUresult_t (*execNodeSetParams)(void*, void*, const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
+};
+
+Driver& driver() {
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_LOCAL);
+        if (!h) h = dlopen("libcuda.so", RTLD_NOW | RTLD_LOCAL);
+        if (!h) {
+            d.why = "the CUDA driver library could not be opened";
+            return;
+        }
+        d.moduleLoadData = reinterpret_cast<decltype(d.moduleLoadData)>(dlsym(h, "cuModuleLoadData"));
+        d.moduleGetFunction = reinterpret_cast<decltype(d.moduleGetFunction)>(dlsym(h, "cuModuleGetFunction"));
+        d.launchKernel = reinterpret_cast<decltype(d.launchKernel)>(dlsym(h, "cuLaunchKernel"));
+        d.occupancy = reinterpret_cast<decltype(d.occupancy)>(dlsym(h, "cuOccupancyMaxActiveBlocksPerMultiprocessor"));
+        d.nodeGetParams = reinterpret_cast<decltype(d.nodeGetParams)>(dlsym(h, "cuGraphKernelNodeGetParams_v2"));
+        d.execNodeSetParams =
+            reinterpret_cast<decltype(d.execNodeSetParams)>(dlsym(h, "cuGraphExecKernelNodeSetParams_v2"));
+        d.ok = d.moduleLoadData && d.moduleGetFunction && d.launchKernel && d.occupancy && d.nodeGetParams &&
+               d.execNodeSetParams;
+        if (!d.ok) d.why = "the CUDA driver library lacks a needed entry point";
+    });
+    return d;
+}
+
+std::mutex g_cache_mu;
+std::map<std::pair<int, std::string>, CUfunction_t> g_cache;  // (device, source) -> kernel
+}  // namespace
+
+// Compile (or find in the cache) the program's kernel on the current device.
+int jit_prepare(const std::vector<Compiled>& ch, int block, bool mixed, int device, void** fn, std::string* err) {
+    for (const Compiled& C : ch)
+        if (!all_finite(C.imm)) {
+            *err = "a channel has a non-finite immediate";
+            return PS_ERR_GRAPH;
+        }
+    Driver& d = driver();
+    if (!d.ok) {
+        *err = d.why;
+        return PS_ERR_CUDA;
+    }
+    const std::string src = jit_source(ch, block, mixed);
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    auto key = std::make_pair(device, src);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *fn = it->second;
+        return PS_OK;
+    }
+    std::vector<char> cubin;
+    std::string log;
+    int st = jit_compile(src, &cubin, &log);
+    if (st != PS_OK) {
+        *err = "NVRTC: " + log;
+        return st;
+    }
+    CUmodule_t mod = nullptr;
+    CUfunction_t f = nullptr;
+    if (d.moduleLoadData(&mod, cubin.data()) != 0 || d.moduleGetFunction(&f, mod, "ps_jit_map") != 0) {
+        *err = "loading the compiled module failed";
+        return PS_ERR_CUDA;
+    }
+    g_cache[key] = f;
+    *fn = f;
+    return PS_OK;
+}
+
+int jit_occupancy(void* fn, int block, size_t smem, int* per_sm) {
+    Driver& d = driver();
+    if (!d.ok || d.occupancy(per_sm, fn, block, smem) != 0) return PS_ERR_CUDA;
+    return PS_OK;
+}
+
+int jit_launch(void* fn, const LaunchParams& lp, int grid, size_t smem, void* stream, std::string* err) {
+    if (lp.n_tiles == 0) return PS_OK;
+    Driver& d = driver();
+    void* args[] = {const_cast<LaunchParams*>(&lp)};
+    const int r = d.launchKernel(fn, static_cast<unsigned>(grid), 1, 1, static_cast<unsigned>(lp.block), 1, 1,
+                                 static_cast<unsigned>(smem), stream, args, nullptr);
+    if (r != 0) {
+        *err = "compiled kernel launch failed (driver error " + std::to_string(r) + ")";
+        return PS_ERR_CUDA;
+    }
+    count_launches(1);
+    return PS_OK;
+}
+
+bool jit_node_runs(void* node, void* fn) {
+    Driver& d = driver();
+    if (!d.ok || !fn) return false;
+    CUDA_KERNEL_NODE_PARAMS kp;
+    std::memset(&kp, 0, sizeof(kp));
+    return d.nodeGetParams(node, &kp) == 0 && static_cast<void*>(kp.func) == fn;
+}
+
+int jit_node_set(void* exec, void* node, void* fn, const LaunchParams& lp, int grid, size_t smem, std::string* err) {
+    Driver& d = driver();
+    if (!d.ok) {
+        *err = d.why;
+        return PS_ERR_CUDA;
+    }
+    CUDA_KERNEL_NODE_PARAMS kp;
+    std::memset(&kp, 0, sizeof(kp));
+    void* args[] = {const_cast<LaunchParams*>(&lp)};
+    kp.func = static_cast<CUfunction>(fn);
+    kp.gridDimX = static_cast<unsigned>(grid);
+    kp.gridDimY = kp.gridDimZ = 1;
+    kp.blockDimX = static_cast<unsigned>(lp.block);
+    kp.blockDimY = kp.blockDimZ = 1;
+    kp.sharedMemBytes = static_cast<unsigned>(smem);
+    kp.kernelParams = args;  // copied by the call
+    const int r = d.execNodeSetParams(exec, node, &kp);
+    if (r != 0) {
+        *err = "updating the compiled kernel's graph node failed (driver error " + std::to_string(r) + ")";
+        return PS_ERR_CUDA;
+    }
+    return PS_OK;
+}
+
+}  // namespace ps

@@ -1,0 +1,1088 @@
+// map_device.cuh -- device code of the phase-space interpreter: the invariant maps, decays and
+// 2->2 blocks (FP64 and mixed forms), the slot-file frame and the op implementations.  Included
+// by kernels.cu, and compiled at run time together with a channel's generated instruction list
+// (jit.cpp), so it includes only headers that NVRTC can also read.
+#pragma once
+
+#include "kin.cuh"
+#include "launch_params.h"
+#include "philox.cuh"
+#include "ps.h"
+
+namespace ps {
+namespace dev {
+
+using rng::philox4x32_10;
+using rng::unit_from_bits;
+
+// ---------------------------------------------------------------- invariant maps (Sec. 2.2.1)
+// Power law G_nu / log map, anchored at x_min for nu <= 1 and at m^2 for nu > 1, so that
+// 1 + z >= 1 and x - m^2 (and, for nu <= 1, x - x_min) keep full precision:
+//   L = log1p((x_max - x_min)/lo), lo = x_min - m^2, hi = x_max - m^2, w = 1 - nu
+//   nu == 1: x = x_min + lo expm1(r L),              J = (x - m^2) L
+//   nu <  1: z = r expm1(w L),  x = x_min + lo expm1(log1p(z)/w),  J = (x - m^2) rho/(w (1+z))
+//   nu >  1: z = (1-r) expm1(-w L), x - m^2 = hi exp(log1p(z)/w), J = -(x - m^2) rho'/(w (1+z))
+__device__ __forceinline__ bool map_nu(double r, double m, double nu, double xmin, double xmax, double a,
+                                       double& x, double& jac) {
+    double m2 = pos_bits(m) ? m * m : -a;
+    double lo = xmin - m2, hi = xmax - m2;
+    bool ok = pos_bits(lo) && ge_pos_bits(hi, lo);
+    double L = log1p((xmax - xmin) / lo);
+    if (dbits(nu) == dbits(1.0)) {
+        double e = expm1(r * L);
+        double xm = fma(lo, e, lo);
+        x = fma(lo, e, xmin);
+        jac = xm * L;
+    } else if (dbits(nu) < dbits(1.0)) {  // nu < 1 (nu is never NaN)
+        double w = 1.0 - nu;
+        double rho = expm1(w * L);
+        double z = r * rho;
+        double e = expm1(log1p(z) / w);
+        double xm = fma(lo, e, lo);
+        x = fma(lo, e, xmin);
+        jac = xm * rho / (w * (1.0 + z));
+    } else {
+        double w = 1.0 - nu;
+        double rho = expm1(-w * L);
+        double z = (1.0 - r) * rho;
+        double xm = hi * exp(log1p(z) / w);
+        x = m2 + xm;
+        jac = -xm * rho / (w * (1.0 + z));
+    }
+    x = clamp_nonneg(x, xmin, xmax);  // the map lands in [x_min, x_max] (rounding at the ends)
+    if (!ok) { x = xmin; jac = 0.0; }
+    return ok;
+}
+
+// Breit-Wigner G_BW with a = tan u1, b = tan u2, D = atan2(b - a, 1 + ab), u = u1 + D r.
+// One tan per event, argument and combination chosen by selects:
+//   u < -pi/4: T = tan(D r),     x = x_min + mG T(1+a^2)/(1-aT), 1+tan^2u = (1+a^2)(1+T^2)/(1-aT)^2
+//   u >  pi/4: T = tan(D (1-r)), tan u = (b-T)/(1+bT), 1+tan^2u = (1+b^2)(1+T^2)/(1+bT)^2
+//   otherwise: T = tan(u).        J = D mG (1 + tan^2 u)
+// u1 = atan(a) may come in as the channel's constant (x_min immediate); have_u1 selects it.
+__device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin, double xmax,
+                                       double& x, double& jac, bool have_u1 = false, double u1 = 0.0) {
+    double mg = M * G, m2 = M * M;
+    bool ok = pos_bits(mg) && ge_pos_bits(xmax, xmin);  // x_min >= 0 here (a squared mass)
+    double inv_mg = 1.0 / mg;
+    double a = (xmin - m2) * inv_mg, b = (xmax - m2) * inv_mg;
+    double D = atan2((xmax - xmin) * inv_mg, fma(a, b, 1.0));
+    double u = (have_u1 ? u1 : atan(a)) + D * r;
+    bool low = below_neg_bits(u, 0.25 * kPi), high = above_pos_bits(u, 0.25 * kPi);
+    double arg = low ? D * r : (high ? D * (1.0 - r) : u);
+    double T = tan(arg);
+    double sec2;
+    if (low) {
+        double den = 1.0 - a * T;
+        double rd = 1.0 / den;
+        x = xmin + mg * (T * (1.0 + a * a) * rd);
+        sec2 = (1.0 + a * a) * (1.0 + T * T) * (rd * rd);
+    } else if (high) {
+        double den = 1.0 + b * T;
+        double rd = 1.0 / den;
+        x = m2 + mg * ((b - T) * rd);
+        sec2 = (1.0 + b * b) * (1.0 + T * T) * (rd * rd);
+    } else {
+        x = m2 + mg * T;
+        sec2 = 1.0 + T * T;
+    }
+    jac = D * mg * sec2;
+    x = clamp_nonneg(x, xmin, xmax);
+    if (!ok) { x = xmin; jac = 0.0; }
+    return ok;
+}
+
+// 2->2 block in (phi, t), Sec. 2.2.4: the polar axis is the direction of pA in the rest
+// frame of p0 = pA + pB; cos(theta) from |t| via 1 -+ cos = (|t| - |t|_min)/B resp.
+// (|t|_max - |t|)/B, whichever is smaller; the momentum is rotated by R(phi_A, theta_A)
+// = Rz(phi_A) Ry(theta_A) (Sec. 2.2.6) and boosted back.
+__device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double tabs, double m1, double m2,
+                                             double s, double mA2, double mB2, P4& p1, P4& p2) {
+    P4 p0 = p4_add(pA, pB);
+    const double inv_s = 1.0 / s;
+    double m0 = sqrt(s);
+    const BoostFrame bf = boost_frame(p0, m0, m0 * inv_s);  // 1/m0 = m0/s
+    P4 a = boost_in(pA, bf);
+    double pt2 = a.x * a.x + a.y * a.y;
+    bool has_pt = pos_bits(pt2);
+    double ipt = has_pt ? rsqrt(pt2) : 0.0;
+    double pt = pt2 * ipt;
+    double rp = rsqrt(pt2 + a.z * a.z);
+    double ca = a.z * rp, sa = pt * rp;
+    double cpa = has_pt ? a.x * ipt : 1.0, spa = has_pt ? a.y * ipt : 0.0;
+
+    double tlo, thi, B;
+    t_range(s, mA2, mB2, m1, m2, tlo, thi, B);
+    double dlo = tabs - tlo, dhi = thi - tabs;
+    bool near_lo = dlo <= dhi;
+    double iB = (B > 0.0) ? 1.0 / B : 0.0;
+    double first = (near_lo ? dlo : dhi) * iB;  // 1 - cos (near_lo) or 1 + cos
+    double omc = (B > 0.0) ? (near_lo ? first : 2.0 - first) : 1.0;
+    double opc = (B > 0.0) ? (near_lo ? 2.0 - first : first) : 1.0;
+    double cth = (omc <= opc) ? 1.0 - omc : opc - 1.0;
+    double sth = sqrt(fmax(omc * opc, 0.0));
+    double sph, cph;
+    sincospi(2.0 * rphi, &sph, &cph);
+
+    double m12 = m1 * m1, m22 = m2 * m2;
+    double i2m0 = 0.5 * bf.inv_m;
+    double pabs = sqrt(kallen(s, m12, m22)) * i2m0;
+    double e1 = (s + m12 - m22) * i2m0, e2 = (s + m22 - m12) * i2m0;
+    double vx = pabs * sth * cph, vy = pabs * sth * sph, vz = pabs * cth;
+    // Ry(theta_A) then Rz(phi_A)
+    double rx = ca * vx + sa * vz, rz = -sa * vx + ca * vz;
+    P4 q1 = {e1, cpa * rx - spa * vy, spa * rx + cpa * vy, rz};
+    P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
+    p1 = boost_out(q1, bf);
+    p2 = boost_out(q2, bf);
+    return 0.5 * kPi * rsqrt(kallen(s, mA2, mB2));
+}
+
+// 1->2 decay in (phi, theta), Sec. 2.2.3: cos = 2 r_theta - 1, sin = 2 sqrt(r_theta (1 - r_theta)),
+// phi = 2 pi r_phi, built at rest and optionally boosted to the frame of p0.
+template <bool kBoost>
+__device__ __forceinline__ double two_body(double rphi, double rth, double s0, double m1, double m2, P4 p0,
+                                           P4& p1, P4& p2) {
+    double m0 = sqrt(s0);
+    const double inv_s0 = 1.0 / s0;
+    const double inv_m0 = m0 * inv_s0;  // 1/m0 = m0/s0: one division per decay
+    double m12 = m1 * m1, m22 = m2 * m2;
+    // sqrt(lambda) = s0 exactly for two massless daughters
+    double sl = (zero_bits(m12) && zero_bits(m22)) ? s0 : sqrt(kallen(s0, m12, m22));
+    double i2m0 = 0.5 * inv_m0;
+    double pabs = sl * i2m0;
+    double e1 = (s0 + m12 - m22) * i2m0, e2 = (s0 + m22 - m12) * i2m0;
+    double cth = 2.0 * rth - 1.0;
+    double sth = 2.0 * sqrt(rth * (1.0 - rth));
+    double sph, cph;
+    sincospi(2.0 * rphi, &sph, &cph);
+    P4 q1 = {e1, pabs * sth * cph, pabs * sth * sph, pabs * cth};
+    P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
+    if (kBoost) {
+        const BoostFrame bf = boost_frame(p0, m0, inv_m0);
+        p1 = boost_out(q1, bf);
+        p2 = boost_out(q2, bf);
+    } else {
+        p1 = q1;
+        p2 = q2;
+    }
+    return 0.5 * kPi * sl * inv_s0;
+}
+
+// ---------------------------------------------------------------- interpreter
+struct Frame {
+    static constexpr bool kStatic = false;  // slots addressed at run time
+    double* S;            // slot file base for this thread: slot k at S[k * block]
+    const double* imm;    // channel immediates (shared memory)
+    int block;
+    const float* immf;    // the immediates rounded to float (mixed kernel only)
+};
+
+__device__ __forceinline__ double ld(const Frame& f, int a) { return a >= 0 ? f.S[a * f.block] : f.imm[~a]; }
+__device__ __forceinline__ void st(const Frame& f, int slot, double v) { f.S[slot * f.block] = v; }
+__device__ __forceinline__ P4 ldp(const Frame& f, int a) {
+    const double* q = f.S + a * f.block;
+    return {q[0], q[f.block], q[2 * f.block], q[3 * f.block]};
+}
+__device__ __forceinline__ void stp(const Frame& f, int slot, P4 p) {
+    double* q = f.S + slot * f.block;
+    q[0] = p.e;
+    q[f.block] = p.x;
+    q[2 * f.block] = p.y;
+    q[3 * f.block] = p.z;
+}
+
+// Loops of an op over its arguments.  For a register frame, whose slots must be indexed by
+// constants, the loop is fully unrolled: its bounds are constants once the generated instruction
+// list is inlined.  The shared-memory frame keeps a plain loop.
+template <class Fr, class F>
+__device__ __forceinline__ void op_loop(int b, int e, int step, F&& body) {
+    if constexpr (Fr::kStatic) {
+#pragma unroll
+        for (int j = b; j < e; j += step) body(j);
+    } else {
+        for (int j = b; j < e; j += step) body(j);
+    }
+}
+// body(i) for every set bit i < nbits of mask
+template <class Fr, class F>
+__device__ __forceinline__ void op_bits(int mask, int nbits, F&& body) {
+    if constexpr (Fr::kStatic) {
+#pragma unroll
+        for (int i = 0; i < nbits; ++i)
+            if ((mask >> i) & 1) body(i);
+    } else {
+        while (mask) {
+            const int i = __ffs(mask) - 1;
+            mask &= mask - 1;
+            body(i);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- register frame
+// A compiled channel (jit.cpp) keeps its slot file in registers: RegFrame<NS, Imm> holds NS slots
+// and reads immediates from the compile-time functions Imm::v(i), Imm::f(i).  Every access is
+// by a constant index once the generated instruction list is inlined, so the array lives in
+// registers.  Mixed-precision momenta are held as the doubles of their float components.
+template <int NS, class Imm>
+struct RegFrame {
+    static constexpr bool kStatic = true;
+    mutable double v[NS > 0 ? NS : 1];
+};
+template <int NS, class Imm>
+__device__ __forceinline__ double ld(const RegFrame<NS, Imm>& f, int a) { return a >= 0 ? f.v[a] : Imm::v(~a); }
+template <int NS, class Imm>
+__device__ __forceinline__ void st(const RegFrame<NS, Imm>& f, int slot, double x) { f.v[slot] = x; }
+template <int NS, class Imm>
+__device__ __forceinline__ P4 ldp(const RegFrame<NS, Imm>& f, int a) { return {f.v[a], f.v[a + 1], f.v[a + 2], f.v[a + 3]}; }
+template <int NS, class Imm>
+__device__ __forceinline__ void stp(const RegFrame<NS, Imm>& f, int slot, P4 p) {
+    f.v[slot] = p.e;
+    f.v[slot + 1] = p.x;
+    f.v[slot + 2] = p.y;
+    f.v[slot + 3] = p.z;
+}
+// Small integers held as immediates (counts, kinds, masks): decoded from their bits for the
+// shared-memory frame (integer ALU), by a conversion for a register frame, where they are
+// compile-time constants that the conversion folds away (the bit decode would stay opaque).
+template <class Fr>
+__device__ __forceinline__ int op_int(double v) {
+    if constexpr (Fr::kStatic) return static_cast<int>(v);
+    else return small_int(v);
+}
+
+// One propagator denominator of an SDE channel weight (Sec. 2.1): kind 1 a t-channel 1/(t - M^2)^2,
+// kind 0 an s-channel 1/((s - M^2)^2 + M^2 Gamma^2); the product is kept in range by dividing
+// it out into P.  P_j = P / den at the end.
+__device__ __forceinline__ void sde_factor(double& den, double& P, const P4& q, int kind, double M, double G) {
+    const double d = p4_sq(q) - M * M, mg = M * G;
+    den *= (kind == 1) ? d * d : fma(d, d, mg * mg);
+    if (above_pos_bits(den, 1e200)) {  // keep the running product in range
+        P /= den;
+        den = 1.0;
+    }
+}
+
+// One instruction of the FP64 interpreter on frame Fr (the shared-memory slot file of the
+// interpreter kernel, or the register frame of a compiled channel).
+template <class Fr>
+__device__ __forceinline__ void exec_op(const int op, const int32_t* a, const int32_t* o, const int na, const int no,
+                                        const Fr& f, const double* grid, int vbins, unsigned long long* cut_count,
+                                        bool active) {
+        switch (op) {
+            case PS_OP_VEGAS: {
+                double jac = 1.0;
+                const double nb = static_cast<double>(vbins);
+                op_loop<Fr>(0, na, 1, [&](int j) {
+                    double r = ld(f, a[j]);
+                    double rn = r * nb;
+                    int k = min(static_cast<int>(rn), vbins - 1);
+                    k = max(k, 0);
+                    const double* e = grid + j * (vbins + 1);
+                    double e0 = e[k], wdt = e[k + 1] - e0;
+                    st(f, o[j], fma(rn - static_cast<double>(k), wdt, e0));
+                    jac *= nb * wdt;
+                });
+                st(f, o[na], jac);
+                break;
+            }
+            case PS_OP_INVARIANT_NU: {
+                double x, j;
+                map_nu(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), ld(f, a[5]), x, j);
+                st(f, o[0], x);
+                st(f, o[1], j);
+                break;
+            }
+            case PS_OP_INVARIANT_BW: {
+                double x, j;
+                map_bw(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), x, j, na > 5,
+                       na > 5 ? ld(f, a[5]) : 0.0);
+                st(f, o[0], x);
+                st(f, o[1], j);
+                break;
+            }
+            case PS_OP_R_TO_X1X2: {
+                double r = ld(f, a[0]), shat = ld(f, a[1]), S = ld(f, a[2]);
+                double L = log(shat / S);
+                const double l1 = r * L, l2 = (1.0 - r) * L;  // log x1, log x2
+                st(f, o[0], exp(l1));
+                st(f, o[1], exp(l2));
+                st(f, o[2], -L / S);
+                if (no > 3) {
+                    st(f, o[3], l1);
+                    st(f, o[4], l2);
+                }
+                break;
+            }
+            case PS_OP_COM_P_IN: {
+                double h = 0.5 * ld(f, a[0]);
+                stp(f, o[0], P4{h, 0.0, 0.0, h});
+                stp(f, o[1], P4{h, 0.0, 0.0, -h});
+                break;
+            }
+            case PS_OP_T_INV_MIN_MAX: {
+                double lo, hi, B;
+                t_range(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), lo, hi, B);
+                st(f, o[0], lo);
+                st(f, o[1], hi);
+                break;
+            }
+            case PS_OP_TWO_TO_TWO_COM: {
+                P4 p1, p2;
+                double j = two_to_two(ld(f, a[0]), ldp(f, a[1]), ldp(f, a[2]), ld(f, a[3]), ld(f, a[4]),
+                                      ld(f, a[5]), ld(f, a[6]), ld(f, a[7]), ld(f, a[8]), p1, p2);
+                stp(f, o[0], p1);
+                stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_TWO_BODY_DECAY: {
+                P4 p1, p2;
+                double j = two_body<true>(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]),
+                                          ldp(f, a[5]), p1, p2);
+                stp(f, o[0], p1);
+                stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_TWO_BODY_DECAY_COM: {
+                P4 p1, p2;
+                double j = two_body<false>(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]),
+                                           P4{0, 0, 0, 0}, p1, p2);
+                stp(f, o[0], p1);
+                stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_BOOST_BEAM: {
+                // light-cone form of the longitudinal boost: E+p_z scales by rho = sqrt(x1/x2),
+                // E-p_z by 1/rho (no cancellation for extreme boosts)
+                double x1 = ld(f, a[na - 2]), x2 = ld(f, a[na - 1]);
+                const double t = rsqrt(x1 * x2);  // rho = sqrt(x1/x2) = x1 t, 1/rho = x2 t
+                double rho = x1 * t;
+                double irho = x2 * t;
+                op_loop<Fr>(0, na - 2, 1, [&](int k) {
+                    P4 p = ldp(f, a[k]);
+                    double plus = rho * (p.e + p.z), minus = (p.e - p.z) * irho;
+                    stp(f, o[k], P4{0.5 * (plus + minus), p.x, p.y, 0.5 * (plus - minus)});
+                });
+                break;
+            }
+            case PS_OP_REDUCE_PRODUCT: {
+                double v = ld(f, a[0]);
+                op_loop<Fr>(1, na, 1, [&](int k) { v *= ld(f, a[k]); });
+                st(f, o[0], v);
+                break;
+            }
+            case PS_OP_CUT_UNPHYSICAL: {
+                double w = ld(f, a[0]), x1 = ld(f, a[1]), x2 = ld(f, a[2]);
+                bool bad = !finite_bits(w) || !(in_unit_bits(x1) && in_unit_bits(x2));
+                op_loop<Fr>(3, na, 1, [&](int k) {
+                    P4 p = ldp(f, a[k]);
+                    bad |= !(finite_bits(p.e) && finite_bits(p.x) && finite_bits(p.y) && finite_bits(p.z));
+                });
+                if (bad && active) atomicAdd(cut_count, 1ULL);
+                st(f, o[0], bad ? 0.0 : w);
+                break;
+            }
+            case PS_OP_ADD: st(f, o[0], ld(f, a[0]) + ld(f, a[1])); break;
+            case PS_OP_SUB: st(f, o[0], ld(f, a[0]) - ld(f, a[1])); break;
+            case PS_OP_MUL: st(f, o[0], ld(f, a[0]) * ld(f, a[1])); break;
+            case PS_OP_DIV: st(f, o[0], ld(f, a[0]) / ld(f, a[1])); break;
+            case PS_OP_SQRT: st(f, o[0], sqrt(ld(f, a[0]))); break;
+            case PS_OP_SQUARE: { double v = ld(f, a[0]); st(f, o[0], v * v); break; }
+            case PS_OP_MAX: st(f, o[0], fmax(ld(f, a[0]), ld(f, a[1]))); break;
+            case PS_OP_MOM_ADD: stp(f, o[0], p4_add(ldp(f, a[0]), ldp(f, a[1]))); break;
+            case PS_OP_MOM_SUB: stp(f, o[0], p4_sub(ldp(f, a[0]), ldp(f, a[1]))); break;
+            case PS_OP_PDF_POWER: {
+                double x = ld(f, a[0]), al = ld(f, a[1]), be = ld(f, a[2]);
+                double fx = exp(al * (na > 3 ? ld(f, a[3]) : log(x)));
+                double y = 1.0 - x;
+                double fy;
+                if (be == 3.0) fy = y * y * y;
+                else if (be == 2.0) fy = y * y;
+                else if (be == 1.0) fy = y;
+                else if (be == 0.0) fy = 1.0;
+                else fy = pow(y, be);
+                st(f, o[0], fx * fy);
+                break;
+            }
+            case PS_OP_PROPAGATOR: {
+                double s = ld(f, a[0]), M = ld(f, a[1]), G = ld(f, a[2]);
+                double d = s - M * M;
+                st(f, o[0], 1.0 / (d * d + M * M * G * G));
+                break;
+            }
+            case PS_OP_ONE_PLUS_COS2: {
+                P4 p = ldp(f, a[0]);
+                double c2 = p.z * p.z / (p.x * p.x + p.y * p.y + p.z * p.z);
+                st(f, o[0], 1.0 + c2);
+                break;
+            }
+            case PS_OP_CHANNEL_WEIGHT: {
+                // P_j = 1 / prod(denominators): one division per channel; kind and mask decoded
+                // from their bits, the momentum sum over the set bits of the mask only
+                const int k = op_int<Fr>(ld(f, a[0]));
+                const P4 pa = ldp(f, a[1]);
+                double den = 1.0, P = 1.0;
+                op_loop<Fr>(2 + k, na - 3, 4, [&](int j) {
+                    const int kind = op_int<Fr>(ld(f, a[j]));
+                    const int mask = op_int<Fr>(ld(f, a[j + 1]));
+                    const double M = ld(f, a[j + 2]), G = ld(f, a[j + 3]);
+                    P4 q = (kind == 1) ? pa : P4{0.0, 0.0, 0.0, 0.0};
+                    op_bits<Fr>(mask, k, [&](int i) {
+                        q = (kind == 1) ? p4_sub(q, ldp(f, a[2 + i])) : p4_add(q, ldp(f, a[2 + i]));
+                    });
+                    sde_factor(den, P, q, kind, M, G);
+                });
+                st(f, o[0], P / den);
+                break;
+            }
+            default: break;
+        }
+}
+
+// Executes one channel's instruction list for the calling thread's event.
+__device__ void run_code(const int32_t* code, int len, const Frame& f, const double* grid, int vbins,
+                         unsigned long long* cut_count, bool active) {
+    int pc = 0;
+    while (pc < len) {
+        const int op = code[pc], na = code[pc + 1], no = code[pc + 2];
+        const int32_t* a = code + pc + 3;
+        exec_op(op, a, a + na, na, no, f, grid, vbins, cut_count, active);
+        pc += 3 + na + no;
+    }
+}
+
+
+// ================================================================ mixed precision
+// PS_PRECISION_MIXED: bulk kinematics in FP32 (momenta are carried as float in the slot file,
+// angles, boosts, rotations, transcendentals of the maps, parton densities), FP64 kept for the
+// islands that are sensitive to cancellation: invariant assembly x = x_min + lo e and s - m^2,
+// the Kallen function at threshold, the t range and 1 - cos(theta) for small |t|, the s-order
+// bounds, and every Jacobian product.  Scalars stay FP64 in the slot file.
+namespace mx {
+
+struct F4 {
+    float e, x, y, z;
+};
+
+__device__ __forceinline__ F4 f4_add(F4 a, F4 b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ F4 f4_sub(F4 a, F4 b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
+
+// float momentum in 4 consecutive slots (low half of each 8-byte slot)
+__device__ __forceinline__ F4 ldp(const Frame& f, int a) {
+    const float* q = reinterpret_cast<const float*>(f.S + a * f.block);
+    const int st = 2 * f.block;
+    return {q[0], q[st], q[2 * st], q[3 * st]};
+}
+__device__ __forceinline__ void stp(const Frame& f, int slot, F4 p) {
+    float* q = reinterpret_cast<float*>(f.S + slot * f.block);
+    const int st = 2 * f.block;
+    q[0] = p.e;
+    q[st] = p.x;
+    q[2 * st] = p.y;
+    q[3 * st] = p.z;
+}
+// immediates come from their float copy: no FP64-pipe conversion per read
+__device__ __forceinline__ float ldf(const Frame& f, int a) {
+    return a >= 0 ? static_cast<float>(f.S[a * f.block]) : f.immf[~a];
+}
+
+// sqrt in FP64 from a float reciprocal-square-root seed and one Newton step in FP64:
+// s = x r, e = x - s^2, s += e r/2 (relative error ~ 1.5 delta^2 for a seed error delta).
+__device__ __forceinline__ double sqrt64(double x) {
+    if (!pos_bits(x)) return 0.0;
+    double r = static_cast<double>(rsqrtf(static_cast<float>(x)));
+    double s = x * r;
+    double e = fma(-s, s, x);
+    return fma(e, 0.5 * r, s);
+}
+
+// 1/x in FP64 from a float reciprocal seed and one Newton step.
+__device__ __forceinline__ double rcp64(double x) {
+    double r = static_cast<double>(__frcp_rn(static_cast<float>(x)));
+    double e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+__device__ __forceinline__ double kallen64(double x, double y, double z) {
+    double l;
+    if (zero_bits(y) && zero_bits(z)) {
+        l = x * x;
+    } else if (nonneg_bits(y) && nonneg_bits(z)) {
+        double ry = sqrt64(y), rz = sqrt64(z);
+        double hi = ry + rz, lo = ry - rz;
+        l = (x - hi * hi) * (x - lo * lo);
+    } else if (nonpos_bits(y) && nonpos_bits(z)) {
+        double d = z - y;
+        l = x * x - 2.0 * x * (y + z) + d * d;
+    } else {
+        double d = x - y - z;
+        l = d * d - 4.0 * y * z;
+    }
+    return pos_bits(l) ? l : 0.0;
+}
+
+__device__ __forceinline__ F4 boost_out(F4 p, F4 q, float mq) {
+    float qp = q.x * p.x + q.y * p.y + q.z * p.z;
+    float inv = 1.0f / mq;
+    float c = qp / (mq * (q.e + mq)) + p.e * inv;
+    return {(q.e * p.e + qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
+}
+__device__ __forceinline__ F4 boost_in(F4 p, F4 q, float mq) {
+    float qp = q.x * p.x + q.y * p.y + q.z * p.z;
+    float inv = 1.0f / mq;
+    float c = qp / (mq * (q.e + mq)) - p.e * inv;
+    return {(q.e * p.e - qp) * inv, p.x + q.x * c, p.y + q.y * c, p.z + q.z * c};
+}
+
+// power law / log map: transcendentals in float, x = x_min + lo e assembled in FP64
+__device__ __forceinline__ void map_nu(float r, double m, double nu, double xmin, double xmax, double a,
+                                       double& x, double& jac) {
+    double m2 = pos_bits(m) ? m * m : -a;
+    double lo = xmin - m2, hi = xmax - m2;
+    bool ok = pos_bits(lo) && ge_pos_bits(hi, lo);
+    float L = log1pf(static_cast<float>(xmax - xmin) / static_cast<float>(lo));
+    float e, jf;
+    if (dbits(nu) == dbits(1.0)) {
+        e = expm1f(r * L);
+        jf = (1.0f + e) * L;
+        x = fma(lo, static_cast<double>(e), xmin);
+        jac = lo * static_cast<double>(jf);
+    } else if (dbits(nu) < dbits(1.0)) {  // nu < 1 (nu is never NaN)
+        float w = static_cast<float>(1.0 - nu);
+        float rho = expm1f(w * L);
+        float z = r * rho;
+        e = expm1f(log1pf(z) / w);
+        jf = (1.0f + e) * rho / (w * (1.0f + z));
+        x = fma(lo, static_cast<double>(e), xmin);
+        jac = lo * static_cast<double>(jf);
+    } else {
+        float w = static_cast<float>(1.0 - nu);
+        float rho = expm1f(-w * L);
+        float z = (1.0f - r) * rho;
+        float g = expf(log1pf(z) / w);
+        double xm = hi * static_cast<double>(g);
+        x = m2 + xm;
+        jac = -xm * static_cast<double>(rho / (w * (1.0f + z)));
+    }
+    x = clamp_nonneg(x, xmin, xmax);
+    if (!ok) { x = xmin; jac = 0.0; }
+}
+
+// Breit-Wigner: angles and tan in float (same endpoint-relative branches as the FP64 form),
+// s - m^2 and the assembly of x in FP64
+__device__ __forceinline__ void map_bw(float r, double M, double G, double xmin, double xmax, double& x, double& jac,
+                                       bool have_u1 = false, double u1 = 0.0) {
+    double mg = M * G, m2 = M * M;
+    bool ok = pos_bits(mg) && ge_pos_bits(xmax, xmin);  // x_min >= 0 here (a squared mass)
+    float mgf = static_cast<float>(mg);
+    float imgf = 1.0f / mgf;
+    float a = static_cast<float>(xmin - m2) * imgf, b = static_cast<float>(xmax - m2) * imgf;
+    float D = atan2f(static_cast<float>(xmax - xmin) * imgf, fmaf(a, b, 1.0f));
+    float u = (have_u1 ? static_cast<float>(u1) : atanf(a)) + D * r;
+    bool low = u < -0.785398163f, high = u > 0.785398163f;
+    float arg = low ? D * r : (high ? D * (1.0f - r) : u);
+    float T = tanf(arg);
+    float sec2;
+    if (low) {
+        float rd = 1.0f / (1.0f - a * T);
+        x = xmin + static_cast<double>(mgf * (T * (1.0f + a * a) * rd));
+        sec2 = (1.0f + a * a) * (1.0f + T * T) * (rd * rd);
+    } else if (high) {
+        float rd = 1.0f / (1.0f + b * T);
+        x = m2 + static_cast<double>(mgf * ((b - T) * rd));
+        sec2 = (1.0f + b * b) * (1.0f + T * T) * (rd * rd);
+    } else {
+        x = m2 + static_cast<double>(mgf * T);
+        sec2 = 1.0f + T * T;
+    }
+    jac = static_cast<double>(D * mgf * sec2);
+    x = clamp_nonneg(x, xmin, xmax);
+    if (!ok) { x = xmin; jac = 0.0; }
+}
+
+// t range: FP64 island (small |t|), with the fast sqrt/reciprocal
+__device__ __forceinline__ void t_range(double s, double mA2, double mB2, double m1, double m2, double& tabs_min,
+                                        double& tabs_max, double& B) {
+    double m12 = m1 * m1, m22 = m2 * m2;
+    double is = rcp64(s);
+    double A = mA2 + m12 - 0.5 * (s + mA2 - mB2) * (s + m12 - m22) * is;
+    B = 0.5 * sqrt64(kallen64(s, mA2, mB2) * kallen64(s, m12, m22)) * is;
+    double prod = (m12 - mA2) * (m22 - mB2) + (m12 * mB2 - m22 * mA2) * (m12 - m22 - mA2 + mB2) * is;
+    double big = (A <= 0.0) ? A - B : A + B;
+    double small = (big != 0.0) ? prod * rcp64(big) : 0.0;
+    tabs_min = -((A <= 0.0) ? small : big);
+    tabs_max = -((A <= 0.0) ? big : small);
+}
+
+__device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double tabs, double m1, double m2, double s,
+                                             double mA2, double mB2, F4& p1, F4& p2) {
+    F4 p0 = f4_add(pA, pB);
+    float m0 = static_cast<float>(sqrt64(s));
+    F4 a = boost_in(pA, p0, m0);
+    float pt = sqrtf(a.x * a.x + a.y * a.y);
+    float rp = rsqrtf(pt * pt + a.z * a.z);
+    float ca = a.z * rp, sa = pt * rp;
+    bool has_pt = pt > 0.0f;
+    float ipt = has_pt ? 1.0f / pt : 0.0f;
+    float cpa = has_pt ? a.x * ipt : 1.0f, spa = has_pt ? a.y * ipt : 0.0f;
+    double tlo, thi, B;
+    t_range(s, mA2, mB2, m1, m2, tlo, thi, B);
+    double dlo = tabs - tlo, dhi = thi - tabs;
+    bool near_lo = dlo <= dhi;
+    double first = (B > 0.0) ? (near_lo ? dlo : dhi) * rcp64(B) : 1.0;  // 1 - cos or 1 + cos (FP64)
+    float f1 = static_cast<float>(first);
+    float omc = (B > 0.0) ? (near_lo ? f1 : 2.0f - f1) : 1.0f;
+    float opc = (B > 0.0) ? (near_lo ? 2.0f - f1 : f1) : 1.0f;
+    float cth = (omc <= opc) ? 1.0f - omc : opc - 1.0f;
+    float sth = sqrtf(fmaxf(omc * opc, 0.0f));
+    float sph, cph;
+    sincospif(2.0f * rphi, &sph, &cph);
+    double m12 = m1 * m1, m22 = m2 * m2;
+    float i2m0 = 0.5f / m0;
+    float pabs = static_cast<float>(sqrt64(kallen64(s, m12, m22))) * i2m0;
+    float e1 = static_cast<float>(s + m12 - m22) * i2m0, e2 = static_cast<float>(s + m22 - m12) * i2m0;
+    float vx = pabs * sth * cph, vy = pabs * sth * sph, vz = pabs * cth;
+    float rx = ca * vx + sa * vz, rz = -sa * vx + ca * vz;
+    F4 q1 = {e1, cpa * rx - spa * vy, spa * rx + cpa * vy, rz};
+    F4 q2 = {e2, -q1.x, -q1.y, -q1.z};
+    p1 = boost_out(q1, p0, m0);
+    p2 = boost_out(q2, p0, m0);
+    return 0.5 * kPi * rcp64(sqrt64(kallen64(s, mA2, mB2)));
+}
+
+template <bool kBoost>
+__device__ __forceinline__ double two_body(float rphi, float rth, double s0, double m1, double m2, F4 p0, F4& p1,
+                                           F4& p2) {
+    double m12 = m1 * m1, m22 = m2 * m2;
+    double lam = kallen64(s0, m12, m22);                   // FP64 island at threshold
+    float sl = sqrtf(static_cast<float>(lam));
+    float m0 = sqrtf(static_cast<float>(s0));
+    float i2m0 = 0.5f / m0;
+    float pabs = sl * i2m0;
+    float e1 = static_cast<float>(s0 + m12 - m22) * i2m0, e2 = static_cast<float>(s0 + m22 - m12) * i2m0;
+    float cth = 2.0f * rth - 1.0f;
+    float sth = 2.0f * sqrtf(rth * (1.0f - rth));
+    float sph, cph;
+    sincospif(2.0f * rphi, &sph, &cph);
+    F4 q1 = {e1, pabs * sth * cph, pabs * sth * sph, pabs * cth};
+    F4 q2 = {e2, -q1.x, -q1.y, -q1.z};
+    if (kBoost) {
+        p1 = boost_out(q1, p0, m0);
+        p2 = boost_out(q2, p0, m0);
+    } else {
+        p1 = q1;
+        p2 = q2;
+    }
+    return static_cast<double>(0.5f * static_cast<float>(kPi) * sl / static_cast<float>(s0));
+}
+
+}  // namespace mx
+
+// Mixed-precision interpreter: same byte-code, same slot file; scalar slots hold FP64, momentum
+// slots hold FP32.
+namespace mx {
+template <int NS, class Imm>
+__device__ __forceinline__ float ldf(const RegFrame<NS, Imm>& f, int a) {
+    return a >= 0 ? static_cast<float>(f.v[a]) : Imm::f(~a);
+}
+template <int NS, class Imm>
+__device__ __forceinline__ F4 ldp(const RegFrame<NS, Imm>& f, int a) {
+    return {static_cast<float>(f.v[a]), static_cast<float>(f.v[a + 1]), static_cast<float>(f.v[a + 2]),
+            static_cast<float>(f.v[a + 3])};
+}
+template <int NS, class Imm>
+__device__ __forceinline__ void stp(const RegFrame<NS, Imm>& f, int slot, F4 p) {
+    f.v[slot] = p.e;
+    f.v[slot + 1] = p.x;
+    f.v[slot + 2] = p.y;
+    f.v[slot + 3] = p.z;
+}
+}  // namespace mx
+
+
+namespace mx {
+// The FP32 form of sde_factor: the product as a float mantissa in [1, 2) and an integer exponent
+// (no FP64 work per propagator); sde_weight turns it into P_j = 1/(acc 2^ex) once per channel.
+__device__ __forceinline__ void sde_factor(float& acc, int& ex, const F4& q, int kind, float M, float G) {
+    const float s = fmaf(q.e, q.e, -fmaf(q.x, q.x, fmaf(q.y, q.y, q.z * q.z)));
+    const float d = s - M * M, mg = M * G;
+    acc *= (kind == 1) ? d * d : fmaf(d, d, mg * mg);
+    const int bits = __float_as_int(acc);  // acc = 1.m 2^e with e moved into ex
+    ex += ((bits >> 23) & 0xFF) - 127;
+    acc = __int_as_float((bits & 0x807FFFFF) | 0x3F800000);
+}
+// 1 / (acc 2^ex) with 2^-ex built from its bits (|ex| stays far below 1022 here)
+__device__ __forceinline__ double sde_weight(float acc, int ex) {
+    const double scale = __longlong_as_double(static_cast<long long>(1023 - ex) << 52);
+    return static_cast<double>(1.0f / acc) * scale;
+}
+}  // namespace mx
+
+template <class Fr>
+__device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, const int32_t* o, const int na,
+                                              const int no, const Fr& f, const float* gridf, int vbins,
+                                              unsigned long long* cut_count, bool active) {
+    using mx::F4;
+        switch (op) {
+            case PS_OP_VEGAS: {
+                float jac = 1.0f;
+                const float nb = static_cast<float>(vbins);
+                op_loop<Fr>(0, na, 1, [&](int j) {
+                    float r = mx::ldf(f, a[j]);
+                    float rn = r * nb;
+                    int k = max(min(static_cast<int>(rn), vbins - 1), 0);
+                    const float* e = gridf + j * (vbins + 1);
+                    float e0 = e[k], wdt = e[k + 1] - e0;
+                    st(f, o[j], static_cast<double>(fmaf(rn - static_cast<float>(k), wdt, e0)));
+                    jac *= nb * wdt;
+                });
+                st(f, o[na], static_cast<double>(jac));
+                break;
+            }
+            case PS_OP_INVARIANT_NU: {
+                double x, j;
+                mx::map_nu(mx::ldf(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), ld(f, a[5]), x, j);
+                st(f, o[0], x);
+                st(f, o[1], j);
+                break;
+            }
+            case PS_OP_INVARIANT_BW: {
+                double x, j;
+                mx::map_bw(mx::ldf(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), x, j, na > 5,
+                           na > 5 ? ld(f, a[5]) : 0.0);
+                st(f, o[0], x);
+                st(f, o[1], j);
+                break;
+            }
+            case PS_OP_R_TO_X1X2: {
+                float r = mx::ldf(f, a[0]);
+                float S = mx::ldf(f, a[2]);
+                float L = logf(mx::ldf(f, a[1]) / S);
+                const float l1 = r * L, l2 = (1.0f - r) * L;  // log x1, log x2
+                st(f, o[0], static_cast<double>(fminf(expf(l1), 1.0f)));
+                st(f, o[1], static_cast<double>(fminf(expf(l2), 1.0f)));
+                st(f, o[2], static_cast<double>(-L / S));
+                if (no > 3) {
+                    st(f, o[3], static_cast<double>(fminf(l1, 0.0f)));
+                    st(f, o[4], static_cast<double>(fminf(l2, 0.0f)));
+                }
+                break;
+            }
+            case PS_OP_COM_P_IN: {
+                float h = 0.5f * mx::ldf(f, a[0]);
+                mx::stp(f, o[0], F4{h, 0.0f, 0.0f, h});
+                mx::stp(f, o[1], F4{h, 0.0f, 0.0f, -h});
+                break;
+            }
+            case PS_OP_T_INV_MIN_MAX: {
+                double lo, hi, B;
+                mx::t_range(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]), lo, hi, B);
+                st(f, o[0], lo);
+                st(f, o[1], hi);
+                break;
+            }
+            case PS_OP_TWO_TO_TWO_COM: {
+                F4 p1, p2;
+                double j = mx::two_to_two(mx::ldf(f, a[0]), mx::ldp(f, a[1]), mx::ldp(f, a[2]), ld(f, a[3]),
+                                          ld(f, a[4]), ld(f, a[5]), ld(f, a[6]), ld(f, a[7]), ld(f, a[8]), p1, p2);
+                mx::stp(f, o[0], p1);
+                mx::stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_TWO_BODY_DECAY: {
+                F4 p1, p2;
+                double j = mx::two_body<true>(mx::ldf(f, a[0]), mx::ldf(f, a[1]), ld(f, a[2]), ld(f, a[3]),
+                                              ld(f, a[4]), mx::ldp(f, a[5]), p1, p2);
+                mx::stp(f, o[0], p1);
+                mx::stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_TWO_BODY_DECAY_COM: {
+                F4 p1, p2;
+                double j = mx::two_body<false>(mx::ldf(f, a[0]), mx::ldf(f, a[1]), ld(f, a[2]), ld(f, a[3]),
+                                               ld(f, a[4]), F4{0, 0, 0, 0}, p1, p2);
+                mx::stp(f, o[0], p1);
+                mx::stp(f, o[1], p2);
+                st(f, o[2], j);
+                break;
+            }
+            case PS_OP_BOOST_BEAM: {
+                float x1 = mx::ldf(f, a[na - 2]), x2 = mx::ldf(f, a[na - 1]);
+                float rho = sqrtf(x1 / x2);
+                float irho = 1.0f / rho;
+                op_loop<Fr>(0, na - 2, 1, [&](int k) {
+                    F4 p = mx::ldp(f, a[k]);
+                    float plus = rho * (p.e + p.z), minus = (p.e - p.z) * irho;
+                    mx::stp(f, o[k], F4{0.5f * (plus + minus), p.x, p.y, 0.5f * (plus - minus)});
+                });
+                break;
+            }
+            case PS_OP_REDUCE_PRODUCT: {
+                double v = ld(f, a[0]);
+                op_loop<Fr>(1, na, 1, [&](int k) { v *= ld(f, a[k]); });
+                st(f, o[0], v);
+                break;
+            }
+            case PS_OP_CUT_UNPHYSICAL: {
+                double w = ld(f, a[0]), x1 = ld(f, a[1]), x2 = ld(f, a[2]);
+                bool bad = !finite_bits(w) || !(in_unit_bits(x1) && in_unit_bits(x2));
+                op_loop<Fr>(3, na, 1, [&](int k) {
+                    F4 p = mx::ldp(f, a[k]);
+                    bad |= !(isfinite(p.e) && isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
+                });
+                if (bad && active) atomicAdd(cut_count, 1ULL);
+                st(f, o[0], bad ? 0.0 : w);
+                break;
+            }
+            case PS_OP_ADD: st(f, o[0], ld(f, a[0]) + ld(f, a[1])); break;
+            case PS_OP_SUB: st(f, o[0], ld(f, a[0]) - ld(f, a[1])); break;
+            case PS_OP_MUL: st(f, o[0], ld(f, a[0]) * ld(f, a[1])); break;
+            case PS_OP_DIV: st(f, o[0], ld(f, a[0]) / ld(f, a[1])); break;
+            case PS_OP_SQRT: st(f, o[0], mx::sqrt64(ld(f, a[0]))); break;
+            case PS_OP_SQUARE: { double v = ld(f, a[0]); st(f, o[0], v * v); break; }
+            case PS_OP_MAX: st(f, o[0], fmax(ld(f, a[0]), ld(f, a[1]))); break;
+            case PS_OP_MOM_ADD: mx::stp(f, o[0], mx::f4_add(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
+            case PS_OP_MOM_SUB: mx::stp(f, o[0], mx::f4_sub(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
+            case PS_OP_PDF_POWER: {
+                double xd = ld(f, a[0]);
+                float x = static_cast<float>(xd), al = mx::ldf(f, a[1]), be = mx::ldf(f, a[2]);
+                float fx = expf(al * (na > 3 ? static_cast<float>(ld(f, a[3])) : logf(x)));
+                float y = static_cast<float>(1.0 - xd);
+                float fy;
+                if (be == 3.0f) fy = y * y * y;
+                else if (be == 2.0f) fy = y * y;
+                else if (be == 1.0f) fy = y;
+                else if (be == 0.0f) fy = 1.0f;
+                else fy = powf(y, be);
+                st(f, o[0], static_cast<double>(fx * fy));
+                break;
+            }
+            case PS_OP_PROPAGATOR: {
+                double M = ld(f, a[1]);
+                float d = static_cast<float>(ld(f, a[0]) - M * M);   // s - M^2 in FP64
+                float mg = static_cast<float>(M * ld(f, a[2]));
+                st(f, o[0], static_cast<double>(1.0f / (d * d + mg * mg)));
+                break;
+            }
+            case PS_OP_ONE_PLUS_COS2: {
+                F4 p = mx::ldp(f, a[0]);
+                float c2 = p.z * p.z / (p.x * p.x + p.y * p.y + p.z * p.z);
+                st(f, o[0], static_cast<double>(1.0f + c2));
+                break;
+            }
+            case PS_OP_CHANNEL_WEIGHT: {
+                // FP32 throughout, as the momenta it starts from: momentum sums, invariants and
+                // denominators; the product of the denominators is kept as an FP32 mantissa in
+                // [1, 2) and an integer exponent (no FP64 work per propagator), and P_j becomes a
+                // double once per channel
+                const int k = op_int<Fr>(ld(f, a[0]));
+                const F4 pa = mx::ldp(f, a[1]);
+                float acc = 1.0f;
+                int ex = 0;
+                op_loop<Fr>(2 + k, na - 3, 4, [&](int j) {
+                    const int kind = op_int<Fr>(ld(f, a[j]));
+                    const int mask = op_int<Fr>(ld(f, a[j + 1]));
+                    const float M = mx::ldf(f, a[j + 2]), G = mx::ldf(f, a[j + 3]);
+                    F4 q = (kind == 1) ? pa : F4{0.0f, 0.0f, 0.0f, 0.0f};
+                    op_bits<Fr>(mask, k, [&](int i) {
+                        q = (kind == 1) ? mx::f4_sub(q, mx::ldp(f, a[2 + i])) : mx::f4_add(q, mx::ldp(f, a[2 + i]));
+                    });
+                    mx::sde_factor(acc, ex, q, kind, M, G);
+                });
+                st(f, o[0], mx::sde_weight(acc, ex));
+                break;
+            }
+            default: break;
+        }
+}
+
+__device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, const float* gridf, int vbins,
+                               unsigned long long* cut_count, bool active) {
+    int pc = 0;
+    while (pc < len) {
+        const int op = code[pc], na = code[pc + 1], no = code[pc + 2];
+        const int32_t* a = code + pc + 3;
+        exec_op_mixed(op, a, a + na, na, no, f, gridf, vbins, cut_count, active);
+        pc += 3 + na + no;
+    }
+}
+
+// Locate the output descriptor [kOpOutput, n, 0, (role, slot)...] after the instructions.
+__device__ __forceinline__ int find_output(const int32_t* code, int len) {
+    int pc = 0;
+    while (pc < len && code[pc] != kOpOutput) pc += 3 + code[pc + 1] + code[pc + 2];
+    return pc;
+}
+
+
+// ---------------------------------------------------------------- event input and output
+// Random inputs of one event into slots 0..n_random-1: explicit SoA, or Philox4x32-10 with
+// counter (ev_lo, ev_hi, channel, j/2) and key (seed_lo, seed_hi).
+template <class Fr>
+__device__ __forceinline__ void load_inputs(const Fr& f, const LaunchParams& lp, int c, int n_random, int64_t ev,
+                                            int64_t local, bool active) {
+    if (lp.r != nullptr) {
+        op_loop<Fr>(0, n_random, 1, [&](int j) { st(f, j, active ? lp.r[j * lp.ld_r + local] : 0.5); });
+    } else {
+        op_loop<Fr>(0, n_random, 2, [&](int j) {
+            uint4 o = philox4x32_10(make_uint4(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32),
+                                               static_cast<uint32_t>(c), static_cast<uint32_t>(j >> 1)),
+                                    static_cast<uint32_t>(lp.seed), static_cast<uint32_t>(lp.seed >> 32));
+            st(f, j, unit_from_bits(o.y, o.x));
+            if (j + 1 < n_random) st(f, j + 1, unit_from_bits(o.w, o.z));
+        });
+    }
+}
+
+// The declared outputs of one event (descriptor od = (role, slot) x n_out): FP64 programs write
+// f64 everywhere, mixed programs momenta, x and alpha as f32.  Returns the weight.
+template <bool kMix, class Fr>
+__device__ __forceinline__ double store_outputs(const Fr& f, const int32_t* od, int n_out, const LaunchParams& lp,
+                                                const ChannelLaunch& C, int64_t local, bool active) {
+    double w = 0.0;
+    int mom_k = 0;
+    const int64_t col = C.col_off + local;
+    op_loop<Fr>(0, n_out, 1, [&](int k) {
+        const int role = od[2 * k], slot = od[2 * k + 1];
+        if (role == PS_ROLE_MOMENTUM) {
+            if (active && lp.mom != nullptr) {
+                if constexpr (kMix) {
+                    mx::F4 p = mx::ldp(f, slot);
+                    float* m = static_cast<float*>(lp.mom) + static_cast<int64_t>(4 * mom_k) * lp.ld + col;
+                    __stcs(m, p.e);
+                    __stcs(m + lp.ld, p.x);
+                    __stcs(m + 2 * lp.ld, p.y);
+                    __stcs(m + 3 * lp.ld, p.z);
+                } else {
+                    P4 p = ldp(f, slot);
+                    double* m = static_cast<double*>(lp.mom) + static_cast<int64_t>(4 * mom_k) * lp.ld + col;
+                    __stcs(m, p.e);
+                    __stcs(m + lp.ld, p.x);
+                    __stcs(m + 2 * lp.ld, p.y);
+                    __stcs(m + 3 * lp.ld, p.z);
+                }
+            }
+            ++mom_k;
+        } else {
+            double v = ld(f, slot);
+            if (role == PS_ROLE_WEIGHT) {
+                w = v;
+                if (active && lp.w != nullptr) __stcs(lp.w + col, v);
+            } else {
+                void* dst = role == PS_ROLE_X1 ? lp.x1 : role == PS_ROLE_X2 ? lp.x2 : lp.alpha;
+                if (active && dst != nullptr) {
+                    if constexpr (kMix) __stcs(static_cast<float*>(dst) + col, static_cast<float>(v));
+                    else __stcs(static_cast<double*>(dst) + col, v);
+                }
+            }
+        }
+    });
+    return w;
+}
+
+// ---------------------------------------------------------------- tile loop
+// The persistent tile loop shared by the interpreter kernel and compiled kernels: tiles of
+// `block` events over all channels (tile -> channel by the prefix sums in the parameters), a
+// channel change stages the channel's shared data (pol.stage), every thread evaluates one event
+// (pol.event -> weight), then the VEGAS histogram (training) and the tile's partial sums.
+template <class Policy>
+__device__ __forceinline__ void map_tiles(const LaunchParams& lp, Policy& pol, double* s_red) {
+    const int B = lp.block;
+    const int tid = threadIdx.x;
+    int cur = -1;
+    for (int64_t tile = blockIdx.x; tile < lp.n_tiles; tile += gridDim.x) {
+        int c = 0;
+        while (c + 1 < lp.n_ch && tile >= lp.ch[c + 1].tile_begin) ++c;
+        const ChannelLaunch& C = lp.ch[c];
+        if (c != cur) {
+            __syncthreads();
+            pol.stage(c, C);
+            __syncthreads();
+            cur = c;
+        }
+        const int64_t local = (tile - C.tile_begin) * B + tid;
+        const bool active = local < C.n_events;
+        const int64_t ev = C.ev_offset + local;
+        double w = pol.event(c, C, ev, local, active);
+        if (!active) w = 0.0;
+        if (active && !finite_bits(w)) atomicAdd(lp.status + 0, 1ULL);
+
+        // VEGAS training: sum of w^2 per (dimension, bin of the unmapped r)
+        if (lp.hist != nullptr && C.vdims > 0 && active) {
+            for (int j = 0; j < C.vdims; ++j) {
+                double r;
+                if (lp.r != nullptr) {
+                    r = lp.r[j * lp.ld_r + local];
+                } else {
+                    uint4 o = philox4x32_10(make_uint4(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32),
+                                                       static_cast<uint32_t>(c), static_cast<uint32_t>(j >> 1)),
+                                            static_cast<uint32_t>(lp.seed), static_cast<uint32_t>(lp.seed >> 32));
+                    r = (j & 1) ? unit_from_bits(o.w, o.z) : unit_from_bits(o.y, o.x);
+                }
+                int k = min(max(static_cast<int>(r * C.vbins), 0), C.vbins - 1);
+                atomicAdd(lp.hist + C.hist_off + j * C.vbins + k, w * w);
+            }
+        }
+
+        // per-tile partial statistics: nonzero count, sum w, sum w^2, max w
+        double v0 = (w != 0.0) ? 1.0 : 0.0, v1 = w, v2 = w * w, v3 = w;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v0 += __shfl_down_sync(0xffffffffu, v0, off);
+            v1 += __shfl_down_sync(0xffffffffu, v1, off);
+            v2 += __shfl_down_sync(0xffffffffu, v2, off);
+            v3 = fmax(v3, __shfl_down_sync(0xffffffffu, v3, off));
+        }
+        const int warp = tid >> 5, lane = tid & 31;
+        __syncthreads();  // s_red reuse across tiles
+        if (lane == 0) {
+            s_red[4 * warp + 0] = v0;
+            s_red[4 * warp + 1] = v1;
+            s_red[4 * warp + 2] = v2;
+            s_red[4 * warp + 3] = v3;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            for (int k = 0; k < B / 32; ++k) {
+                a0 += s_red[4 * k];
+                a1 += s_red[4 * k + 1];
+                a2 += s_red[4 * k + 2];
+                a3 = fmax(a3, s_red[4 * k + 3]);
+            }
+            double* tp = lp.tile_partials + 4 * tile;
+            tp[0] = a0;
+            tp[1] = a1;
+            tp[2] = a2;
+            tp[3] = a3;
+        }
+    }
+}
+
+// A compiled program's policy: the VEGAS grid is the only shared data; the generated `Events`
+// evaluates channel c's instruction list on a register frame.
+template <bool kMix, class Events>
+struct CompiledPolicy {
+    const LaunchParams& lp;
+    double* s_grid;
+    __device__ __forceinline__ void stage(int c, const ChannelLaunch& C) {
+        const int ng = C.vdims * (C.vbins + 1);
+        float* s_gridf = reinterpret_cast<float*>(s_grid);
+        for (int i = threadIdx.x; i < ng; i += lp.block) {
+            if constexpr (kMix) s_gridf[i] = static_cast<float>(lp.grid[C.grid_off + i]);
+            else s_grid[i] = lp.grid[C.grid_off + i];
+        }
+    }
+    __device__ __forceinline__ double event(int c, const ChannelLaunch& C, int64_t ev, int64_t local, bool active) {
+        return Events::run(c, lp, C, ev, local, active, s_grid, lp.status + 1);
+    }
+};
+
+}  // namespace dev
+}  // namespace ps

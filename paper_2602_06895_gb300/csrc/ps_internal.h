@@ -6,13 +6,12 @@
 #include <string>
 #include <vector>
 
+#include "launch_params.h"
 #include "ps.h"
 
 namespace ps {
 
-constexpr int kMaxChannels = 32;
 constexpr int kMaxOutMomenta = 24;
-constexpr int kOpOutput = 1000;  // pseudo-op closing each channel's byte-code
 constexpr int kNoallocTiles = 131072;  // tiles of the allocation-free entry point's fixed scratch
 constexpr int kMaxDevices = 64;
 
@@ -53,49 +52,6 @@ struct Compiled {
 
 int compile_graph(const Graph& g, Compiled* out, std::string* err);
 
-// ---------------------------------------------------------------- launch description
-struct ChannelLaunch {
-    int32_t code_off, code_len;    // ints in the code buffer
-    int32_t imm_off, imm_len;      // doubles in the immediates buffer
-    int32_t grid_off;              // doubles in the grid buffer
-    int32_t vdims, vbins;
-    int32_t n_slots;
-    int32_t n_random;
-    int32_t hist_off;              // doubles in the histogram buffer
-    int64_t n_events;
-    int64_t col_off;               // first output column
-    int64_t tile_begin;            // first global tile index
-    int64_t ev_offset;             // event id of the channel's first event
-};
-
-struct LaunchParams {
-    int32_t n_ch;
-    int32_t block;                 // threads per CTA = events per tile
-    int32_t smem_code_ints, smem_imm, smem_grid, smem_slots;  // per-CTA staging sizes
-    int64_t n_tiles;
-    const int32_t* code;
-    const double* imm;
-    const double* grid;
-    // inputs
-    const double* r;               // explicit-input mode (SoA), or nullptr for Philox
-    int64_t ld_r;
-    uint64_t seed;
-    // outputs: f64 in FP64 programs; momenta, x1, x2 and alpha are f32 in mixed programs
-    void* mom;
-    void* x1;
-    void* x2;
-    double* w;
-    void* alpha;
-    int64_t ld;
-    int32_t mixed;
-    // scratch and program state
-    double* tile_partials;         // [n_tiles][4]
-    double* hist;                  // VEGAS histograms (program-owned), or nullptr
-    unsigned long long* status;    // [4]
-    const int32_t* stats_mode;     // device flag: nonzero adds each launch's sums into the statistics
-    ChannelLaunch ch[kMaxChannels];
-};
-
 // ---------------------------------------------------------------- inverse map plan
 // Everything the inverse kernel needs about one channel, flattened on the host from its
 // ps_channel_desc (the same layout, bounds recipe and propagators as the forward builder).
@@ -131,6 +87,19 @@ int build_inverse_plan(const ps_channel_desc* d, InvPlan* plan, std::string* err
 int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem_bytes, void* stream, std::string* err);
 int launch_reduce(const LaunchParams& lp, double* stats_dev, void* stream, std::string* err);
 int launch_copy(double* dst, const double* src, int n, void* stream, std::string* err);
+void count_launches(int n);
+
+// Compiled programs (jit.cpp): the CUDA source of a program, NVRTC to a cubin (host only), the
+// cached kernel on the current device, its occupancy and its launch.
+std::string jit_source(const std::vector<Compiled>& ch, int block, bool mixed);
+int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* log);
+int jit_prepare(const std::vector<Compiled>& ch, int block, bool mixed, int device, void** fn, std::string* err);
+int jit_occupancy(void* fn, int block, size_t smem, int* per_sm);
+int jit_launch(void* fn, const LaunchParams& lp, int grid, size_t smem, void* stream, std::string* err);
+// Whether a captured kernel node runs the compiled kernel fn.
+bool jit_node_runs(void* node, void* fn);
+// Point an instantiated graph's compiled-kernel node at new launch parameters.
+int jit_node_set(void* exec, void* node, void* fn, const LaunchParams& lp, int grid, size_t smem, std::string* err);
 size_t smem_bytes_for(const LaunchParams& lp);
 int max_ctas_per_sm(int block, size_t smem_bytes, int mixed, int* out, std::string* err);
 // Device address and size of the fixed scratch of ps_generate_noalloc on `device` (which must be

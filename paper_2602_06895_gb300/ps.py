@@ -58,7 +58,7 @@ class ChannelDesc(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("precision", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flags", C.c_int32)]
 
 
 class OutBuffers(C.Structure):
@@ -102,6 +102,7 @@ _SIGS = {
     "ps_exec_free": (C.c_int, [C.c_void_p]),
     "ps_stats": (C.c_int, [C.c_void_p, C.POINTER(ChannelStats), C.c_int, C.c_void_p]),
     "ps_stats_accumulate": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "ps_jit_check": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_char_p, C.c_size_t]),
     "ps_vegas_training": (C.c_int, [C.c_void_p, C.c_int]),
     "ps_vegas_histogram": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "ps_vegas_adapt": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
@@ -301,17 +302,19 @@ def _ptr(t):
 
 
 PRECISION = {"f64": 0, "mixed": 1}
+PS_PROGRAM_JIT = 1
 
 
 class Program:
     """A compiled multi-channel program on one device (ps_program)."""
 
-    def __init__(self, graphs, block_threads=128, ctas_per_sm=0, device=0, precision="f64"):
+    def __init__(self, graphs, block_threads=128, ctas_per_sm=0, device=0, precision="f64", jit=False):
         self.graphs = list(graphs)
         self.n_ch = len(self.graphs)
         self.precision = precision
+        self.jit = bool(jit)
         hs = (C.c_void_p * self.n_ch)(*[g.h.value for g in self.graphs])
-        opt = Options(block_threads, ctas_per_sm, PRECISION[precision], 0)
+        opt = Options(block_threads, ctas_per_sm, PRECISION[precision], PS_PROGRAM_JIT if jit else 0)
         h = C.c_void_p()
         _check(lib().ps_program_create(hs, self.n_ch, C.byref(opt), device, C.byref(h)), "ps_program_create")
         self.h = h
@@ -486,7 +489,7 @@ class Exec:
 
 
 def autotune(channels, events, precision="f64", blocks=(64, 128, 256), ctas=(1, 2, 3, 4), seed=1, reps=3,
-             device=0):
+             device=0, jit=False):
     """Pick block_threads and CTAs per SM for a workload by timing ps_generate on it.
 
     Every candidate compiles the program, generates the full event counts `reps` times after
@@ -497,7 +500,8 @@ def autotune(channels, events, precision="f64", blocks=(64, 128, 256), ctas=(1, 
     for b in blocks:
         for k in ctas:
             try:
-                prog = program_for(channels, block_threads=b, ctas_per_sm=k, device=device, precision=precision)
+                prog = program_for(channels, block_threads=b, ctas_per_sm=k, device=device, precision=precision,
+                                   jit=jit)
             except PSError:
                 continue
             n_mom = channels[0]["n"] + 2
@@ -523,11 +527,22 @@ def launch_count():
     return lib().ps_launch_count()
 
 
-def program_for(channels, block_threads=128, ctas_per_sm=0, device=0, precision="f64"):
-    """Build every channel of a workload list and compile them into one program."""
+def program_for(channels, block_threads=128, ctas_per_sm=0, device=0, precision="f64", jit=False):
+    """Build every channel of a workload list and compile them into one program (jit: the
+    instruction lists compiled into one kernel at creation, PS_PROGRAM_JIT)."""
     graphs = [build_channel(channels, c) for c in range(len(channels))]
     return Program(graphs, block_threads=block_threads, ctas_per_sm=ctas_per_sm, device=device,
-                   precision=precision)
+                   precision=precision, jit=jit)
+
+
+def jit_check(channels, block_threads=128, precision="f64"):
+    """Generate and compile (NVRTC, no device) the kernel of a compiled program; returns the log."""
+    graphs = [build_channel(channels, c) for c in range(len(channels))]
+    hs = (C.c_void_p * len(graphs))(*[g.h.value for g in graphs])
+    opt = Options(block_threads, 0, PRECISION[precision], PS_PROGRAM_JIT)
+    log = C.create_string_buffer(1 << 16)
+    _check(lib().ps_jit_check(hs, len(graphs), C.byref(opt), log, len(log)), "ps_jit_check")
+    return log.value.decode(errors="replace")
 
 
 # ------------------------------------------------------------------ coupling flow (ps_flow_*)

@@ -65,9 +65,9 @@ def torch_cuda():
     return torch
 
 
-def run_map(torch, channels, which, r, grid=None, block=128):
+def run_map(torch, channels, which, r, grid=None, block=128, jit=False):
     """Explicit-input map of channel `which` on the GPU; r [B, d] numpy."""
-    prog = ps.program_for(channels, block_threads=block)
+    prog = ps.program_for(channels, block_threads=block, jit=jit)
     ch = channels[which]
     if grid is not None:
         prog.set_vegas(which, grid)

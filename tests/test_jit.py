@@ -1,0 +1,31 @@
+"""Compiled programs (PS_PROGRAM_JIT): the generated kernel compiles for sm_103a with NVRTC on the
+host (no device), and keeps every slot in registers (no local-memory frame beyond the math
+library's, no spills)."""
+import re
+
+from paper_2602_06895_gb300 import ps
+from paper_2602_06895_gb300 import workloads as W
+
+
+def _stats(log):
+    stack = [int(m) for m in re.findall(r"(\d+) bytes stack frame", log)]
+    spills = [int(m) for m in re.findall(r"(\d+) bytes spill stores", log)]
+    return max(stack), max(spills)
+
+
+def test_compiled_2to4_builds_in_registers(monkeypatch):
+    monkeypatch.setenv("PS_JIT_PTXAS_VERBOSE", "1")
+    for precision in ("f64", "mixed"):
+        log = ps.jit_check([W.ww_hadronic()], 128, precision)
+        stack, spills = _stats(log)
+        assert spills == 0 and stack <= 64, (precision, log)
+
+
+def test_compiled_channel_weights_stay_in_registers(monkeypatch):
+    """The six 2->5 channels, each with the SDE weights of all six: the weights are generated as
+    straight-line code, so the register frame is never indexed at run time."""
+    monkeypatch.setenv("PS_JIT_PTXAS_VERBOSE", "1")
+    chans = W.multichannel_2to5()
+    log = ps.jit_check(chans, 128, "f64")
+    stack, spills = _stats(log)
+    assert spills == 0 and stack <= 64, log
