@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--no-streamed", action="store_true")
     ap.add_argument("--no-c5-importance", action="store_true")
     ap.add_argument("--no-jit", action="store_true",
-                    help="run the 2->4 and 2->5 steps on the interpreter instead of compiled programs")
+                    help="run every map on the interpreter instead of compiled programs")
     ap.add_argument("--stream-events", type=int, default=None, help="streamed leg: total events (default 1e8)")
     ap.add_argument("--stream-chunk", type=int, default=None, help="streamed leg: events per chunk (default 2^22)")
     ap.add_argument("--stream-config", default=None, help="streamed leg: 'threads,ctas_per_sm' instead of autotuning")
@@ -219,13 +219,14 @@ def c1_leg(ps, W, torch, stream, local, events=100_000, reps=20):
 
 
 def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best=None, host_copy=False,
-                 total=None, chunk=None):
+                 total=None, chunk=None, jit=False):
     """The 2->8 workload (six massless partons and two 173 GeV particles, 24 channels, SDE weights
     in-kernel) streamed: 1e8 events in chunks of 2^22, each chunk one persistent launch for all 24
     channels (CUDA graph, tiles and schedule from the autotuner) into one of two output buffers, its
     per-channel sums added on the device (streaming statistics, read once at the end).  With
     host_copy the record of each chunk also goes to pinned host memory on a second stream while
-    the next chunk is generated."""
+    the next chunk is generated.  With jit the program is compiled (one unit per channel, compiled
+    in parallel and linked; the compile time is reported, outside the timed region)."""
     import numpy as np
 
     from paper_2602_06895_gb300 import distributed as D
@@ -237,10 +238,13 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
     split = lambda n: [n // nc + (1 if c < n % nc else 0) for c in range(nc)]
     n_full, tail = divmod(total, chunk)
     table = None
+    t_compile = time.perf_counter()
     if best is None:
-        best, table = ps.autotune(chans, split(chunk // 4), precision=precision, blocks=(64, 128, 256),
-                                  ctas=(1, 2, 3, 4), reps=2, device=local)
-    prog = ps.program_for(chans, device=local, precision=precision, **best)
+        best, table = ps.autotune(chans, split(chunk // 4), precision=precision,
+                                  blocks=(64, 128) if jit else (64, 128, 256), ctas=(1, 2, 3, 4), reps=2,
+                                  device=local, jit=jit)
+    prog = ps.program_for(chans, device=local, precision=precision, jit=jit, **best)
+    t_compile = time.perf_counter() - t_compile
     n_mom = chans[0]["n"] + 2
     bufs = [prog.alloc(split(chunk), n_mom, alpha=True, device=local) for _ in range(2)]
     execs = [prog.exec_create(split(chunk), o, w) for o, w in bufs]
@@ -312,7 +316,9 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
            "wall_s": wall, "map_launches_per_chunk": 1, "gpu_launches": int(launches), "cuda_graph": True,
            "autotuned": best, "integral": integral, "rel_err": math.sqrt(var_mean) * nc / integral,
            "ess": ess, "effective_events_per_s": ess / (ms / 1e3), "max_w": max_w,
-           "nonzero_fraction": acc[:, 1].sum() / n_ev}
+           "nonzero_fraction": acc[:, 1].sum() / n_ev,
+           "kernel": "compiled program (24 channel units, NVRTC in parallel, nvJitLink)" if jit else "interpreter",
+           "setup_s": t_compile}
     if table is not None:
         res["autotune_table"] = table
     if host_copy:
@@ -325,7 +331,7 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
 
 
 def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=1 << 21, flow_steps=150,
-                      flow_batch=1 << 14, eval_events=1 << 22):
+                      flow_batch=1 << 14, eval_events=1 << 22, jit=False):
     """Importance sampling on the 2->8 workload (24 channels, d = 22): uniform r, a VEGAS grid per
     channel (22 dims x 64 bins, adapted in one multichannel launch per iteration), the same grids
     in the mixed-precision program, and one RQ-spline flow per channel trained on top of its grid.
@@ -334,7 +340,9 @@ def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=
     eval_events events with the variance-optimal counts n_c ~ sigma_c of its own pilot (the
     multichannel estimate I = sum_c mean_c has Var = sum_c sigma_c^2 / n_c).  Figure of merit:
     N_eff = I^2 / Var (unit-weight-equivalent events) per second of generation; the integrals
-    must agree.  The median per-channel Kish ESS fraction shows the sampler quality alone."""
+    must agree.  The median per-channel Kish ESS fraction shows the sampler quality alone.  With jit
+    every timed program is a compiled one (the VEGAS adaptation and the flow training, untimed, run
+    on the interpreter)."""
     import numpy as np
 
     chans = W.channels_2to8()
@@ -385,7 +393,10 @@ def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=
             return [(sc["n"], sc["sum_w"], sc["sum_w2"]) for sc in prog.stats(stream)]
         return run
 
-    prog_u = ps.program_for(chans, device=local, block_threads=64, ctas_per_sm=3)
+    # compiled programs: as many CTAs per SM as the registers allow (ctas_per_sm 0)
+    opts = {"block_threads": 128, "ctas_per_sm": 0, "jit": True} if jit else {"block_threads": 64, "ctas_per_sm": 3}
+    res["kernel"] = "compiled programs" if jit else "interpreter"
+    prog_u = ps.program_for(chans, device=local, **opts)
     measure("uniform_fp64", program_runner(prog_u, {}, 51))
     del prog_u
 
@@ -402,10 +413,15 @@ def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=
     prog_v.vegas_training(False)
     grids = [prog_v.get_vegas(c, d) for c in range(nc)]
     del out_v, ws_v
-    vegas = measure("vegas_fp64", program_runner(prog_v, {}, 52))
+    prog_vt = prog_v
+    if jit:
+        prog_vt = ps.program_for(vchans, device=local, **opts)
+        for c in range(nc):
+            prog_vt.set_vegas(c, grids[c])
+    vegas = measure("vegas_fp64", program_runner(prog_vt, {}, 52))
     res["vegas_fp64"]["adaptation"] = f"{vegas_iters} iterations x {vegas_events} events, alpha 1.5"
 
-    prog_m = ps.program_for(vchans, device=local, block_threads=64, ctas_per_sm=3, precision="mixed")
+    prog_m = ps.program_for(vchans, device=local, precision="mixed", **opts)
     for c in range(nc):
         prog_m.set_vegas(c, grids[c])
     measure("vegas_mixed", program_runner(prog_m, {}, 52))
@@ -457,7 +473,7 @@ def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=
             return out
         return run_f
 
-    flow = measure("flow_on_vegas", flow_runner(prog_v))
+    flow = measure("flow_on_vegas", flow_runner(prog_vt))
     res["flow_on_vegas"]["training"] = {"steps_per_channel": flow_steps, "batch": flow_batch, "seconds": train_s,
                                         "flows": nc, "layers": FLOW_LAYERS, "bins": FLOW_BINS,
                                         "hidden": FLOW_HIDDEN, "lr": 1e-3, "map": "fp64"}
@@ -466,7 +482,7 @@ def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=
     res["flow_n_eff_per_s_over_vegas_fp64"] = flow["n_eff_per_s"] / vegas["n_eff_per_s"]
     res["flow_mixed_map_n_eff_per_s_over_vegas_fp64"] = flow_m["n_eff_per_s"] / vegas["n_eff_per_s"]
     res["mixed_n_eff_per_s_over_vegas_fp64"] = res["vegas_mixed"]["n_eff_per_s"] / vegas["n_eff_per_s"]
-    del flows, prog_m
+    del flows, prog_m, prog_vt
     return res
 
 FLOW_LAYERS, FLOW_BINS, FLOW_HIDDEN, FLOW_BATCH = 6, 16, 128, 1 << 16
@@ -666,9 +682,10 @@ def main():
                 b, k = (int(x) for x in args.stream_config.split(","))
                 cfg = {"block_threads": b, "ctas_per_sm": k}
             res = streamed_leg(ps, W, torch, stream, rank, world, local, precision=args.stream_precision, best=cfg,
+                               jit=not args.no_jit,
                                total=args.stream_events, chunk=args.stream_chunk)
         elif args.leg == "c5_importance":
-            res = c5_importance_leg(ps, W, torch, stream, local)
+            res = c5_importance_leg(ps, W, torch, stream, local, jit=not args.no_jit)
         elif args.leg == "unweight":
             res = unweight_leg(ps, torch, out["weight"], stream)
         else:
@@ -861,11 +878,11 @@ def main():
     # records copied to the host) and the mixed-precision form on the same events
     streamed = None
     if not args.no_streamed:
-        streamed = streamed_leg(ps, W, torch, stream, rank, world, local)
+        streamed = streamed_leg(ps, W, torch, stream, rank, world, local, jit=jit)
         if not args.no_e2e:
             streamed["e2e"] = streamed_leg(ps, W, torch, stream, rank, world, local, best=streamed["autotuned"],
-                                           host_copy=True)["e2e"]
-        sm = streamed_leg(ps, W, torch, stream, rank, world, local, precision="mixed")
+                                           host_copy=True, jit=jit)["e2e"]
+        sm = streamed_leg(ps, W, torch, stream, rank, world, local, precision="mixed", jit=jit)
         streamed["mixed_precision"] = {k: sm[k] for k in ("value", "ms_total", "integral", "rel_err", "ess",
                                                           "effective_events_per_s", "autotuned")}
         streamed["mixed_precision"]["integral_rel_diff_vs_fp64_same_events"] = sm["integral"] / streamed["integral"] - 1
@@ -875,7 +892,7 @@ def main():
 
     c5imp = None
     if not args.no_c5_importance and rank == 0:
-        c5imp = c5_importance_leg(ps, W, torch, stream, local)
+        c5imp = c5_importance_leg(ps, W, torch, stream, local, jit=jit)
 
     flow = None
     if not args.no_flow and rank == 0:

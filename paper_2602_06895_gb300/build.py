@@ -94,7 +94,7 @@ def build(force=False, verbose=False, ptxas_verbose=False):
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     libdir = cuda_lib_dir()
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-L", libdir, "-lnvrtc", "-ldl",
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-L", libdir, "-lnvrtc", "-lnvJitLink", "-ldl",
            "-Xlinker", "-rpath", "-Xlinker", libdir]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:

@@ -1656,7 +1656,7 @@ int ps_jit_check(const ps_graph* graphs, int n_ch, const ps_options* opt, char* 
     }
     std::vector<char> cubin;
     std::string lg;
-    int st = ps::jit_compile(ps::jit_source(ch, block, mixed), &cubin, &lg);
+    int st = ps::jit_build(ch, block, mixed, &cubin, &lg);
     if (log_bytes > 0) {
         std::snprintf(log, log_bytes, "%s", lg.c_str());
     }

@@ -13,8 +13,11 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <dlfcn.h>
+#include <nvJitLink.h>
 #include <nvrtc.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cinttypes>
 #include <cstdio>
 #include <cstdlib>
@@ -22,6 +25,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ps_internal.h"
@@ -105,75 +109,116 @@ std::string channel_weight_source(const Compiled& C, const int32_t* a, int na, b
 
 }  // namespace
 
+namespace {
+// The immediates of channel c as constexpr functions of their index: a constant index folds to a
+// literal (an array would be a device variable, whose loads the compiler cannot fold).
+std::string imm_source(const Compiled& C, size_t c) {
+    std::string s = "struct I" + std::to_string(c) + " {\n    static __forceinline__ constexpr double v(int i) {\n        switch (i) {\n";
+    for (size_t i = 0; i < C.imm.size(); ++i)
+        s += "            case " + std::to_string(i) + ": return " + hexlit(C.imm[i]) + ";\n";
+    s += "            default: return 0.0;\n        }\n    }\n"
+         "    static __forceinline__ constexpr float f(int i) { return static_cast<float>(v(i)); }\n};\n";
+    return s;
+}
+
+// One channel's event: its instruction list on a register frame, from the inputs to the stores.
+// Names in scope: lp, C, ev, local, active, s_grid, cut.
+std::string channel_body(const Compiled& C, size_t c, bool mixed) {
+    const std::string cs = std::to_string(c);
+    std::string s;
+    s += "                const dev::RegFrame<" + std::to_string(std::max(C.n_slots, 1)) + ", I" + cs + "> f{};\n";
+    s += "                dev::load_inputs(f, lp, " + cs + ", " + std::to_string(C.n_random) + ", ev, local, active);\n";
+    size_t pc = 0;
+    while (pc < C.code.size() && C.code[pc] != kOpOutput) {
+        const int op = C.code[pc], na = C.code[pc + 1], no = C.code[pc + 2];
+        const int32_t* a = C.code.data() + pc + 3;
+        if (op == PS_OP_CHANNEL_WEIGHT) {  // unrolled here: counts, kinds and masks are known now
+            s += channel_weight_source(C, a, na, mixed);
+            pc += 3 + na + no;
+            continue;
+        }
+        s += "                {";
+        s += na ? " constexpr int32_t a[] = {" + ints(a, na) + "};" : " const int32_t* a = nullptr;";
+        s += no ? " constexpr int32_t o[] = {" + ints(a + na, no) + "};" : " const int32_t* o = nullptr;";
+        if (mixed)
+            s += " dev::exec_op_mixed(" + std::to_string(op) + ", a, o, " + std::to_string(na) + ", " +
+                 std::to_string(no) + ", f, reinterpret_cast<const float*>(s_grid), C.vbins, cut, active); }\n";
+        else
+            s += " dev::exec_op(" + std::to_string(op) + ", a, o, " + std::to_string(na) + ", " + std::to_string(no) +
+                 ", f, s_grid, C.vbins, cut, active); }\n";
+        pc += 3 + na + no;
+    }
+    const int n_out = pc + 1 < C.code.size() ? C.code[pc + 1] : 0;
+    s += "                constexpr int32_t od[] = {" +
+         (n_out ? ints(C.code.data() + pc + 3, 2 * n_out) : std::string("0, 0")) + "};\n";
+    s += "                return dev::store_outputs<kMix>(f, od, " + std::to_string(n_out) + ", lp, C, local, active);\n";
+    return s;
+}
+
+const char* kChanParams =
+    "(const ps::LaunchParams& lp, const ps::ChannelLaunch& C, int64_t ev, int64_t local, bool active, "
+    "double* s_grid, unsigned long long* cut)";
+
+std::string kernel_source(int block) {
+    return "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(block) +
+           ") ps_jit_map(const __grid_constant__ ps::LaunchParams lp) {\n"
+           "    extern __shared__ __align__(16) double smem[];\n"
+           "    ps::dev::CompiledPolicy<psjit::kMix, psjit::Events> pol{lp, smem};\n"
+           "    ps::dev::map_tiles(lp, pol, smem + lp.smem_grid);\n"
+           "}\n";
+}
+
+std::string prologue(bool mixed) {
+    return std::string("#include \"map_device.cuh\"\n\nnamespace psjit {\nusing namespace ps;\n") +
+           (mixed ? "constexpr bool kMix = true;\n" : "constexpr bool kMix = false;\n");
+}
+}  // namespace
+
 // The CUDA source of a compiled program (all channels, one precision, one block size).
 std::string jit_source(const std::vector<Compiled>& ch, int block, bool mixed) {
-    std::string s;
-    s += "#include \"map_device.cuh\"\n\nnamespace psjit {\nusing namespace ps;\n";
-    s += mixed ? "constexpr bool kMix = true;\n" : "constexpr bool kMix = false;\n";
-    // immediates as constexpr functions of their index: a constant index folds to a literal (an
-    // array would be a device variable, whose loads the compiler cannot fold)
-    for (size_t c = 0; c < ch.size(); ++c) {
-        const Compiled& C = ch[c];
-        s += "struct I" + std::to_string(c) + " {\n    static __forceinline__ constexpr double v(int i) {\n        switch (i) {\n";
-        for (size_t i = 0; i < C.imm.size(); ++i)
-            s += "            case " + std::to_string(i) + ": return " + hexlit(C.imm[i]) + ";\n";
-        s += "            default: return 0.0;\n        }\n    }\n"
-             "    static __forceinline__ constexpr float f(int i) { return static_cast<float>(v(i)); }\n};\n";
-    }
+    std::string s = prologue(mixed);
+    for (size_t c = 0; c < ch.size(); ++c) s += imm_source(ch[c], c);
     s += "struct Events {\n"
          "    static __device__ __forceinline__ double run(int c, const LaunchParams& lp, const ChannelLaunch& C,\n"
          "                                                 int64_t ev, int64_t local, bool active, double* s_grid,\n"
          "                                                 unsigned long long* cut) {\n"
          "        switch (C.channel) {\n";
     for (size_t c = 0; c < ch.size(); ++c) {
-        const Compiled& C = ch[c];
-        const std::string cs = std::to_string(c);
-        s += "            case " + cs + ": {\n";
-        s += "                const dev::RegFrame<" + std::to_string(std::max(C.n_slots, 1)) + ", I" + cs + "> f{};\n";
-        s += "                dev::load_inputs(f, lp, " + cs + ", " + std::to_string(C.n_random) + ", ev, local, active);\n";
-        size_t pc = 0;
-        while (pc < C.code.size() && C.code[pc] != kOpOutput) {
-            const int op = C.code[pc], na = C.code[pc + 1], no = C.code[pc + 2];
-            const int32_t* a = C.code.data() + pc + 3;
-            if (op == PS_OP_CHANNEL_WEIGHT) {  // unrolled here: counts, kinds and masks are known now
-                s += channel_weight_source(C, a, na, mixed);
-                pc += 3 + na + no;
-                continue;
-            }
-            s += "                {";
-            s += na ? " constexpr int32_t a[] = {" + ints(a, na) + "};" : " const int32_t* a = nullptr;";
-            s += no ? " constexpr int32_t o[] = {" + ints(a + na, no) + "};" : " const int32_t* o = nullptr;";
-            if (mixed)
-                s += " dev::exec_op_mixed(" + std::to_string(op) + ", a, o, " + std::to_string(na) + ", " +
-                     std::to_string(no) + ", f, reinterpret_cast<const float*>(s_grid), C.vbins, cut, active); }\n";
-            else
-                s += " dev::exec_op(" + std::to_string(op) + ", a, o, " + std::to_string(na) + ", " + std::to_string(no) +
-                     ", f, s_grid, C.vbins, cut, active); }\n";
-            pc += 3 + na + no;
-        }
-        const int n_out = pc + 1 < C.code.size() ? C.code[pc + 1] : 0;
-        s += "                constexpr int32_t od[] = {" + (n_out ? ints(C.code.data() + pc + 3, 2 * n_out) : std::string("0, 0")) + "};\n";
-        s += "                return dev::store_outputs<kMix>(f, od, " + std::to_string(n_out) + ", lp, C, local, active);\n";
-        s += "            }\n";
+        s += "            case " + std::to_string(c) + ": {\n" + channel_body(ch[c], c, mixed) + "            }\n";
     }
     s += "        }\n        return 0.0;\n    }\n};\n}  // namespace psjit\n\n";
-    s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(block) +
-         ") ps_jit_map(const __grid_constant__ ps::LaunchParams lp) {\n"
-         "    extern __shared__ __align__(16) double smem[];\n"
-         "    ps::dev::CompiledPolicy<psjit::kMix, psjit::Events> pol{lp, smem};\n"
-         "    ps::dev::map_tiles(lp, pol, smem + lp.smem_grid);\n"
-         "}\n";
-    return s;
+    return s + kernel_source(block);
+}
+
+// The split form of a large program: one unit per channel, each defining the channel's event as
+// an external device function, and a kernel unit that dispatches on the channel. The units are
+// compiled separately (in parallel) as relocatable code and linked into one kernel.
+std::vector<std::string> jit_sources_split(const std::vector<Compiled>& ch, int block, bool mixed) {
+    std::vector<std::string> units;
+    std::string k = prologue(mixed) + "}  // namespace psjit\n";
+    for (size_t c = 0; c < ch.size(); ++c)
+        k += "extern \"C\" __device__ double psjit_channel_" + std::to_string(c) + kChanParams + ";\n";
+    k += "namespace psjit {\nstruct Events {\n"
+         "    static __device__ __forceinline__ double run(int c, const LaunchParams& lp, const ChannelLaunch& C,\n"
+         "                                                 int64_t ev, int64_t local, bool active, double* s_grid,\n"
+         "                                                 unsigned long long* cut) {\n"
+         "        switch (C.channel) {\n";
+    for (size_t c = 0; c < ch.size(); ++c)
+        k += "            case " + std::to_string(c) + ": return psjit_channel_" + std::to_string(c) +
+             "(lp, C, ev, local, active, s_grid, cut);\n";
+    k += "        }\n        return 0.0;\n    }\n};\n}  // namespace psjit\n\n" + kernel_source(block);
+    units.push_back(k);
+    for (size_t c = 0; c < ch.size(); ++c) {
+        std::string u = prologue(mixed) + imm_source(ch[c], c) + "}  // namespace psjit\n\n";
+        u += "extern \"C\" __device__ double psjit_channel_" + std::to_string(c) + kChanParams + " {\n"
+             "    using namespace ps;\n    using namespace psjit;\n    {\n" + channel_body(ch[c], c, mixed) + "    }\n}\n";
+        units.push_back(u);
+    }
+    return units;
 }
 
 // NVRTC: source -> cubin for sm_103a (host only, no device needed).
-int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* log) {
-    if (const char* dump = std::getenv("PS_JIT_DUMP")) {  // diagnostic: the generated source
-        if (FILE* fp = std::fopen(dump, "w")) {
-            std::fputs(src.c_str(), fp);
-            std::fclose(fp);
-        }
-    }
+int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* log, bool relocatable) {
     std::vector<const char*> names, texts;
     for (int i = 0; i < kJitHeaderCount; ++i) {
         names.push_back(kJitHeaderNames[i]);
@@ -193,6 +238,7 @@ int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* l
         return PS_ERR_CUDA;
     }
     std::vector<const char*> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
+    if (relocatable) opts.push_back("--relocatable-device-code=true");
     if (std::getenv("PS_JIT_PTXAS_VERBOSE")) opts.push_back("--ptxas-options=-v");  // register and spill report in the log
     r = nvrtcCompileProgram(prog, static_cast<int>(opts.size()), opts.data());
     size_t n = 0;
@@ -210,6 +256,130 @@ int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* l
     nvrtcGetCUBIN(prog, cubin->data());
     nvrtcDestroyProgram(&prog);
     return PS_OK;
+}
+
+namespace {
+void dump_source(const std::string& src) {
+    if (const char* dump = std::getenv("PS_JIT_DUMP")) {  // diagnostic: the generated source
+        if (FILE* fp = std::fopen(dump, "w")) {
+            std::fputs(src.c_str(), fp);
+            std::fclose(fp);
+        }
+    }
+}
+
+std::mutex g_unit_mu;
+std::map<std::string, std::vector<char>> g_units;  // channel unit source -> relocatable cubin
+
+bool split_program(size_t n_ch) {
+    if (const char* e = std::getenv("PS_JIT_SPLIT")) return e[0] == '1';  // diagnostic override
+    return n_ch > static_cast<size_t>(kJitInlineChannels);
+}
+
+// nvJitLink: relocatable cubins -> one executable cubin for sm_103a (host only).
+int link_cubins(const std::vector<std::vector<char>>& bins, std::vector<char>* cubin, std::string* log) {
+    nvJitLinkHandle h;
+    const bool verbose = std::getenv("PS_JIT_PTXAS_VERBOSE") != nullptr;  // the linker's register report
+    const char* opts[] = {"-arch=sm_103a", "-verbose"};
+    if (nvJitLinkCreate(&h, verbose ? 2 : 1, opts) != NVJITLINK_SUCCESS) {
+        *log += "nvJitLinkCreate failed\n";
+        return PS_ERR_CUDA;
+    }
+    nvJitLinkResult r = NVJITLINK_SUCCESS;
+    for (size_t i = 0; i < bins.size() && r == NVJITLINK_SUCCESS; ++i) {
+        const std::string name = "ps_jit_unit_" + std::to_string(i);
+        r = nvJitLinkAddData(h, NVJITLINK_INPUT_CUBIN, bins[i].data(), bins[i].size(), name.c_str());
+    }
+    if (r == NVJITLINK_SUCCESS) r = nvJitLinkComplete(h);
+    if (r != NVJITLINK_SUCCESS) {
+        size_t n = 0;
+        nvJitLinkGetErrorLogSize(h, &n);
+        std::string lg(n, '\0');
+        if (n) nvJitLinkGetErrorLog(h, &lg[0]);
+        *log += "nvJitLink: " + lg;
+        nvJitLinkDestroy(&h);
+        return PS_ERR_GRAPH;
+    }
+    size_t n = 0;
+    if (verbose && nvJitLinkGetInfoLogSize(h, &n) == NVJITLINK_SUCCESS && n > 1) {
+        std::string lg(n, '\0');
+        nvJitLinkGetInfoLog(h, &lg[0]);
+        *log += lg;
+    }
+    nvJitLinkGetLinkedCubinSize(h, &n);
+    cubin->resize(n);
+    nvJitLinkGetLinkedCubin(h, cubin->data());
+    nvJitLinkDestroy(&h);
+    return PS_OK;
+}
+
+// The source (or the split units joined) that identifies a compiled program in the cache.
+struct Plan {
+    bool split = false;
+    std::vector<std::string> units;
+    std::string key;
+};
+
+Plan make_plan(const std::vector<Compiled>& ch, int block, bool mixed) {
+    Plan p;
+    p.split = split_program(ch.size());
+    if (p.split) {
+        p.units = jit_sources_split(ch, block, mixed);
+        for (const std::string& u : p.units) p.key += u + "\n// ---- unit\n";
+    } else {
+        p.units = {jit_source(ch, block, mixed)};
+        p.key = p.units[0];
+    }
+    return p;
+}
+
+int build_plan(const Plan& p, std::vector<char>* cubin, std::string* log) {
+    dump_source(p.key);
+    if (!p.split) return jit_compile(p.units[0], cubin, log, false);
+    // the units are independent NVRTC programs: compile them on a pool of host threads; a unit
+    // compiled before (the same channel in a program of another block size) is taken from the cache
+    const size_t n = p.units.size();
+    std::vector<std::vector<char>> bins(n);
+    std::vector<std::string> logs(n);
+    std::vector<int> sts(n, PS_OK);
+    std::vector<char> cached(n, 0);
+    {
+        std::lock_guard<std::mutex> lock(g_unit_mu);
+        for (size_t i = 0; i < n; ++i) {
+            auto it = g_units.find(p.units[i]);
+            if (it != g_units.end()) {
+                bins[i] = it->second;
+                cached[i] = 1;
+            }
+        }
+    }
+    std::atomic<size_t> next{0};
+    auto worker = [&] {
+        for (size_t i = next++; i < n; i = next++)
+            if (!cached[i]) sts[i] = jit_compile(p.units[i], &bins[i], &logs[i], true);
+    };
+    const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < std::min(n, hw); ++t) pool.emplace_back(worker);
+    worker();
+    for (std::thread& t : pool) t.join();
+    int st = PS_OK;
+    for (size_t i = 0; i < n; ++i) {
+        *log += logs[i];
+        if (sts[i] != PS_OK && st == PS_OK) st = sts[i];
+    }
+    if (st != PS_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_unit_mu);
+        for (size_t i = 1; i < n; ++i)  // the channel units (the kernel unit depends on the block size)
+            if (!cached[i]) g_units.emplace(p.units[i], bins[i]);
+    }
+    return link_cubins(bins, cubin, log);
+}
+}  // namespace
+
+int jit_build(const std::vector<Compiled>& ch, int block, bool mixed, std::vector<char>* cubin, std::string* log) {
+    return build_plan(make_plan(ch, block, mixed), cubin, log);
 }
 
 namespace {
@@ -271,9 +441,9 @@ int jit_prepare(const std::vector<Compiled>& ch, int block, bool mixed, int devi
         *err = d.why;
         return PS_ERR_CUDA;
     }
-    const std::string src = jit_source(ch, block, mixed);
+    const Plan plan = make_plan(ch, block, mixed);
     std::lock_guard<std::mutex> lock(g_cache_mu);
-    auto key = std::make_pair(device, src);
+    auto key = std::make_pair(device, plan.key);
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
         *fn = it->second;
@@ -281,7 +451,7 @@ int jit_prepare(const std::vector<Compiled>& ch, int block, bool mixed, int devi
     }
     std::vector<char> cubin;
     std::string log;
-    int st = jit_compile(src, &cubin, &log);
+    int st = build_plan(plan, &cubin, &log);
     if (st != PS_OK) {
         *err = "NVRTC: " + log;
         return st;

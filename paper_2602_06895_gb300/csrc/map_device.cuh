@@ -444,7 +444,7 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
 }
 
 // Executes one channel's instruction list for the calling thread's event.
-__device__ void run_code(const int32_t* code, int len, const Frame& f, const double* grid, int vbins,
+static __device__ void run_code(const int32_t* code, int len, const Frame& f, const double* grid, int vbins,
                          unsigned long long* cut_count, bool active) {
     int pc = 0;
     while (pc < len) {
@@ -902,7 +902,7 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
         }
 }
 
-__device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, const float* gridf, int vbins,
+static __device__ void run_code_mixed(const int32_t* code, int len, const Frame& f, const float* gridf, int vbins,
                                unsigned long long* cut_count, bool active) {
     int pc = 0;
     while (pc < len) {

@@ -29,3 +29,12 @@ def test_compiled_channel_weights_stay_in_registers(monkeypatch):
     log = ps.jit_check(chans, 128, "f64")
     stack, spills = _stats(log)
     assert spills == 0 and stack <= 64, log
+
+
+def test_split_program_compiles_and_links(monkeypatch):
+    """The split form (one NVRTC unit per channel, compiled in parallel as relocatable code, linked
+    with nvJitLink into one kernel), forced on the six 2->5 channels."""
+    monkeypatch.setenv("PS_JIT_SPLIT", "1")
+    monkeypatch.setenv("PS_JIT_PTXAS_VERBOSE", "1")
+    log = ps.jit_check(W.multichannel_2to5(), 128, "f64")
+    assert "ps_jit_map" in log, log
