@@ -393,8 +393,10 @@ def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=
             return [(sc["n"], sc["sum_w"], sc["sum_w2"]) for sc in prog.stats(stream)]
         return run
 
-    # compiled programs: as many CTAs per SM as the registers allow (ctas_per_sm 0)
-    opts = {"block_threads": 128, "ctas_per_sm": 0, "jit": True} if jit else {"block_threads": 64, "ctas_per_sm": 3}
+    # compiled programs: the shapes the streamed leg's autotuner picks on this workload (FP64: 2 CTAs
+    # of 128 threads per SM at up to 255 registers; mixed: 4 CTAs, registers capped at 128)
+    opts = {"block_threads": 128, "ctas_per_sm": 2, "jit": True} if jit else {"block_threads": 64, "ctas_per_sm": 3}
+    opts_m = dict(opts, ctas_per_sm=4) if jit else opts
     res["kernel"] = "compiled programs" if jit else "interpreter"
     prog_u = ps.program_for(chans, device=local, **opts)
     measure("uniform_fp64", program_runner(prog_u, {}, 51))
@@ -421,7 +423,7 @@ def c5_importance_leg(ps, W, torch, stream, local, vegas_iters=10, vegas_events=
     vegas = measure("vegas_fp64", program_runner(prog_vt, {}, 52))
     res["vegas_fp64"]["adaptation"] = f"{vegas_iters} iterations x {vegas_events} events, alpha 1.5"
 
-    prog_m = ps.program_for(vchans, device=local, precision="mixed", **opts)
+    prog_m = ps.program_for(vchans, device=local, precision="mixed", **opts_m)
     for c in range(nc):
         prog_m.set_vegas(c, grids[c])
     measure("vegas_mixed", program_runner(prog_m, {}, 52))

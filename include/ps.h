@@ -232,16 +232,19 @@ int ps_graph_build_channel(const ps_channel_desc* ch, int n_ch, int which, ps_gr
 
 typedef struct {
     int32_t block_threads; /* events per tile = threads per CTA (multiple of 32; 0 = default 128) */
-    int32_t ctas_per_sm;   /* resident CTAs requested per SM (0 = as many as fit, up to 4)      */
+    int32_t ctas_per_sm;   /* resident CTAs requested per SM (0 = as many as fit, up to 4; a
+                            * compiled program, PS_PROGRAM_JIT, caps its registers so that this
+                            * many fit, and takes as many as fit when 0)                        */
     int32_t precision;     /* PS_PRECISION_*                                                  */
     int32_t flags;         /* PS_PROGRAM_* bits                                               */
 } ps_options;
 
 /* Compile the program's instruction lists into one kernel at creation (NVRTC, sm_103a): the
  * slot file in registers, the byte-code's slots and immediates as constants.  Same results as
- * the interpreter up to the rounding of fused multiply-adds across op boundaries.  Creation
- * fails (PS_ERR_GRAPH with the compiler's message, PS_ERR_CUDA) if the kernel cannot be built;
- * kernels are cached per device and source. */
+ * the interpreter up to the rounding of fused multiply-adds across op boundaries.  Programs of
+ * more than six channels are compiled one unit per channel, in parallel on host threads, and
+ * linked (nvJitLink) into one kernel.  Creation fails (PS_ERR_GRAPH with the compiler's message,
+ * PS_ERR_CUDA) if the kernel cannot be built; kernels are cached per device and source. */
 #define PS_PROGRAM_JIT 1
 
 /* Generate and compile (NVRTC, no device needed) the kernel a program with these graphs and

@@ -1358,7 +1358,10 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
     int want = p->opt.ctas_per_sm > 0 ? p->opt.ctas_per_sm : 4;
     p->grid_ctas = p->sm_count * std::min(per_sm, want);
     if (p->opt.flags & PS_PROGRAM_JIT) {  // the compiled kernel: VEGAS grid and reduction scratch in shared memory
-        st = ps::jit_prepare(p->ch, p->block, p->opt.precision == PS_PRECISION_MIXED, device, &p->jit_fn, &err);
+        // a requested CTA count also caps the compiled kernel's registers so that many CTAs fit
+        const int min_blocks = std::min(p->opt.ctas_per_sm, 2048 / p->block);
+        st = ps::jit_prepare(p->ch, p->block, min_blocks, p->opt.precision == PS_PRECISION_MIXED, device, &p->jit_fn,
+                             &err);
         int jit_per_sm = 0;
         p->jit_smem = (static_cast<size_t>(p->max_grid) + 4 * (p->block / 32)) * sizeof(double);
         if (st == PS_OK) st = ps::jit_occupancy(p->jit_fn, p->block, p->jit_smem, &jit_per_sm);
@@ -1656,7 +1659,8 @@ int ps_jit_check(const ps_graph* graphs, int n_ch, const ps_options* opt, char* 
     }
     std::vector<char> cubin;
     std::string lg;
-    int st = ps::jit_build(ch, block, mixed, &cubin, &lg);
+    const int min_blocks = opt ? std::min(opt->ctas_per_sm, 2048 / block) : 0;
+    int st = ps::jit_build(ch, block, min_blocks, mixed, &cubin, &lg);
     if (log_bytes > 0) {
         std::snprintf(log, log_bytes, "%s", lg.c_str());
     }

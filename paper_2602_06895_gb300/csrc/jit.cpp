@@ -159,8 +159,10 @@ const char* kChanParams =
     "(const ps::LaunchParams& lp, const ps::ChannelLaunch& C, int64_t ev, int64_t local, bool active, "
     "double* s_grid, unsigned long long* cut)";
 
-std::string kernel_source(int block) {
-    return "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(block) +
+std::string kernel_source(int block, int min_blocks) {
+    const std::string bounds =
+        std::to_string(block) + (min_blocks > 0 ? ", " + std::to_string(min_blocks) : std::string());
+    return "extern \"C\" __global__ void __launch_bounds__(" + bounds +
            ") ps_jit_map(const __grid_constant__ ps::LaunchParams lp) {\n"
            "    extern __shared__ __align__(16) double smem[];\n"
            "    ps::dev::CompiledPolicy<psjit::kMix, psjit::Events> pol{lp, smem};\n"
@@ -175,7 +177,7 @@ std::string prologue(bool mixed) {
 }  // namespace
 
 // The CUDA source of a compiled program (all channels, one precision, one block size).
-std::string jit_source(const std::vector<Compiled>& ch, int block, bool mixed) {
+std::string jit_source(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed) {
     std::string s = prologue(mixed);
     for (size_t c = 0; c < ch.size(); ++c) s += imm_source(ch[c], c);
     s += "struct Events {\n"
@@ -187,13 +189,13 @@ std::string jit_source(const std::vector<Compiled>& ch, int block, bool mixed) {
         s += "            case " + std::to_string(c) + ": {\n" + channel_body(ch[c], c, mixed) + "            }\n";
     }
     s += "        }\n        return 0.0;\n    }\n};\n}  // namespace psjit\n\n";
-    return s + kernel_source(block);
+    return s + kernel_source(block, min_blocks);
 }
 
 // The split form of a large program: one unit per channel, each defining the channel's event as
 // an external device function, and a kernel unit that dispatches on the channel. The units are
 // compiled separately (in parallel) as relocatable code and linked into one kernel.
-std::vector<std::string> jit_sources_split(const std::vector<Compiled>& ch, int block, bool mixed) {
+std::vector<std::string> jit_sources_split(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed) {
     std::vector<std::string> units;
     std::string k = prologue(mixed) + "}  // namespace psjit\n";
     for (size_t c = 0; c < ch.size(); ++c)
@@ -206,7 +208,7 @@ std::vector<std::string> jit_sources_split(const std::vector<Compiled>& ch, int 
     for (size_t c = 0; c < ch.size(); ++c)
         k += "            case " + std::to_string(c) + ": return psjit_channel_" + std::to_string(c) +
              "(lp, C, ev, local, active, s_grid, cut);\n";
-    k += "        }\n        return 0.0;\n    }\n};\n}  // namespace psjit\n\n" + kernel_source(block);
+    k += "        }\n        return 0.0;\n    }\n};\n}  // namespace psjit\n\n" + kernel_source(block, min_blocks);
     units.push_back(k);
     for (size_t c = 0; c < ch.size(); ++c) {
         std::string u = prologue(mixed) + imm_source(ch[c], c) + "}  // namespace psjit\n\n";
@@ -218,7 +220,7 @@ std::vector<std::string> jit_sources_split(const std::vector<Compiled>& ch, int 
 }
 
 // NVRTC: source -> cubin for sm_103a (host only, no device needed).
-int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* log, bool relocatable) {
+int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* log, bool relocatable, int max_regs) {
     std::vector<const char*> names, texts;
     for (int i = 0; i < kJitHeaderCount; ++i) {
         names.push_back(kJitHeaderNames[i]);
@@ -239,6 +241,8 @@ int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* l
     }
     std::vector<const char*> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
     if (relocatable) opts.push_back("--relocatable-device-code=true");
+    const std::string regs = "--maxrregcount=" + std::to_string(max_regs);
+    if (max_regs > 0) opts.push_back(regs.c_str());
     if (std::getenv("PS_JIT_PTXAS_VERBOSE")) opts.push_back("--ptxas-options=-v");  // register and spill report in the log
     r = nvrtcCompileProgram(prog, static_cast<int>(opts.size()), opts.data());
     size_t n = 0;
@@ -316,26 +320,39 @@ int link_cubins(const std::vector<std::vector<char>>& bins, std::vector<char>* c
 // The source (or the split units joined) that identifies a compiled program in the cache.
 struct Plan {
     bool split = false;
+    int max_regs = 0;  // the channel units' register cap (split form; 0 = none)
     std::vector<std::string> units;
     std::string key;
 };
 
-Plan make_plan(const std::vector<Compiled>& ch, int block, bool mixed) {
+// The register cap under which min_blocks CTAs of `block` threads fit on an SM (65536 registers,
+// allocated in steps of 8 per thread), or 0 for no cap.
+int register_cap(int block, int min_blocks) {
+    if (min_blocks <= 0) return 0;
+    const int regs = (65536 / (block * min_blocks)) & ~7;
+    return std::max(32, std::min(255, regs));
+}
+
+Plan make_plan(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed) {
     Plan p;
     p.split = split_program(ch.size());
     if (p.split) {
-        p.units = jit_sources_split(ch, block, mixed);
+        p.max_regs = register_cap(block, min_blocks);
+        p.units = jit_sources_split(ch, block, min_blocks, mixed);
         for (const std::string& u : p.units) p.key += u + "\n// ---- unit\n";
+        p.key += "// maxrregcount " + std::to_string(p.max_regs) + "\n";
     } else {
-        p.units = {jit_source(ch, block, mixed)};
+        p.units = {jit_source(ch, block, min_blocks, mixed)};
         p.key = p.units[0];
     }
     return p;
 }
 
+std::string unit_key(const Plan& p, size_t i) { return p.units[i] + "// maxrregcount " + std::to_string(p.max_regs); }
+
 int build_plan(const Plan& p, std::vector<char>* cubin, std::string* log) {
     dump_source(p.key);
-    if (!p.split) return jit_compile(p.units[0], cubin, log, false);
+    if (!p.split) return jit_compile(p.units[0], cubin, log, false, 0);
     // the units are independent NVRTC programs: compile them on a pool of host threads; a unit
     // compiled before (the same channel in a program of another block size) is taken from the cache
     const size_t n = p.units.size();
@@ -346,7 +363,7 @@ int build_plan(const Plan& p, std::vector<char>* cubin, std::string* log) {
     {
         std::lock_guard<std::mutex> lock(g_unit_mu);
         for (size_t i = 0; i < n; ++i) {
-            auto it = g_units.find(p.units[i]);
+            auto it = g_units.find(unit_key(p, i));
             if (it != g_units.end()) {
                 bins[i] = it->second;
                 cached[i] = 1;
@@ -356,7 +373,7 @@ int build_plan(const Plan& p, std::vector<char>* cubin, std::string* log) {
     std::atomic<size_t> next{0};
     auto worker = [&] {
         for (size_t i = next++; i < n; i = next++)
-            if (!cached[i]) sts[i] = jit_compile(p.units[i], &bins[i], &logs[i], true);
+            if (!cached[i]) sts[i] = jit_compile(p.units[i], &bins[i], &logs[i], true, i > 0 ? p.max_regs : 0);
     };
     const size_t hw = std::max(1u, std::thread::hardware_concurrency());
     std::vector<std::thread> pool;
@@ -372,14 +389,15 @@ int build_plan(const Plan& p, std::vector<char>* cubin, std::string* log) {
     {
         std::lock_guard<std::mutex> lock(g_unit_mu);
         for (size_t i = 1; i < n; ++i)  // the channel units (the kernel unit depends on the block size)
-            if (!cached[i]) g_units.emplace(p.units[i], bins[i]);
+            if (!cached[i]) g_units.emplace(unit_key(p, i), bins[i]);
     }
     return link_cubins(bins, cubin, log);
 }
 }  // namespace
 
-int jit_build(const std::vector<Compiled>& ch, int block, bool mixed, std::vector<char>* cubin, std::string* log) {
-    return build_plan(make_plan(ch, block, mixed), cubin, log);
+int jit_build(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed, std::vector<char>* cubin,
+              std::string* log) {
+    return build_plan(make_plan(ch, block, min_blocks, mixed), cubin, log);
 }
 
 namespace {
@@ -430,7 +448,8 @@ std::map<std::pair<int, std::string>, CUfunction_t> g_cache;  // (device, source
 }  // namespace
 
 // Compile (or find in the cache) the program's kernel on the current device.
-int jit_prepare(const std::vector<Compiled>& ch, int block, bool mixed, int device, void** fn, std::string* err) {
+int jit_prepare(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed, int device, void** fn,
+                std::string* err) {
     for (const Compiled& C : ch)
         if (!all_finite(C.imm)) {
             *err = "a channel has a non-finite immediate";
@@ -441,7 +460,7 @@ int jit_prepare(const std::vector<Compiled>& ch, int block, bool mixed, int devi
         *err = d.why;
         return PS_ERR_CUDA;
     }
-    const Plan plan = make_plan(ch, block, mixed);
+    const Plan plan = make_plan(ch, block, min_blocks, mixed);
     std::lock_guard<std::mutex> lock(g_cache_mu);
     auto key = std::make_pair(device, plan.key);
     auto it = g_cache.find(key);

@@ -91,15 +91,19 @@ void count_launches(int n);
 
 // Compiled programs (jit.cpp): the CUDA source of a program, NVRTC to a cubin (host only), the
 // cached kernel on the current device, its occupancy and its launch.
-std::string jit_source(const std::vector<Compiled>& ch, int block, bool mixed);
-int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* log, bool relocatable);
+// min_blocks > 0: the kernel is compiled so that that many CTAs of `block` threads fit on an SM
+// (launch bounds; the split form's channel units get the matching register cap).
+std::string jit_source(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed);
+int jit_compile(const std::string& src, std::vector<char>* cubin, std::string* log, bool relocatable, int max_regs);
 // Programs of more than this many channels are compiled one unit per channel, in parallel, and
 // linked: one unit of all channels compiles in time that grows faster than the channel count.
 constexpr int kJitInlineChannels = 6;
-std::vector<std::string> jit_sources_split(const std::vector<Compiled>& ch, int block, bool mixed);
+std::vector<std::string> jit_sources_split(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed);
 // The program's kernel as one executable cubin: a single unit, or the split units linked.
-int jit_build(const std::vector<Compiled>& ch, int block, bool mixed, std::vector<char>* cubin, std::string* log);
-int jit_prepare(const std::vector<Compiled>& ch, int block, bool mixed, int device, void** fn, std::string* err);
+int jit_build(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed, std::vector<char>* cubin,
+              std::string* log);
+int jit_prepare(const std::vector<Compiled>& ch, int block, int min_blocks, bool mixed, int device, void** fn,
+                std::string* err);
 int jit_occupancy(void* fn, int block, size_t smem, int* per_sm);
 int jit_launch(void* fn, const LaunchParams& lp, int grid, size_t smem, void* stream, std::string* err);
 // Whether a captured kernel node runs the compiled kernel fn.
