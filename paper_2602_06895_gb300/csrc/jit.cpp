@@ -74,33 +74,79 @@ bool all_finite(const std::vector<double>& v) {
     return true;
 }
 
+// The invariants s = q^2 of a channel's SDE weights, each computed once per event: the channel
+// weights of all other channels (one PS_OP_CHANNEL_WEIGHT each) share most of their momentum
+// sums (81 distinct among 110 propagators in a 2->8 channel). An invariant is named by how it
+// is formed (kind, p_a, the summed slots in order); the expression is the one the interpreter
+// evaluates, so the values are the same bits.
+struct InvariantMemo {
+    std::map<std::string, std::string> names;           // formation -> variable
+    std::map<std::string, std::vector<int32_t>> reads;  // formation -> slots it reads
+    int next = 0;
+    // an op wrote slots [o, o + 4): forget the invariants that read them
+    void written(int32_t o) {
+        for (auto it = reads.begin(); it != reads.end();) {
+            bool hit = false;
+            for (int32_t r : it->second) hit |= (r >= o && r < o + 4);
+            if (hit) {
+                names.erase(it->first);
+                it = reads.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+};
+
 // The SDE weight of another channel (PS_OP_CHANNEL_WEIGHT: k, p_a, q_1..q_k, (kind, mask, M,
-// Gamma)...) as straight-line code: the momentum sums over each mask written out, the
-// propagator arithmetic from the interpreter's sde_factor.
-std::string channel_weight_source(const Compiled& C, const int32_t* a, int na, bool mixed) {
+// Gamma)...) as straight-line code: each propagator's invariant from the memo (declared in *decl
+// before the op's block at its first use), the propagator arithmetic from the interpreter's
+// sde_factor_s.
+std::string channel_weight_source(const Compiled& C, const int32_t* a, int na, bool mixed, InvariantMemo* memo,
+                                  std::string* decl) {
     auto imm = [&](int32_t arg) { return C.imm[~arg]; };
     const int k = static_cast<int>(imm(a[0]));
     const int32_t out = a[na];
+    const std::string ldp = mixed ? "dev::mx::ldp(f, " : "dev::ldp(f, ";
     std::string s = "                {";
-    if (mixed) s += " const dev::mx::F4 pa = dev::mx::ldp(f, " + std::to_string(a[1]) + "); float acc = 1.0f; int ex = 0;\n";
-    else s += " const dev::P4 pa = dev::ldp(f, " + std::to_string(a[1]) + "); double den = 1.0, P = 1.0;\n";
+    s += mixed ? " float acc = 1.0f; int ex = 0;\n" : " double den = 1.0, P = 1.0;\n";
     for (int j = 2 + k; j + 3 < na; j += 4) {
         const int kind = static_cast<int>(imm(a[j]));
         const int mask = static_cast<int>(imm(a[j + 1]));
         const double M = imm(a[j + 2]), G = imm(a[j + 3]);
-        s += mixed ? "                  { dev::mx::F4 q = " : "                  { dev::P4 q = ";
-        s += kind == 1 ? "pa;" : (mixed ? "dev::mx::F4{0.0f, 0.0f, 0.0f, 0.0f};" : "dev::P4{0.0, 0.0, 0.0, 0.0};");
-        for (int i = 0; i < k; ++i) {
-            if (!((mask >> i) & 1)) continue;
-            const std::string ld = (mixed ? "dev::mx::ldp(f, " : "dev::ldp(f, ") + std::to_string(a[2 + i]) + ")";
-            if (mixed) s += std::string(" q = dev::mx::") + (kind == 1 ? "f4_sub" : "f4_add") + "(q, " + ld + ");";
-            else s += std::string(" q = dev::") + (kind == 1 ? "p4_sub" : "p4_add") + "(q, " + ld + ");";
+        std::string form = std::to_string(kind) + (kind == 1 ? ":" + std::to_string(a[1]) : std::string());
+        std::vector<int32_t> reads;
+        if (kind == 1) reads.push_back(a[1]);
+        for (int i = 0; i < k; ++i)
+            if ((mask >> i) & 1) {
+                form += "," + std::to_string(a[2 + i]);
+                reads.push_back(a[2 + i]);
+            }
+        auto it = memo->names.find(form);
+        std::string var;
+        if (it != memo->names.end()) {
+            var = it->second;
+        } else {
+            var = "cw" + std::to_string(memo->next++);
+            std::string q = kind == 1 ? ldp + std::to_string(a[1]) + ")"
+                                      : (mixed ? "dev::mx::F4{0.0f, 0.0f, 0.0f, 0.0f}" : "dev::P4{0.0, 0.0, 0.0, 0.0}");
+            for (int i = 0; i < k; ++i) {
+                if (!((mask >> i) & 1)) continue;
+                const std::string fn = mixed ? (kind == 1 ? "dev::mx::f4_sub(" : "dev::mx::f4_add(")
+                                             : (kind == 1 ? "dev::p4_sub(" : "dev::p4_add(");
+                q = fn + q + ", " + ldp + std::to_string(a[2 + i]) + "))";
+            }
+            *decl += mixed ? "                const float " + var + " = dev::mx::sde_sq(" + q + ");\n"
+                           : "                const double " + var + " = dev::p4_sq(" + q + ");\n";
+            memo->names[form] = var;
+            memo->reads[form] = reads;
         }
         if (mixed)
-            s += " dev::mx::sde_factor(acc, ex, q, " + std::to_string(kind) + ", static_cast<float>(" + hexlit(M) +
-                 "), static_cast<float>(" + hexlit(G) + ")); }\n";
+            s += "                  dev::mx::sde_factor_s(acc, ex, " + var + ", " + std::to_string(kind) +
+                 ", static_cast<float>(" + hexlit(M) + "), static_cast<float>(" + hexlit(G) + "));\n";
         else
-            s += " dev::sde_factor(den, P, q, " + std::to_string(kind) + ", " + hexlit(M) + ", " + hexlit(G) + "); }\n";
+            s += "                  dev::sde_factor_s(den, P, " + var + ", " + std::to_string(kind) + ", " + hexlit(M) +
+                 ", " + hexlit(G) + ");\n";
     }
     s += mixed ? "                  dev::st(f, " + std::to_string(out) + ", dev::mx::sde_weight(acc, ex)); }\n"
                : "                  dev::st(f, " + std::to_string(out) + ", P / den); }\n";
@@ -129,14 +175,19 @@ std::string channel_body(const Compiled& C, size_t c, bool mixed) {
     s += "                const dev::RegFrame<" + std::to_string(std::max(C.n_slots, 1)) + ", I" + cs + "> f{};\n";
     s += "                dev::load_inputs(f, lp, " + cs + ", " + std::to_string(C.n_random) + ", ev, local, active);\n";
     size_t pc = 0;
+    InvariantMemo memo;
     while (pc < C.code.size() && C.code[pc] != kOpOutput) {
         const int op = C.code[pc], na = C.code[pc + 1], no = C.code[pc + 2];
         const int32_t* a = C.code.data() + pc + 3;
         if (op == PS_OP_CHANNEL_WEIGHT) {  // unrolled here: counts, kinds and masks are known now
-            s += channel_weight_source(C, a, na, mixed);
+            std::string decl;
+            const std::string body = channel_weight_source(C, a, na, mixed, &memo, &decl);
+            s += decl + body;
+            for (int i = 0; i < no; ++i) memo.written(a[na + i]);
             pc += 3 + na + no;
             continue;
         }
+        for (int i = 0; i < no; ++i) memo.written(a[na + i]);
         s += "                {";
         s += na ? " constexpr int32_t a[] = {" + ints(a, na) + "};" : " const int32_t* a = nullptr;";
         s += no ? " constexpr int32_t o[] = {" + ints(a + na, no) + "};" : " const int32_t* o = nullptr;";

@@ -255,13 +255,18 @@ __device__ __forceinline__ int op_int(double v) {
 // One propagator denominator of an SDE channel weight (Sec. 2.1): kind 1 a t-channel 1/(t - M^2)^2,
 // kind 0 an s-channel 1/((s - M^2)^2 + M^2 Gamma^2); the product is kept in range by dividing
 // it out into P.  P_j = P / den at the end.
-__device__ __forceinline__ void sde_factor(double& den, double& P, const P4& q, int kind, double M, double G) {
-    const double d = p4_sq(q) - M * M, mg = M * G;
+// The factor from the invariant s = q^2 (a compiled channel computes each distinct invariant once
+// and shares it between the channels whose propagators use it).
+__device__ __forceinline__ void sde_factor_s(double& den, double& P, double s, int kind, double M, double G) {
+    const double d = s - M * M, mg = M * G;
     den *= (kind == 1) ? d * d : fma(d, d, mg * mg);
     if (above_pos_bits(den, 1e200)) {  // keep the running product in range
         P /= den;
         den = 1.0;
     }
+}
+__device__ __forceinline__ void sde_factor(double& den, double& P, const P4& q, int kind, double M, double G) {
+    sde_factor_s(den, P, p4_sq(q), kind, M, G);
 }
 
 // One instruction of the FP64 interpreter on frame Fr (the shared-memory slot file of the
@@ -707,13 +712,16 @@ __device__ __forceinline__ void stp(const RegFrame<NS, Imm>& f, int slot, F4 p) 
 namespace mx {
 // The FP32 form of sde_factor: the product as a float mantissa in [1, 2) and an integer exponent
 // (no FP64 work per propagator); sde_weight turns it into P_j = 1/(acc 2^ex) once per channel.
-__device__ __forceinline__ void sde_factor(float& acc, int& ex, const F4& q, int kind, float M, float G) {
-    const float s = fmaf(q.e, q.e, -fmaf(q.x, q.x, fmaf(q.y, q.y, q.z * q.z)));
+__device__ __forceinline__ float sde_sq(const F4& q) { return fmaf(q.e, q.e, -fmaf(q.x, q.x, fmaf(q.y, q.y, q.z * q.z))); }
+__device__ __forceinline__ void sde_factor_s(float& acc, int& ex, float s, int kind, float M, float G) {
     const float d = s - M * M, mg = M * G;
     acc *= (kind == 1) ? d * d : fmaf(d, d, mg * mg);
     const int bits = __float_as_int(acc);  // acc = 1.m 2^e with e moved into ex
     ex += ((bits >> 23) & 0xFF) - 127;
     acc = __int_as_float((bits & 0x807FFFFF) | 0x3F800000);
+}
+__device__ __forceinline__ void sde_factor(float& acc, int& ex, const F4& q, int kind, float M, float G) {
+    sde_factor_s(acc, ex, sde_sq(q), kind, M, G);
 }
 // 1 / (acc 2^ex) with 2^-ex built from its bits (|ex| stays far below 1022 here)
 __device__ __forceinline__ double sde_weight(float acc, int ex) {

@@ -38,3 +38,17 @@ def test_split_program_compiles_and_links(monkeypatch):
     monkeypatch.setenv("PS_JIT_PTXAS_VERBOSE", "1")
     log = ps.jit_check(W.multichannel_2to5(), 128, "f64")
     assert "ps_jit_map" in log, log
+
+
+def test_channel_weight_invariants_named_once(monkeypatch, tmp_path):
+    """The generated channel weights of the six 2->5 channels declare each distinct invariant once
+    (110 propagator factors over 35 momentum sums) and reuse it; a write to a slot an invariant
+    reads would end its reuse."""
+    dump = tmp_path / "src.cu"
+    monkeypatch.setenv("PS_JIT_DUMP", str(dump))
+    ps.jit_check(W.multichannel_2to5(), 128, "f64")
+    src = dump.read_text()
+    decls = re.findall(r"const double (cw\d+) = dev::p4_sq\(", src)
+    uses = re.findall(r"dev::sde_factor_s\(den, P, (cw\d+),", src)
+    assert len(uses) == 110 and len(decls) == 35  # the names restart in each channel's scope
+    assert set(uses) == set(decls)
