@@ -12,7 +12,12 @@ channel, the Jacobian product, integrand, cut_unphysical, SoA stores of the even
 events on the launching stream with the outputs resident in HBM; `e2e` adds the
 device->host read of the whole event record into pinned host memory every step.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Every timed map runs the program compiled at creation (NVRTC, the slot file in registers;
+programs of more than six channels compiled one unit per channel and linked); `--no-jit` runs
+the interpreter kernel instead, and the main leg reports the interpreter's time beside it.
+Compile times fall outside the timed regions.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-jit]
 """
 from __future__ import annotations
 

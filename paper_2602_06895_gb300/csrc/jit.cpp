@@ -8,6 +8,11 @@
 // cancel the float<->double round trips of the mixed form.  The tile loop, inputs, outputs and
 // per-tile sums are the interpreter's (map_tiles).  Modules are cached per device and source.
 //
+// A program of many channels is written as one relocatable unit per channel and a kernel unit
+// that dispatches on the channel; NVRTC compiles the units concurrently on host threads (each
+// thread its own NVRTC program) and nvJitLink links them into one kernel.  A requested number of
+// CTAs per SM becomes the kernel's launch bounds and the channel units' register cap.
+//
 // The driver API (module load, launch, occupancy) is opened with dlopen at first use, so the
 // library also loads on machines without a GPU driver.
 #include <cuda.h>
@@ -428,7 +433,13 @@ int build_plan(const Plan& p, std::vector<char>* cubin, std::string* log) {
     };
     const size_t hw = std::max(1u, std::thread::hardware_concurrency());
     std::vector<std::thread> pool;
-    for (size_t t = 1; t < std::min(n, hw); ++t) pool.emplace_back(worker);
+    for (size_t t = 1; t < std::min(n, hw); ++t) {
+        try {
+            pool.emplace_back(worker);
+        } catch (...) {  // no more threads: the ones started (and this one) share the rest
+            break;
+        }
+    }
     worker();
     for (std::thread& t : pool) t.join();
     int st = PS_OK;
