@@ -202,6 +202,31 @@ def timed(torch, fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
+def vegas_all_dims_leg(ps, W, torch, stream, local, jit, reps=3):
+    """The 2->4 workload with VEGAS on all 10 random dimensions instead of 8: the two angles of the
+    second W decay, on which the integrand does not depend, are mapped too.  Adapted like the
+    8-dim grid (10 x 1e6 events, alpha 1.5), then 1e7 events per step; the ESS fraction shows what
+    the two extra dimensions change."""
+    ch = W.ww_hadronic(vegas_dims=10)
+    prog = ps.program_for([ch], device=local)
+    prog.vegas_training(True)
+    out, ws = prog.alloc([VEGAS_EVENTS], 6, device=local)
+    for it in range(VEGAS_ITERS):
+        prog.generate([VEGAS_EVENTS], 7_000_000 + it, out, ws)
+        prog.vegas_adapt(0, alpha=1.5)
+    grid = prog.get_vegas(0, 10)
+    del prog, out, ws
+    tprog = ps.program_for([ch], device=local, jit=jit)
+    tprog.set_vegas(0, grid)
+    out, ws = tprog.alloc([EVENTS], 6, device=local)
+    ms = timed(torch, lambda: tprog.generate([EVENTS], SEED, out, ws), reps, stream)
+    st = tprog.stats()[0]
+    ess = st["sum_w"] ** 2 / st["sum_w2"]
+    return {"workload": "the main workload with VEGAS on all 10 dimensions (10 x 64 bins)", "events": EVENTS,
+            "ms_per_step": ms, "events_per_s": EVENTS / (ms / 1e3), "ess_fraction": ess / EVENTS,
+            "effective_events_per_s": ess / (ms / 1e3), "integral": st["sum_w"] / st["n"]}
+
+
 def c1_leg(ps, W, torch, stream, local, events=100_000, reps=20):
     """2->2 at fixed sqrt(s) = 1000 GeV (two_body_decay of p0 = (1000, 0, 0, 0)): the phase-space
     volume (every weight is 1/(8 pi)) and the integral of 1 + cos^2(theta) (closed form 1/(6 pi)),
@@ -896,6 +921,7 @@ def main():
         streamed["mixed_precision"]["speedup_vs_fp64"] = streamed["ms_total"] / sm["ms_total"]
 
     c1 = c1_leg(ps, W, torch, stream, local) if rank == 0 else None
+    dv10 = vegas_all_dims_leg(ps, W, torch, stream, local, jit) if rank == 0 else None
 
     c5imp = None
     if not args.no_c5_importance and rank == 0:
@@ -946,7 +972,7 @@ def main():
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
             "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi, "streamed_2to8": streamed,
-            "importance_2to8": c5imp, "fixed_2to2": c1, "flow": flow, "unweighting": unweight, "global_multichannel": glob}
+            "importance_2to8": c5imp, "fixed_2to2": c1, "vegas_all_10_dims": dv10, "flow": flow, "unweighting": unweight, "global_multichannel": glob}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

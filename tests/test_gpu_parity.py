@@ -360,6 +360,7 @@ def test_full_size_sampled(torch_cuda):
     assert abs(s["max_w"] / full["w"][k] - 1.0) <= weight_tol(orc_k)[0]
     assert np.array_equal(w == 0, full["w"] == 0)
     assert prog.status()["nonfinite"] == 0
+    assert prog.status()["cut"] == 0  # the stable forms leave cut_unphysical nothing to cut
 
 
 def _multichannel_full_size(torch, chans, counts, seed, offset, block, ctas, per_channel, label):
@@ -375,6 +376,7 @@ def _multichannel_full_size(torch, chans, counts, seed, offset, block, ctas, per
     st = prog.stats()
     assert [s["n"] for s in st] == counts
     assert prog.status()["nonfinite"] == 0
+    assert prog.status()["cut"] == 0  # the stable forms leave cut_unphysical nothing to cut
     rng = np.random.default_rng(seed)
     col = 0
     for c, n in enumerate(counts):
