@@ -1,6 +1,6 @@
 """Oracle checks on the 24-channel 2->8 workload (six massless and two 173 GeV particles, t-chains
 and s-channel trees from the builder; workloads.channels_2to8): four-momentum conservation and
-on-shell masses to 1e-12 relative (the spec bar), finite non-negative weights, and the
+on-shell masses to 1e-12 relative (the parity bar of the FP64 path), finite non-negative weights, and the
 forward -> inverse round trip in the partonic frame."""
 import numpy as np
 import pytest
