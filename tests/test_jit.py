@@ -52,3 +52,23 @@ def test_channel_weight_invariants_named_once(monkeypatch, tmp_path):
     uses = re.findall(r"dev::sde_factor_s\(den, P, (cw\d+),", src)
     assert len(uses) == 110 and len(decls) == 35  # the names restart in each channel's scope
     assert set(uses) == set(decls)
+
+
+def test_cta_request_becomes_launch_bounds(monkeypatch, tmp_path):
+    """A program asking for k CTAs per SM gets a compiled kernel that fits them: launch bounds
+    (block, k) on the kernel and, in the split form, the matching register cap on the channel
+    units (65536 / (128 x 4) = 128 registers)."""
+    dump = tmp_path / "src.cu"
+    monkeypatch.setenv("PS_JIT_DUMP", str(dump))
+    monkeypatch.setenv("PS_JIT_SPLIT", "1")
+    import ctypes as C
+
+    chans = W.multichannel_2to5()
+    graphs = [ps.build_channel(chans, c) for c in range(len(chans))]
+    hs = (C.c_void_p * len(graphs))(*[g.h.value for g in graphs])
+    opt = ps.Options(128, 4, ps.PRECISION["f64"], ps.PS_PROGRAM_JIT)
+    log = C.create_string_buffer(1 << 16)
+    assert ps.lib().ps_jit_check(hs, len(graphs), C.byref(opt), log, len(log)) == 0, log.value
+    src = dump.read_text()
+    assert "__launch_bounds__(128, 4)" in src
+    assert src.rstrip().endswith("// maxrregcount 128")
