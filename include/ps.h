@@ -244,7 +244,9 @@ typedef struct {
  * the interpreter up to the rounding of fused multiply-adds across op boundaries.  Programs of
  * more than six channels are compiled one unit per channel, in parallel on host threads, and
  * linked (nvJitLink) into one kernel.  Creation fails (PS_ERR_GRAPH with the compiler's message,
- * PS_ERR_CUDA) if the kernel cannot be built; kernels are cached per device and source. */
+ * PS_ERR_CUDA) if the kernel cannot be built.  Compiled kernels (and the split form's channel
+ * units) are cached per device and source for the life of the process: a second program with
+ * the same channels and options costs no compilation, and the cached modules are never unloaded. */
 #define PS_PROGRAM_JIT 1
 
 /* Generate and compile (NVRTC, no device needed) the kernel a program with these graphs and
