@@ -62,6 +62,9 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07
 COMPILED_COUNTERS = {"instr": 716.8, "flops": 1122.4, "dram": 185.9, "pipe": 0.854}
 INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
                         "pipe": 0.854}
+# FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from
+# the ncu captures of one 2^20-event launch (profiles/ps_jit_map_c5_2to8.md, ps_map_kernel_c5_2to8.md).
+C5_FP64_INSTR_PER_EVENT = {"compiled": 4596.1, "interpreter": 6559.0}
 
 
 def parse():
@@ -349,6 +352,13 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
            "nonzero_fraction": acc[:, 1].sum() / n_ev,
            "kernel": "compiled program (24 channel units, NVRTC in parallel, nvJitLink)" if jit else "interpreter",
            "setup_s": t_compile}
+    if precision == "f64":  # the FP64 pipe's roofline, from this workload's ncu instruction counts
+        instr = C5_FP64_INSTR_PER_EVENT["compiled" if jit else "interpreter"]
+        achieved = instr * res["value"] / world / 1e9
+        res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GINSTR,
+                           "unit": "G FP64-pipe instructions/s", "frac": achieved / FP64_PEAK_GINSTR,
+                           "fp64_instr_per_event": instr,
+                           "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz"}
     if table is not None:
         res["autotune_table"] = table
     if host_copy:
