@@ -3,6 +3,8 @@ host (no device), and keeps every slot in registers (no local-memory frame beyon
 library's, no spills)."""
 import re
 
+import pytest
+
 from paper_2602_06895_gb300 import ps
 from paper_2602_06895_gb300 import workloads as W
 
@@ -31,12 +33,13 @@ def test_compiled_channel_weights_stay_in_registers(monkeypatch):
     assert spills == 0 and stack <= 64, log
 
 
-def test_split_program_compiles_and_links(monkeypatch):
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_split_program_compiles_and_links(monkeypatch, precision):
     """The split form (one NVRTC unit per channel, compiled in parallel as relocatable code, linked
     with nvJitLink into one kernel), forced on the six 2->5 channels."""
     monkeypatch.setenv("PS_JIT_SPLIT", "1")
     monkeypatch.setenv("PS_JIT_PTXAS_VERBOSE", "1")
-    log = ps.jit_check(W.multichannel_2to5(), 128, "f64")
+    log = ps.jit_check(W.multichannel_2to5(), 128, precision)
     assert "ps_jit_map" in log, log
 
 
