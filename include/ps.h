@@ -250,7 +250,10 @@ typedef struct {
 #define PS_PROGRAM_JIT 1
 
 /* Generate and compile (NVRTC, no device needed) the kernel a program with these graphs and
- * options would use under PS_PROGRAM_JIT; the compiler log goes to log[log_bytes]. */
+ * options would use under PS_PROGRAM_JIT; the compiler log goes to log[log_bytes].
+ * Diagnostics, read from the environment at each compilation: PS_JIT_DUMP=<file> writes the
+ * generated source (the split form's units joined); PS_JIT_PTXAS_VERBOSE=1 puts the register
+ * and spill report into the log; PS_JIT_SPLIT=1 or 0 forces or forbids the split form. */
 int ps_jit_check(const ps_graph* graphs, int n_ch, const ps_options* opt, char* log, size_t log_bytes);
 
 /* Compile n_ch graphs (channel c = graphs[c]) for `device`.  Every channel must declare
