@@ -75,3 +75,21 @@ def test_cta_request_becomes_launch_bounds(monkeypatch, tmp_path):
     src = dump.read_text()
     assert "__launch_bounds__(128, 4)" in src
     assert src.rstrip().endswith("// maxrregcount 128")
+
+
+def test_jit_check_rejects_bad_arguments():
+    """ps_jit_check returns an error status (never aborts) for a null graph list, a channel count
+    out of range, a null graph, or a log buffer that is missing while its size is not zero."""
+    import ctypes as C
+
+    L = ps.lib()
+    g = ps.build_channel([W.ww_hadronic()], 0)
+    one = (C.c_void_p * 1)(g.h.value)
+    opt = ps.Options(128, 0, ps.PRECISION["f64"], ps.PS_PROGRAM_JIT)
+    buf = C.create_string_buffer(256)
+    assert L.ps_jit_check(None, 1, C.byref(opt), buf, len(buf)) != 0
+    assert L.ps_jit_check(one, 0, C.byref(opt), buf, len(buf)) != 0
+    assert L.ps_jit_check(one, 1000, C.byref(opt), buf, len(buf)) != 0
+    assert L.ps_jit_check((C.c_void_p * 1)(None), 1, C.byref(opt), buf, len(buf)) != 0
+    assert L.ps_jit_check(one, 1, C.byref(opt), None, 16) != 0
+    assert "ps_jit_check" in L.ps_last_error().decode()
