@@ -317,7 +317,9 @@ int ps_map(ps_program p, int ch, int64_t batch, const double* r_dev, int64_t ld_
  * graph and instantiates it; ps_exec_launch replays it on `stream` with a new seed and event
  * offset, which it writes into the captured kernel nodes, so that successive replays draw new
  * events without a new capture.  The buffers given at creation must stay valid while the
- * executor is used.  Capture happens on a private stream of the program's device. */
+ * executor is used.  Capture happens on a private stream of the program's device.  A compiled
+ * program's kernel (PS_PROGRAM_JIT) is captured and updated through the CUDA driver API, since
+ * it comes from a module loaded at run time; the behaviour is the same. */
 typedef struct ps_exec_s* ps_exec;
 int ps_exec_create(ps_program p, const int64_t* events_per_ch, const ps_out_buffers* out, void* workspace,
                    size_t workspace_bytes, ps_exec* exec_out);
