@@ -67,6 +67,22 @@ INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EV
 C5_FP64_INSTR_PER_EVENT = {"compiled": 4596.1, "interpreter": 6559.0}
 
 
+def fp64_pipe_roofline(instr_per_event, events_per_s, flops_per_event=None):
+    """The FP64-pipe roofline object of a kernel: its FP64 arithmetic instructions per event (from
+    ncu) times its events per second (per GPU) against the derived issue peak; with flops per event
+    also the flop form against 1.25 TFLOP/s.  Unknown counters give null fields."""
+    achieved = None if instr_per_event is None else instr_per_event * events_per_s / 1e9
+    r = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GINSTR, "unit": "G FP64-pipe instructions/s",
+         "frac": None if achieved is None else achieved / FP64_PEAK_GINSTR,
+         "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz"}
+    if flops_per_event is not None or instr_per_event is not None:
+        gflops = None if flops_per_event is None else flops_per_event * events_per_s / 1e9
+        r["flops"] = {"achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                      "frac": None if gflops is None else gflops / FP64_PEAK_GFLOPS,
+                      "peak_source": "derived: 1.25 TFLOP/s FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
+    return r
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,11 +370,8 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
            "setup_s": t_compile}
     if precision == "f64":  # the FP64 pipe's roofline, from this workload's ncu instruction counts
         instr = C5_FP64_INSTR_PER_EVENT["compiled" if jit else "interpreter"]
-        achieved = instr * res["value"] / world / 1e9
-        res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GINSTR,
-                           "unit": "G FP64-pipe instructions/s", "frac": achieved / FP64_PEAK_GINSTR,
-                           "fp64_instr_per_event": instr,
-                           "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz"}
+        res["roofline"] = fp64_pipe_roofline(instr, res["value"] / world)
+        res["roofline"]["fp64_instr_per_event"] = instr
     if table is not None:
         res["autotune_table"] = table
     if host_copy:
@@ -951,18 +964,10 @@ def main():
     # the FP64-pipe roofline: FP64 arithmetic instructions issued per second against the pipe's
     # issue rate (a DADD or DMUL takes a slot exactly like a DFMA); the flop form beside it
     kc = COMPILED_COUNTERS if jit else INTERPRETER_COUNTERS
-    achieved = None if kc["instr"] is None else kc["instr"] * N / (ms / 1e3) / 1e9
-    gflops = None if kc["flops"] is None else kc["flops"] * N / (ms / 1e3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GINSTR,
-                "unit": "G FP64-pipe instructions/s", "frac": None if achieved is None else achieved / FP64_PEAK_GINSTR,
-                "traffic": None if kc["dram"] is None else kc["dram"] * N,
-                "kernel": "ps_jit_map (compiled program)" if jit else "ps_map_kernel<0> (interpreter)",
-                "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz",
-                "fp64_pipe_active_ncu": kc["pipe"],
-                "flops": {"achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                          "frac": None if gflops is None else gflops / FP64_PEAK_GFLOPS,
-                          "peak_source": "derived: 1.25 TFLOP/s FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)"},
-                "hbm_gbs": BYTES_PER_EVENT * N / (ms / 1e3) / 1e9}
+    roofline = fp64_pipe_roofline(kc["instr"], N / (ms / 1e3), flops_per_event=kc["flops"])
+    roofline.update({"traffic": None if kc["dram"] is None else kc["dram"] * N,
+                     "kernel": "ps_jit_map (compiled program)" if jit else "ps_map_kernel<0> (interpreter)",
+                     "fp64_pipe_active_ncu": kc["pipe"], "hbm_gbs": BYTES_PER_EVENT * N / (ms / 1e3) / 1e9})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

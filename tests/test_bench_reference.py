@@ -1,7 +1,8 @@
 """The benchmark's reference arm (the oracle timed on the host cores) keeps the one-line JSON
 contract without a GPU: the metric, unit and direction of the main arm, `impl`, a
 `cpu_baseline` of kind "oracle" describing the run, and an `e2e` object with no host-device
-bytes. Under several ranks only rank 0 runs and prints; the others exit without work."""
+bytes. Under several ranks only rank 0 runs and prints; the others exit without work. The FP64
+roofline arithmetic of the main arm is checked on its measured counters."""
 import json
 import os
 import subprocess
@@ -36,3 +37,18 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_exit_without_work():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_fp64_pipe_roofline_arithmetic():
+    """The roofline object of the main leg, from the measured counters of the compiled 2->4 kernel
+    (716.8 FP64 instructions, 1122.4 flops per event) at 6.28e8 events/s: 0.715 of the issue
+    peak (152 SMs x 2 per clock x 2.07 GHz) and 0.56 of 1.25 TFLOP/s."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    r = bench.fp64_pipe_roofline(716.8, 6.28e8, flops_per_event=1122.4)
+    assert r["bound"] == "alu" and abs(r["peak"] - 629.28) < 1e-9
+    assert abs(r["achieved"] - 450.15) < 0.01 and abs(r["frac"] - 0.7153) < 1e-4
+    assert abs(r["flops"]["frac"] - 0.5639) < 1e-4
+    n = bench.fp64_pipe_roofline(None, 6.28e8)
+    assert n["achieved"] is None and n["frac"] is None and "flops" not in n
