@@ -1695,39 +1695,40 @@ int ps_vegas_histogram(ps_program p, int ch, double* hist, void* stream) {
     return st;
 }
 
-// Lepage's rebinning of one dimension (Lepage 1978): 3-point smoothing of the bin importances,
-// normalisation, compression m_k = ((1 - d_k)/ln(1/d_k))^alpha and new edges holding equal
-// shares of sum m_k, interpolated linearly inside the old bins.
+// VEGAS grid refinement of one dimension (Lepage 1978; the adaptive VEGAS sampling of
+// Sec. 3.2.2).  The importance of a bin is the mean of its histogram entry and those of its
+// neighbours inside the grid; the shares d_k of these means are damped to
+// m_k = ((1 - d_k) / ln(1/d_k))^alpha.  Spread evenly across each old bin, m has a piecewise-linear
+// cumulative M(x); the new edge j is the point where M reaches j/N of its total, found by a
+// binary search over the old bins' cumulative ends.
 static void rebin_row(const double* h, const double* e, double* out, int N, double alpha) {
-    std::vector<double> sm(N), m(N);
-    double tot = 0.0;
+    std::vector<double> imp(N), cum(N + 1, 0.0);
+    double total = 0.0;
     for (int k = 0; k < N; ++k) {
-        double v;
-        if (N == 1) v = h[0];
-        else if (k == 0) v = (h[0] + h[1]) / 2.0;
-        else if (k == N - 1) v = (h[N - 2] + h[N - 1]) / 2.0;
-        else v = (h[k - 1] + h[k] + h[k + 1]) / 3.0;
-        sm[k] = v;
-        tot += v;
+        const int first = std::max(k - 1, 0), last = std::min(k + 1, N - 1);
+        double s = 0.0;
+        for (int i = first; i <= last; ++i) s += h[i];
+        imp[k] = s / static_cast<double>(last - first + 1);
+        total += imp[k];
     }
-    if (!(tot > 0.0)) { std::memcpy(out, e, sizeof(double) * (N + 1)); return; }
-    double msum = 0.0;
+    if (!(total > 0.0)) {  // nothing was sampled (or the sums overflowed): keep the grid
+        std::copy(e, e + N + 1, out);
+        return;
+    }
     for (int k = 0; k < N; ++k) {
-        double dk = sm[k] / tot;
-        m[k] = dk >= 1.0 ? 1.0 : (dk > 0.0 ? std::pow((1.0 - dk) / std::log(1.0 / dk), alpha) : 0.0);
-        msum += m[k];
+        const double d = imp[k] / total;
+        imp[k] = d <= 0.0 ? 0.0 : d >= 1.0 ? 1.0 : std::pow((1.0 - d) / -std::log(d), alpha);
+        cum[k + 1] = cum[k] + imp[k];
     }
-    const double share = msum / N;
     out[0] = e[0];
     out[N] = e[N];
-    int k = 0;
-    double below = 0.0;
     for (int j = 1; j < N; ++j) {
-        const double target = share * j;
-        while (k < N - 1 && below + m[k] < target) below += m[k++];
-        double frac = m[k] > 0.0 ? (target - below) / m[k] : 0.0;
-        frac = std::min(1.0, std::max(0.0, frac));
-        out[j] = e[k] + frac * (e[k + 1] - e[k]);
+        const double target = cum[N] * static_cast<double>(j) / static_cast<double>(N);
+        // the first old bin whose cumulative end reaches the target holds the new edge
+        const int k = std::min(static_cast<int>(std::lower_bound(cum.begin() + 1, cum.end(), target) - cum.begin()) - 1,
+                               N - 1);
+        const double u = imp[k] > 0.0 ? std::clamp((target - cum[k]) / imp[k], 0.0, 1.0) : 0.0;
+        out[j] = e[k] + u * (e[k + 1] - e[k]);
     }
 }
 

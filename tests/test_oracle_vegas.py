@@ -75,3 +75,89 @@ def test_accumulate_counts_bins(oracle_mod):
     h = oracle_mod.vegas_accumulate(r, w, 2, 4)
     assert np.array_equal(h[0], [5.0, 0.0, 0.0, 9.0])
     assert np.array_equal(h[1], [0.0, 0.0, 13.0, 1.0])
+
+
+def _refine_by_interp(h, e, alpha):
+    """The refinement rule restated with numpy: neighbour-mean importances, damped shares,
+    and the inverse of the piecewise-linear cumulative by linear interpolation."""
+    N = h.size
+    pad = np.concatenate([[0.0], h, [0.0]])
+    counts = np.full(N, 3.0)
+    counts[0] = counts[-1] = 2.0
+    if N == 1:
+        counts[:] = 1.0
+    s = (pad[:-2] + pad[1:-1] + pad[2:]) / counts
+    d = s / s.sum()
+    m = ((1.0 - d) / np.log(1.0 / d)) ** alpha
+    cum = np.concatenate([[0.0], np.cumsum(m)])
+    return np.interp(cum[-1] * np.arange(N + 1) / N, cum, e)
+
+
+def _mass_per_new_bin(h, e, new, alpha):
+    """Integral of the damped importance density (m_k spread evenly over old bin k) over
+    each new bin, and the total."""
+    N = h.size
+    pad = np.concatenate([[0.0], h, [0.0]])
+    counts = np.full(N, 3.0)
+    counts[0] = counts[-1] = 2.0
+    s = (pad[:-2] + pad[1:-1] + pad[2:]) / counts
+    d = s / s.sum()
+    m = np.zeros(N)
+    pos = d > 0
+    m[pos] = ((1.0 - d[pos]) / np.log(1.0 / d[pos])) ** alpha
+    dens = m / np.diff(e)
+    out = np.zeros(N)
+    for j in range(N):
+        a, b = new[j], new[j + 1]
+        lo = np.clip(e[:-1], a, b)
+        hi = np.clip(e[1:], a, b)
+        out[j] = np.sum(dens * (hi - lo))
+    return out, m.sum()
+
+
+def test_rebin_matches_interpolated_cumulative(oracle_mod):
+    """Random positive histograms on random grids, alpha 0.5 and 1.5: the oracle's new edges
+    equal the numpy restatement (cumulative of the damped weights inverted by np.interp)."""
+    rng = np.random.default_rng(17)
+    for alpha in (0.5, 1.5):
+        for trial in range(6):
+            N = int(rng.choice([4, 16, 64]))
+            e = W.vegas_grid_random(100 + trial, 1, N)
+            h = rng.gamma(0.7, 1.0, size=(1, N)) * 10.0 ** rng.uniform(-3, 3)
+            new = oracle_mod.vegas_rebin(h, e, alpha=alpha)[0]
+            ref = _refine_by_interp(h[0], e[0], alpha)
+            assert np.max(np.abs(new - ref)) <= 1e-13, (alpha, trial)
+
+
+def test_rebin_equalises_damped_mass(oracle_mod):
+    """The defining property of the refinement: every new bin holds 1/N of the damped
+    importance, with zero-importance bins and fixed end points included."""
+    rng = np.random.default_rng(23)
+    for alpha in (0.5, 1.0, 1.5):
+        for N in (3, 8, 64):
+            e = W.vegas_grid_random(200 + N, 1, N)
+            h = rng.exponential(1.0, size=(1, N))
+            h[0, rng.random(N) < 0.3] = 0.0
+            h[0, N // 2] = 1.0  # never all zero
+            new = oracle_mod.vegas_rebin(h, e, alpha=alpha)[0]
+            assert new[0] == e[0, 0] and new[-1] == e[0, -1]
+            assert np.all(np.diff(new) >= 0)
+            mass, tot = _mass_per_new_bin(h[0], e[0], new, alpha)
+            assert np.max(np.abs(mass / (tot / N) - 1.0)) <= 1e-12, (alpha, N)
+
+
+def test_rebin_hand_computed_four_bins(oracle_mod):
+    """N = 4 on the uniform grid with h = (0, 0, 3, 3): the neighbour means are (0, 1, 2, 3),
+    so d = (0, 1/6, 1/3, 1/2); at alpha = 1 the damped weights are m1 = (5/6)/ln 6,
+    m2 = (2/3)/ln 3, m3 = (1/2)/ln 2 and m0 = 0.  Each new edge sits where the running sum
+    of m reaches j/4 of the total, linearly inside its old bin of width 1/4."""
+    e = W.vegas_grid_uniform(1, 4)
+    new = oracle_mod.vegas_rebin(np.array([[0.0, 0.0, 3.0, 3.0]]), e, alpha=1.0)[0]
+    m1, m2, m3 = (5 / 6) / math.log(6), (2 / 3) / math.log(3), 0.5 / math.log(2)
+    q = (m1 + m2 + m3) / 4
+    assert q < m1 < 2 * q < m1 + m2 < 3 * q < m1 + m2 + m3  # edge j lies in old bin j
+    want = [0.0, 0.25 + 0.25 * q / m1, 0.5 + 0.25 * (2 * q - m1) / m2,
+            0.75 + 0.25 * (3 * q - m1 - m2) / m3, 1.0]
+    assert np.max(np.abs(new - np.array(want))) <= 1e-15
+    # numerically: 0.4910, 0.6778, 0.8446
+    assert np.allclose(new[1:4], [0.49098, 0.67778, 0.84463], atol=5e-5)
