@@ -349,8 +349,15 @@ int ps_stats(ps_program p, ps_channel_stats* host_out, int n_ch, void* stream);
  * ordered after it.  Errors: PS_ERR_INVALID_ARGUMENT for a null program, PS_ERR_CUDA. */
 int ps_stats_accumulate(ps_program p, int enable, void* stream);
 
-/* VEGAS training: while enabled, ps_generate also accumulates, per channel, mapped
- * dimension j and bin k, the sum of w^2 over events whose r_j falls in bin k. */
+/* VEGAS training (the adaptive sampling of Sec. 3.2.2, Lepage's grid refinement): while
+ * enabled, ps_generate, ps_map and executors also accumulate, per channel, mapped dimension j
+ * and bin k, the sum of w^2 over events whose r_j falls in bin k.  Two extra kernels per launch
+ * read the stored weights (the weight output is then required, else PS_ERR_INVALID_ARGUMENT) and
+ * add the sums in a fixed order: 128 equal slices of each channel's events, each summed in
+ * event order, then the slices in order.  The histogram, and every grid adapted from it, is
+ * therefore the same bit for bit for the same events, whatever the block size, CTA count or
+ * compiled form.  The first enable allocates the partial sums (n_channels x 128 x dims x bins
+ * doubles); PS_ERR_CAPACITY if dims > 64, bins > 256 or dims x bins > 4096. */
 int ps_vegas_training(ps_program p, int enable);
 /* Copy channel ch's accumulated histogram [dims][bins] (synchronises). */
 int ps_vegas_histogram(ps_program p, int ch, double* hist_host, void* stream);

@@ -1116,6 +1116,8 @@ struct ps_program_s {
     double* d_grid = nullptr;
     double* d_stats = nullptr;
     double* d_hist = nullptr;
+    double* d_hist_part = nullptr;    // training: per-(channel, chunk) partial histograms
+    int hist_stride = 0;              // doubles per partial histogram (largest dims x bins)
     unsigned long long* d_status = nullptr;
     int32_t* d_stats_mode = nullptr;  // nonzero: reductions add into d_stats (ps_stats_accumulate)
     double* h_stats = nullptr;        // host-mapped pinned copy of d_stats (read-back of ps_stats)
@@ -1151,6 +1153,7 @@ void free_device(ps_program p) {
     cudaFree(p->d_grid);
     cudaFree(p->d_stats);
     cudaFree(p->d_hist);
+    cudaFree(p->d_hist_part);
     cudaFree(p->d_status);
     cudaFree(p->d_stats_mode);
     if (p->h_stats) cudaFreeHost(p->h_stats);
@@ -1215,7 +1218,9 @@ int fill_launch(ps_program p, const int* chans, const int64_t* counts, int n, co
     lp->status = p->d_status;
     lp->stats_mode = p->d_stats_mode;
     lp->mixed = p->opt.precision == PS_PRECISION_MIXED ? 1 : 0;
-    lp->hist = p->training ? p->d_hist : nullptr;
+    lp->hist = (p->training && p->hist_total > 0) ? p->d_hist : nullptr;
+    if (lp->hist && tiles > 0 && (!out || !out->weight))
+        return fail(PS_ERR_INVALID_ARGUMENT, "VEGAS training reads the weights: the weight output is required");
     if (out) {
         const Compiled& C0 = p->ch[chans[0]];
         if (C0.n_momenta_out > 0 && out->momenta && out->ld < cols)
@@ -1433,6 +1438,7 @@ int ps_generate(ps_program p, const int64_t* events, uint64_t seed, uint64_t eve
         if (st != PS_OK) return fail(st, err);
     }
     st = ps::launch_reduce(lp, p->d_stats, stream, &err);
+    if (st == PS_OK && lp.n_tiles > 0) st = ps::launch_hist(lp, p->d_hist_part, p->hist_stride, stream, &err);
     if (st != PS_OK) return fail(st, err);
     return PS_OK;
 }
@@ -1444,6 +1450,7 @@ struct ps_exec_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t map_node = nullptr, reduce_node = nullptr;
+    std::vector<cudaGraphNode_t> hist_nodes;  // VEGAS training histogram kernels (training programs)
     ps::LaunchParams lp;
     double* stats = nullptr;
     int grid = 0;
@@ -1473,6 +1480,7 @@ int ps_exec_create(ps_program p, const int64_t* events, const ps_out_buffers* ou
     st = cuda_check(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
     if (st == PS_OK && e->lp.n_tiles > 0) st = launch_program_map(p, e->lp, cs, &err);
     if (st == PS_OK) st = ps::launch_reduce(e->lp, e->stats, cs, &err);
+    if (st == PS_OK && e->lp.n_tiles > 0) st = ps::launch_hist(e->lp, p->d_hist_part, p->hist_stride, cs, &err);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
@@ -1498,6 +1506,7 @@ int ps_exec_create(ps_program p, const int64_t* events, const ps_out_buffers* ou
             continue;
         }
         if (ps::is_reduce_kernel(kp.func)) e->reduce_node = nodes[k];
+        else if (ps::is_hist_kernel(kp.func)) e->hist_nodes.push_back(nodes[k]);
         else if (!p->jit_fn) e->map_node = nodes[k];
     }
     if (e->lp.n_tiles > 0 && !e->map_node) {
@@ -1530,8 +1539,20 @@ int ps_exec_launch(ps_exec e, uint64_t seed, uint64_t event_offset, void* stream
         st = cuda_check(cudaGraphExecKernelNodeSetParams(e->exec, e->map_node, &kp), "cudaGraphExecKernelNodeSetParams");
         if (st != PS_OK) return st;
     }
+    for (cudaGraphNode_t hn : e->hist_nodes) {  // the histogram kernels read the same seed and offsets
+        cudaKernelNodeParams kp;
+        int st = cuda_check(cudaGraphKernelNodeGetParams(hn, &kp), "cudaGraphKernelNodeGetParams");
+        if (st != PS_OK) return st;
+        double* part = e->p->d_hist_part;
+        int stride = e->p->hist_stride;
+        void* args[3] = {&e->lp, &part, &stride};
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        st = cuda_check(cudaGraphExecKernelNodeSetParams(e->exec, hn, &kp), "cudaGraphExecKernelNodeSetParams");
+        if (st != PS_OK) return st;
+    }
     int st = cuda_check(cudaGraphLaunch(e->exec, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
-    if (st == PS_OK) ps::count_launches(e->map_node ? 2 : 1);
+    if (st == PS_OK) ps::count_launches((e->map_node ? 2 : 1) + static_cast<int>(e->hist_nodes.size()));
     return st;
 }
 
@@ -1584,6 +1605,7 @@ int ps_map(ps_program p, int ch, int64_t batch, const double* r, int64_t ld_r, c
         if (st != PS_OK) return fail(st, err);
     }
     st = ps::launch_reduce(lp, p->d_stats + 5 * ch, stream, &err);
+    if (st == PS_OK && lp.n_tiles > 0) st = ps::launch_hist(lp, p->d_hist_part, p->hist_stride, stream, &err);
     if (st != PS_OK) return fail(st, err);
     return PS_OK;
 }
@@ -1680,6 +1702,22 @@ int ps_stats_accumulate(ps_program p, int enable, void* stream) {
 
 int ps_vegas_training(ps_program p, int enable) {
     if (!p) return fail(PS_ERR_INVALID_ARGUMENT, "ps_vegas_training: null program");
+    if (enable && p->hist_total > 0 && !p->d_hist_part) {
+        int stride = 0;
+        for (int c = 0; c < p->n_ch; ++c) {
+            const int dv = p->ch[c].vegas_dims;
+            if (dv == 0) continue;
+            const int bins = (p->grid_off[c + 1] - p->grid_off[c]) / dv - 1;
+            if (dv > ps::kHistMaxDims || bins > 256 || dv * bins > ps::kHistThreads * ps::kHistEntries)
+                return fail(PS_ERR_CAPACITY, "ps_vegas_training: VEGAS grid too large for the training histogram");
+            stride = std::max(stride, dv * bins);
+        }
+        DeviceGuard dg(p->device);
+        const size_t bytes = static_cast<size_t>(p->n_ch) * ps::kHistChunks * stride * sizeof(double);
+        int st = cuda_check(cudaMalloc(&p->d_hist_part, bytes), "cudaMalloc training histogram");
+        if (st != PS_OK) return st;
+        p->hist_stride = stride;
+    }
     p->training = enable != 0;
     return PS_OK;
 }

@@ -160,6 +160,88 @@ __global__ void __launch_bounds__(kReduceThreads) ps_reduce_kernel(const __grid_
     }
 }
 
+// ---------------------------------------------------------------- VEGAS training histogram
+// The importance sums of VEGAS training, sum of w^2 per (dimension, bin of the unmapped r), for
+// every channel of a launch, added in a fixed order so that an adaptation is reproducible bit for
+// bit and does not depend on how tiles were scheduled.  Chunk k of a channel is one CTA of the
+// first kernel: kHistChunks equal slices of the channel's events, walked in event order in blocks
+// of kHistThreads.  Each block stages w^2 (from the stored weights) and the bin of every mapped
+// dimension (the event's random numbers, regenerated from Philox or read back), then thread t adds,
+// in event order, the w^2 of the events that fall into its entries t, t + kHistThreads, ...  The
+// second kernel adds a channel's chunks in chunk order into the histogram.
+__global__ void __launch_bounds__(kHistThreads) ps_hist_partial_kernel(const __grid_constant__ LaunchParams lp,
+                                                                         double* part, int stride) {
+    const int c = blockIdx.y, k = blockIdx.x, tid = threadIdx.x;
+    const ChannelLaunch& C = lp.ch[c];
+    const int nb = C.vdims * C.vbins;
+    if (nb == 0) return;
+    __shared__ double s_w2[kHistThreads];
+    __shared__ uint8_t s_bin[kHistMaxDims * kHistThreads];
+    const int64_t len = (C.n_events + kHistChunks - 1) / kHistChunks;
+    const int64_t e0 = min(C.n_events, k * len), e1 = min(C.n_events, e0 + len);
+    double acc[kHistEntries];
+#pragma unroll
+    for (int i = 0; i < kHistEntries; ++i) acc[i] = 0.0;
+    for (int64_t base = e0; base < e1; base += kHistThreads) {
+        const int64_t e = base + tid;
+        if (e < e1) {
+            const double w = lp.w[C.col_off + e];
+            s_w2[tid] = w * w;
+            const int64_t ev = C.ev_offset + e;
+            for (int j = 0; j < C.vdims; j += 2) {
+                double r0, r1 = 0.5;
+                if (lp.r != nullptr) {
+                    r0 = lp.r[j * lp.ld_r + e];
+                    if (j + 1 < C.vdims) r1 = lp.r[(j + 1) * lp.ld_r + e];
+                } else {
+                    const uint4 o = rng::philox4x32_10(make_uint4(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32),
+                                                             static_cast<uint32_t>(c), static_cast<uint32_t>(j >> 1)),
+                                                  static_cast<uint32_t>(lp.seed), static_cast<uint32_t>(lp.seed >> 32));
+                    r0 = rng::unit_from_bits(o.y, o.x);
+                    r1 = rng::unit_from_bits(o.w, o.z);
+                }
+                s_bin[j * kHistThreads + tid] = static_cast<uint8_t>(min(max(static_cast<int>(r0 * C.vbins), 0), C.vbins - 1));
+                if (j + 1 < C.vdims)
+                    s_bin[(j + 1) * kHistThreads + tid] =
+                        static_cast<uint8_t>(min(max(static_cast<int>(r1 * C.vbins), 0), C.vbins - 1));
+            }
+        }
+        __syncthreads();
+        const int n = static_cast<int>(min(static_cast<int64_t>(kHistThreads), e1 - base));
+#pragma unroll
+        for (int i = 0; i < kHistEntries; ++i) {
+            const int idx = tid + i * kHistThreads;
+            if (idx < nb) {
+                const int j = idx / C.vbins, b = idx - j * C.vbins;
+                const uint8_t* bins = s_bin + j * kHistThreads;
+                double a = acc[i];
+                for (int t = 0; t < n; ++t)
+                    if (bins[t] == b) a += s_w2[t];
+                acc[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+    double* o = part + (static_cast<int64_t>(c) * kHistChunks + k) * stride;
+#pragma unroll
+    for (int i = 0; i < kHistEntries; ++i) {
+        const int idx = tid + i * kHistThreads;
+        if (idx < nb) o[idx] = acc[i];
+    }
+}
+
+__global__ void __launch_bounds__(kHistThreads) ps_hist_reduce_kernel(const __grid_constant__ LaunchParams lp,
+                                                                        const double* part, int stride) {
+    const int c = blockIdx.y;
+    const ChannelLaunch& C = lp.ch[c];
+    const int idx = blockIdx.x * kHistThreads + threadIdx.x;
+    if (idx >= C.vdims * C.vbins) return;
+    const double* q = part + static_cast<int64_t>(c) * kHistChunks * stride + idx;
+    double s = 0.0;
+    for (int k = 0; k < kHistChunks; ++k) s += q[static_cast<int64_t>(k) * stride];
+    lp.hist[C.hist_off + idx] += s;
+}
+
 size_t smem_bytes_for(const LaunchParams& lp) {
     size_t doubles = static_cast<size_t>(lp.smem_imm) + lp.smem_grid + static_cast<size_t>(lp.smem_slots) * lp.block +
                      4 * (lp.block / 32);
@@ -183,9 +265,13 @@ int max_ctas_per_sm(int block, size_t smem, int mixed, int* out, std::string* er
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", err);
+    if (dev < 0 || dev >= kMaxDevices) {
+        *err = "device index beyond the library's limit";
+        return PS_ERR_INVALID_ARGUMENT;
+    }
     {
         std::lock_guard<std::mutex> lock(mu);
-        int& cur = limit[dev < kMaxDevices ? dev : 0][mixed ? 1 : 0];
+        int& cur = limit[dev][mixed ? 1 : 0];
         if (static_cast<int>(smem) > cur) {
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", err);
@@ -213,6 +299,25 @@ int launch_reduce(const LaunchParams& lp, double* stats, void* stream, std::stri
     if (e != cudaSuccess) return cuda_fail(e, "ps_reduce_kernel launch", err);
     __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
     return PS_OK;
+}
+
+int launch_hist(const LaunchParams& lp, double* part, int stride, void* stream, std::string* err) {
+    if (lp.hist == nullptr || stride <= 0) return PS_OK;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    ps_hist_partial_kernel<<<dim3(kHistChunks, lp.n_ch), kHistThreads, 0, cs>>>(lp, part, stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ps_hist_partial_kernel launch", err);
+    ps_hist_reduce_kernel<<<dim3((stride + kHistThreads - 1) / kHistThreads, lp.n_ch), kHistThreads, 0, cs>>>(lp, part,
+                                                                                                            stride);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ps_hist_reduce_kernel launch", err);
+    __atomic_add_fetch(&g_launches, 2ULL, __ATOMIC_RELAXED);
+    return PS_OK;
+}
+
+bool is_hist_kernel(const void* func) {
+    return func == reinterpret_cast<const void*>(ps_hist_partial_kernel) ||
+           func == reinterpret_cast<const void*>(ps_hist_reduce_kernel);
 }
 
 // Copies the statistics into host-mapped pinned memory: the read-back of ps_stats uses no copy

@@ -998,7 +998,8 @@ __device__ __forceinline__ double store_outputs(const Fr& f, const int32_t* od, 
 // The persistent tile loop shared by the interpreter kernel and compiled kernels: tiles of
 // `block` events over all channels (tile -> channel by the prefix sums in the parameters), a
 // channel change stages the channel's shared data (pol.stage), every thread evaluates one event
-// (pol.event -> weight), then the VEGAS histogram (training) and the tile's partial sums.
+// (pol.event -> weight), then the tile's partial sums.  (The VEGAS training histogram is a separate
+// pass over the stored weights, in a fixed order.)
 template <class Policy>
 __device__ __forceinline__ void map_tiles(const LaunchParams& lp, Policy& pol, double* s_red) {
     const int B = lp.block;
@@ -1020,23 +1021,6 @@ __device__ __forceinline__ void map_tiles(const LaunchParams& lp, Policy& pol, d
         double w = pol.event(c, C, ev, local, active);
         if (!active) w = 0.0;
         if (active && !finite_bits(w)) atomicAdd(lp.status + 0, 1ULL);
-
-        // VEGAS training: sum of w^2 per (dimension, bin of the unmapped r)
-        if (lp.hist != nullptr && C.vdims > 0 && active) {
-            for (int j = 0; j < C.vdims; ++j) {
-                double r;
-                if (lp.r != nullptr) {
-                    r = lp.r[j * lp.ld_r + local];
-                } else {
-                    uint4 o = philox4x32_10(make_uint4(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32),
-                                                       static_cast<uint32_t>(c), static_cast<uint32_t>(j >> 1)),
-                                            static_cast<uint32_t>(lp.seed), static_cast<uint32_t>(lp.seed >> 32));
-                    r = (j & 1) ? unit_from_bits(o.w, o.z) : unit_from_bits(o.y, o.x);
-                }
-                int k = min(max(static_cast<int>(r * C.vbins), 0), C.vbins - 1);
-                atomicAdd(lp.hist + C.hist_off + j * C.vbins + k, w * w);
-            }
-        }
 
         // per-tile partial statistics: nonzero count, sum w, sum w^2, max w
         double v0 = (w != 0.0) ? 1.0 : 0.0, v1 = w, v2 = w * w, v3 = w;

@@ -14,6 +14,12 @@ namespace ps {
 constexpr int kMaxOutMomenta = 24;
 constexpr int kNoallocTiles = 131072;  // tiles of the allocation-free entry point's fixed scratch
 constexpr int kMaxDevices = 64;
+// VEGAS training histogram (kernels.cu): chunks per channel, threads per chunk, and the largest
+// grid it takes (dimensions x bins <= kHistThreads * kHistEntries, bins <= 256)
+constexpr int kHistChunks = 128;
+constexpr int kHistThreads = 256;
+constexpr int kHistEntries = 16;
+constexpr int kHistMaxDims = 64;
 
 // ---------------------------------------------------------------- graph IR
 struct Arg {
@@ -87,6 +93,10 @@ int build_inverse_plan(const ps_channel_desc* d, InvPlan* plan, std::string* err
 int launch_map(const LaunchParams& lp, int grid_ctas, size_t smem_bytes, void* stream, std::string* err);
 int launch_reduce(const LaunchParams& lp, double* stats_dev, void* stream, std::string* err);
 int launch_copy(double* dst, const double* src, int n, void* stream, std::string* err);
+// The VEGAS training histogram of a launch whose weights are stored (lp.hist non-null): partial
+// sums per (channel, chunk) into part [n_ch][kHistChunks][stride], then added in a fixed order.
+int launch_hist(const LaunchParams& lp, double* part, int stride, void* stream, std::string* err);
+bool is_hist_kernel(const void* func);
 void count_launches(int n);
 
 // Compiled programs (jit.cpp): the CUDA source of a program, NVRTC to a cubin (host only), the

@@ -7,13 +7,6 @@ sums into the global estimate: sum of (n, nonzero, sum w, sum w^2) and max of ma
 from __future__ import annotations
 
 
-def event_offset(rank, events_per_rank, first_step=0):
-    """First event id of `rank` in step `first_step` of a run in which every rank generates
-    `events_per_rank` events per step; ranks are interleaved per step so that every step covers
-    one contiguous range of world * events_per_rank ids."""
-    return first_step, rank * events_per_rank
-
-
 def step_offset(rank, world, events_per_rank, step):
     """Event id of the first event of `rank` in `step`: disjoint across ranks and steps."""
     return (step * world + rank) * events_per_rank

@@ -324,6 +324,47 @@ def test_vegas_training_histogram_and_rebin(torch_cuda):
     assert np.all(prog.vegas_histogram(0, 8) == 0.0)
 
 
+def test_vegas_adaptation_bit_reproducible(torch_cuda):
+    """VEGAS training sums the histogram in a fixed order: three adaptation rounds give the same
+    grid bit for bit when repeated, also with another block size and as a compiled program, and
+    a multichannel histogram does not depend on the launch shape either."""
+    ch = W.ww_hadronic()
+
+    def adapt(block, jit):
+        prog = ps.program_for([ch], block_threads=block, jit=jit)
+        prog.vegas_training(True)
+        B = 300_001
+        out, ws = prog.alloc([B], 6)
+        hists = []
+        for it in range(3):
+            prog.generate([B], 90 + it, out, ws)
+            torch_cuda.cuda.synchronize()
+            hists.append(prog.vegas_histogram(0, 8))
+            prog.vegas_adapt(0, alpha=1.5)
+        return prog.get_vegas(0, 8), hists
+
+    g0, h0 = adapt(128, False)
+    for block, jit in ((128, False), (64, False), (256, True)):
+        g, h = adapt(block, jit)
+        assert np.array_equal(g, g0), (block, jit)
+        for a, b in zip(h, h0):
+            assert np.array_equal(a, b), (block, jit)
+    chans = W.multichannel_2to5()
+    vch = [dict(c, vegas_dims=6) for c in chans]
+    counts = [1000, 20_000, 0, 7_777, 130, 50_000]
+    res = []
+    for block, cps in ((128, 0), (64, 3)):
+        prog = ps.program_for(vch, block_threads=block, ctas_per_sm=cps)
+        prog.vegas_training(True)
+        out, ws = prog.alloc(counts, 7, alpha=True)
+        prog.generate(counts, 5, out, ws)
+        torch_cuda.cuda.synchronize()
+        res.append([prog.vegas_histogram(c, 6) for c in range(6)])
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+    assert np.all(res[0][2] == 0) and np.all(res[0][1] > 0)
+
+
 def test_full_size_sampled(torch_cuda):
     """1e7 events of the 2->4 W W workload in the benchmark's launch configuration:
     sampled events against the oracle one by one, and the channel sums against a full

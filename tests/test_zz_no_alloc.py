@@ -74,3 +74,31 @@ def test_noalloc_multichannel_and_limit(torch_cuda):
     too_many[1] = 131072 * 128 + 1
     with pytest.raises(ps.PSError, match="exceed the fixed scratch"):
         prog.generate_noalloc(too_many, 1, got)
+
+
+def test_noalloc_exactly_at_the_limit(torch_cuda):
+    """Ragged channel counts whose tiles add up to exactly the fixed scratch (131072 tiles of
+    32 events here) run and match ps_generate with a caller workspace; one tile more is refused."""
+    chans = W.multichannel_2to5()
+    prog = ps.program_for(chans, block_threads=32)
+    counts = [31, 32_001, 0, 1_600_000 - 5, 5, 80_069 * 32 - 17]
+    tiles = sum(-(-c // 32) for c in counts)
+    assert tiles == 131072
+    ref, ws = prog.alloc(counts, 7, alpha=True)
+    prog.generate(counts, 4242, ref, ws)
+    ref_stats = prog.stats()
+    del ws
+    got, _ = prog.alloc(counts, 7, alpha=True)
+    prog.generate_noalloc(counts, 4242, got)
+    got_stats = prog.stats()
+    torch_cuda.cuda.synchronize()
+    assert torch_cuda.equal(got["weight"], ref["weight"])
+    _same(torch_cuda, got, ref)
+    for a, b in zip(got_stats, ref_stats):
+        assert a["n"] == b["n"] and a["n_nonzero"] == b["n_nonzero"]
+        for k in ("sum_w", "sum_w2", "max_w"):
+            assert abs(a[k] - b[k]) <= RTOL * abs(b[k]), k
+    over = list(counts)
+    over[2] = 1  # one more tile
+    with pytest.raises(ps.PSError, match="exceed the fixed scratch"):
+        prog.generate_noalloc(over, 4242, got)
