@@ -59,28 +59,115 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07
 # The same counters for the compiled program's kernel (ps_jit_map) on this workload, from its own
 # ncu capture (profiles/ps_jit_map_ww_2to4.md): DFMA 405.6 + DADD 113.6 + DMUL 197.6 = 716.8 FP64
 # arithmetic instructions (1122.4 flops) and 185.9 DRAM bytes per event; FP64 pipe 85.4 % active.
-COMPILED_COUNTERS = {"instr": 716.8, "flops": 1122.4, "dram": 185.9, "pipe": 0.854}
+# Re-captured on the current build (profiles/fp64_pipe_probes.md): the same 716.8, 793.8 FP64-pipe
+# instructions in all (conversions included), 185.3 DRAM bytes per event, pipe active 0.836 of the
+# elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
+COMPILED_COUNTERS = {"instr": 716.8, "flops": 1122.4, "dram": 185.3, "pipe": 0.836, "pipe_instr": 793.8}
 INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from
 # the ncu captures of one 2^20-event launch (profiles/ps_jit_map_c5_2to8.md, ps_map_kernel_c5_2to8.md).
 C5_FP64_INSTR_PER_EVENT = {"compiled": 4596.1, "interpreter": 6559.0}
+# The same for the compiled six-channel 2->5 program, from one 2e6-event launch in the benchmark's
+# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1116.1 + DADD 278.4 + DMUL 413.3.
+C3_FP64_INSTR_PER_EVENT = 1807.9
+# FP64-pipe instructions per call of CUDA's double functions on the GB300, from the ncu counters of
+# ps_fp64_probe's function loops less the empty loop (profiles/fp64_pipe_probes.md); an add or a
+# multiply is one.  They convert the oracle's operation counts into the pipe's work.
+FP64_PIPE_PER_CALL = {"add": 1.0, "mul": 1.0, "div": 5.0, "sqrt": 8.0, "exp": 15.0, "expm1": 19.0, "log": 28.0,
+                      "log1p": 28.3, "pow": 83.0, "atan": 27.9, "atan2": 34.3, "tan": 28.8, "sin": 18.0,
+                      "cos": 18.0}
+# The measured FP64 issue rate of this run (fp64_peak), once taken; the derived figure otherwise.
+_FP64_PEAK = {"value": None, "source": None}
+
+
+def fp64_peak(ps, torch, local, reps=5):
+    """The FP64 pipe's issue rate, measured: ps_fp64_probe's DFMA loop (eight independent chains
+    per thread, 8 CTAs of 256 threads per SM, ~56 ms per launch) timed with CUDA events on the
+    launching stream, median of `reps`; DADD and DMUL once each beside it."""
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    blocks, iters = sms * 8, 12000
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    n = 8.0 * iters * blocks * 256
+    res = {"sm_count": sms, "blocks": blocks, "iters": iters}
+    for kind, k in (("dfma", reps), ("dadd", 1), ("dmul", 1)):
+        ps.fp64_probe(kind, blocks, iters, sink, stream)
+        ts = []
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ps.fp64_probe(kind, blocks, iters, sink, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[kind + "_ginstr_per_s"] = n / (statistics.median(ts) / 1e3) / 1e9
+    _FP64_PEAK["value"] = res["dfma_ginstr_per_s"]
+    _FP64_PEAK["source"] = (f"measured: DFMA issue loop (ps_fp64_probe), {sms} SMs x 8 CTAs x 256 threads, "
+                            f"median of {reps} launches of {n:.3g} instructions")
+    res["derived_ginstr_per_s"] = FP64_PEAK_GINSTR
+    return res
 
 
 def fp64_pipe_roofline(instr_per_event, events_per_s, flops_per_event=None):
     """The FP64-pipe roofline object of a kernel: its FP64 arithmetic instructions per event (from
-    ncu) times its events per second (per GPU) against the derived issue peak; with flops per event
-    also the flop form against 1.25 TFLOP/s.  Unknown counters give null fields."""
+    ncu) times its events per second (per GPU) against the FP64 issue peak measured in this run
+    (fp64_peak; the derived 629.3 G/s if it was not taken); with flops per event also the flop form
+    against 1.25 TFLOP/s.  Unknown counters give null fields."""
     achieved = None if instr_per_event is None else instr_per_event * events_per_s / 1e9
-    r = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GINSTR, "unit": "G FP64-pipe instructions/s",
-         "frac": None if achieved is None else achieved / FP64_PEAK_GINSTR,
-         "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz"}
+    peak = _FP64_PEAK["value"] or FP64_PEAK_GINSTR
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP64-pipe instructions/s",
+         "frac": None if achieved is None else achieved / peak,
+         "peak_source": _FP64_PEAK["source"] or "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz",
+         "frac_of_derived_peak": None if achieved is None else achieved / FP64_PEAK_GINSTR}
     if flops_per_event is not None or instr_per_event is not None:
         gflops = None if flops_per_event is None else flops_per_event * events_per_s / 1e9
         r["flops"] = {"achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                       "frac": None if gflops is None else gflops / FP64_PEAK_GFLOPS,
                       "peak_source": "derived: 1.25 TFLOP/s FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
     return r
+
+
+def _r(x, nd=4):
+    return None if x is None else float(f"{x:.{nd}g}")
+
+
+def summary(line):
+    """The headline figures of every leg in one short object, placed last in the JSON line so that
+    a reader of the line's tail sees all of them."""
+    g = lambda d, *ks: None if d is None else (g(d.get(ks[0]), *ks[1:]) if len(ks) > 1 else d.get(ks[0]))
+    rf = line["roofline"]
+    out = {"fp64_2to4": {"events_per_s": _r(line["value"]), "fp64_pipe_frac": _r(rf["frac"], 3),
+                         "frac_of_derived_peak": _r(rf["frac_of_derived_peak"], 3), "e2e": _r(g(line, "e2e", "value")),
+                         "interpreter": _r(g(line, "interpreter", "value"))},
+           "fp64_peak_ginstr_per_s": _r(g(rf, "fp64_peak", "dfma_ginstr_per_s")),
+           "sm_count": g(rf, "fp64_peak", "sm_count"),
+           "method_pipe_equiv_per_event": _r(g(rf, "method", "fp64_pipe_equivalent_per_event")),
+           "mixed_2to4": {"events_per_s": _r(g(line, "mixed_precision", "value")),
+                          "speedup": _r(g(line, "mixed_precision", "speedup_vs_fp64"), 3)},
+           "multichannel_2to5": {"fp64": _r(g(line, "multichannel", "value")),
+                                 "fp64_pipe_frac": _r(g(line, "multichannel", "roofline", "frac"), 3),
+                                 "mixed": _r(g(line, "multichannel", "mixed_precision", "value"))},
+           "streamed_2to8": {"fp64": _r(g(line, "streamed_2to8", "value")),
+                             "fp64_pipe_frac": _r(g(line, "streamed_2to8", "roofline", "frac"), 3),
+                             "e2e": _r(g(line, "streamed_2to8", "e2e", "value")),
+                             "mixed": _r(g(line, "streamed_2to8", "mixed_precision", "value"))},
+           "neff_per_s_over_fp64_vegas_2to8": {
+               "mixed_vegas": _r(g(line, "importance_2to8", "mixed_n_eff_per_s_over_vegas_fp64"), 3),
+               "flows_mixed_map": _r(g(line, "importance_2to8", "flow_mixed_map_n_eff_per_s_over_vegas_fp64"), 3),
+               "flows_fp64_map": _r(g(line, "importance_2to8", "flow_n_eff_per_s_over_vegas_fp64"), 3)},
+           "flow_2to4": {"ess_fraction": _r(g(line, "flow", "ess_fraction_flow"), 4),
+                         "ess_fraction_vegas": _r(g(line, "flow", "ess_fraction_vegas"), 4),
+                         "ess_per_s_over_vegas": None if g(line, "flow", "ess_per_s_flow") is None else
+                         _r(line["flow"]["ess_per_s_flow"] / line["flow"]["ess_per_s_vegas"], 3),
+                         "sample_ms": _r(g(line, "flow", "sample_ms"), 3),
+                         "train_ms_per_step": _r(g(line, "flow", "train_ms_per_step"), 3),
+                         "train_steps": g(line, "flow", "train_steps")},
+           "unweighting_events_per_s": _r(g(line, "unweighting", "events_per_s")),
+           "global_multichannel_events_per_s": _r(g(line, "global_multichannel", "events_per_s")),
+           "cpu_oracle_events_per_s": _r(g(line, "cpu_baseline", "value")),
+           "cpu_cores": g(line, "cpu_baseline", "cores")}
+    return out
 
 
 def parse():
@@ -189,7 +276,14 @@ def cpu_baseline(events, grid, seconds_target=12.0):
     t1 = time.perf_counter()
     O.generate(ch, SEED, 0, 200_000, grid=grid, keep_momenta=True, threads=1)
     single = 200_000 / (time.perf_counter() - t1)
+    # the method's operations per event, counted by class in the oracle's own arithmetic (its
+    # operation-counting build), on 2e4 events of the same stream; with the FP64-pipe cost of each
+    # class on the GPU, the pipe work a literal evaluation of those operations would take
+    ops, _ = O.op_counts(ch, O.random(SEED, 0, 0, 20_000, O.dims(ch)), grid=grid)
+    pipe = sum(ops[k] * FP64_PIPE_PER_CALL[k] for k in FP64_PIPE_PER_CALL)
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "single_core_value": single,
+            "method_ops_per_event": {k: round(v, 2) for k, v in ops.items()},
+            "method_fp64_pipe_equivalent_per_event": pipe,
             "sample": f"{steps} consecutive steps of {events} events (seed {SEED}, events 0..{n - 1}) of the "
                       f"workload, full event record kept, {dt:.2f} s wall ({dt * threads:.0f} core-s) on "
                       f"{threads} OpenMP threads"}
@@ -373,7 +467,7 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
         res["roofline"] = fp64_pipe_roofline(instr, res["value"] / world)
         res["roofline"]["fp64_instr_per_event"] = instr
     if table is not None:
-        res["autotune_table"] = table
+        res["autotune_candidates"] = len(table)
     if host_copy:
         res["e2e"] = {"value": world * total / wall, "unit": "streamed events/s", "h2d_bytes_per_chunk": 16,
                       "d2h_bytes_per_chunk": int(d2h / len(plan)) + 40 * nc,
@@ -811,6 +905,9 @@ def main():
         interpreter = {"value": world * N / (ims / 1e3), "ms_per_step": ims, "kernel": "ps_map_kernel<0>"}
         del iprog
 
+    # the FP64 pipe's measured issue rate: the denominator of every FP64 roofline below
+    peak = fp64_peak(ps, torch, local)
+
     # end to end: same call, event record read back to pinned host memory every step
     e2e = None
     if not args.no_e2e:
@@ -899,12 +996,14 @@ def main():
                  "value": world * sum(counts) / (cms / 1e3), "unit": UNIT, "ms_per_step": cms,
                  "precision": "fp64", "map_launches_per_step": 1, "compiled": jit,
                  "gpu_launches": int(ps.launch_count() - l0), "cuda_graph": True,
-                 "autotuned": best, "autotune_table": table,
+                 "autotuned": best,
                  "integral": sum(c["sum_w"] for c in cst) / 1.0,
                  "integral_mean": sum(c["sum_w"] / c["n"] for c in cst if c["n"]),
                  "integral_sigma": math.sqrt(sum((c["sum_w2"] / c["n"] - (c["sum_w"] / c["n"]) ** 2) / c["n"]
-                                                 for c in cst if c["n"])),
-                 "per_channel_sum_w": [c["sum_w"] for c in cst]}
+                                                 for c in cst if c["n"]))}
+        # the FP64 pipe's roofline of the compiled program (instructions per event from its ncu capture)
+        multi["roofline"] = fp64_pipe_roofline(C3_FP64_INSTR_PER_EVENT if jit else None, multi["value"] / world)
+        multi["roofline"]["fp64_instr_per_event"] = C3_FP64_INSTR_PER_EVENT if jit else None
         # the mixed-precision form of the same step on the same events
         mbest, _ = ps.autotune(chans, [c // 8 for c in counts], precision="mixed",
                                blocks=(128,) if jit else (64, 128, 256), ctas=(2, 3, 4, 5, 6) if jit else (1, 2, 3, 4),
@@ -961,17 +1060,28 @@ def main():
     if not args.no_global and rank == 0:
         glob = global_leg(ps, W, torch, stream)
 
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(N, grid)
+
     # the FP64-pipe roofline: FP64 arithmetic instructions issued per second against the pipe's
-    # issue rate (a DADD or DMUL takes a slot exactly like a DFMA); the flop form beside it
+    # measured issue rate (a DADD or DMUL takes a slot exactly like a DFMA); the flop form beside it
     kc = COMPILED_COUNTERS if jit else INTERPRETER_COUNTERS
     roofline = fp64_pipe_roofline(kc["instr"], N / (ms / 1e3), flops_per_event=kc["flops"])
     roofline.update({"traffic": None if kc["dram"] is None else kc["dram"] * N,
                      "kernel": "ps_jit_map (compiled program)" if jit else "ps_map_kernel<0> (interpreter)",
-                     "fp64_pipe_active_ncu": kc["pipe"], "hbm_gbs": BYTES_PER_EVENT * N / (ms / 1e3) / 1e9})
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(N, grid)
+                     "fp64_pipe_active_ncu": kc["pipe"], "hbm_gbs": BYTES_PER_EVENT * N / (ms / 1e3) / 1e9,
+                     "fp64_peak": peak})
+    if kc.get("pipe_instr"):  # every FP64-pipe instruction (conversions included) against the same peak
+        roofline["pipe_instr_frac"] = kc["pipe_instr"] * N / (ms / 1e3) / 1e9 / roofline["peak"]
+    if cpu is not None:  # the method's work beside the executed instructions
+        meq = cpu["method_fp64_pipe_equivalent_per_event"]
+        roofline["method"] = {"fp64_pipe_equivalent_per_event": meq, "executed_per_event": kc["instr"],
+                              "executed_over_method": kc["instr"] / meq,
+                              "note": "the oracle's operations per event (cpu_baseline.method_ops_per_event) at "
+                                      "the GPU's FP64-pipe cost per operation class; the kernel issues fewer "
+                                      "(contracted multiply-adds, shared reciprocals, log x handed to the "
+                                      "densities, integer-ALU decisions)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -988,6 +1098,7 @@ def main():
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
             "cpu_baseline": cpu, "mixed_precision": mixed, "multichannel": multi, "streamed_2to8": streamed,
             "importance_2to8": c5imp, "fixed_2to2": c1, "vegas_all_10_dims": dv10, "flow": flow, "unweighting": unweight, "global_multichannel": glob}
+    line["summary"] = summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

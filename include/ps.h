@@ -540,6 +540,38 @@ int ps_unweight_select(const double* w, int64_t n, const double* w_max, uint64_t
 /* Number of kernel launches issued by the library since load (all programs). */
 int64_t ps_launch_count(void);
 
+/* ------------------------------------------------------------------------------------------
+ * FP64-pipe probes (no counterpart in the paper: they measure the device the FP64 kernels'
+ * roofline is stated against).  ps_fp64_probe launches `blocks` CTAs of 256 threads on
+ * `stream`; every thread runs `iters` iterations and writes one double to sink[] (device,
+ * blocks x 256 doubles, caller-owned).  Asynchronous; the caller times it with CUDA events.
+ *   PS_PROBE_DFMA/DADD/DMUL: eight independent chains of that instruction per iteration, i.e.
+ *     8 x iters x blocks x 256 FP64 instructions per launch (the issue rate's numerator);
+ *   PS_PROBE_EMPTY and the function kinds: one call of the function per iteration (sincospi:
+ *     one call, both results) with arguments spread over a fixed range, next to the empty loop;
+ *     the difference of their FP64-pipe instruction counters (a profiler's) over blocks x 256 x
+ *     iters is the function's FP64-pipe instructions per call.
+ * Returns PS_ERR_INVALID_ARGUMENT for an unknown kind, blocks < 1, iters < 1 or a null sink. */
+#define PS_PROBE_DFMA 0
+#define PS_PROBE_DADD 1
+#define PS_PROBE_DMUL 2
+#define PS_PROBE_EMPTY 9
+#define PS_PROBE_DIV 10
+#define PS_PROBE_SQRT 11
+#define PS_PROBE_RSQRT 12
+#define PS_PROBE_EXP 13
+#define PS_PROBE_EXPM1 14
+#define PS_PROBE_LOG 15
+#define PS_PROBE_LOG1P 16
+#define PS_PROBE_POW 17
+#define PS_PROBE_ATAN 18
+#define PS_PROBE_ATAN2 19
+#define PS_PROBE_TAN 20
+#define PS_PROBE_SIN 21
+#define PS_PROBE_COS 22
+#define PS_PROBE_SINCOSPI 23
+int ps_fp64_probe(int kind, int blocks, int iters, double* sink, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,17 +23,29 @@ _SRC = os.path.join(_HERE, "ps_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _PROBE = os.path.join(_HERE, "rounding_probe.h")
 _RLIB = os.path.join(_HERE, "liboracle_rounding.so")
+_FLIB = os.path.join(_HERE, "liboracle_fma.so")
+_FRLIB = os.path.join(_HERE, "liboracle_fma_rounding.so")
+_COUNT_H = os.path.join(_HERE, "op_count.h")
+_CLIB = os.path.join(_HERE, "liboracle_count.so")
 _lock = threading.Lock()
 _lib = None
 _rlib = None
+_flib = None
+_frlib = None
+_clib = None
 
 MAXN, MAXK, MAXP, MAXC, NAUX = 32, 10, 16, 32, 10
 AUX = {"shat": 0, "w_ps": 1, "f": 2, "jac_vegas": 3, "p_own": 4, "cut": 5, "fail": 6, "p_own_momenta": 7, "cond": 8, "cond_p": 9}
 
 
 def build(force=False):
-    """Compile ps_oracle.c into liboracle.so (gcc, -O2 -ffp-contract=off, OpenMP), and the
-    rounding-probe copy liboracle_rounding.so (rounding_probe.h force-included, no OpenMP)."""
+    """Compile ps_oracle.c into liboracle.so (gcc, -O2 -ffp-contract=off, OpenMP), the
+    rounding-probe copy liboracle_rounding.so (rounding_probe.h force-included, no OpenMP), and
+    liboracle_fma.so with multiply-adds contracted wherever the compiler may (-ffp-contract=fast;
+    on machines with a fused multiply-add instruction, e.g. aarch64, that is a second, equally
+    valid rounding of the same formulas), liboracle_fma_rounding.so (both: contracted and with
+    the rounding probe), and liboracle_count.so, compiled as C++ with op_count.h
+    force-included: the same arithmetic, with every operation counted by class."""
     src_time = max(os.path.getmtime(_SRC), os.path.getmtime(_PROBE))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
@@ -45,6 +57,22 @@ def build(force=False):
                "-o", _RLIB + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_RLIB + ".tmp", _RLIB)
+    if force or not os.path.exists(_FLIB) or os.path.getmtime(_FLIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-ffp-contract=fast", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+               "-o", _FLIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_FLIB + ".tmp", _FLIB)
+    if force or not os.path.exists(_FRLIB) or os.path.getmtime(_FRLIB) < src_time:
+        cmd = ["gcc", "-O2", "-ffp-contract=fast", "-fno-fast-math", "-fPIC", "-shared", "-include", _PROBE,
+               "-o", _FRLIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_FRLIB + ".tmp", _FRLIB)
+    ctime = max(os.path.getmtime(_SRC), os.path.getmtime(_COUNT_H))
+    if force or not os.path.exists(_CLIB) or os.path.getmtime(_CLIB) < ctime:
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-x", "c++",
+               "-DORC_BOOKKEEPING=0", "-include", _COUNT_H, "-o", _CLIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_CLIB + ".tmp", _CLIB)
     return _LIB
 
 
@@ -135,6 +163,59 @@ def rounding_lib():
             L.orc_rounding_seed.argtypes = [C.c_uint64]
             _rlib = L
     return _rlib
+
+
+def fma_lib():
+    """The oracle compiled with contracted multiply-adds (see build)."""
+    global _flib
+    with _lock:
+        if _flib is None:
+            build()
+            _flib = _setup(C.CDLL(_FLIB))
+    return _flib
+
+
+def count_lib():
+    """The operation-counting copy of the oracle (see op_count.h)."""
+    global _clib
+    with _lock:
+        if _clib is None:
+            build()
+            L = _setup(C.CDLL(_CLIB))
+            L.orc_count_classes.restype = C.c_int
+            L.orc_count_get.argtypes = [C.POINTER(C.c_ulonglong)]
+            _clib = L
+    return _clib
+
+
+OP_CLASSES = ("add", "mul", "div", "sqrt", "exp", "expm1", "log", "log1p", "pow", "atan", "atan2", "tan", "sin",
+              "cos", "cmp", "other")
+
+
+def op_counts(ch, r, grid=None, channels=None, chan=0):
+    """Operations of the forward map per event, by class (op_count.h), averaged over the points r
+    [B, d]: the method's arithmetic as the oracle performs it (condition-number bookkeeping
+    excluded).  Returns (counts per event as a dict, the forward result)."""
+    L = count_lib()
+    assert L.orc_count_classes() == len(OP_CLASSES)
+    L.orc_count_reset()
+    res = _forward(L, ch, r, grid, channels, chan, 1, False)
+    buf = (C.c_ulonglong * len(OP_CLASSES))()
+    L.orc_count_get(buf)
+    B = r.shape[0]
+    return {k: buf[i] / B for i, k in enumerate(OP_CLASSES)}, res
+
+
+def fma_rounding_lib():
+    """The oracle compiled with contracted multiply-adds and the rounding probe (see build)."""
+    global _frlib
+    with _lock:
+        if _frlib is None:
+            build()
+            L = _setup(C.CDLL(_FRLIB))
+            L.orc_rounding_seed.argtypes = [C.c_uint64]
+            _frlib = L
+    return _frlib
 
 
 def max_threads():
@@ -249,6 +330,21 @@ def _threads(threads):
 def forward(ch, r, grid=None, channels=None, chan=0, threads=None, aux=False):
     """Forward map of a batch: r [B, d] -> dict(mom [B, n+2, 4], x [B, 2], w [B], alpha [B], aux)."""
     return _forward(lib(), ch, r, grid, channels, chan, threads, aux)
+
+
+def forward_fma(ch, r, grid=None, channels=None, chan=0, threads=None):
+    """The forward map of the oracle compiled with contracted multiply-adds."""
+    return _forward(fma_lib(), ch, r, grid, channels, chan, threads, False)
+
+
+def forward_fma_perturbed(ch, r, seed, grid=None, channels=None, chan=0):
+    """One run of the oracle compiled with contracted multiply-adds and with every elementary-
+    function result moved by a random whole number of ulps in [-2, 2] (rounding_probe.h): a
+    second FP64 evaluation that differs from the plain oracle the way another machine's
+    compiler and libm can."""
+    L = fma_rounding_lib()
+    L.orc_rounding_seed(seed)
+    return _forward(L, ch, r, grid, channels, chan, 1, False)
 
 
 def rounding_spread(ch, r, grid=None, channels=None, chan=0, runs=8, base=None):

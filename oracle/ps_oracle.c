@@ -29,12 +29,21 @@
 #include <omp.h>
 #endif
 
+#ifdef __cplusplus  /* the operation-counting copy is compiled as C++ (op_count.h) */
+extern "C" {
+#endif
+
 #define ORC_PI 3.14159265358979323846
 #define ORC_MAXN 32   /* topology nodes per channel */
 #define ORC_MAXK 10   /* children per node (t-chain legs) */
 #define ORC_MAXP 16   /* propagators per channel in the multichannel table */
 #define ORC_MAXC 32   /* channels in the multichannel table */
 #define ORC_NAUX 10
+/* The condition numbers reported in aux[] (parity-test bookkeeping, not part of the method) are
+ * computed unless a build sets ORC_BOOKKEEPING to 0, as the operation-counting build does. */
+#ifndef ORC_BOOKKEEPING
+#define ORC_BOOKKEEPING 1
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* Topology description (oracle-private layout; filled by oracle/__init__.py) */
@@ -694,7 +703,7 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
         if (mhi < mlo) { fail = 1; smax = smin; }
         /* condition number of the range width: sqrt(s_r) / (m_max - m_min), with sqrt(s_r) = m_max + (the
          * masses subtracted); a rounding of the masses is amplified by it in the width */
-        {
+        if (ORC_BOOKKEEPING) {
             double top = mhi + (max_mass_sub);
             double wdt = mhi - mlo;
             double k = wdt > 0.0 ? top / wdt : 1e300;
@@ -708,10 +717,12 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
         sampled[j] = 1;
         if (nd->sde) {
             P_own *= prop_factor(sv, nd->M, nd->G);
-            /* a propagator near a narrow peak amplifies an ulp of s by 2 s |s-M^2| / ((s-M^2)^2 + M^2 G^2) */
-            double dd = sv - nd->M * nd->M;
-            double k = 2.0 * sv * fabs(dd) / (dd * dd + nd->M * nd->M * nd->G * nd->G);
-            if (k > cond) cond = k;
+            if (ORC_BOOKKEEPING) {
+                /* a propagator near a narrow peak amplifies an ulp of s by 2 s |s-M^2| / ((s-M^2)^2 + M^2 G^2) */
+                double dd = sv - nd->M * nd->M;
+                double k = 2.0 * sv * fabs(dd) / (dd * dd + nd->M * nd->M * nd->G * nd->G);
+                if (k > cond) cond = k;
+            }
         }
     }
 
@@ -742,7 +753,7 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
             double mx = sqrt(sts[i - 1]) - mi;
             double smax = mx > 0.0 ? mx * mx : 0.0;
             if (smax < smin) { fail = 1; smax = smin; }
-            {
+            if (ORC_BOOKKEEPING) {
                 double wdt = mx - msum;
                 double k = wdt > 0.0 ? sqrt(sts[i - 1]) / wdt : 1e300;
                 if (k > cond) cond = k;
@@ -759,10 +770,12 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
     if (ch->hadronic) {
         orc_r_to_x1x2(r[L.d_x], shat, ch->S, &x1, &x2, &j1);
         jac *= j1;
-        /* J_x = -log(tau)/S: shat carries up to ~30 ulps (an exponential of an argument up to
-         * log(S/a)), which 1/|log tau| amplifies as tau -> 1 */
-        double k = 30.0 / fabs(log(shat / ch->S));
-        if (k > cond) cond = k;
+        if (ORC_BOOKKEEPING) {
+            /* J_x = -log(tau)/S: shat carries up to ~30 ulps (an exponential of an argument up to
+             * log(S/a)), which 1/|log tau| amplifies as tau -> 1 */
+            double k = 30.0 / fabs(log(shat / ch->S));
+            if (k > cond) cond = k;
+        }
     }
 
     /* incoming partons in the partonic rest frame (com_p_in) */
@@ -797,7 +810,7 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
             orc_t_min_max(scur, mA2, mB2, mt1, mt2, &tlo, &thi);
             if (tlo < 0.0) tlo = 0.0;
             if (thi < tlo) { fail = 1; thi = tlo; }
-            {   /* condition number of the |t| range width: both bounds carry rounding relative to |t|_max,
+            if (ORC_BOOKKEEPING) {   /* condition number of the |t| range width: both bounds carry rounding relative to |t|_max,
                  * and the Jacobian of the |t| map is proportional to |t|_max - |t|_min; spacelike
                  * incoming legs of a light block make the range a sliver of a large |t| */
                 double k = thi > tlo ? thi / (thi - tlo) : 1e300;
@@ -806,13 +819,13 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
             fail |= orc_map_nu(r[L.d_tt[i]], 0.0, ch->t_nu, tlo, thi, ch->a, &tabs, &jt);
             double q1[4], q2[4];
             double j22 = orc_two_to_two(r[L.d_tphi[i]], pA, pB, tabs, mt1, mt2, scur, mA2, mB2, q1, q2);
-            {   /* the legs' components and the sampled block invariant agree only to eps E0^2, which the
+            if (ORC_BOOKKEEPING) {   /* the legs' components and the sampled block invariant agree only to eps E0^2, which the
                  * boost into and out of the block rest frame amplifies by gamma^2 = E0^2/s */
                 double e0 = pA[0] + pB[0];
                 double g2 = e0 * e0 / scur;
                 if (g2 > condp) condp = g2;
             }
-            {
+            if (ORC_BOOKKEEPING) {
                 double gap = scur - (mt1 + mt2) * (mt1 + mt2);
                 double k = gap > 0.0 ? scur / gap : 1e300;
                 if (k > cond) cond = k;
@@ -853,11 +866,11 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
         double jd = orc_two_body_decay(r[L.d_dphi[j]], r[L.d_dth[j]], s[j], m1, m2,
                                        j == 0 ? NULL : p[j], p[c1], p[c2]);
         jac *= jd;
-        if (j != 0) {   /* the parent momentum's rounding, boosted with gamma = E0/m0 */
+        if (ORC_BOOKKEEPING && j != 0) {   /* the parent momentum's rounding, boosted with gamma = E0/m0 */
             double g2 = p[j][0] * p[j][0] / s[j];
             if (g2 > condp) condp = g2;
         }
-        {   /* closeness to threshold: lambda's factor s0 - (m1+m2)^2 amplifies rounding by s0/(...) */
+        if (ORC_BOOKKEEPING) {   /* closeness to threshold: lambda's factor s0 - (m1+m2)^2 amplifies rounding by s0/(...) */
             double gap = s[j] - (m1 + m2) * (m1 + m2);
             double k = gap > 0.0 ? s[j] / gap : 1e300;
             if (k > cond) cond = k;
@@ -877,7 +890,7 @@ static double forward_event(const orc_channel* ch, const orc_sde* sde, int chan,
 
     /* integrand and multichannel weight */
     double f = 1.0, alpha = 1.0, p_mom = 0.0;
-    if (ch->hadronic && (ch->integrand == 2 || ch->integrand == 3 || ch->integrand == 4)) {
+    if (ORC_BOOKKEEPING && ch->hadronic && (ch->integrand == 2 || ch->integrand == 3 || ch->integrand == 4)) {
         /* (1-x)^beta of the parton density: an ulp of x is amplified by beta x/(1-x) */
         double k = fabs(ch->pdf_b) * fmax(x1 / (1.0 - x1), x2 / (1.0 - x2));
         if (k > cond) cond = k;
@@ -1176,3 +1189,7 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+#ifdef __cplusplus
+}
+#endif

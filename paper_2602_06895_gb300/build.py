@@ -1,7 +1,7 @@
 """Builds the native library libps.so in-tree with nvcc for sm_103a.
 
 The translation units (the phase-space kernels, the host compiler/runtime, the coupling
-flow, the unweighting and the inverse maps) are compiled in parallel and linked into one shared library with the
+flow, the unweighting, the inverse maps and the FP64-pipe probes) are compiled in parallel and linked into one shared library with the
 CUDA runtime linked statically.
 """
 from __future__ import annotations
@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libps.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "graph.cpp", "flow.cu", "unweight.cu", "inverse.cu", "jit.cpp"]
+SOURCES = ["kernels.cu", "graph.cpp", "flow.cu", "unweight.cu", "inverse.cu", "jit.cpp", "probe.cu"]
 # device headers that compiled programs (jit.cpp) hand to NVRTC, embedded as text
 JIT_HEADERS = [("map_device.cuh", CSRC), ("kin.cuh", CSRC), ("philox.cuh", CSRC), ("launch_params.h", CSRC),
                ("ps.h", INCLUDE)]

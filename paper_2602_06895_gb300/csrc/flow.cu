@@ -882,35 +882,49 @@ __global__ void __launch_bounds__(kFWarps * 32, 1)
 
 // ------------------------------------------------------------------------------------------
 // Fused coupling layer on the 5th-generation tensor cores (tcgen05), for sampling and density
-// evaluation with hidden width 128 and 16 bins.  A CTA takes 128 events per tile, one event per
-// TMEM lane: the three GEMMs are single-thread tcgen05.mma issues (M = 128; operands in shared
-// memory in the K-major canonical layout of 8-row x 16-byte core matrices; FP32 accumulators in
-// TMEM), and each epilogue thread reads its own event's row back with tcgen05.ld -- the SiLU of
-// the hidden layers writes the next operand tile, and the raw spline parameters of a transformed
-// dim arrive in that thread's registers, so the spline needs no staging.  8 warps: warpgroup g
-// takes columns 64g..64g+63 of the hidden layers and the dim 2p+g of each pair p of transformed
-// dims.  Every wait on the tensor cores is bounded; on a timeout the kernel records it in the
-// status word, still frees its TMEM and returns.
+// evaluation with hidden width 128 and 16 bins.  A tile is 128 events, one event per TMEM lane:
+// the three GEMMs are single-thread tcgen05.mma issues (M = 128; operands in shared memory in the
+// K-major canonical layout of 8-row x 16-byte core matrices; FP32 accumulators in TMEM), and each
+// epilogue thread reads its own event's row back with tcgen05.ld -- the SiLU of the hidden layers
+// writes the next operand tile, and the raw spline parameters of a transformed dim arrive in that
+// thread's registers, so the spline needs no staging.
+//
+// Two tiles are in flight per CTA: the 512 threads form two independent groups of two warpgroups,
+// each with its own operand tiles, its own 256 TMEM columns, its own issuing thread, completion
+// barriers and named barrier, so that one group's MMAs run on the tensor cores while the other
+// group evaluates SiLUs and splines on the CUDA cores.  The weights in shared memory serve both.
+// Within a group, warpgroup h takes hidden columns 64h..64h+63 and the transformed dim 2p+h of
+// each set p; the layer-3 output of set p lands in one of the group's two 128-column regions,
+// alternately, so the MMAs of set p+1 run during the splines of set p.  Every wait on the tensor
+// cores is bounded; on a timeout the kernel records it in the status word, still waits (bounded)
+// for all its MMAs, frees its TMEM and returns.
 namespace umma {
 
-constexpr int kTile = 128;        // events per tile (TMEM lanes)
-constexpr int kGroups = 4;        // warpgroups: hidden columns 32g.., transformed dim 4 s + g of set s
-constexpr int kThreads = 128 * kGroups;
-constexpr int kSetRows = 64 * kGroups;  // B rows of one set of transformed dims: 49 + 15 zero rows each
-constexpr int kTmemCols = 512;    // two blocks of 256: raw parameters of alternate sets; [0,128) hidden
+constexpr int kTile = 128;          // events per tile (TMEM lanes)
+constexpr int kGroupThreads = 256;  // one tile in flight per group of two warpgroups
+constexpr int kInFlight = 2;        // groups (tiles in flight) per CTA
+constexpr int kThreads = kGroupThreads * kInFlight;
+constexpr int kQRowsU = 56;         // W3 rows per transformed dim in shared memory (3K+1 = 49 used)
+constexpr int kTmemCols = 512;      // group g owns [256g, 256g + 256): two regions of 128 columns
 
+// Shared memory: the weights, then per group an input tile and an activation tile, the biases and
+// the log-det hand-over.  W3 holds the nb transformed dims at a stride of 56 rows plus 8 zero
+// rows, so that the 64-row B operand of the last dim stays inside it (its rows 49..63 only feed
+// output columns that are never read).
 struct Smem {
-    static constexpr size_t w1 = 0;                                    // 128 x 16 bf16
-    static constexpr size_t w2 = w1 + 128 * kInPad * 2;                // 128 x 128
-    static constexpr size_t w3 = w2 + 128 * 128 * 2;                   // up to 8 dims x 64 rows x 128
-    static constexpr size_t in = w3 + 8 * 64 * 128 * 2;                // 128 x 16 operand tile
-    static constexpr size_t act = in + kTile * kInPad * 2;             // 128 x 128 operand tile
-    static constexpr size_t b1 = act + kTile * 128 * 2;
-    static constexpr size_t b2 = b1 + 128 * 4;
-    static constexpr size_t b3 = b2 + 128 * 4;                         // 8 x 56 floats
-    static constexpr size_t ld = b3 + 8 * 56 * 4;                      // log-det exchange [kGroups-1][128]
-    static constexpr size_t total = ld + (kGroups - 1) * kTile * 4;
+    static constexpr size_t w1 = 0;                          // 128 x 16 bf16
+    static constexpr size_t w2 = w1 + 128 * kInPad * 2;      // 128 x 128
+    static constexpr size_t w3 = w2 + 128 * 128 * 2;         // (nb x 56 + 8) x 128
+    static constexpr size_t in_bytes = kTile * kInPad * 2;
+    static constexpr size_t act_bytes = kTile * 128 * 2;
+    static constexpr size_t tail_bytes = (128 + 128 + 8 * 56 + kInFlight * kTile) * 4;
+    __host__ __device__ static constexpr size_t w3_bytes(int nb) { return static_cast<size_t>(nb * kQRowsU + 8) * 128 * 2; }
+    __host__ __device__ static constexpr size_t in(int nb) { return w3 + w3_bytes(nb); }
+    __host__ __device__ static constexpr size_t act(int nb) { return in(nb) + kInFlight * in_bytes; }
+    __host__ __device__ static constexpr size_t tail(int nb) { return act(nb) + kInFlight * act_bytes; }
+    __host__ __device__ static constexpr size_t total(int nb) { return tail(nb) + tail_bytes; }
 };
+static_assert(Smem::total(kMaxNb) <= 232448, "the tcgen05 layer must fit the 227 KB of shared memory of a CTA");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -1074,6 +1088,20 @@ __device__ __forceinline__ Bin locate_regs(const float (&raw)[3 * K + 1], float 
     return b;
 }
 
+__device__ __forceinline__ void group_sync(int grp) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1 + grp), "r"(kGroupThreads) : "memory");
+}
+
+// layer 3 of transformed dims 2p and 2p+1 (those below nb): one N = 64 chain each, B from row 56q
+// of W3, into columns 0 and 64 of the region
+__device__ __forceinline__ void issue_set(uint32_t region, uint32_t act_addr, uint32_t w3_addr, int p, int nb) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int q = 2 * p + u;
+        if (q < nb) mma_chain(region + 64 * u, act_addr, w3_addr + q * (kQRowsU / 8) * 2048, 128, 64);
+    }
+}
+
 template <bool kInverse>
 __global__ void __launch_bounds__(kThreads, 1)
     k_layer_umma(int64_t B, int d, float* X, float* logdet, const __grid_constant__ LayerDesc ld, const bf16* W1,
@@ -1081,25 +1109,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                  unsigned long long* status, int wait_limit, int debug_flags) {
     constexpr int K = 16, PQ = 3 * K + 1;
     extern __shared__ __align__(1024) unsigned char smem[];
+    const int nb = ld.nb;
     bf16* w1s = reinterpret_cast<bf16*>(smem + Smem::w1);
     bf16* w2s = reinterpret_cast<bf16*>(smem + Smem::w2);
     bf16* w3s = reinterpret_cast<bf16*>(smem + Smem::w3);
-    bf16* ins = reinterpret_cast<bf16*>(smem + Smem::in);
-    bf16* act = reinterpret_cast<bf16*>(smem + Smem::act);
-    float* b1s = reinterpret_cast<float*>(smem + Smem::b1);
-    float* b2s = reinterpret_cast<float*>(smem + Smem::b2);
-    float* b3s = reinterpret_cast<float*>(smem + Smem::b3);
-    float* lds = reinterpret_cast<float*>(smem + Smem::ld);
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ __align__(8) uint64_t drain;  // end-of-kernel completion of every MMA issued
+    float* b1s = reinterpret_cast<float*>(smem + Smem::tail(nb));
+    float* b2s = b1s + 128;
+    float* b3s = b2s + 128;
+    float* lds = b3s + 8 * 56;  // log-det hand-over, [group][row]
+    __shared__ __align__(8) uint64_t mbar[kInFlight][2];  // per group: L1, L2, even sets | odd sets
+    __shared__ __align__(8) uint64_t drain;               // end-of-kernel completion of every MMA issued
     __shared__ uint32_t tmem_holder;
     __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = warp >> 2;                     // warpgroup: hidden column block / dim of a set
-    const int row = 32 * (warp & 3) + lane;      // this thread's event in the tile (TMEM lane)
-    const int nsets = (ld.nb + kGroups - 1) / kGroups;
+    const int grp = tid / kGroupThreads;          // the group (tile slot) of this thread
+    const int h = (warp >> 2) & 1;                // warpgroup within the group
+    const int row = 32 * (warp & 3) + lane;       // this thread's event in the tile (TMEM lane)
+    const bool issuer = (tid % kGroupThreads) == 0;
+    bf16* ins = reinterpret_cast<bf16*>(smem + Smem::in(nb) + grp * Smem::in_bytes);
+    bf16* act = reinterpret_cast<bf16*>(smem + Smem::act(nb) + grp * Smem::act_bytes);
+    const int nsets = (nb + 1) / 2;
 
-    // weights into the canonical layout, biases
     // weights into the canonical layout, 8 consecutive k (one core-matrix row) per 16-byte copy
     for (int i = tid; i < 128 * kInPad / 8; i += kThreads) {
         const int r = i / (kInPad / 8), k = (i % (kInPad / 8)) * 8;
@@ -1109,12 +1139,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int r = i >> 4, k = (i & 15) * 8;
         *reinterpret_cast<uint4*>(w2s + coff(r, k, 128)) = *reinterpret_cast<const uint4*>(W2 + r * 128 + k);
     }
-    for (int i = tid; i < nsets * kSetRows * 16; i += kThreads) {
+    for (int i = tid; i < (nb * kQRowsU + 8) * 16; i += kThreads) {
         const int r = i >> 4, k = (i & 15) * 8;
-        const int p = r / kSetRows, rr = r % kSetRows, q = kGroups * p + rr / 64, j = rr % 64;
+        const int q = r / kQRowsU, j = r % kQRowsU;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (q < ld.nb && j < PQ) v = *reinterpret_cast<const uint4*>(W3 + (q * PQ + j) * 128 + k);
-        *reinterpret_cast<uint4*>(w3s + p * kSetRows * 128 + coff(rr, k, 128)) = v;
+        if (q < nb && j < PQ) v = *reinterpret_cast<const uint4*>(W3 + (q * PQ + j) * 128 + k);
+        *reinterpret_cast<uint4*>(w3s + coff(r, k, 128)) = v;
     }
     for (int i = tid; i < 128; i += kThreads) {
         b1s[i] = b1[i];
@@ -1122,12 +1152,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = tid; i < 8 * 56; i += kThreads) {
         const int q = i / 56, j = i % 56;
-        b3s[i] = (q < ld.nb && j < PQ) ? b3[q * PQ + j] : 0.0f;
+        b3s[i] = (q < nb && j < PQ) ? b3[q * PQ + j] : 0.0f;
     }
     if (tid == 0) {
         failed = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&mbar)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&drain)));
+        for (int g = 0; g < kInFlight; ++g)
+            for (int k = 0; k < 2; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&mbar[g][k])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(&drain)), "r"(kInFlight));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -1139,72 +1170,75 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = tmem_holder;
-    const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);  // this warp's TMEM lanes
-    uint32_t phase = 0;
+    const uint32_t tg = tmem_holder + 256 * grp;                                 // this group's columns
+    const uint32_t tlane = tg + (static_cast<uint32_t>(32 * (warp & 3)) << 16);  // this warp's TMEM lanes
+    uint32_t phase[2] = {0u, 0u};
+    // one bounded wait on barrier k of this group
+    auto wait_on = [&](int k) {
+        if (!wait_phase(&mbar[grp][k], phase[k], wait_limit)) failed = 1;
+        phase[k] ^= 1u;
+        fence_after();
+    };
 
     const int64_t n_tiles = (B + kTile - 1) / kTile;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t first = 2 * static_cast<int64_t>(blockIdx.x) + grp;
+    for (int64_t tile = first; tile < n_tiles; tile += kInFlight * static_cast<int64_t>(gridDim.x)) {
         const int64_t ev = tile * kTile + row;
         const bool valid = ev < B;
-        // operand tile of the conditioning dims (warpgroup g writes k = 4g .. 4g+3)
+        // operand tile of the conditioning dims (warpgroup h writes k = 8h .. 8h+7)
         {
-            __align__(8) bf16 o[4];
+            __align__(16) bf16 o[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int k = 4 * g + e;
+            for (int e = 0; e < 8; ++e) {
+                const int k = 8 * h + e;
                 o[e] = __float2bfloat16((valid && k < ld.na) ? X[ev * d + ld.ta[k]] : 0.0f);
             }
-            *reinterpret_cast<uint2*>(ins + coff(row, 4 * g, kInPad)) = *reinterpret_cast<const uint2*>(o);
+            *reinterpret_cast<uint4*>(ins + coff(row, 8 * h, kInPad)) = *reinterpret_cast<const uint4*>(o);
         }
         // layer 1
         fence_async_smem();
         fence_before();
-        __syncthreads();
-        if (tid == 0) {
+        group_sync(grp);
+        if (issuer) {
             fence_after();
-            mma_chain(tmem, su32(ins), su32(w1s), kInPad, 128);
-            // test flag: withhold the first completion signal, so that the wait runs out
-            if (!((debug_flags & 1) && tile == blockIdx.x)) commit(&mbar);
+            mma_chain(tg, su32(ins), su32(w1s), kInPad, 128);
+            // test flag: withhold the group's first completion signal, so that the wait runs out
+            if (!((debug_flags & 1) && tile == first)) commit(&mbar[grp][0]);
         }
-        if (!wait_phase(&mbar, phase, wait_limit)) failed = 1;
-        phase ^= 1;
-        fence_after();
-        hidden_epilogue(tlane, b1s, act, row, 32 * g);
+        wait_on(0);
+        hidden_epilogue(tlane, b1s, act, row, 64 * h);
+        hidden_epilogue(tlane, b1s, act, row, 64 * h + 32);
         // layer 2
         fence_async_smem();
         fence_before();
-        __syncthreads();
-        if (tid == 0) {
+        group_sync(grp);
+        if (issuer) {
             fence_after();
-            mma_chain(tmem, su32(act), su32(w2s), 128, 128);
-            commit(&mbar);
+            mma_chain(tg, su32(act), su32(w2s), 128, 128);
+            commit(&mbar[grp][0]);
         }
-        if (!wait_phase(&mbar, phase, wait_limit)) failed = 1;
-        phase ^= 1;
-        fence_after();
-        hidden_epilogue(tlane, b2s, act, row, 32 * g);  // layer-2 reads of act are complete
+        wait_on(0);
+        hidden_epilogue(tlane, b2s, act, row, 64 * h);  // layer-2 reads of act are complete
+        hidden_epilogue(tlane, b2s, act, row, 64 * h + 32);
         fence_async_smem();
         fence_before();
-        __syncthreads();
-        // layer 3 and the splines, one set of kGroups transformed dims per MMA chain (N = 256); the
-        // raw columns of set p land in TMEM block 256 (p even) or 0 (p odd), so the chain of set
-        // p+1 runs while the splines of set p are evaluated
+        group_sync(grp);
+        // layer 3 and the splines, set p = dims 2p, 2p+1 in region 128 (p even) or 0 (p odd) of the
+        // group; completions alternate between the group's two barriers, so a wait can never see
+        // a later completion on its barrier before every thread has passed the group barrier
         float lsum = 0.0f;
-        if (tid == 0) {
+        if (issuer) {
             fence_after();
-            mma_chain(tmem + 256, su32(act), su32(w3s), 128, kSetRows);
-            commit(&mbar);
+            issue_set(tg + 128, su32(act), su32(w3s), 0, nb);
+            commit(&mbar[grp][0]);
         }
         for (int p = 0; p < nsets; ++p) {
-            if (!wait_phase(&mbar, phase, wait_limit)) failed = 1;
-            phase ^= 1;
-            fence_after();
-            const int q = kGroups * p + g;
+            wait_on(p & 1);
+            const int q = 2 * p + h;
             float raw[PQ];
             {
                 uint32_t v[56];
-                const uint32_t a = tlane + ((p & 1) ? 0 : 256) + 64 * g;  // column-aligned loads
+                const uint32_t a = tlane + ((p & 1) ? 0 : 128) + 64 * h;  // column-aligned loads
                 PS_TMEM_LD32(v, a);
                 uint32_t* v2 = v + 32;
                 PS_TMEM_LD16(v2, a + 32);
@@ -1214,14 +1248,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int j = 0; j < PQ; ++j) raw[j] = __uint_as_float(v[j]) + b3s[q < 8 ? q * 56 + j : j];
             }
-            // the other column block was read completely before the previous iteration's barrier
-            if (tid == 0 && p + 1 < nsets) {
+            // the other region was read completely before the previous group barrier
+            if (issuer && p + 1 < nsets) {
                 fence_after();
-                mma_chain(tmem + ((p & 1) ? 256 : 0), su32(act), su32(w3s + (p + 1) * kSetRows * 128), 128,
-                          kSetRows);
-                commit(&mbar);
+                issue_set(tg + ((p & 1) ? 128 : 0), su32(act), su32(w3s), p + 1, nb);
+                commit(&mbar[grp][(p + 1) & 1]);
             }
-            if (valid && q < ld.nb) {
+            if (valid && q < nb) {
                 const int jd = ld.tb[q];
                 const float xv = fminf(fmaxf(X[ev * d + jd], 0.0f), 1.0f);
                 const Bin bn = locate_regs<K>(raw, xv, kInverse);
@@ -1243,25 +1276,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             fence_before();
-            __syncthreads();  // every thread's reads of this column block precede the chain of set p+2
+            group_sync(grp);  // every thread's reads of this region precede the MMAs of set p+2
         }
-        if (g > 0) lds[(g - 1) * kTile + row] = lsum;
-        __syncthreads();
-        if (g == 0 && valid) {
-            float t = lsum;
-#pragma unroll
-            for (int k = 0; k < kGroups - 1; ++k) t += lds[k * kTile + row];
-            logdet[ev] += t;
-        }
+        if (h == 1) lds[grp * kTile + row] = lsum;
+        group_sync(grp);
+        if (h == 0 && valid) logdet[ev] += lsum + lds[grp * kTile + row];
     }
-    // drain: after a wait that ran out, MMAs may still be in flight; the TMEM is freed only after
-    // a commit issued behind all of them has arrived (default bound)
-    if (tid == 0) commit(&drain);
+    // drain: after a wait that ran out, MMAs may still be in flight; the TMEM is freed only after a
+    // commit issued by each group behind all of its MMAs has arrived (default bound)
+    if (issuer) commit(&drain);
     if (!wait_phase(&drain, 0, kWaitPolls)) failed = 1;
     fence_after();
     fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_holder), "r"(kTmemCols));
     if (tid == 0 && failed) atomicAdd(status, 1ULL);
 }
 
@@ -1615,7 +1644,7 @@ int ensure_gen(ps_flow f) {
     for (auto kern : {umma::k_layer_umma<false>, umma::k_layer_umma<true>})
         if (s == PS_OK)
             s = fcheck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            static_cast<int>(umma::Smem::total)),
+                                            static_cast<int>(umma::Smem::total(kMaxNb))),
                        "cudaFuncSetAttribute");
     return s;
 }
@@ -1623,14 +1652,15 @@ int ensure_gen(ps_flow f) {
 // all layers of the fused path on X [B][d] in place, log-determinant accumulated into ld
 int fused_layers(ps_flow f, int64_t B, float* X, float* ld, bool inverse, cudaStream_t st) {
     const FlowDesc& fd = f->fd;
-    if (fd.K == 16) {  // the tcgen05 form: 128 events per tile, one persistent CTA per SM
+    if (fd.K == 16) {  // the tcgen05 form: 128 events per tile, two tiles in flight, one CTA per SM
         const int64_t tiles = (B + umma::kTile - 1) / umma::kTile;
-        const unsigned grid = static_cast<unsigned>(std::min<int64_t>(f->sms, tiles));
+        const unsigned grid =
+            static_cast<unsigned>(std::min<int64_t>(f->sms, (tiles + umma::kInFlight - 1) / umma::kInFlight));
         for (int k = 0; k < fd.L; ++k) {
             const int l = inverse ? fd.L - 1 - k : k;
             const LayerDesc& lay = fd.layer[l];
             auto kern = inverse ? umma::k_layer_umma<true> : umma::k_layer_umma<false>;
-            kern<<<grid, umma::kThreads, umma::Smem::total, st>>>(
+            kern<<<grid, umma::kThreads, umma::Smem::total(lay.nb), st>>>(
                 B, fd.d, X, ld, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2, f->p + lay.off_b2,
                 f->pb + lay.off_W3, f->p + lay.off_b3, f->gen_status, f->wait_limit, f->debug_flags);
         }

@@ -110,6 +110,7 @@ _SIGS = {
     "ps_status_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ps_program_free": (C.c_int, [C.c_void_p]),
     "ps_launch_count": (C.c_int64, []),
+    "ps_fp64_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "ps_inverse_map": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ChannelDesc), C.c_int64, C.c_void_p, C.c_int64,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ps_global_weights": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -525,6 +526,16 @@ def autotune(channels, events, precision="f64", blocks=(64, 128, 256), ctas=(1, 
 
 def launch_count():
     return lib().ps_launch_count()
+
+
+PROBES = {"dfma": 0, "dadd": 1, "dmul": 2, "empty": 9, "div": 10, "sqrt": 11, "rsqrt": 12, "exp": 13,
+          "expm1": 14, "log": 15, "log1p": 16, "pow": 17, "atan": 18, "atan2": 19, "tan": 20, "sin": 21,
+          "cos": 22, "sincospi": 23}
+
+
+def fp64_probe(kind, blocks, iters, sink, stream=None):
+    """Launch one FP64-pipe probe (ps_fp64_probe) writing blocks x 256 doubles to `sink`."""
+    _check(lib().ps_fp64_probe(PROBES[kind], blocks, iters, _ptr(sink), _stream_ptr(stream)), "ps_fp64_probe")
 
 
 def program_for(channels, block_threads=128, ctas_per_sm=0, device=0, precision="f64", jit=False):

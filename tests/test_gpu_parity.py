@@ -174,6 +174,29 @@ def _alpha_tolerance(orc, spread=None):
     return t if spread is None else np.maximum(t, 4.0 * spread["alpha"])
 
 
+def _flat_agreement(a, orc, interior):
+    """Per event (both weights nonzero, random numbers inside [1e-8, 1-1e-8]): whether every
+    momentum component agrees with the oracle within 1e-12 of the event's largest energy and the
+    weight within 1e-12 relative -- the flat bar, with no condition number."""
+    ok = (a["w"] != 0) & (orc["w"] != 0) & interior
+    scale = np.max(np.abs(orc["mom"][:, :, 0]), axis=1)
+    dm = np.max(np.abs(a["mom"] - orc["mom"]), axis=(1, 2))
+    rw = np.abs(a["w"] / np.where(orc["w"] != 0, orc["w"], 1.0) - 1.0)
+    return ok, (dm <= RTOL * scale) & (rw <= RTOL)
+
+
+# The flat 1e-12 bar against a second FP64 evaluation of the same formulas: the oracle compiled
+# with contracted multiply-adds (as the GPU evaluates them) and with every elementary-function
+# result moved by a random whole number of ulps in [-2, 2] (CUDA's double functions are within
+# 1-2 ulps, glibc's within about 1).  The GPU may miss the flat bar on at most twice as many
+# events as that evaluation does (mean of two seeds), plus 0.5 % of the events; and on at most
+# 8 percentage points more events than the contracted oracle alone, where the host compiler
+# contracts at all.  Measured on the GB300 over these workloads: the ratio of misses is at most
+# 1.74 (one 2->8 channel; 1.2 or less elsewhere), the excess over the contracted oracle at most
+# 7.1 points.
+FLAT_MISS_RATIO, FLAT_MISS_SLACK, FLAT_FMA_MARGIN = 2.0, 0.005, 0.08
+
+
 @pytest.mark.parametrize("case", parity_channels(), ids=lambda c: c[0])
 def test_explicit_input_parity(torch_cuda, case):
     name, chans, which, grid = case
@@ -186,6 +209,22 @@ def test_explicit_input_parity(torch_cuda, case):
     spread = O.rounding_spread(ch, r, grid=grid, channels=chans, chan=which, base=orc)
     at = _alpha_tolerance(orc, spread) if ch["integrand"] == "pdf_sde" else None
     n_thr = compare(gpu, orc, ch, name, alpha_tol=at, r=r, spread=spread)
+    # the flat-bar fraction against the second FP64 evaluation and the contracted oracle
+    interior = np.all((r > 1e-8) & (r < 1 - 1e-8), axis=1)
+    ok_g, flat_g = _flat_agreement(gpu, orc, interior)
+    miss_ref = []
+    for seed in (1, 2):
+        ok_p, flat_p = _flat_agreement(O.forward_fma_perturbed(ch, r, seed, grid=grid, channels=chans, chan=which),
+                                       orc, interior)
+        m = ok_p & ok_g
+        miss_ref.append(1.0 - float(flat_p[m].mean()))
+    miss_gpu = 1.0 - float(flat_g[ok_g].mean())
+    assert miss_gpu <= FLAT_MISS_RATIO * np.mean(miss_ref) + FLAT_MISS_SLACK, (name, miss_gpu, miss_ref)
+    fma = O.forward_fma(ch, r, grid=grid, channels=chans, chan=which)
+    if not np.array_equal(fma["w"], orc["w"]):  # the host compiler contracted multiply-adds
+        ok_f, flat_f = _flat_agreement(fma, orc, interior)
+        m = ok_f & ok_g
+        assert float(flat_g[m].mean()) >= float(flat_f[m].mean()) - FLAT_FMA_MARGIN, (name, "vs contracted oracle")
     st = O.stats(orc["w"])
     s = gpu["stats"]
     assert s["n"] == st["n"] and abs(s["n_nonzero"] - st["n_nonzero"]) <= n_thr
