@@ -160,6 +160,7 @@ def summary(line):
                          "ess_fraction_vegas": _r(g(line, "flow", "ess_fraction_vegas"), 4),
                          "ess_per_s_over_vegas": None if g(line, "flow", "ess_per_s_flow") is None else
                          _r(line["flow"]["ess_per_s_flow"] / line["flow"]["ess_per_s_vegas"], 3),
+                         "mixed_map_ess_per_s_over_vegas": _r(g(line, "flow", "mixed_map", "ess_per_s_over_fp64_vegas"), 3),
                          "sample_ms": _r(g(line, "flow", "sample_ms"), 3),
                          "train_ms_per_step": _r(g(line, "flow", "train_ms_per_step"), 3),
                          "train_steps": g(line, "flow", "train_steps")},
@@ -192,7 +193,8 @@ def parse():
     ap.add_argument("--stream-chunk", type=int, default=None, help="streamed leg: events per chunk (default 2^22)")
     ap.add_argument("--stream-config", default=None, help="streamed leg: 'threads,ctas_per_sm' instead of autotuning")
     ap.add_argument("--stream-precision", default="f64", choices=["f64", "mixed"])
-    ap.add_argument("--flow-steps", type=int, default=400)
+    ap.add_argument("--flow-steps", type=int, default=20000,
+                    help="flow training steps of 2^16 events (the learned-proposal workload trains 2e4)")
     ap.add_argument("--flow-infer-events", type=int, default=EVENTS)
     ap.add_argument("--leg", default="all", choices=["all", "flow", "unweight", "global", "streamed", "c5_importance"],
                     help="run one secondary leg alone (for profiling); prints its object only")
@@ -644,7 +646,7 @@ def flow_leg(args, ps, W, torch, grid, vegas_ess_per_event, vegas_ms_per_event, 
     weights), against VEGAS alone on the same integrand."""
     ch = W.ww_hadronic()
     d = W.n_random_dims(ch)
-    prog = ps.program_for([ch])
+    prog = ps.program_for([ch], jit=True)  # the compiled FP64 map, as in the VEGAS main leg
     prog.set_vegas(0, grid)
     fl = ps.Flow(d, FLOW_LAYERS, FLOW_BINS, FLOW_HIDDEN, max_batch=FLOW_BATCH, init_seed=1004)
     B = FLOW_BATCH
@@ -679,6 +681,21 @@ def flow_leg(args, ps, W, torch, grid, vegas_ess_per_event, vegas_ms_per_event, 
     w = wi
     s1, s2 = float(w.sum()), float((w * w).sum())
     ess = s1 * s1 / s2
+    # the same flow with the mixed-precision compiled map (FP32 bulk, FP64 islands)
+    mprog = ps.program_for([ch], jit=True, precision="mixed")
+    mprog.set_vegas(0, grid)
+    mo, mws = mprog.alloc([N], 6)
+    wm = torch.empty(N, dtype=torch.float64, device="cuda")
+
+    def infer_mixed():
+        fl.generate(N, 2004, ri, ldi)
+        mprog.map(0, ri, mo, mws)
+        fl.weights(mo["weight"], ldi, wm)
+
+    infer_mixed_ms = timed(torch, infer_mixed, 2, stream)
+    m1, m2 = float(wm.sum()), float((wm * wm).sum())
+    ess_m = m1 * m1 / m2
+    del mo, mws, mprog
     # forward GEMM FLOPs per event: 2 (16 H + H^2 + H P_l) per layer, P_l = n_B (3K + 1) padded
     flops = 0.0
     for l in range(FLOW_LAYERS):
@@ -694,6 +711,10 @@ def flow_leg(args, ps, W, torch, grid, vegas_ess_per_event, vegas_ms_per_event, 
             "ess_per_s_flow": ess / (infer_ms / 1e3),
             "ess_per_s_vegas": vegas_ess_per_event / vegas_ms_per_event * 1e3,
             "integral_flow": s1 / N,
+            "mixed_map": {"inference_ms": infer_mixed_ms, "ess_fraction": ess_m / N,
+                          "ess_per_s": ess_m / (infer_mixed_ms / 1e3), "integral": m1 / N,
+                          "ess_per_s_over_fp64_vegas": (ess_m / (infer_mixed_ms / 1e3)) /
+                                                       (vegas_ess_per_event / vegas_ms_per_event * 1e3)},
             "tensor_gflop_per_event": flops / 1e9,
             "tensor_tflops_over_sample": flops * N / (sample_ms / 1e3) / 1e12,
             "sampling_path": "ps_flow_generate: one fused kernel per coupling layer",

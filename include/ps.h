@@ -464,10 +464,12 @@ int ps_flow_status(ps_flow f, int64_t* timeouts);
  * (default 2^24; polls <= 0 restores it).  A small bound makes the waits run out: the failure
  * path of ps_flow_status can be exercised without faulting or hanging the device. */
 int ps_flow_set_wait_limit(ps_flow f, int polls);
-/* Test flags of the fused tcgen05 sampling kernels (0 = none, the default).  Bit 0: each CTA
+/* Test flags of the fused tcgen05 kernels (0 = none, the default).  Bit 0: each group of a CTA
  * withholds the completion signal of its first MMA chain, so that the bounded wait on it runs
  * out (use with a small ps_flow_set_wait_limit); the outputs of that run are invalid, the
- * timeouts appear in ps_flow_status, and nothing faults or hangs.  Tests only. */
+ * timeouts appear in ps_flow_status, and nothing faults or hangs.  Bit 1: ps_flow_sample (the
+ * training forward) runs layer by layer -- separate GEMM, gather and spline kernels -- instead
+ * of the tcgen05 layer kernel, so that the two forms can be compared.  Tests only. */
 int ps_flow_set_debug(ps_flow f, int flags);
 /* Loss and sum of w of the last train_step / gradients call.  Synchronises `stream`. */
 int ps_flow_loss(ps_flow f, double* loss, double* sum_w, void* stream);

@@ -66,11 +66,26 @@ struct GemmArgs {
     int a_vec, b_vec;  // 1: the operand's base is 16-byte aligned (16-byte loads allowed)
 };
 
-// SiLU x sigma(x) with the hardware exponential and reciprocal (a few ulp in FP32, far below the
-// bfloat16 rounding that follows); for x -> -inf the denominator overflows and the result is 0.
-__device__ __forceinline__ float silu(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
+// The hardware base-2 exponential and reciprocal (a few ulp in FP32).  Every exponential of the
+// flow is taken as 2^(x log2 e), with the same roundings in every kernel, so that the fused
+// sampling layers and the layer-by-layer kernels compute identical activations and splines.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;\n" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;\n" : "=f"(r) : "f"(x));
+    return r;
+}
+constexpr float kLog2e = 1.4426950408889634f;
+
+// SiLU x sigma(x) = x / (1 + 2^(-x log2 e)) (a few ulp in FP32, far below the bfloat16 rounding
+// that follows); for x -> -inf the denominator overflows and the result is 0.
+__device__ __forceinline__ float silu(float x) { return x * rcp_approx(1.0f + ex2_approx(x * -kLog2e)); }
 __device__ __forceinline__ float silu_grad(float x) {
-    const float s = __fdividef(1.0f, 1.0f + __expf(-x));
+    const float s = rcp_approx(1.0f + ex2_approx(x * -kLog2e));
     return s * (1.0f + x * (1.0f - s));
 }
 
@@ -327,12 +342,16 @@ __device__ __forceinline__ float sigmoid(float a) { return __fdividef(1.0f, 1.0f
 // Raw MLP outputs of one transformed dim are read as raw[i * ld] (parameter-major layout: the
 // events of a warp read one parameter row, coalesced): widths 0..K-1, heights K..2K-1, knot
 // derivatives 2K..3K.
+// e^(a - m) of a softmax, as 2^(a log2 e - m log2 e)
+__device__ __forceinline__ float softmax_exp(float a, float nm) { return ex2_approx(fmaf(a, kLog2e, nm)); }
+
 __device__ __forceinline__ void softmax_norm(const float* raw, int64_t ld, int K, float& m, float& iz) {
     m = -INFINITY;
     for (int i = 0; i < K; ++i) m = fmaxf(m, raw[i * ld]);
+    const float nm = -m * kLog2e;
     float z = 0.0f;
-    for (int i = 0; i < K; ++i) z += __expf(raw[i * ld] - m);
-    iz = 1.0f / z;
+    for (int i = 0; i < K; ++i) z += softmax_exp(raw[i * ld], nm);
+    iz = rcp_approx(z);
 }
 
 // The bin holding v among the width knots (v = x) or the height knots (v = y, inverse), with
@@ -353,9 +372,10 @@ __device__ __forceinline__ Bin locate(const float* raw, int64_t ld, int K, float
     const float cw = 1.0f - K * kMinW, chh = 1.0f - K * kMinH;
     float x0 = 0.0f, y0 = 0.0f, sx = 0.0f, sy = 0.0f;
     int k = 0;
+    const float nmw = -b.mw * kLog2e, nmh = -b.mh * kLog2e;
     for (;; ++k) {
-        float pw = __expf(raw[k * ld] - b.mw) * b.iw;
-        float ph = __expf(raw[(K + k) * ld] - b.mh) * b.ih;
+        float pw = softmax_exp(raw[k * ld], nmw) * b.iw;
+        float ph = softmax_exp(raw[(K + k) * ld], nmh) * b.ih;
         float w = kMinW + cw * pw, h = kMinH + chh * ph;
         if (k == K - 1 || (by_height ? v < y0 + h : v < x0 + w)) {
             b.w = w;
@@ -397,10 +417,11 @@ __device__ __forceinline__ Bin locate_fixed(const float* raw, int64_t ld, float 
         mh = fmaxf(mh, h[i]);
     }
     float zw = 0.0f, zh = 0.0f;
+    const float nmw = -mw * kLog2e, nmh = -mh * kLog2e;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        w[i] = __expf(w[i] - mw);
-        h[i] = __expf(h[i] - mh);
+        w[i] = softmax_exp(w[i], nmw);
+        h[i] = softmax_exp(h[i], nmh);
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) zw += w[i];
@@ -409,8 +430,8 @@ __device__ __forceinline__ Bin locate_fixed(const float* raw, int64_t ld, float 
     Bin b;
     b.mw = mw;
     b.mh = mh;
-    b.iw = 1.0f / zw;
-    b.ih = 1.0f / zh;
+    b.iw = rcp_approx(zw);
+    b.ih = rcp_approx(zh);
     const float cw = 1.0f - K * kMinW, chh = 1.0f - K * kMinH;
     float cx = 0.0f, cy = 0.0f, csx = 0.0f, csy = 0.0f;
     bool found = false;
@@ -576,9 +597,10 @@ __global__ void k_spline_backward(int64_t B, int d, int K, const float* Xl, cons
             const float doth = gt[3] * bn.sy + gt[4] * bn.ph;
             float* g = G + row0 * ldp + b;
             bf16* gb = Gb + row0 * ldp + b;
+            const float nmw = -bn.mw * kLog2e, nmh = -bn.mh * kLog2e;
             for (int i = 0; i < K; ++i) {
-                float pw = __expf(raw[i * ldp] - bn.mw) * bn.iw;
-                float ph = __expf(raw[(K + i) * ldp] - bn.mh) * bn.ih;
+                float pw = softmax_exp(raw[i * ldp], nmw) * bn.iw;
+                float ph = softmax_exp(raw[(K + i) * ldp], nmh) * bn.ih;
                 float aw = i < bn.k ? gt[1] : (i == bn.k ? gt[2] : 0.0f);
                 float ah = i < bn.k ? gt[3] : (i == bn.k ? gt[4] : 0.0f);
                 float vw = cw * pw * (aw - dotw), vh = chh * ph * (ah - doth);
@@ -1004,87 +1026,106 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// 32 hidden columns of this thread's event: + bias, SiLU, bf16 into the operand tile
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, bf16* act, int row, int c0) {
+// SiLU of two hidden columns, z / (1 + 2^(-z log2 e)) with z = acc + bias, in paired FP32
+// arithmetic (one instruction per pair for the adds and multiplies, each exactly rounded like
+// its scalar form) and the hardware exponential and reciprocal, as bfloat16x2.  For z -> -inf
+// the denominator overflows and the result is 0.
+__device__ __forceinline__ uint32_t silu_pair_bf16(float a0, float a1, float c0, float c1, float2& z) {
+    z = __fadd2_rn(make_float2(a0, a1), make_float2(c0, c1));
+    const float2 t = __fmul2_rn(z, make_float2(-kLog2e, -kLog2e));
+    const float2 den = __fadd2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), make_float2(1.0f, 1.0f));
+    const float2 y = __fmul2_rn(z, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    return pack_bf16(y.x, y.y);
+}
+
+// 32 hidden columns of this thread's event: + bias, SiLU, bf16 into the operand tile; for training
+// (kStore) also the pre-activations z (FP32) and the activations (bf16) into this event's rows zg,
+// ag where `store` holds.  The TMEM load is warp-collective (.sync.aligned): every lane of the warp
+// executes it, whatever `store` is.
+template <bool kStore>
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, bf16* act, int row, int c0,
+                                                bool store = false, float* zg = nullptr, bf16* ag = nullptr) {
+    uint32_t v[32];
+    __syncwarp();  // the warp-collective TMEM load is issued by a converged warp
+    PS_TMEM_LD32(v, taddr + c0);
+    tmem_wait_ld();
 #pragma unroll
-    for (int h = 0; h < 1; ++h) {
-        uint32_t v[32];
-        PS_TMEM_LD32(v, taddr + c0 + 32 * h);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; j += 8) {
-            const float4 b0 = *reinterpret_cast<const float4*>(bias + c0 + 32 * h + j);
-            const float4 b1v = *reinterpret_cast<const float4*>(bias + c0 + 32 * h + j + 4);
-            const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1v.x, b1v.y, b1v.z, b1v.w};
-            uint4 o;
-            uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
-#pragma unroll
-            for (int e = 0; e < 8; e += 2)
-                ow[e / 2] = pack_bf16(silu(__uint_as_float(v[j + e]) + bb[e]), silu(__uint_as_float(v[j + e + 1]) + bb[e + 1]));
-            *reinterpret_cast<uint4*>(act + coff(row, c0 + 32 * h + j, 128)) = o;
+    for (int j = 0; j < 32; j += 8) {
+        const float4 b0 = *reinterpret_cast<const float4*>(bias + c0 + j);
+        const float4 b1v = *reinterpret_cast<const float4*>(bias + c0 + j + 4);
+        uint4 o;
+        float2 z0, z1, z2, z3;
+        o.x = silu_pair_bf16(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), b0.x, b0.y, z0);
+        o.y = silu_pair_bf16(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]), b0.z, b0.w, z1);
+        o.z = silu_pair_bf16(__uint_as_float(v[j + 4]), __uint_as_float(v[j + 5]), b1v.x, b1v.y, z2);
+        o.w = silu_pair_bf16(__uint_as_float(v[j + 6]), __uint_as_float(v[j + 7]), b1v.z, b1v.w, z3);
+        *reinterpret_cast<uint4*>(act + coff(row, c0 + j, 128)) = o;
+        if (kStore && store) {
+            *reinterpret_cast<float4*>(zg + c0 + j) = make_float4(z0.x, z0.y, z1.x, z1.y);
+            *reinterpret_cast<float4*>(zg + c0 + j + 4) = make_float4(z2.x, z2.y, z3.x, z3.y);
+            *reinterpret_cast<uint4*>(ag + c0 + j) = o;
         }
     }
 }
 
-// the bin of v from raw parameters held in registers (compile-time indices only)
+// The bin of v and what the forward and inverse bin formulas need, from raw parameters held in
+// registers (compile-time indices only): widths and heights are handled as pairs in paired FP32
+// arithmetic, softmax exponentials as 2^(a log2 e - max log2 e).
+struct BinF {
+    float x0, y0, w, h, d0, d1;
+};
+
 template <int K>
-__device__ __forceinline__ Bin locate_regs(const float (&raw)[3 * K + 1], float v, bool by_height) {
-    float w[K], h[K];
-    float mw = -INFINITY, mh = -INFINITY;
+__device__ __forceinline__ BinF locate_pairs(const float (&raw)[3 * K + 1], float v, bool by_height) {
+    static_assert((K & (K - 1)) == 0, "pairwise maxima need a power-of-two bin count");
+    // the maxima by a tree (a maximum is exact in any order)
+    float mxw[K], mxh[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        w[i] = raw[i];
-        h[i] = raw[K + i];
-        mw = fmaxf(mw, w[i]);
-        mh = fmaxf(mh, h[i]);
+        mxw[i] = raw[i];
+        mxh[i] = raw[K + i];
     }
-    float zw = 0.0f, zh = 0.0f;
+#pragma unroll
+    for (int s = K / 2; s > 0; s >>= 1)
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            mxw[i] = fmaxf(mxw[i], mxw[i + s]);
+            mxh[i] = fmaxf(mxh[i], mxh[i + s]);
+        }
+    const float mw = mxw[0], mh = mxh[0];
+    const float2 l2e = make_float2(kLog2e, kLog2e), nm = make_float2(-mw * kLog2e, -mh * kLog2e);
+    float2 e[K];
+    float2 z = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        w[i] = __expf(w[i] - mw);
-        h[i] = __expf(h[i] - mh);
+        const float2 t = __ffma2_rn(make_float2(raw[i], raw[K + i]), l2e, nm);
+        e[i] = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+        z = __fadd2_rn(z, e[i]);
     }
-#pragma unroll
-    for (int i = 0; i < K; ++i) zw += w[i];
-#pragma unroll
-    for (int i = 0; i < K; ++i) zh += h[i];
-    Bin b;
-    b.mw = mw;
-    b.mh = mh;
-    b.iw = 1.0f / zw;
-    b.ih = 1.0f / zh;
-    const float cw = 1.0f - K * kMinW, chh = 1.0f - K * kMinH;
-    float cx = 0.0f, cy = 0.0f, csx = 0.0f, csy = 0.0f, a0 = 0.0f, a1 = 0.0f;
+    const float2 iz = make_float2(rcp_approx(z.x), rcp_approx(z.y));
+    const float2 c = make_float2(1.0f - K * kMinW, 1.0f - K * kMinH), mins = make_float2(kMinW, kMinH);
+    BinF b;
+    float a0 = 0.0f, a1 = 0.0f;
+    float2 cum = make_float2(0.0f, 0.0f);
     bool found = false;
-    b.k = K - 1;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        const float pw = w[i] * b.iw, ph = h[i] * b.ih;
-        const float ww = kMinW + cw * pw, hh = kMinH + chh * ph;
-        const bool hit = !found && (i == K - 1 || (by_height ? v < cy + hh : v < cx + ww));
+        const float2 wh = __ffma2_rn(c, __fmul2_rn(e[i], iz), mins);  // (width, height) of bin i
+        const float2 next = __fadd2_rn(cum, wh);
+        const bool hit = !found && (i == K - 1 || (by_height ? v < next.y : v < next.x));
         if (hit) {
-            b.k = i;
-            b.x0 = cx;
-            b.y0 = cy;
-            b.sx = csx;
-            b.sy = csy;
-            b.w = ww;
-            b.h = hh;
-            b.pw = pw;
-            b.ph = ph;
+            b.x0 = cum.x;
+            b.y0 = cum.y;
+            b.w = wh.x;
+            b.h = wh.y;
             a0 = raw[2 * K + i];
             a1 = raw[2 * K + i + 1];
             found = true;
         }
-        cx += ww;
-        cy += hh;
-        csx += pw;
-        csy += ph;
+        cum = next;
     }
     b.d0 = kMinD + softplus(a0);
     b.d1 = kMinD + softplus(a1);
-    b.sg0 = sigmoid(a0);
-    b.sg1 = sigmoid(a1);
     return b;
 }
 
@@ -1102,11 +1143,27 @@ __device__ __forceinline__ void issue_set(uint32_t region, uint32_t act_addr, ui
     }
 }
 
-template <bool kInverse>
+// What the training forward keeps for the backward pass (row-major per event unless stated):
+// the bf16 MLP input In [B][16], pre-activations Z1, Z2 (FP32) and activations A1, A2 (bf16)
+// [B][128], the raw spline parameters P parameter-major [q (3K+1) + j][ldp], and the next
+// layer's state Xn [B][d] (X itself is left unchanged).
+struct TrainOut {
+    bf16* In;
+    float* Z1;
+    float* Z2;
+    bf16* A1;
+    bf16* A2;
+    float* P;
+    int64_t ldp;
+    float* Xn;
+};
+
+template <bool kInverse, bool kTrain>
 __global__ void __launch_bounds__(kThreads, 1)
     k_layer_umma(int64_t B, int d, float* X, float* logdet, const __grid_constant__ LayerDesc ld, const bf16* W1,
                  const float* b1, const bf16* W2, const float* b2, const bf16* W3, const float* b3,
-                 unsigned long long* status, int wait_limit, int debug_flags) {
+                 unsigned long long* status, int wait_limit, int debug_flags, const __grid_constant__ TrainOut tr) {
+    static_assert(!(kInverse && kTrain), "the training forward runs the forward direction");
     constexpr int K = 16, PQ = 3 * K + 1;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nb = ld.nb;
@@ -1182,19 +1239,48 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int64_t n_tiles = (B + kTile - 1) / kTile;
     const int64_t first = 2 * static_cast<int64_t>(blockIdx.x) + grp;
-    for (int64_t tile = first; tile < n_tiles; tile += kInFlight * static_cast<int64_t>(gridDim.x)) {
+    const int64_t stride = kInFlight * static_cast<int64_t>(gridDim.x);
+    // the conditioning dims of the tile (warpgroup h: k = 8h .. 8h+7), loaded one tile ahead so that
+    // the loads overlap the previous tile's work
+    float cond[8];
+    auto load_cond = [&](int64_t t) {
+        const int64_t e = t * kTile + row;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = 8 * h + i;
+            cond[i] = (e < B && k < ld.na) ? X[e * d + ld.ta[k]] : 0.0f;
+        }
+    };
+    load_cond(first);
+    for (int64_t tile = first; tile < n_tiles; tile += stride) {
         const int64_t ev = tile * kTile + row;
         const bool valid = ev < B;
-        // operand tile of the conditioning dims (warpgroup h writes k = 8h .. 8h+7)
-        {
-            __align__(16) bf16 o[8];
+        // this thread's transformed dims (2p + h of set p), loaded now so that the loads overlap the
+        // MLP rather than stall the splines
+        float xq[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = 8 * h + e;
-                o[e] = __float2bfloat16((valid && k < ld.na) ? X[ev * d + ld.ta[k]] : 0.0f);
-            }
-            *reinterpret_cast<uint4*>(ins + coff(row, 8 * h, kInPad)) = *reinterpret_cast<const uint4*>(o);
+        for (int p = 0; p < 4; ++p) {
+            const int q = 2 * p + h;
+            xq[p] = (valid && q < nb) ? X[ev * d + ld.tb[q]] : 0.0f;
         }
+        // operand tile of the conditioning dims, then the next tile's conditioning dims
+        {
+            uint4 o;
+            o.x = pack_bf16(cond[0], cond[1]);
+            o.y = pack_bf16(cond[2], cond[3]);
+            o.z = pack_bf16(cond[4], cond[5]);
+            o.w = pack_bf16(cond[6], cond[7]);
+            *reinterpret_cast<uint4*>(ins + coff(row, 8 * h, kInPad)) = o;
+            if constexpr (kTrain) {  // the MLP input, and the conditioning dims carried into Xn
+                if (valid) {
+                    *reinterpret_cast<uint4*>(tr.In + ev * kInPad + 8 * h) = o;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (8 * h + i < ld.na) tr.Xn[ev * d + ld.ta[8 * h + i]] = cond[i];
+                }
+            }
+        }
+        load_cond(tile + stride);
         // layer 1
         fence_async_smem();
         fence_before();
@@ -1206,8 +1292,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!((debug_flags & 1) && tile == first)) commit(&mbar[grp][0]);
         }
         wait_on(0);
-        hidden_epilogue(tlane, b1s, act, row, 64 * h);
-        hidden_epilogue(tlane, b1s, act, row, 64 * h + 32);
+        {  // warp-uniform calls: the stores are predicated per lane inside
+            float* zg = kTrain ? tr.Z1 + ev * 128 : nullptr;
+            bf16* ag = kTrain ? tr.A1 + ev * 128 : nullptr;
+            hidden_epilogue<kTrain>(tlane, b1s, act, row, 64 * h, valid, zg, ag);
+            hidden_epilogue<kTrain>(tlane, b1s, act, row, 64 * h + 32, valid, zg, ag);
+        }
         // layer 2
         fence_async_smem();
         fence_before();
@@ -1218,8 +1308,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             commit(&mbar[grp][0]);
         }
         wait_on(0);
-        hidden_epilogue(tlane, b2s, act, row, 64 * h);  // layer-2 reads of act are complete
-        hidden_epilogue(tlane, b2s, act, row, 64 * h + 32);
+        {  // layer-2 reads of act are complete; warp-uniform calls as above
+            float* zg = kTrain ? tr.Z2 + ev * 128 : nullptr;
+            bf16* ag = kTrain ? tr.A2 + ev * 128 : nullptr;
+            hidden_epilogue<kTrain>(tlane, b2s, act, row, 64 * h, valid, zg, ag);
+            hidden_epilogue<kTrain>(tlane, b2s, act, row, 64 * h + 32, valid, zg, ag);
+        }
         fence_async_smem();
         fence_before();
         group_sync(grp);
@@ -1239,14 +1333,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             {
                 uint32_t v[56];
                 const uint32_t a = tlane + ((p & 1) ? 0 : 128) + 64 * h;  // column-aligned loads
+                __syncwarp();
                 PS_TMEM_LD32(v, a);
                 uint32_t* v2 = v + 32;
                 PS_TMEM_LD16(v2, a + 32);
                 uint32_t* v3 = v + 48;
                 PS_TMEM_LD8(v3, a + 48);
                 tmem_wait_ld();
+                const float* bq = b3s + (q < 8 ? q * 56 : 0);
 #pragma unroll
-                for (int j = 0; j < PQ; ++j) raw[j] = __uint_as_float(v[j]) + b3s[q < 8 ? q * 56 + j : j];
+                for (int j = 0; j + 1 < PQ; j += 2) {
+                    const float2 t = __fadd2_rn(make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])),
+                                                make_float2(bq[j], bq[j + 1]));
+                    raw[j] = t.x;
+                    raw[j + 1] = t.y;
+                }
+                raw[PQ - 1] = __uint_as_float(v[PQ - 1]) + bq[PQ - 1];
             }
             // the other region was read completely before the previous group barrier
             if (issuer && p + 1 < nsets) {
@@ -1254,14 +1356,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 issue_set(tg + ((p & 1) ? 128 : 0), su32(act), su32(w3s), p + 1, nb);
                 commit(&mbar[grp][(p + 1) & 1]);
             }
+            if constexpr (kTrain) {  // the raw spline parameters, parameter-major
+                if (valid && q < nb)
+#pragma unroll
+                    for (int j = 0; j < PQ; ++j) tr.P[static_cast<int64_t>(q * PQ + j) * tr.ldp + ev] = raw[j];
+            }
             if (valid && q < nb) {
                 const int jd = ld.tb[q];
-                const float xv = fminf(fmaxf(X[ev * d + jd], 0.0f), 1.0f);
-                const Bin bn = locate_regs<K>(raw, xv, kInverse);
+                const float xv = fminf(fmaxf(p == 0 ? xq[0] : p == 1 ? xq[1] : p == 2 ? xq[2] : xq[3], 0.0f), 1.0f);
+                const BinF bn = locate_pairs<K>(raw, xv, kInverse);
                 float F, Fp;
                 if (!kInverse) {
                     bin_eval<float>(xv, bn.x0, bn.w, bn.y0, bn.h, bn.d0, bn.d1, F, Fp);
-                    X[ev * d + jd] = fminf(fmaxf(F, 1e-7f), 1.0f - 1e-7f);
+                    (kTrain ? tr.Xn : X)[ev * d + jd] = fminf(fmaxf(F, 1e-7f), 1.0f - 1e-7f);
                     lsum += __logf(Fp);
                 } else {
                     const float sl = bn.h / bn.w, dy = xv - bn.y0, e = bn.d1 + bn.d0 - 2.0f * sl;
@@ -1503,11 +1610,42 @@ int mlp(ps_flow f, int l, int64_t B, const float* Xl, cudaStream_t st) {
 }
 
 // forward of all layers for a chunk of `B` events starting at event ev0; stores activations
+bool fused_ok(const FlowDesc& fd);
+int ensure_gen(ps_flow f);
+
 int forward(ps_flow f, int64_t B, uint64_t seed, uint64_t ev0, cudaStream_t st) {
     const FlowDesc& fd = f->fd;
     const int d = fd.d, T = 256;
     k_init_z<<<blocks(B, T), T, 0, st>>>(B, d, seed, ev0, f->X);
     cudaMemsetAsync(f->logdet, 0, B * sizeof(float), st);
+    if (fd.K == 16 && fused_ok(fd) && !(f->debug_flags & 2)) {
+        // the tcgen05 layer in its training form: one launch per layer writes what the backward
+        // pass reads (MLP input, pre-activations, activations, raw spline parameters, next state)
+        int s = ensure_gen(f);
+        if (s != PS_OK) return s;
+        const int64_t tiles = (B + umma::kTile - 1) / umma::kTile;
+        const unsigned grid =
+            static_cast<unsigned>(std::min<int64_t>(f->sms, (tiles + umma::kInFlight - 1) / umma::kInFlight));
+        for (int l = 0; l < fd.L; ++l) {
+            const LayerDesc& lay = fd.layer[l];
+            float* Xl = f->X + static_cast<int64_t>(l) * f->max_batch * d;
+            umma::TrainOut tr;
+            tr.In = f->In + static_cast<int64_t>(l) * f->max_batch * kInPad;
+            tr.Z1 = f->Z1 + static_cast<int64_t>(l) * f->max_batch * fd.H;
+            tr.Z2 = f->Z2 + static_cast<int64_t>(l) * f->max_batch * fd.H;
+            tr.A1 = f->A1 + static_cast<int64_t>(l) * f->max_batch * fd.H;
+            tr.A2 = f->A2 + static_cast<int64_t>(l) * f->max_batch * fd.H;
+            tr.P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
+            tr.ldp = f->max_batch;
+            tr.Xn = Xl + f->max_batch * d;
+            umma::k_layer_umma<false, true><<<grid, umma::kThreads, umma::Smem::total(lay.nb), st>>>(
+                B, d, Xl, f->logdet, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2,
+                f->p + lay.off_b2, f->pb + lay.off_W3, f->p + lay.off_b3, f->gen_status, f->wait_limit,
+                f->debug_flags & 1, tr);
+        }
+        ps::count_launches(1 + fd.L);
+        return fcheck(cudaGetLastError(), "flow forward (tcgen05)");
+    }
     for (int l = 0; l < fd.L; ++l) {
         const LayerDesc& ld = fd.layer[l];
         float* Xl = f->X + static_cast<int64_t>(l) * f->max_batch * d;
@@ -1641,7 +1779,7 @@ int ensure_gen(ps_flow f) {
             s = fcheck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             static_cast<int>(FusedSmem::total)),
                        "cudaFuncSetAttribute");
-    for (auto kern : {umma::k_layer_umma<false>, umma::k_layer_umma<true>})
+    for (auto kern : {umma::k_layer_umma<false, false>, umma::k_layer_umma<true, false>, umma::k_layer_umma<false, true>})
         if (s == PS_OK)
             s = fcheck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             static_cast<int>(umma::Smem::total(kMaxNb))),
@@ -1659,10 +1797,11 @@ int fused_layers(ps_flow f, int64_t B, float* X, float* ld, bool inverse, cudaSt
         for (int k = 0; k < fd.L; ++k) {
             const int l = inverse ? fd.L - 1 - k : k;
             const LayerDesc& lay = fd.layer[l];
-            auto kern = inverse ? umma::k_layer_umma<true> : umma::k_layer_umma<false>;
+            auto kern = inverse ? umma::k_layer_umma<true, false> : umma::k_layer_umma<false, false>;
             kern<<<grid, umma::kThreads, umma::Smem::total(lay.nb), st>>>(
                 B, fd.d, X, ld, lay, f->pb + lay.off_W1, f->p + lay.off_b1, f->pb + lay.off_W2, f->p + lay.off_b2,
-                f->pb + lay.off_W3, f->p + lay.off_b3, f->gen_status, f->wait_limit, f->debug_flags);
+                f->pb + lay.off_W3, f->p + lay.off_b3, f->gen_status, f->wait_limit, f->debug_flags & 1,
+                umma::TrainOut{});
         }
         ps::count_launches(fd.L);
         return fcheck(cudaGetLastError(), "k_layer_umma");
@@ -2046,7 +2185,7 @@ int ps_flow_set_wait_limit(ps_flow f, int polls) {
 }
 
 int ps_flow_set_debug(ps_flow f, int flags) {
-    if (!f || flags < 0 || flags > 1) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_set_debug: bad arguments");
+    if (!f || flags < 0 || flags > 3) return ffail(PS_ERR_INVALID_ARGUMENT, "ps_flow_set_debug: bad arguments");
     f->debug_flags = flags;
     return PS_OK;
 }

@@ -655,7 +655,8 @@ class Flow:
         _fcheck(lib().ps_flow_set_wait_limit(self.h, int(polls)), "ps_flow_set_wait_limit")
 
     def set_debug(self, flags):
-        """Test flags of the fused kernels (bit 0: withhold the first completion signal)."""
+        """Test flags of the fused kernels (bit 0: withhold the first completion signal; bit 1: the
+        training forward layer by layer instead of the tcgen05 layer kernel)."""
         _fcheck(lib().ps_flow_set_debug(self.h, int(flags)), "ps_flow_set_debug")
 
     def loss(self, stream=None):

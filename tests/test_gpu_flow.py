@@ -161,11 +161,16 @@ def test_inverse_matches_oracle_and_round_trips(torch_cuda):
     assert np.abs(lq.cpu().numpy() + ld.cpu().numpy()).mean() <= 1e-3
 
 
-def test_gradients_match_oracle(torch_cuda):
+@pytest.mark.parametrize("layered", [False, True], ids=["tcgen05_forward", "layer_by_layer_forward"])
+def test_gradients_match_oracle(torch_cuda, layered):
+    """The training gradients against the oracle's autograd, with the training forward on the
+    tcgen05 layer kernel (the default) and layer by layer (test flag)."""
     torch = torch_cuda
     fl = ps.Flow(D, L, K, H, max_batch=4096)
     p, orc, layout = random_params(fl, 14)
     fl.set_params(p)
+    if layered:
+        fl.set_debug(2)
     B = 3000
     r, ld, z = sample(torch, fl, B, 31)
     # a correlated test integrand on the unit cube as the phase-space weight
@@ -261,9 +266,16 @@ def test_fused_generate_matches_layer_by_layer_and_oracle(torch_cuda, B):
     r2 = torch.empty_like(r)
     ld2 = torch.empty_like(ld)
     z2 = torch.empty_like(r)
+    fl.set_debug(2)  # the training forward layer by layer: GEMM, gather and spline kernels
     fl.sample(B, 8, r2, ld2, z2, event_offset=3)
+    fl.set_debug(0)
+    r3 = torch.empty_like(r)
+    ld3 = torch.empty_like(ld)
+    fl.sample(B, 8, r3, ld3, event_offset=3)  # the training forward on the tcgen05 layer kernel
     torch.cuda.synchronize()
     assert torch.equal(z, z2)
+    # the tcgen05 training forward and the fused sampling kernel evaluate the same arithmetic
+    assert torch.max(torch.abs(r - r3)).item() <= 1e-6 and torch.max(torch.abs(ld - ld3)).item() <= 1e-5
     assert torch.max(torch.abs(r - r2)).item() <= 1e-5, torch.max(torch.abs(r - r2)).item()
     assert torch.max(torch.abs(ld - ld2)).item() <= 1e-3
     idx = torch.arange(0, B, max(1, B // 4096), device="cuda")
