@@ -59,18 +59,25 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07
 # The same counters for the compiled program's kernel (ps_jit_map) on this workload, from its own
 # ncu capture (profiles/ps_jit_map_ww_2to4.md): DFMA 405.6 + DADD 113.6 + DMUL 197.6 = 716.8 FP64
 # arithmetic instructions (1122.4 flops) and 185.9 DRAM bytes per event; FP64 pipe 85.4 % active.
-# Re-captured on the current build (profiles/fp64_pipe_probes.md): the same 716.8, 793.8 FP64-pipe
-# instructions in all (conversions included), 185.3 DRAM bytes per event, pipe active 0.836 of the
-# elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
-COMPILED_COUNTERS = {"instr": 716.8, "flops": 1122.4, "dram": 185.3, "pipe": 0.836, "pipe_instr": 793.8}
+# Re-captured on the current build, with the Kallen function of decays and 2->2 blocks taken from
+# the masses (no square roots; profiles/fp64_pipe_probes.md): DFMA 399.1 + DADD 113.3 + DMUL 195.1
+# = 707.5 (1106.6 flops), 784.6 FP64-pipe instructions in all (conversions included), 185.5 DRAM
+# bytes per event, pipe active 0.834 of the elapsed cycles -- the FP64 issue probe's saturating
+# loop reaches 0.84.
+COMPILED_COUNTERS = {"instr": 707.5, "flops": 1106.6, "dram": 185.5, "pipe": 0.834, "pipe_instr": 784.6}
 INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from
-# the ncu captures of one 2^20-event launch (profiles/ps_jit_map_c5_2to8.md, ps_map_kernel_c5_2to8.md).
-C5_FP64_INSTR_PER_EVENT = {"compiled": 4596.1, "interpreter": 6559.0}
+# the ncu captures of one 2^20-event launch: the compiled program on the current build
+# (profiles/fp64_pipe_probes.md: 2544.7 + 1044.5 + 859.8); the interpreter's from an earlier build
+# (profiles/ps_map_kernel_c5_2to8.md, before the mass-based Kallen function; an upper bound).
+C5_FP64_INSTR_PER_EVENT = {"compiled": 4449.0, "interpreter": 6559.0}
 # The same for the compiled six-channel 2->5 program, from one 2e6-event launch in the benchmark's
-# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1116.1 + DADD 278.4 + DMUL 413.3.
-C3_FP64_INSTR_PER_EVENT = 1807.9
+# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1078.9 + DADD 280.5 + DMUL 389.9.
+C3_FP64_INSTR_PER_EVENT = 1749.3
+# FP64-pipe instructions in all (arithmetic and conversions) per event of the compiled mixed-precision
+# programs (profiles/fp64_pipe_probes.md): the FP64 pipe also bounds the mixed form.
+MIXED_FP64_PIPE_PER_EVENT = {"2to4": 108.4, "2to5": 396.7, "2to8": 601.7}
 # FP64-pipe instructions per call of CUDA's double functions on the GB300, from the ncu counters of
 # ps_fp64_probe's function loops less the empty loop (profiles/fp64_pipe_probes.md); an add or a
 # multiply is one.  They convert the oracle's operation counts into the pipe's work.
@@ -144,7 +151,8 @@ def summary(line):
            "sm_count": g(rf, "fp64_peak", "sm_count"),
            "method_pipe_equiv_per_event": _r(g(rf, "method", "fp64_pipe_equivalent_per_event")),
            "mixed_2to4": {"events_per_s": _r(g(line, "mixed_precision", "value")),
-                          "speedup": _r(g(line, "mixed_precision", "speedup_vs_fp64"), 3)},
+                          "speedup": _r(g(line, "mixed_precision", "speedup_vs_fp64"), 3),
+                          "fp64_pipe_frac": _r(g(line, "mixed_precision", "fp64_pipe", "frac"), 3)},
            "multichannel_2to5": {"fp64": _r(g(line, "multichannel", "value")),
                                  "fp64_pipe_frac": _r(g(line, "multichannel", "roofline", "frac"), 3),
                                  "mixed": _r(g(line, "multichannel", "mixed_precision", "value"))},
@@ -468,6 +476,9 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
         instr = C5_FP64_INSTR_PER_EVENT["compiled" if jit else "interpreter"]
         res["roofline"] = fp64_pipe_roofline(instr, res["value"] / world)
         res["roofline"]["fp64_instr_per_event"] = instr
+    elif jit:  # the mixed form: every FP64-pipe instruction (islands and conversions)
+        res["roofline"] = fp64_pipe_roofline(MIXED_FP64_PIPE_PER_EVENT["2to8"], res["value"] / world)
+        res["roofline"]["fp64_pipe_instr_per_event"] = MIXED_FP64_PIPE_PER_EVENT["2to8"]
     if table is not None:
         res["autotune_candidates"] = len(table)
     if host_copy:
@@ -987,6 +998,9 @@ def main():
                  "speedup_vs_fp64": ms / mms,
                  "bytes_per_event": 6 * 4 * 4 + 4 + 4 + 8,
                  "hbm_gbs": (6 * 4 * 4 + 4 + 4 + 8) * N / (mms / 1e3) / 1e9}
+        if jit:  # the mixed form is bound by the FP64 pipe too (islands and conversions)
+            mixed["fp64_pipe"] = fp64_pipe_roofline(MIXED_FP64_PIPE_PER_EVENT["2to4"], N / (mms / 1e3))
+            mixed["fp64_pipe"]["counts"] = "every FP64-pipe instruction per event (arithmetic and conversions)"
 
     # multichannel 2->5: six channels of mixed topology, uneven counts (1e5 .. 4e6, 2e7 in all), one
     # persistent launch per step, tiles and schedule from the autotuner, replayed as a CUDA graph
@@ -1044,6 +1058,8 @@ def main():
         xms = xev[0].elapsed_time(xev[1]) / args.steps
         xst = xprog.stats()  # the last step drew the same events as the last FP64 step
         multi["mixed_precision"] = {"value": world * sum(counts) / (xms / 1e3), "ms_per_step": xms,
+                                    "fp64_pipe_frac": (MIXED_FP64_PIPE_PER_EVENT["2to5"] * sum(counts) / (xms / 1e3)
+                                                       / 1e9 / (_FP64_PEAK["value"] or FP64_PEAK_GINSTR)) if jit else None,
                                     "speedup_vs_fp64": cms / xms, "autotuned": mbest,
                                     "integral_rel_diff_vs_fp64_same_events":
                                         sum(c["sum_w"] for c in xst) / multi["integral"] - 1.0}
@@ -1058,8 +1074,8 @@ def main():
             streamed["e2e"] = streamed_leg(ps, W, torch, stream, rank, world, local, best=streamed["autotuned"],
                                            host_copy=True, jit=jit)["e2e"]
         sm = streamed_leg(ps, W, torch, stream, rank, world, local, precision="mixed", jit=jit)
-        streamed["mixed_precision"] = {k: sm[k] for k in ("value", "ms_total", "integral", "rel_err", "ess",
-                                                          "effective_events_per_s", "autotuned")}
+        streamed["mixed_precision"] = {k: sm.get(k) for k in ("value", "ms_total", "integral", "rel_err", "ess",
+                                                              "effective_events_per_s", "autotuned", "roofline")}
         streamed["mixed_precision"]["integral_rel_diff_vs_fp64_same_events"] = sm["integral"] / streamed["integral"] - 1
         streamed["mixed_precision"]["speedup_vs_fp64"] = streamed["ms_total"] / sm["ms_total"]
 

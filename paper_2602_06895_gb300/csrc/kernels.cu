@@ -56,7 +56,7 @@ struct InterpPolicy {
         out_pc = dev::find_output(s_code, C.code_len);
     }
     __device__ __forceinline__ double event(int c, const ChannelLaunch& C, int64_t ev, int64_t local, bool active) {
-        dev::load_inputs(f, lp, c, C.n_random, ev, local, active);
+        dev::load_inputs<kMix>(f, lp, c, C.n_random, ev, local, active);
         if (kMix) dev::run_code_mixed(s_code, out_pc, f, reinterpret_cast<float*>(s_grid), C.vbins, lp.status + 1, active);
         else dev::run_code(s_code, out_pc, f, s_grid, C.vbins, lp.status + 1, active);
         return dev::store_outputs<kMix>(f, s_code + out_pc + 3, s_code[out_pc + 1], lp, C, local, active);

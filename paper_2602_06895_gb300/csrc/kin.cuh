@@ -86,6 +86,20 @@ __device__ __forceinline__ double kallen(double x, double y, double z) {
     }
     return pos_bits(l) ? l : 0.0;  // clamped at zero (NaN -> 0)
 }
+// lambda(x, m1^2, m2^2) from the masses m1, m2 >= 0 themselves: the factorised form above with
+// sqrt(m^2) replaced by m.  For a double m the correctly rounded sqrt of fl(m^2) is m exactly
+// (its error is below half an ulp of m), so this equals kallen(x, m1 m1, m2 m2) bit for bit,
+// without the two square roots.
+__device__ __forceinline__ double kallen_m(double x, double m1, double m2) {
+    double l;
+    if (zero_bits(m1 * m1) && zero_bits(m2 * m2)) {
+        l = x * x;
+    } else {
+        double hi = m1 + m2, lo = m1 - m2;
+        l = fma(-hi, hi, x) * fma(-lo, lo, x);  // explicit: the same roundings with constant masses
+    }
+    return pos_bits(l) ? l : 0.0;
+}
 
 // Pure boosts out of the rest frame of q (mass mq) sharing their reciprocals: 1/mq and
 // 1/(mq (E_q + mq)) are taken once per frame, for every momentum boosted with it.
@@ -131,7 +145,7 @@ __device__ __forceinline__ void t_range(double s, double mA2, double mB2, double
     double m12 = m1 * m1, m22 = m2 * m2;
     double inv2s = 0.5 / s;
     double A = mA2 + m12 - (s + mA2 - mB2) * (s + m12 - m22) * inv2s;
-    B = sqrt(kallen(s, mA2, mB2) * kallen(s, m12, m22)) * inv2s;
+    B = sqrt(kallen(s, mA2, mB2) * kallen_m(s, m1, m2)) * inv2s;
     double prod = (m12 - mA2) * (m22 - mB2) + (m12 * mB2 - m22 * mA2) * (m12 - m22 - mA2 + mB2) / s;
     double big = (A <= 0.0) ? A - B : A + B;   // root without cancellation
     double small = (big != 0.0) ? prod / big : 0.0;

@@ -126,7 +126,7 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
 
     double m12 = m1 * m1, m22 = m2 * m2;
     double i2m0 = 0.5 * bf.inv_m;
-    double pabs = sqrt(kallen(s, m12, m22)) * i2m0;
+    double pabs = sqrt(kallen_m(s, m1, m2)) * i2m0;
     double e1 = (s + m12 - m22) * i2m0, e2 = (s + m22 - m12) * i2m0;
     double vx = pabs * sth * cph, vy = pabs * sth * sph, vz = pabs * cth;
     // Ry(theta_A) then Rz(phi_A)
@@ -148,7 +148,7 @@ __device__ __forceinline__ double two_body(double rphi, double rth, double s0, d
     const double inv_m0 = m0 * inv_s0;  // 1/m0 = m0/s0: one division per decay
     double m12 = m1 * m1, m22 = m2 * m2;
     // sqrt(lambda) = s0 exactly for two massless daughters
-    double sl = (zero_bits(m12) && zero_bits(m22)) ? s0 : sqrt(kallen(s0, m12, m22));
+    double sl = (zero_bits(m12) && zero_bits(m22)) ? s0 : sqrt(kallen_m(s0, m1, m2));
     double i2m0 = 0.5 * inv_m0;
     double pabs = sl * i2m0;
     double e1 = (s0 + m12 - m22) * i2m0, e2 = (s0 + m22 - m12) * i2m0;
@@ -512,6 +512,18 @@ __device__ __forceinline__ double rcp64(double x) {
     return fma(r, e, r);
 }
 
+// lambda(x, m1^2, m2^2) from the masses m1, m2 >= 0 (the factorised form, no square roots)
+__device__ __forceinline__ double kallen64_m(double x, double m1, double m2) {
+    double l;
+    if (zero_bits(m1 * m1) && zero_bits(m2 * m2)) {
+        l = x * x;
+    } else {
+        double hi = m1 + m2, lo = m1 - m2;
+        l = fma(-hi, hi, x) * fma(-lo, lo, x);  // explicit: the same roundings with constant masses
+    }
+    return pos_bits(l) ? l : 0.0;
+}
+
 __device__ __forceinline__ double kallen64(double x, double y, double z) {
     double l;
     if (zero_bits(y) && zero_bits(z)) {
@@ -615,7 +627,7 @@ __device__ __forceinline__ void t_range(double s, double mA2, double mB2, double
     double m12 = m1 * m1, m22 = m2 * m2;
     double is = rcp64(s);
     double A = mA2 + m12 - 0.5 * (s + mA2 - mB2) * (s + m12 - m22) * is;
-    B = 0.5 * sqrt64(kallen64(s, mA2, mB2) * kallen64(s, m12, m22)) * is;
+    B = 0.5 * sqrt64(kallen64(s, mA2, mB2) * kallen64_m(s, m1, m2)) * is;
     double prod = (m12 - mA2) * (m22 - mB2) + (m12 * mB2 - m22 * mA2) * (m12 - m22 - mA2 + mB2) * is;
     double big = (A <= 0.0) ? A - B : A + B;
     double small = (big != 0.0) ? prod * rcp64(big) : 0.0;
@@ -648,7 +660,7 @@ __device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double ta
     sincospif(2.0f * rphi, &sph, &cph);
     double m12 = m1 * m1, m22 = m2 * m2;
     float i2m0 = 0.5f / m0;
-    float pabs = static_cast<float>(sqrt64(kallen64(s, m12, m22))) * i2m0;
+    float pabs = static_cast<float>(sqrt64(kallen64_m(s, m1, m2))) * i2m0;
     float e1 = static_cast<float>(s + m12 - m22) * i2m0, e2 = static_cast<float>(s + m22 - m12) * i2m0;
     float vx = pabs * sth * cph, vy = pabs * sth * sph, vz = pabs * cth;
     float rx = ca * vx + sa * vz, rz = -sa * vx + ca * vz;
@@ -662,13 +674,24 @@ __device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double ta
 template <bool kBoost>
 __device__ __forceinline__ double two_body(float rphi, float rth, double s0, double m1, double m2, F4 p0, F4& p1,
                                            F4& p2) {
-    double m12 = m1 * m1, m22 = m2 * m2;
-    double lam = kallen64(s0, m12, m22);                   // FP64 island at threshold
-    float sl = sqrtf(static_cast<float>(lam));
-    float m0 = sqrtf(static_cast<float>(s0));
-    float i2m0 = 0.5f / m0;
+    float sl, m0, i2m0, e1, e2;
+    bool massless = zero_bits(m1) && zero_bits(m2);
+    if (massless) {  // massless daughters: sqrt(lambda) = s0, E1 = E2 = s0/(2 m0)
+        const float s0f = static_cast<float>(s0);
+        sl = s0f;
+        m0 = sqrtf(s0f);
+        i2m0 = 0.5f / m0;
+        e1 = e2 = s0f * i2m0;
+    } else {
+        double m12 = m1 * m1, m22 = m2 * m2;
+        double lam = kallen64_m(s0, m1, m2);                   // FP64 island at threshold
+        sl = sqrtf(static_cast<float>(lam));
+        m0 = sqrtf(static_cast<float>(s0));
+        i2m0 = 0.5f / m0;
+        e1 = static_cast<float>(s0 + m12 - m22) * i2m0;
+        e2 = static_cast<float>(s0 + m22 - m12) * i2m0;
+    }
     float pabs = sl * i2m0;
-    float e1 = static_cast<float>(s0 + m12 - m22) * i2m0, e2 = static_cast<float>(s0 + m22 - m12) * i2m0;
     float cth = 2.0f * rth - 1.0f;
     float sth = 2.0f * sqrtf(rth * (1.0f - rth));
     float sph, cph;
@@ -681,6 +704,13 @@ __device__ __forceinline__ double two_body(float rphi, float rth, double s0, dou
     } else {
         p1 = q1;
         p2 = q2;
+    }
+    // J = (pi/2) sqrt(lambda)/s0: pi/2 itself for massless daughters (NaN where s0 is not a
+    // positive finite float, as the division would give), with no FP64 conversion
+    if (massless) {
+        const float s0f = static_cast<float>(s0);
+        return (s0f > 0.0f && s0f <= 3.40282347e38f) ? static_cast<double>(0.5f * static_cast<float>(kPi))
+                                              : __longlong_as_double(0x7FF8000000000000LL);
     }
     return static_cast<double>(0.5f * static_cast<float>(kPi) * sl / static_cast<float>(s0));
 }
@@ -838,8 +868,17 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
                 break;
             }
             case PS_OP_CUT_UNPHYSICAL: {
-                double w = ld(f, a[0]), x1 = ld(f, a[1]), x2 = ld(f, a[2]);
-                bool bad = !finite_bits(w) || !(in_unit_bits(x1) && in_unit_bits(x2));
+                // x1, x2 are float values in the mixed form: a register frame tests them as floats
+                // (no conversion), the shared-memory slot file on their FP64 bit patterns
+                double w = ld(f, a[0]);
+                bool xin;
+                if constexpr (Fr::kStatic) {
+                    const float x1 = mx::ldf(f, a[1]), x2 = mx::ldf(f, a[2]);
+                    xin = x1 > 0.0f && x1 <= 1.0f && x2 > 0.0f && x2 <= 1.0f;
+                } else {
+                    xin = in_unit_bits(ld(f, a[1])) && in_unit_bits(ld(f, a[2]));
+                }
+                bool bad = !finite_bits(w) || !xin;
                 op_loop<Fr>(3, na, 1, [&](int k) {
                     F4 p = mx::ldp(f, a[k]);
                     bad |= !(isfinite(p.e) && isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
@@ -858,10 +897,11 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
             case PS_OP_MOM_ADD: mx::stp(f, o[0], mx::f4_add(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
             case PS_OP_MOM_SUB: mx::stp(f, o[0], mx::f4_sub(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
             case PS_OP_PDF_POWER: {
-                double xd = ld(f, a[0]);
-                float x = static_cast<float>(xd), al = mx::ldf(f, a[1]), be = mx::ldf(f, a[2]);
-                float fx = expf(al * (na > 3 ? static_cast<float>(ld(f, a[3])) : logf(x)));
-                float y = static_cast<float>(1.0 - xd);
+                // x is a float value here (r_to_x1x2 of the mixed form), so 1 - x in float is the
+                // correctly rounded difference, as the FP64 difference rounded to float would be
+                float x = mx::ldf(f, a[0]), al = mx::ldf(f, a[1]), be = mx::ldf(f, a[2]);
+                float fx = expf(al * (na > 3 ? mx::ldf(f, a[3]) : logf(x)));
+                float y = 1.0f - x;
                 float fy;
                 if (be == 3.0f) fy = y * y * y;
                 else if (be == 2.0f) fy = y * y;
@@ -931,8 +971,10 @@ __device__ __forceinline__ int find_output(const int32_t* code, int len) {
 
 // ---------------------------------------------------------------- event input and output
 // Random inputs of one event into slots 0..n_random-1: explicit SoA, or Philox4x32-10 with
-// counter (ev_lo, ev_hi, channel, j/2) and key (seed_lo, seed_hi).
-template <class Fr>
+// counter (ev_lo, ev_hi, channel, j/2) and key (seed_lo, seed_hi).  Mixed-precision programs
+// (kMix), whose maps read the random numbers as floats, take the float form of each coordinate
+// directly from the bits (no FP64 work, no conversion).
+template <bool kMix, class Fr>
 __device__ __forceinline__ void load_inputs(const Fr& f, const LaunchParams& lp, int c, int n_random, int64_t ev,
                                             int64_t local, bool active) {
     if (lp.r != nullptr) {
@@ -942,8 +984,13 @@ __device__ __forceinline__ void load_inputs(const Fr& f, const LaunchParams& lp,
             uint4 o = philox4x32_10(make_uint4(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32),
                                                static_cast<uint32_t>(c), static_cast<uint32_t>(j >> 1)),
                                     static_cast<uint32_t>(lp.seed), static_cast<uint32_t>(lp.seed >> 32));
-            st(f, j, unit_from_bits(o.y, o.x));
-            if (j + 1 < n_random) st(f, j + 1, unit_from_bits(o.w, o.z));
+            if constexpr (kMix) {
+                st(f, j, static_cast<double>(rng::unit_from_bits_f(o.y)));
+                if (j + 1 < n_random) st(f, j + 1, static_cast<double>(rng::unit_from_bits_f(o.w)));
+            } else {
+                st(f, j, unit_from_bits(o.y, o.x));
+                if (j + 1 < n_random) st(f, j + 1, unit_from_bits(o.w, o.z));
+            }
         });
     }
 }

@@ -26,5 +26,14 @@ __device__ __forceinline__ double unit_from_bits(uint32_t hi, uint32_t lo) {
     return one_plus - 0x1.fffffffffffffp-1;
 }
 
+// The float form of a point coordinate, for the mixed-precision programs: (k + 1/2) 2^-23 for the
+// top 23 bits k of hi, exactly: the float 1 + k 2^-23 assembled from bits minus (1 - 2^-24),
+// exact by Sterbenz's lemma.  It lies in the same 2^-23 cell as the double form, so every VEGAS
+// bin and grid cell agrees with it.
+__device__ __forceinline__ float unit_from_bits_f(uint32_t hi) {
+    const float one_plus = __int_as_float(0x3F800000u | (hi >> 9));
+    return one_plus - 0x1.fffffep-1f;
+}
+
 }  // namespace rng
 }  // namespace ps
