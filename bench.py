@@ -59,25 +59,26 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07
 # The same counters for the compiled program's kernel (ps_jit_map) on this workload, from its own
 # ncu capture (profiles/ps_jit_map_ww_2to4.md): DFMA 405.6 + DADD 113.6 + DMUL 197.6 = 716.8 FP64
 # arithmetic instructions (1122.4 flops) and 185.9 DRAM bytes per event; FP64 pipe 85.4 % active.
-# Re-captured on the current build, with the Kallen function of decays and 2->2 blocks taken from
-# the masses (no square roots; profiles/fp64_pipe_probes.md): DFMA 399.1 + DADD 113.3 + DMUL 195.1
-# = 707.5 (1106.6 flops), 784.6 FP64-pipe instructions in all (conversions included), 185.5 DRAM
-# bytes per event, pipe active 0.834 of the elapsed cycles -- the FP64 issue probe's saturating
-# loop reaches 0.84.
-COMPILED_COUNTERS = {"instr": 707.5, "flops": 1106.6, "dram": 185.5, "pipe": 0.834, "pipe_instr": 784.6}
+# Re-captured on the current build (the Kallen function of decays and 2->2 blocks taken from the
+# masses, the per-tile statistics with six FP64 instructions per event;
+# profiles/fp64_pipe_probes.md): DFMA 399.1 + DADD 103.3 + DMUL 195.1 = 697.5 (1096.6 flops),
+# 769.6 FP64-pipe instructions in all, 185.4 DRAM bytes per event, pipe active 0.837 of the
+# elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
+COMPILED_COUNTERS = {"instr": 697.5, "flops": 1096.6, "dram": 185.4, "pipe": 0.837, "pipe_instr": 769.6}
 INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from
 # the ncu captures of one 2^20-event launch: the compiled program on the current build
-# (profiles/fp64_pipe_probes.md: 2544.7 + 1044.5 + 859.8); the interpreter's from an earlier build
+# (profiles/fp64_pipe_probes.md: 2544.7 + 1034.5 + 859.8); the interpreter's from an earlier build
 # (profiles/ps_map_kernel_c5_2to8.md, before the mass-based Kallen function; an upper bound).
-C5_FP64_INSTR_PER_EVENT = {"compiled": 4449.0, "interpreter": 6559.0}
+C5_FP64_INSTR_PER_EVENT = {"compiled": 4438.9, "interpreter": 6559.0}
 # The same for the compiled six-channel 2->5 program, from one 2e6-event launch in the benchmark's
-# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1078.9 + DADD 280.5 + DMUL 389.9.
-C3_FP64_INSTR_PER_EVENT = 1749.3
+# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1078.9 + DADD 270.5 + DMUL 389.9.
+C3_FP64_INSTR_PER_EVENT = 1739.3
 # FP64-pipe instructions in all (arithmetic and conversions) per event of the compiled mixed-precision
-# programs (profiles/fp64_pipe_probes.md): the FP64 pipe also bounds the mixed form.
-MIXED_FP64_PIPE_PER_EVENT = {"2to4": 108.4, "2to5": 396.7, "2to8": 601.7}
+# programs (profiles/fp64_pipe_probes.md): the FP64 pipe's share of the mixed form (with the
+# conversions on the integer ALU, 0.55-0.75 of its cycles: no longer the only bound).
+MIXED_FP64_PIPE_PER_EVENT = {"2to4": 61.4, "2to5": 312.8, "2to8": 432.1}
 # FP64-pipe instructions per call of CUDA's double functions on the GB300, from the ncu counters of
 # ps_fp64_probe's function loops less the empty loop (profiles/fp64_pipe_probes.md); an add or a
 # multiply is one.  They convert the oracle's operation counts into the pipe's work.

@@ -574,6 +574,25 @@ int64_t ps_launch_count(void);
 #define PS_PROBE_SINCOSPI 23
 int ps_fp64_probe(int kind, int blocks, int iters, double* sink, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * The device helpers of the mixed-precision form at the edges of its FP64 islands (no
+ * counterpart in the paper), exposed so that their results can be checked against the
+ * hardware's conversions and FP64 functions.  ps_mixed_helpers applies helper `kind` to each of
+ * the n values of in[] and writes out[] (both device, caller-owned; in[] and out[] of the types
+ * below), asynchronously on `stream`:
+ *   PS_MIXED_F2D     float  -> double: IEEE 754 widening (exact), on the integer ALU;
+ *   PS_MIXED_D2F     double -> float: IEEE 754 narrowing, round to nearest even, integer ALU;
+ *   PS_MIXED_SQRT64  double -> double: sqrt(x) from a seed (exponent on the integer ALU, fraction
+ *                    from a float instruction) and one FP64 Newton step, relative error below
+ *                    1e-13 for normal x > 0; 0 for x <= 0 or NaN;
+ *   PS_MIXED_RCP64   double -> double: 1/x the same way, for normal x of either sign.
+ * Returns PS_ERR_INVALID_ARGUMENT for an unknown kind, n < 0, or a null pointer with n > 0. */
+#define PS_MIXED_F2D 0
+#define PS_MIXED_D2F 1
+#define PS_MIXED_SQRT64 2
+#define PS_MIXED_RCP64 3
+int ps_mixed_helpers(int kind, const void* in, void* out, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -177,7 +177,8 @@ std::string imm_source(const Compiled& C, size_t c) {
 std::string channel_body(const Compiled& C, size_t c, bool mixed) {
     const std::string cs = std::to_string(c);
     std::string s;
-    s += "                const dev::RegFrame<" + std::to_string(std::max(C.n_slots, 1)) + ", I" + cs + "> f{};\n";
+    s += std::string("                const dev::") + (mixed ? "MixRegFrame<" : "RegFrame<") +
+         std::to_string(std::max(C.n_slots, 1)) + ", I" + cs + "> f{};\n";
     s += "                dev::load_inputs<kMix>(f, lp, " + cs + ", " + std::to_string(C.n_random) + ", ev, local, active);\n";
     size_t pc = 0;
     InvariantMemo memo;

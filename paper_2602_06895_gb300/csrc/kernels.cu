@@ -15,6 +15,7 @@
 // or is resolved by selects, so the warps of a channel never diverge.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -340,6 +341,18 @@ unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC
 void count_launches(int n) { __atomic_add_fetch(&g_launches, static_cast<unsigned long long>(n), __ATOMIC_RELAXED); }
 bool is_reduce_kernel(const void* func) { return func == reinterpret_cast<const void*>(ps_reduce_kernel); }
 
+// ---------------------------------------------------------------- mixed-form helpers
+// Elementwise application of one device helper of the mixed form (ps_mixed_helpers).
+template <int kKind, class In, class Out>
+__global__ void __launch_bounds__(256) ps_mixed_helper_kernel(const In* in, Out* out, int64_t n) {
+    for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
+        if constexpr (kKind == PS_MIXED_F2D) out[i] = dev::mx::f2d(in[i]);
+        else if constexpr (kKind == PS_MIXED_D2F) out[i] = dev::mx::d2f(in[i]);
+        else if constexpr (kKind == PS_MIXED_SQRT64) out[i] = dev::mx::sqrt64(in[i]);
+        else out[i] = dev::mx::rcp64(in[i]);
+    }
+}
+
 // ---------------------------------------------------------------- allocation-free scratch
 // Fixed scratch for ps_generate_noalloc: kNoallocTiles per-tile partial-sum records (4 doubles
 // each, 4 MiB) in a file-scope device array.  Every device that loads the library holds it until
@@ -371,3 +384,30 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes, std::string* err) {
 }
 
 }  // namespace ps
+
+extern "C" int ps_mixed_helpers(int kind, const void* in, void* out, int64_t n, void* stream) {
+    using namespace ps;
+    if (n < 0 || (n > 0 && (in == nullptr || out == nullptr))) return PS_ERR_INVALID_ARGUMENT;
+    if (kind < PS_MIXED_F2D || kind > PS_MIXED_RCP64) return PS_ERR_INVALID_ARGUMENT;
+    if (n == 0) return PS_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152LL * 16);
+    const int g = static_cast<int>(blocks);
+    switch (kind) {
+        case PS_MIXED_F2D:
+            ps_mixed_helper_kernel<PS_MIXED_F2D><<<g, 256, 0, s>>>(static_cast<const float*>(in), static_cast<double*>(out), n);
+            break;
+        case PS_MIXED_D2F:
+            ps_mixed_helper_kernel<PS_MIXED_D2F><<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<float*>(out), n);
+            break;
+        case PS_MIXED_SQRT64:
+            ps_mixed_helper_kernel<PS_MIXED_SQRT64><<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), n);
+            break;
+        default:
+            ps_mixed_helper_kernel<PS_MIXED_RCP64><<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), n);
+            break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
+    count_launches(1);
+    return PS_OK;
+}

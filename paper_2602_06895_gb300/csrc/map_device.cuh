@@ -469,6 +469,73 @@ static __device__ void run_code(const int32_t* code, int len, const Frame& f, co
 // bounds, and every Jacobian product.  Scalars stay FP64 in the slot file.
 namespace mx {
 
+// Conversions between binary64 and binary32 written on the IEEE 754 bit layouts and executed by
+// the integer ALU.  The FP64 pipe that bounds these kernels also executes the hardware
+// conversions, and the mixed form converts at every edge of an FP64 island; on the integer
+// ALU a conversion costs issue slots of a pipe with 32 times the FP64 pipe's rate.  Both give
+// the correctly rounded result (round to nearest, ties to even) for every input; NaN comes out
+// as a NaN.
+__device__ __forceinline__ double f2d(float x) {
+    const uint32_t u = __float_as_uint(x), a = u & 0x7FFFFFFFu;
+    uint32_t hi, lo = u << 29;  // the low three fraction bits open the low word
+    if (__builtin_expect(a - 0x00800000u < 0x7F000000u, 1)) {
+        hi = (a >> 3) + 0x38000000u;  // normal: exponent rebiased 127 -> 1023 (+896 << 20)
+    } else if (a >= 0x7F800000u) {
+        hi = 0x7FF00000u | ((a >> 3) & 0xFFFFFu);  // infinity, NaN
+    } else if (a != 0u) {
+        const int lz = __clz(a);                    // subnormal: leading bit at 31 - lz (9..31)
+        const uint32_t m = a << (lz - 8);           // ... moved to bit 23
+        hi = (static_cast<uint32_t>(905 - lz) << 20) | ((m >> 3) & 0xFFFFFu);  // 2^(8 - lz - 126)
+        lo = m << 29;
+    } else {
+        hi = 0u;
+    }
+    return __hiloint2double(static_cast<int>((u & 0x80000000u) | hi), static_cast<int>(lo));
+}
+
+__device__ __forceinline__ float d2f(double x) {
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(x)), lo = static_cast<uint32_t>(__double2loint(x));
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    uint32_t r;
+    if (__builtin_expect(e - 897u < 254u, 1)) {  // a float normal: 23 fraction bits, rounded
+        const uint32_t m = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu, rem = lo & 0x1FFFFFFFu;
+        const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+        r = ((e - 896u) << 23) + m + up;  // a carry out of the fraction raises the exponent
+    } else if (e >= 1151u) {              // beyond the float range, infinity, NaN
+        r = (e == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u) ? 0x7FFFFFFFu : 0x7F800000u;
+    } else if (e >= 873u) {               // a float subnormal: the 53-bit significand shifted
+        const unsigned long long sig =
+            (1ULL << 52) | (static_cast<unsigned long long>(hi & 0xFFFFFu) << 32) | lo;
+        const int sh = static_cast<int>(926u - e);  // to units of 2^-149: 30..53
+        const unsigned long long q = sig >> sh, rem = sig & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1);
+        r = static_cast<uint32_t>(q) + ((rem > half || (rem == half && (q & 1ULL))) ? 1u : 0u);
+    } else {
+        r = 0u;  // zero, or below half the least subnormal
+    }
+    return __uint_as_float((hi & 0x80000000u) | r);
+}
+
+// FP32 seeds from IEEE operations only (a compile-time evaluation of a constant argument gives
+// the device's bits, so compiled and interpreted programs agree):
+// 1/sqrt(m), m in [1, 4): the bit-level estimate 0x5F375A86 - (bits >> 1) (Lomont 2003,
+// relative error below 3.5%) and three Newton steps y (3/2 - m y^2 / 2);
+// 1/m, m in [1, 2): the linear estimate 24/17 - 8/17 m (the minimax line of the Newton-Raphson
+// division, error below 1/17) and three Newton steps y + y (1 - m y).  Both end within a few
+// float ulps.
+__device__ __forceinline__ float rsqrt_m(float m) {
+    float y = __uint_as_float(0x5F375A86u - (__float_as_uint(m) >> 1));
+    const float h = 0.5f * m;
+    y = y * fmaf(-h, y * y, 1.5f);
+    y = y * fmaf(-h, y * y, 1.5f);
+    return y * fmaf(-h, y * y, 1.5f);
+}
+__device__ __forceinline__ float rcp_m(float m) {
+    float y = fmaf(-8.0f / 17.0f, m, 24.0f / 17.0f);
+    y = fmaf(y, fmaf(-m, y, 1.0f), y);
+    y = fmaf(y, fmaf(-m, y, 1.0f), y);
+    return fmaf(y, fmaf(-m, y, 1.0f), y);
+}
+
 struct F4 {
     float e, x, y, z;
 };
@@ -490,24 +557,54 @@ __device__ __forceinline__ void stp(const Frame& f, int slot, F4 p) {
     q[2 * st] = p.y;
     q[3 * st] = p.z;
 }
-// immediates come from their float copy: no FP64-pipe conversion per read
-__device__ __forceinline__ float ldf(const Frame& f, int a) {
-    return a >= 0 ? static_cast<float>(f.S[a * f.block]) : f.immf[~a];
+// immediates come from their float copy: no conversion per read
+__device__ __forceinline__ float ldf(const Frame& f, int a) { return a >= 0 ? d2f(f.S[a * f.block]) : f.immf[~a]; }
+// a float result into a scalar slot (held as its double in the shared-memory slot file)
+__device__ __forceinline__ void stf(const Frame& f, int slot, float x) { f.S[slot * f.block] = f2d(x); }
+
+// Seeds of the FP64 reciprocal square root and reciprocal for any normal double x = 1.f 2^e:
+// the exponent is split off on the integer ALU, the FP32 seed sees only the fraction
+// (truncated to 23 bits) with an exponent of 0 or 1, and the result's exponent is set from e.
+// Relative error below ~2.5e-7 (the truncation and the FP32 rounding).
+__device__ __forceinline__ double rsqrt_seed(double x) {  // x > 0
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(x)), lo = static_cast<uint32_t>(__double2loint(x));
+    const int e = static_cast<int>((hi >> 20) & 0x7FFu) - 1023;
+    const int p = e & 1, k = (e - p) / 2;  // x = 1.f 2^p 4^k: rsqrt(x) = rsqrt(1.f 2^p) 2^-k
+    const float r =
+        rsqrt_m(__uint_as_float((static_cast<uint32_t>(127 + p) << 23) | (__funnelshift_l(lo, hi, 3) & 0x7FFFFFu)));
+    const uint32_t u = __float_as_uint(r);  // in (1/2, 1]
+    return __hiloint2double(static_cast<int>((u >> 3) + 0x38000000u - (static_cast<uint32_t>(k) << 20)),
+                            static_cast<int>(u << 29));
+}
+__device__ __forceinline__ double rcp_seed(double x) {  // x != 0
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(x)), lo = static_cast<uint32_t>(__double2loint(x));
+    const int e = static_cast<int>((hi >> 20) & 0x7FFu) - 1023;
+    const float r = rcp_m(__uint_as_float(0x3F800000u | (__funnelshift_l(lo, hi, 3) & 0x7FFFFFu)));
+    const uint32_t u = __float_as_uint(r);  // 1/(1.f) in (1/2, 1]
+    return __hiloint2double(
+        static_cast<int>((hi & 0x80000000u) | ((u >> 3) + 0x38000000u - (static_cast<uint32_t>(e) << 20))),
+        static_cast<int>(u << 29));
 }
 
-// sqrt in FP64 from a float reciprocal-square-root seed and one Newton step in FP64:
-// s = x r, e = x - s^2, s += e r/2 (relative error ~ 1.5 delta^2 for a seed error delta).
+// sqrt in FP64 from the reciprocal-square-root seed and one Newton step in FP64:
+// s = x r, e = x - s^2, s += e r/2 (relative error ~ 1.5 delta^2 for a seed error delta:
+// below 1e-13).  0 for x <= 0 and NaN; x a normal double otherwise.  The empty asm makes x
+// opaque: a compiled program evaluates sqrt64 of a constant at run time, as the interpreter
+// does, so that no folded result changes how the expressions around it are contracted.
 __device__ __forceinline__ double sqrt64(double x) {
+    asm("" : "+d"(x));
     if (!pos_bits(x)) return 0.0;
-    double r = static_cast<double>(rsqrtf(static_cast<float>(x)));
+    double r = rsqrt_seed(x);
     double s = x * r;
     double e = fma(-s, s, x);
     return fma(e, 0.5 * r, s);
 }
 
-// 1/x in FP64 from a float reciprocal seed and one Newton step.
+// 1/x in FP64 from the reciprocal seed and one Newton step (relative error ~ delta^2), for a
+// normal double x.
 __device__ __forceinline__ double rcp64(double x) {
-    double r = static_cast<double>(__frcp_rn(static_cast<float>(x)));
+    asm("" : "+d"(x));  // opaque, as in sqrt64
+    double r = rcp_seed(x);
     double e = fma(-x, r, 1.0);
     return fma(r, e, r);
 }
@@ -529,9 +626,11 @@ __device__ __forceinline__ double kallen64(double x, double y, double z) {
     if (zero_bits(y) && zero_bits(z)) {
         l = x * x;
     } else if (nonneg_bits(y) && nonneg_bits(z)) {
+        // explicit FMAs: with constant masses a compiled program folds sqrt64(y) and sqrt64(z),
+        // and the contraction of x - hi^2 must not depend on it
         double ry = sqrt64(y), rz = sqrt64(z);
         double hi = ry + rz, lo = ry - rz;
-        l = (x - hi * hi) * (x - lo * lo);
+        l = fma(-hi, hi, x) * fma(-lo, lo, x);
     } else if (nonpos_bits(y) && nonpos_bits(z)) {
         double d = z - y;
         l = x * x - 2.0 * x * (y + z) + d * d;
@@ -561,29 +660,29 @@ __device__ __forceinline__ void map_nu(float r, double m, double nu, double xmin
     double m2 = pos_bits(m) ? m * m : -a;
     double lo = xmin - m2, hi = xmax - m2;
     bool ok = pos_bits(lo) && ge_pos_bits(hi, lo);
-    float L = log1pf(static_cast<float>(xmax - xmin) / static_cast<float>(lo));
+    float L = log1pf(d2f(xmax - xmin) / d2f(lo));
     float e, jf;
     if (dbits(nu) == dbits(1.0)) {
         e = expm1f(r * L);
         jf = (1.0f + e) * L;
-        x = fma(lo, static_cast<double>(e), xmin);
-        jac = lo * static_cast<double>(jf);
+        x = fma(lo, f2d(e), xmin);
+        jac = lo * f2d(jf);
     } else if (dbits(nu) < dbits(1.0)) {  // nu < 1 (nu is never NaN)
-        float w = static_cast<float>(1.0 - nu);
+        float w = d2f(1.0 - nu);
         float rho = expm1f(w * L);
         float z = r * rho;
         e = expm1f(log1pf(z) / w);
         jf = (1.0f + e) * rho / (w * (1.0f + z));
-        x = fma(lo, static_cast<double>(e), xmin);
-        jac = lo * static_cast<double>(jf);
+        x = fma(lo, f2d(e), xmin);
+        jac = lo * f2d(jf);
     } else {
-        float w = static_cast<float>(1.0 - nu);
+        float w = d2f(1.0 - nu);
         float rho = expm1f(-w * L);
         float z = (1.0f - r) * rho;
         float g = expf(log1pf(z) / w);
-        double xm = hi * static_cast<double>(g);
+        double xm = hi * f2d(g);
         x = m2 + xm;
-        jac = -xm * static_cast<double>(rho / (w * (1.0f + z)));
+        jac = -xm * f2d(rho / (w * (1.0f + z)));
     }
     x = clamp_nonneg(x, xmin, xmax);
     if (!ok) { x = xmin; jac = 0.0; }
@@ -595,28 +694,28 @@ __device__ __forceinline__ void map_bw(float r, double M, double G, double xmin,
                                        bool have_u1 = false, double u1 = 0.0) {
     double mg = M * G, m2 = M * M;
     bool ok = pos_bits(mg) && ge_pos_bits(xmax, xmin);  // x_min >= 0 here (a squared mass)
-    float mgf = static_cast<float>(mg);
+    float mgf = d2f(mg);
     float imgf = 1.0f / mgf;
-    float a = static_cast<float>(xmin - m2) * imgf, b = static_cast<float>(xmax - m2) * imgf;
-    float D = atan2f(static_cast<float>(xmax - xmin) * imgf, fmaf(a, b, 1.0f));
-    float u = (have_u1 ? static_cast<float>(u1) : atanf(a)) + D * r;
+    float a = d2f(xmin - m2) * imgf, b = d2f(xmax - m2) * imgf;
+    float D = atan2f(d2f(xmax - xmin) * imgf, fmaf(a, b, 1.0f));
+    float u = (have_u1 ? d2f(u1) : atanf(a)) + D * r;
     bool low = u < -0.785398163f, high = u > 0.785398163f;
     float arg = low ? D * r : (high ? D * (1.0f - r) : u);
     float T = tanf(arg);
     float sec2;
     if (low) {
         float rd = 1.0f / (1.0f - a * T);
-        x = xmin + static_cast<double>(mgf * (T * (1.0f + a * a) * rd));
+        x = xmin + f2d(mgf * (T * (1.0f + a * a) * rd));
         sec2 = (1.0f + a * a) * (1.0f + T * T) * (rd * rd);
     } else if (high) {
         float rd = 1.0f / (1.0f + b * T);
-        x = m2 + static_cast<double>(mgf * ((b - T) * rd));
+        x = m2 + f2d(mgf * ((b - T) * rd));
         sec2 = (1.0f + b * b) * (1.0f + T * T) * (rd * rd);
     } else {
-        x = m2 + static_cast<double>(mgf * T);
+        x = m2 + f2d(mgf * T);
         sec2 = 1.0f + T * T;
     }
-    jac = static_cast<double>(D * mgf * sec2);
+    jac = f2d(D * mgf * sec2);
     x = clamp_nonneg(x, xmin, xmax);
     if (!ok) { x = xmin; jac = 0.0; }
 }
@@ -638,7 +737,7 @@ __device__ __forceinline__ void t_range(double s, double mA2, double mB2, double
 __device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double tabs, double m1, double m2, double s,
                                              double mA2, double mB2, F4& p1, F4& p2) {
     F4 p0 = f4_add(pA, pB);
-    float m0 = static_cast<float>(sqrt64(s));
+    float m0 = d2f(sqrt64(s));
     F4 a = boost_in(pA, p0, m0);
     float pt = sqrtf(a.x * a.x + a.y * a.y);
     float rp = rsqrtf(pt * pt + a.z * a.z);
@@ -651,7 +750,7 @@ __device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double ta
     double dlo = tabs - tlo, dhi = thi - tabs;
     bool near_lo = dlo <= dhi;
     double first = (B > 0.0) ? (near_lo ? dlo : dhi) * rcp64(B) : 1.0;  // 1 - cos or 1 + cos (FP64)
-    float f1 = static_cast<float>(first);
+    float f1 = d2f(first);
     float omc = (B > 0.0) ? (near_lo ? f1 : 2.0f - f1) : 1.0f;
     float opc = (B > 0.0) ? (near_lo ? 2.0f - f1 : f1) : 1.0f;
     float cth = (omc <= opc) ? 1.0f - omc : opc - 1.0f;
@@ -660,8 +759,8 @@ __device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double ta
     sincospif(2.0f * rphi, &sph, &cph);
     double m12 = m1 * m1, m22 = m2 * m2;
     float i2m0 = 0.5f / m0;
-    float pabs = static_cast<float>(sqrt64(kallen64_m(s, m1, m2))) * i2m0;
-    float e1 = static_cast<float>(s + m12 - m22) * i2m0, e2 = static_cast<float>(s + m22 - m12) * i2m0;
+    float pabs = d2f(sqrt64(kallen64_m(s, m1, m2))) * i2m0;
+    float e1 = d2f(s + m12 - m22) * i2m0, e2 = d2f(s + m22 - m12) * i2m0;
     float vx = pabs * sth * cph, vy = pabs * sth * sph, vz = pabs * cth;
     float rx = ca * vx + sa * vz, rz = -sa * vx + ca * vz;
     F4 q1 = {e1, cpa * rx - spa * vy, spa * rx + cpa * vy, rz};
@@ -677,7 +776,7 @@ __device__ __forceinline__ double two_body(float rphi, float rth, double s0, dou
     float sl, m0, i2m0, e1, e2;
     bool massless = zero_bits(m1) && zero_bits(m2);
     if (massless) {  // massless daughters: sqrt(lambda) = s0, E1 = E2 = s0/(2 m0)
-        const float s0f = static_cast<float>(s0);
+        const float s0f = d2f(s0);
         sl = s0f;
         m0 = sqrtf(s0f);
         i2m0 = 0.5f / m0;
@@ -685,11 +784,11 @@ __device__ __forceinline__ double two_body(float rphi, float rth, double s0, dou
     } else {
         double m12 = m1 * m1, m22 = m2 * m2;
         double lam = kallen64_m(s0, m1, m2);                   // FP64 island at threshold
-        sl = sqrtf(static_cast<float>(lam));
-        m0 = sqrtf(static_cast<float>(s0));
+        sl = sqrtf(d2f(lam));
+        m0 = sqrtf(d2f(s0));
         i2m0 = 0.5f / m0;
-        e1 = static_cast<float>(s0 + m12 - m22) * i2m0;
-        e2 = static_cast<float>(s0 + m22 - m12) * i2m0;
+        e1 = d2f(s0 + m12 - m22) * i2m0;
+        e2 = d2f(s0 + m22 - m12) * i2m0;
     }
     float pabs = sl * i2m0;
     float cth = 2.0f * rth - 1.0f;
@@ -708,33 +807,54 @@ __device__ __forceinline__ double two_body(float rphi, float rth, double s0, dou
     // J = (pi/2) sqrt(lambda)/s0: pi/2 itself for massless daughters (NaN where s0 is not a
     // positive finite float, as the division would give), with no FP64 conversion
     if (massless) {
-        const float s0f = static_cast<float>(s0);
-        return (s0f > 0.0f && s0f <= 3.40282347e38f) ? static_cast<double>(0.5f * static_cast<float>(kPi))
+        const float s0f = d2f(s0);
+        return (s0f > 0.0f && s0f <= 3.40282347e38f) ? f2d(0.5f * static_cast<float>(kPi))
                                               : __longlong_as_double(0x7FF8000000000000LL);
     }
-    return static_cast<double>(0.5f * static_cast<float>(kPi) * sl / static_cast<float>(s0));
+    return f2d(0.5f * static_cast<float>(kPi) * sl / d2f(s0));
 }
 
 }  // namespace mx
 
-// Mixed-precision interpreter: same byte-code, same slot file; scalar slots hold FP64, momentum
-// slots hold FP32.
+// The register frame of a compiled mixed-precision channel: every slot has a double and a float
+// register, and each write sets the one of its own type and the other's conversion (f2d, d2f).
+// Reads take the register of the reader's type, so a value produced and consumed in the same
+// precision is never converted, and a conversion nobody reads is dead code that the compiler
+// drops: the conversions that remain are the edges of the FP64 islands, on the integer ALU.
+template <int NS, class Imm>
+struct MixRegFrame {
+    static constexpr bool kStatic = true;
+    mutable double v[NS > 0 ? NS : 1];
+    mutable float w[NS > 0 ? NS : 1];
+};
+template <int NS, class Imm>
+__device__ __forceinline__ double ld(const MixRegFrame<NS, Imm>& f, int a) { return a >= 0 ? f.v[a] : Imm::v(~a); }
+template <int NS, class Imm>
+__device__ __forceinline__ void st(const MixRegFrame<NS, Imm>& f, int slot, double x) {
+    f.v[slot] = x;
+    f.w[slot] = mx::d2f(x);
+}
 namespace mx {
 template <int NS, class Imm>
-__device__ __forceinline__ float ldf(const RegFrame<NS, Imm>& f, int a) {
-    return a >= 0 ? static_cast<float>(f.v[a]) : Imm::f(~a);
+__device__ __forceinline__ float ldf(const MixRegFrame<NS, Imm>& f, int a) { return a >= 0 ? f.w[a] : Imm::f(~a); }
+// An op's float result enters later ops as a stored value, as it does from the shared-memory slot
+// file: the empty asm keeps the compiler from contracting a product at the end of one op with a
+// sum at the start of the next into one FMA (the interpreter rounds the product), so compiled
+// and interpreted programs round the same way.
+template <int NS, class Imm>
+__device__ __forceinline__ void stf(const MixRegFrame<NS, Imm>& f, int slot, float x) {
+    asm("" : "+f"(x));
+    f.w[slot] = x;
+    f.v[slot] = f2d(x);
 }
 template <int NS, class Imm>
-__device__ __forceinline__ F4 ldp(const RegFrame<NS, Imm>& f, int a) {
-    return {static_cast<float>(f.v[a]), static_cast<float>(f.v[a + 1]), static_cast<float>(f.v[a + 2]),
-            static_cast<float>(f.v[a + 3])};
-}
+__device__ __forceinline__ F4 ldp(const MixRegFrame<NS, Imm>& f, int a) { return {f.w[a], f.w[a + 1], f.w[a + 2], f.w[a + 3]}; }
 template <int NS, class Imm>
-__device__ __forceinline__ void stp(const RegFrame<NS, Imm>& f, int slot, F4 p) {
-    f.v[slot] = p.e;
-    f.v[slot + 1] = p.x;
-    f.v[slot + 2] = p.y;
-    f.v[slot + 3] = p.z;
+__device__ __forceinline__ void stp(const MixRegFrame<NS, Imm>& f, int slot, F4 p) {
+    stf(f, slot, p.e);
+    stf(f, slot + 1, p.x);
+    stf(f, slot + 2, p.y);
+    stf(f, slot + 3, p.z);
 }
 }  // namespace mx
 
@@ -753,10 +873,12 @@ __device__ __forceinline__ void sde_factor_s(float& acc, int& ex, float s, int k
 __device__ __forceinline__ void sde_factor(float& acc, int& ex, const F4& q, int kind, float M, float G) {
     sde_factor_s(acc, ex, sde_sq(q), kind, M, G);
 }
-// 1 / (acc 2^ex) with 2^-ex built from its bits (|ex| stays far below 1022 here)
+// 1 / (acc 2^ex): the float 1/acc in (1/2, 1] widened to a double by its bits with -ex added
+// to the exponent, on the integer ALU (|ex| stays far below 1000 here)
 __device__ __forceinline__ double sde_weight(float acc, int ex) {
-    const double scale = __longlong_as_double(static_cast<long long>(1023 - ex) << 52);
-    return static_cast<double>(1.0f / acc) * scale;
+    const uint32_t u = __float_as_uint(1.0f / acc);
+    return __hiloint2double(static_cast<int>((u >> 3) + 0x38000000u - (static_cast<uint32_t>(ex) << 20)),
+                            static_cast<int>(u << 29));
 }
 }  // namespace mx
 
@@ -775,10 +897,10 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
                     int k = max(min(static_cast<int>(rn), vbins - 1), 0);
                     const float* e = gridf + j * (vbins + 1);
                     float e0 = e[k], wdt = e[k + 1] - e0;
-                    st(f, o[j], static_cast<double>(fmaf(rn - static_cast<float>(k), wdt, e0)));
+                    mx::stf(f, o[j], fmaf(rn - static_cast<float>(k), wdt, e0));
                     jac *= nb * wdt;
                 });
-                st(f, o[na], static_cast<double>(jac));
+                mx::stf(f, o[na], jac);
                 break;
             }
             case PS_OP_INVARIANT_NU: {
@@ -801,12 +923,12 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
                 float S = mx::ldf(f, a[2]);
                 float L = logf(mx::ldf(f, a[1]) / S);
                 const float l1 = r * L, l2 = (1.0f - r) * L;  // log x1, log x2
-                st(f, o[0], static_cast<double>(fminf(expf(l1), 1.0f)));
-                st(f, o[1], static_cast<double>(fminf(expf(l2), 1.0f)));
-                st(f, o[2], static_cast<double>(-L / S));
+                mx::stf(f, o[0], fminf(expf(l1), 1.0f));
+                mx::stf(f, o[1], fminf(expf(l2), 1.0f));
+                mx::stf(f, o[2], -L / S);
                 if (no > 3) {
-                    st(f, o[3], static_cast<double>(fminf(l1, 0.0f)));
-                    st(f, o[4], static_cast<double>(fminf(l2, 0.0f)));
+                    mx::stf(f, o[3], fminf(l1, 0.0f));
+                    mx::stf(f, o[4], fminf(l2, 0.0f));
                 }
                 break;
             }
@@ -908,20 +1030,20 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
                 else if (be == 1.0f) fy = y;
                 else if (be == 0.0f) fy = 1.0f;
                 else fy = powf(y, be);
-                st(f, o[0], static_cast<double>(fx * fy));
+                mx::stf(f, o[0], fx * fy);
                 break;
             }
             case PS_OP_PROPAGATOR: {
                 double M = ld(f, a[1]);
-                float d = static_cast<float>(ld(f, a[0]) - M * M);   // s - M^2 in FP64
-                float mg = static_cast<float>(M * ld(f, a[2]));
-                st(f, o[0], static_cast<double>(1.0f / (d * d + mg * mg)));
+                float d = mx::d2f(ld(f, a[0]) - M * M);   // s - M^2 in FP64
+                float mg = mx::d2f(M * ld(f, a[2]));
+                mx::stf(f, o[0], 1.0f / (d * d + mg * mg));
                 break;
             }
             case PS_OP_ONE_PLUS_COS2: {
                 F4 p = mx::ldp(f, a[0]);
                 float c2 = p.z * p.z / (p.x * p.x + p.y * p.y + p.z * p.z);
-                st(f, o[0], static_cast<double>(1.0f + c2));
+                mx::stf(f, o[0], 1.0f + c2);
                 break;
             }
             case PS_OP_CHANNEL_WEIGHT: {
@@ -985,8 +1107,8 @@ __device__ __forceinline__ void load_inputs(const Fr& f, const LaunchParams& lp,
                                                static_cast<uint32_t>(c), static_cast<uint32_t>(j >> 1)),
                                     static_cast<uint32_t>(lp.seed), static_cast<uint32_t>(lp.seed >> 32));
             if constexpr (kMix) {
-                st(f, j, static_cast<double>(rng::unit_from_bits_f(o.y)));
-                if (j + 1 < n_random) st(f, j + 1, static_cast<double>(rng::unit_from_bits_f(o.w)));
+                mx::stf(f, j, rng::unit_from_bits_f(o.y));
+                if (j + 1 < n_random) mx::stf(f, j + 1, rng::unit_from_bits_f(o.w));
             } else {
                 st(f, j, unit_from_bits(o.y, o.x));
                 if (j + 1 < n_random) st(f, j + 1, unit_from_bits(o.w, o.z));
@@ -1032,7 +1154,7 @@ __device__ __forceinline__ double store_outputs(const Fr& f, const int32_t* od, 
             } else {
                 void* dst = role == PS_ROLE_X1 ? lp.x1 : role == PS_ROLE_X2 ? lp.x2 : lp.alpha;
                 if (active && dst != nullptr) {
-                    if constexpr (kMix) __stcs(static_cast<float*>(dst) + col, static_cast<float>(v));
+                    if constexpr (kMix) __stcs(static_cast<float*>(dst) + col, mx::ldf(f, slot));
                     else __stcs(static_cast<double*>(dst) + col, v);
                 }
             }
@@ -1069,22 +1191,33 @@ __device__ __forceinline__ void map_tiles(const LaunchParams& lp, Policy& pol, d
         if (!active) w = 0.0;
         if (active && !finite_bits(w)) atomicAdd(lp.status + 0, 1ULL);
 
-        // per-tile partial statistics: nonzero count, sum w, sum w^2, max w
-        double v0 = (w != 0.0) ? 1.0 : 0.0, v1 = w, v2 = w * w, v3 = w;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            v0 += __shfl_down_sync(0xffffffffu, v0, off);
-            v1 += __shfl_down_sync(0xffffffffu, v1, off);
-            v2 += __shfl_down_sync(0xffffffffu, v2, off);
-            v3 = fmax(v3, __shfl_down_sync(0xffffffffu, v3, off));
-        }
+        // Per-tile partial statistics: nonzero count, sum w, sum w^2, max(0, max w).  The warp
+        // stage spends six FP64 instructions per event: the count is a ballot, the maximum an
+        // integer maximum of bit patterns (positive doubles order like their bits; NaN, negative
+        // and zero weights enter as +0), and the two sums share one butterfly: at the first step
+        // the lower half of the warp keeps sum w and the upper half sum w^2, each lane adding
+        // the partner's copy of the one it keeps, and the remaining four steps run within
+        // each half (lane 0 ends with sum w, lane 16 with sum w^2).
         const int warp = tid >> 5, lane = tid & 31;
+        const unsigned full = 0xffffffffu;
+        const int nz = __popc(__ballot_sync(full, (dbits(w) << 1) != 0));  // w != 0 (NaN counts)
+        const double w2 = w * w;
+        const bool upper = (lane & 16) != 0;
+        double sum = upper ? w2 : w;
+        sum += __shfl_xor_sync(full, upper ? w : w2, 16);
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) sum += __shfl_xor_sync(full, sum, off);
+        const long long key = pos_bits(w) ? dbits(w) : 0LL;
+        const unsigned kh = __reduce_max_sync(full, static_cast<unsigned>(key >> 32));
+        const unsigned kl = __reduce_max_sync(full, static_cast<unsigned>(key >> 32) == kh
+                                                        ? static_cast<unsigned>(key) : 0u);
         __syncthreads();  // s_red reuse across tiles
         if (lane == 0) {
-            s_red[4 * warp + 0] = v0;
-            s_red[4 * warp + 1] = v1;
-            s_red[4 * warp + 2] = v2;
-            s_red[4 * warp + 3] = v3;
+            s_red[4 * warp + 0] = static_cast<double>(nz);
+            s_red[4 * warp + 1] = sum;
+            s_red[4 * warp + 3] = __longlong_as_double((static_cast<long long>(kh) << 32) | kl);
+        } else if (lane == 16) {
+            s_red[4 * warp + 2] = sum;
         }
         __syncthreads();
         if (tid == 0) {

@@ -111,6 +111,7 @@ _SIGS = {
     "ps_program_free": (C.c_int, [C.c_void_p]),
     "ps_launch_count": (C.c_int64, []),
     "ps_fp64_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "ps_mixed_helpers": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "ps_inverse_map": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ChannelDesc), C.c_int64, C.c_void_p, C.c_int64,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ps_global_weights": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -536,6 +537,16 @@ PROBES = {"dfma": 0, "dadd": 1, "dmul": 2, "empty": 9, "div": 10, "sqrt": 11, "r
 def fp64_probe(kind, blocks, iters, sink, stream=None):
     """Launch one FP64-pipe probe (ps_fp64_probe) writing blocks x 256 doubles to `sink`."""
     _check(lib().ps_fp64_probe(PROBES[kind], blocks, iters, _ptr(sink), _stream_ptr(stream)), "ps_fp64_probe")
+
+
+MIXED_HELPERS = {"f2d": 0, "d2f": 1, "sqrt64": 2, "rcp64": 3}
+
+
+def mixed_helper(kind, x, out, stream=None):
+    """Apply one device helper of the mixed form (ps_mixed_helpers) to the device tensor x into
+    out (f2d: float32 -> float64; d2f: float64 -> float32; sqrt64, rcp64: float64 -> float64)."""
+    _check(lib().ps_mixed_helpers(MIXED_HELPERS[kind], _ptr(x), _ptr(out), x.numel(), _stream_ptr(stream)),
+           "ps_mixed_helpers")
 
 
 def program_for(channels, block_threads=128, ctas_per_sm=0, device=0, precision="f64", jit=False):

@@ -51,8 +51,14 @@ def test_compiled_parity(torch_cuda, case):
 
 @pytest.mark.parametrize("precision", ["f64", "mixed"])
 def test_compiled_matches_interpreter(torch_cuda, precision):
-    """2e7 events of the six 2->5 channels generated by both kernels: the weights agree to a few
-    ulps, the cut decisions exactly, the channel sums to 1e-13."""
+    """2e7 events of the six 2->5 channels generated by both kernels: the cut decisions agree
+    exactly, the channel sums to 1e-13 and the weights of almost every event bit for bit.  The
+    two kernels run the same device functions; the compiled one may contract a product of one
+    op with a sum of the next into an FMA, so FP64 results can differ in their last bits.  In
+    FP64 programs that stays below 1e-12.  In mixed programs such a last-bit difference can
+    move one FP32 rounding downstream, a few float ulps of the weight (only near-threshold
+    events with weights below 1e-40 show it, where the mixed form's own error against FP64 is
+    1e-2 and more)."""
     torch = torch_cuda
     chans = W.multichannel_2to5()
     counts = list(W.MULTICHANNEL_EVENTS)
@@ -67,7 +73,9 @@ def test_compiled_matches_interpreter(torch_cuda, precision):
     assert np.array_equal(wa == 0, wb == 0)
     nz = wa != 0
     rel = np.abs(wb[nz] / wa[nz] - 1.0)
-    assert np.median(rel) == 0.0 and rel.max() < 1e-12, (np.median(rel), rel.max())
+    bar = 1e-12 if precision == "f64" else 5e-7
+    assert np.median(rel) == 0.0 and rel.max() < bar, (np.median(rel), rel.max())
+    assert np.mean(rel > 1e-12) < 1e-3
     for a, b in zip(res[False][1], res[True][1]):
         assert a["n"] == b["n"] and a["n_nonzero"] == b["n_nonzero"]
         assert abs(b["sum_w"] / a["sum_w"] - 1.0) < 1e-13

@@ -156,3 +156,101 @@ def test_mixed_integral_matches_fp64_2to8(torch_cuda):
     assert rel < 1e-4 and rel < 0.01 * mc
     for a, b in zip(sums["mixed"], sums["f64"]):
         assert abs(a["n_nonzero"] - b["n_nonzero"]) <= 5e-4 * b["n"]
+
+
+# ---------------------------------------------------------------- the helpers at the islands' edges
+# The mixed kernels convert between FP32 and FP64 on the integer ALU and seed their FP64
+# reciprocal and square root from float approximations.  The conversions must equal the
+# hardware's IEEE 754 conversions bit for bit: float -> double over every one of the 2^32 float
+# bit patterns, double -> float over random patterns of every exponent and, for each float
+# cell, the two neighbours of its rounding boundary and the exact ties (normal and subnormal).
+def _same_or_both_nan(torch, a, b):
+    nan = torch.isnan(a)
+    assert torch.equal(nan, torch.isnan(b))
+    return torch.equal(a[~nan].view(torch.int64 if a.dtype == torch.float64 else torch.int32),
+                       b[~nan].view(torch.int64 if b.dtype == torch.float64 else torch.int32))
+
+
+def test_f2d_matches_hardware_on_every_float(torch_cuda):
+    torch = torch_cuda
+    chunk = 1 << 28
+    out = torch.empty(chunk, dtype=torch.float64, device="cuda")
+    for c in range(1 << 32 >> 28):
+        bits = torch.arange(c * chunk, (c + 1) * chunk, dtype=torch.int64, device="cuda").to(torch.int32)
+        x = bits.view(torch.float32)
+        ps.mixed_helper("f2d", x, out)
+        assert _same_or_both_nan(torch, out, x.double()), c
+        del bits, x
+
+
+def test_d2f_matches_hardware(torch_cuda):
+    torch = torch_cuda
+    g = torch.Generator(device="cuda").manual_seed(20260412)
+    n = 1 << 26
+    # random bit patterns (every exponent, both signs)
+    hi = torch.randint(-(1 << 31), 1 << 31, (n,), generator=g, device="cuda", dtype=torch.int64)
+    lo = torch.randint(0, 1 << 32, (n,), generator=g, device="cuda", dtype=torch.int64)
+    x_rand = ((hi << 32) | lo).view(torch.float64)
+    # exponents around the float range's ends (double exponents 860..910 and 1140..1160)
+    e = torch.cat([torch.randint(860, 911, (n // 2,), generator=g, device="cuda"),
+                   torch.randint(1140, 1161, (n // 2,), generator=g, device="cuda")])
+    x_edge = ((e << 52) | (lo & ((1 << 52) - 1)) | ((hi & 1) << 63)).view(torch.float64)
+    # every float cell's rounding boundary: the double of a float plus k double ulps around
+    # half a float ulp (normal floats: 2^28 double ulps), and the exact subnormal ties
+    f = torch.randint(0, 1 << 31, (n // 8,), generator=g, device="cuda", dtype=torch.int64).to(torch.int32)
+    fb = f.view(torch.float32).double().view(torch.int64)
+    ks = torch.tensor([0, 1, -1, (1 << 28) - 1, 1 << 28, (1 << 28) + 1, (1 << 29) - 1], device="cuda")
+    x_cells = (fb[:, None] + ks[None, :]).reshape(-1).view(torch.float64)
+    q = torch.randint(0, 1 << 23, (n // 8,), generator=g, device="cuda", dtype=torch.int64).double()
+    x_ties = torch.cat([torch.ldexp(q + 0.5, torch.tensor(-149.0, device="cuda")),
+                        torch.ldexp(q + 0.25, torch.tensor(-149.0, device="cuda")),
+                        torch.ldexp(q + 0.75, torch.tensor(-149.0, device="cuda"))])
+    special = torch.tensor([0.0, -0.0, float("inf"), -float("inf"), float("nan"), 3.4028234663852886e38,
+                            3.4028235677973366e38, 3.4028235677973362e38, 1.1754943508222875e-38,
+                            1.401298464324817e-45, 7.006492321624085e-46, 7.006492321624087e-46,
+                            5e-324, -5e-324, 1e300, -1e-300], dtype=torch.float64, device="cuda")
+    for x in (x_rand, x_edge, x_cells, x_ties, special):
+        out = torch.empty(x.numel(), dtype=torch.float32, device="cuda")
+        ps.mixed_helper("d2f", x, out)
+        assert _same_or_both_nan(torch, out, x.float())
+
+
+def test_sqrt64_rcp64_accuracy(torch_cuda):
+    """One Newton step from a seed whose exponent is set on the integer ALU and whose fraction
+    comes from a float instruction (error delta <= ~2.2e-7 from the truncation to 23 bits and
+    the approximate instruction) leaves a relative error of 1.5 delta^2 for the square root and
+    delta^2 for the reciprocal: below 1e-13 over the normal doubles (|ln x| < 700, far outside
+    the float range on both sides)."""
+    torch = torch_cuda
+    g = torch.Generator(device="cuda").manual_seed(7)
+    n = 1 << 24
+    x = torch.exp(torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-700.0, 700.0, generator=g))
+    out = torch.empty_like(x)
+    ps.mixed_helper("sqrt64", x, out)
+    assert torch.max(torch.abs(out / torch.sqrt(x) - 1.0)).item() < 1e-13
+    xs = torch.where(torch.rand(n, generator=g, device="cuda") < 0.5, x, -x)
+    ps.mixed_helper("rcp64", xs, out)
+    assert torch.max(torch.abs(out * xs - 1.0)).item() < 1e-13
+    edge = torch.tensor([0.0, -0.0, -1.0, float("nan"), -float("inf")], dtype=torch.float64, device="cuda")
+    o = torch.empty_like(edge)
+    ps.mixed_helper("sqrt64", edge, o)
+    assert torch.equal(o, torch.zeros_like(o))  # x <= 0 and NaN give 0
+
+
+def test_mixed_keeps_every_fp64_event_multichannel(torch_cuda):
+    """On 2e6 events of the six 2->5 channels the mixed and FP64 programs make the same cut
+    decisions: no event is zeroed in one precision only.  This holds down to the near-threshold
+    events (weights to 1e-70), whose FP64 islands take square roots and reciprocals of numbers
+    outside the float range."""
+    torch = torch_cuda
+    chans = W.multichannel_2to5()
+    counts = [c // 10 for c in W.MULTICHANNEL_EVENTS]
+    w = {}
+    for prec in ("f64", "mixed"):
+        prog = ps.program_for(chans, block_threads=128, ctas_per_sm=3, precision=prec, jit=True)
+        out, ws = prog.alloc(counts, 7, alpha=True)
+        prog.generate(counts, 1003, out, ws)
+        torch.cuda.synchronize()
+        w[prec] = out["weight"].cpu().numpy()
+    assert np.array_equal(w["f64"] == 0, w["mixed"] == 0)
+    assert np.min(w["f64"][w["f64"] > 0]) < 1e-60  # the near-threshold events are in the sample
