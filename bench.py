@@ -60,25 +60,29 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07
 # ncu capture (profiles/ps_jit_map_ww_2to4.md): DFMA 405.6 + DADD 113.6 + DMUL 197.6 = 716.8 FP64
 # arithmetic instructions (1122.4 flops) and 185.9 DRAM bytes per event; FP64 pipe 85.4 % active.
 # Re-captured on the current build (the Kallen function of decays and 2->2 blocks taken from the
-# masses, the per-tile statistics with six FP64 instructions per event;
-# profiles/fp64_pipe_probes.md): DFMA 399.1 + DADD 103.3 + DMUL 195.1 = 697.5 (1096.6 flops),
-# 769.6 FP64-pipe instructions in all, 185.4 DRAM bytes per event, pipe active 0.837 of the
-# elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
-COMPILED_COUNTERS = {"instr": 697.5, "flops": 1096.6, "dram": 185.4, "pipe": 0.837, "pipe_instr": 769.6}
+# masses, the per-tile statistics with six FP64 instructions per event, bins, maxima and sign
+# tests on the integer ALU; profiles/fp64_pipe_probes.md): DFMA 399.1 + DADD 105.3 + DMUL 195.1
+# = 699.5 (1098.6 flops), 752.6 FP64-pipe instructions in all, 185.4 DRAM bytes per event, pipe
+# active 0.835 of the elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
+COMPILED_COUNTERS = {"instr": 699.5, "flops": 1098.6, "dram": 185.4, "pipe": 0.835, "pipe_instr": 752.6}
 INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from
 # the ncu captures of one 2^20-event launch: the compiled program on the current build
-# (profiles/fp64_pipe_probes.md: 2544.7 + 1034.5 + 859.8); the interpreter's from an earlier build
+# (profiles/fp64_pipe_probes.md: 2544.7 + 1055.0 + 859.8); the interpreter's from an earlier build
 # (profiles/ps_map_kernel_c5_2to8.md, before the mass-based Kallen function; an upper bound).
-C5_FP64_INSTR_PER_EVENT = {"compiled": 4438.9, "interpreter": 6559.0}
+C5_FP64_INSTR_PER_EVENT = {"compiled": 4459.4, "interpreter": 6559.0}
 # The same for the compiled six-channel 2->5 program, from one 2e6-event launch in the benchmark's
-# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1078.9 + DADD 270.5 + DMUL 389.9.
-C3_FP64_INSTR_PER_EVENT = 1739.3
+# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1078.9 + DADD 284.9 + DMUL 389.9.
+C3_FP64_INSTR_PER_EVENT = 1753.8
 # FP64-pipe instructions in all (arithmetic and conversions) per event of the compiled mixed-precision
 # programs (profiles/fp64_pipe_probes.md): the FP64 pipe's share of the mixed form (with the
 # conversions on the integer ALU, 0.55-0.75 of its cycles: no longer the only bound).
-MIXED_FP64_PIPE_PER_EVENT = {"2to4": 61.4, "2to5": 312.8, "2to8": 432.1}
+# Launch shapes (threads per CTA, CTAs per SM) the autotuner tries for compiled programs: the
+# CTA count caps the registers (65536 / (threads x CTAs)); the large CTAs keep more warps on the
+# same stretch of a long straight-line program, which the instruction cache rewards.
+JIT_SHAPES = ((128, 2), (128, 3), (128, 4), (256, 1), (256, 2), (256, 3), (512, 1))
+MIXED_FP64_PIPE_PER_EVENT = {"2to4": 61.4, "2to5": 313.6, "2to8": 435.6}
 # FP64-pipe instructions per call of CUDA's double functions on the GB300, from the ncu counters of
 # ps_fp64_probe's function loops less the empty loop (profiles/fp64_pipe_probes.md); an add or a
 # multiply is one.  They convert the oracle's operation counts into the pipe's work.
@@ -395,8 +399,8 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
     t_compile = time.perf_counter()
     if best is None:
         best, table = ps.autotune(chans, split(chunk // 4), precision=precision,
-                                  blocks=(64, 128) if jit else (64, 128, 256), ctas=(1, 2, 3, 4), reps=2,
-                                  device=local, jit=jit)
+                                  blocks=(64, 128, 256), ctas=(1, 2, 3, 4), reps=2, device=local, jit=jit,
+                                  pairs=JIT_SHAPES if jit else None)
     prog = ps.program_for(chans, device=local, precision=precision, jit=jit, **best)
     t_compile = time.perf_counter() - t_compile
     n_mom = chans[0]["n"] + 2
@@ -1009,9 +1013,8 @@ def main():
     if not args.no_multichannel:
         chans = W.multichannel_2to5()
         counts = list(W.MULTICHANNEL_EVENTS)
-        # compiled programs: one block size (one compilation, the kernel cache serves the rest)
-        best, table = ps.autotune(chans, [c // 8 for c in counts], blocks=(128,) if jit else (64, 128, 256),
-                                  ctas=(2, 3, 4, 5, 6) if jit else (1, 2, 3, 4), reps=2, device=local, jit=jit)
+        best, table = ps.autotune(chans, [c // 8 for c in counts], blocks=(64, 128, 256), ctas=(1, 2, 3, 4),
+                                  reps=2, device=local, jit=jit, pairs=JIT_SHAPES + ((128, 5), (128, 6)) if jit else None)
         mprog = ps.program_for(chans, device=local, jit=jit, **best)
         mout, mws = mprog.alloc(counts, 7, alpha=True, device=local)
         ex = mprog.exec_create(counts, mout, mws)
@@ -1041,9 +1044,9 @@ def main():
         multi["roofline"] = fp64_pipe_roofline(C3_FP64_INSTR_PER_EVENT if jit else None, multi["value"] / world)
         multi["roofline"]["fp64_instr_per_event"] = C3_FP64_INSTR_PER_EVENT if jit else None
         # the mixed-precision form of the same step on the same events
-        mbest, _ = ps.autotune(chans, [c // 8 for c in counts], precision="mixed",
-                               blocks=(128,) if jit else (64, 128, 256), ctas=(2, 3, 4, 5, 6) if jit else (1, 2, 3, 4),
-                               reps=2, device=local, jit=jit)
+        mbest, _ = ps.autotune(chans, [c // 8 for c in counts], precision="mixed", blocks=(64, 128, 256),
+                               ctas=(1, 2, 3, 4), reps=2, device=local, jit=jit,
+                               pairs=JIT_SHAPES + ((128, 5), (128, 6)) if jit else None)
         xprog = ps.program_for(chans, device=local, precision="mixed", jit=jit, **mbest)
         xout, xws = xprog.alloc(counts, 7, alpha=True, device=local)
         xex = xprog.exec_create(counts, xout, xws)

@@ -231,7 +231,8 @@ int ps_graph_build_channel(const ps_channel_desc* ch, int n_ch, int which, ps_gr
                               * alpha are written as binary32, weights as binary64 */
 
 typedef struct {
-    int32_t block_threads; /* events per tile = threads per CTA (multiple of 32; 0 = default 128) */
+    int32_t block_threads; /* events per tile = threads per CTA (multiple of 32, at most 256, or 512
+                            * for a compiled program, PS_PROGRAM_JIT; 0 = default 128)         */
     int32_t ctas_per_sm;   /* resident CTAs requested per SM (0 = as many as fit, up to 4; a
                             * compiled program, PS_PROGRAM_JIT, caps its registers so that this
                             * many fit, and takes as many as fit when 0)                        */

@@ -1262,9 +1262,13 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
     p->n_ch = n_ch;
     if (opt) p->opt = *opt;
     p->block = p->opt.block_threads > 0 ? p->opt.block_threads : 128;
-    if (p->block % 32 != 0 || p->block > 256) {
+    // the interpreter keeps a CTA's slot files in shared memory (at most 256 threads); a compiled
+    // program keeps them in registers and may run 512-thread CTAs
+    const bool jit = (p->opt.flags & PS_PROGRAM_JIT) != 0;
+    if (p->block % 32 != 0 || p->block > (jit ? 512 : 256)) {
         delete p;
-        return fail(PS_ERR_INVALID_ARGUMENT, "block_threads must be a multiple of 32 and at most 256");
+        return fail(PS_ERR_INVALID_ARGUMENT, jit ? "block_threads must be a multiple of 32 and at most 512"
+                                                 : "block_threads must be a multiple of 32 and at most 256");
     }
     if (p->opt.precision != PS_PRECISION_F64 && p->opt.precision != PS_PRECISION_MIXED) {
         delete p;
@@ -1347,21 +1351,23 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
     lp.smem_slots = p->max_slots;
     lp.mixed = p->opt.precision == PS_PRECISION_MIXED ? 1 : 0;  // the mixed kernel also stages float immediates
     p->smem = ps::smem_bytes_for(lp);
-    if (p->smem > static_cast<size_t>(prop.sharedMemPerBlockOptin)) {
-        free_device(p);
-        delete p;
-        return fail(PS_ERR_CAPACITY, "channel needs " + std::to_string(p->smem) + " bytes of shared memory per CTA");
-    }
-    int per_sm = 0;
     std::string err;
-    st = ps::max_ctas_per_sm(p->block, p->smem, p->opt.precision == PS_PRECISION_MIXED, &per_sm, &err);
-    if (st != PS_OK || per_sm < 1) {
-        free_device(p);
-        delete p;
-        return fail(st != PS_OK ? st : PS_ERR_CAPACITY, st != PS_OK ? err : "kernel does not fit on an SM");
+    if (p->block <= 256) {  // the interpreter's launch shape (a compiled program never launches it)
+        if (p->smem > static_cast<size_t>(prop.sharedMemPerBlockOptin)) {
+            free_device(p);
+            delete p;
+            return fail(PS_ERR_CAPACITY, "channel needs " + std::to_string(p->smem) + " bytes of shared memory per CTA");
+        }
+        int per_sm = 0;
+        st = ps::max_ctas_per_sm(p->block, p->smem, p->opt.precision == PS_PRECISION_MIXED, &per_sm, &err);
+        if (st != PS_OK || per_sm < 1) {
+            free_device(p);
+            delete p;
+            return fail(st != PS_OK ? st : PS_ERR_CAPACITY, st != PS_OK ? err : "kernel does not fit on an SM");
+        }
+        int want = p->opt.ctas_per_sm > 0 ? p->opt.ctas_per_sm : 4;
+        p->grid_ctas = p->sm_count * std::min(per_sm, want);
     }
-    int want = p->opt.ctas_per_sm > 0 ? p->opt.ctas_per_sm : 4;
-    p->grid_ctas = p->sm_count * std::min(per_sm, want);
     if (p->opt.flags & PS_PROGRAM_JIT) {  // the compiled kernel: VEGAS grid and reduction scratch in shared memory
         // a requested CTA count also caps the compiled kernel's registers so that many CTAs fit
         const int min_blocks = std::min(p->opt.ctas_per_sm, 2048 / p->block);

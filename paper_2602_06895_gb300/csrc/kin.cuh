@@ -45,6 +45,30 @@ __device__ __forceinline__ int small_int(double v) {
     if (e < 0) return 0;
     return static_cast<int>(((b & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL) >> (52 - e));
 }
+// floor(y) for y >= 0 as the conversion to int gives it (saturating at 2^31 - 1; NaN and
+// negative y give 0), from the bits: y = 1.m 2^e gives (1m) >> (52 - e)
+__device__ __forceinline__ int floor_small(double y) {
+    const long long b = dbits(y);
+    const int e = static_cast<int>(b >> 52) - 1023;  // b < 0 (negative y) gives e < 0
+    if (e < 0) return 0;
+    if (e > 30) return b > kInfBits ? 0 : 0x7FFFFFFF;
+    return static_cast<int>(((static_cast<unsigned long long>(b) & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL) >> (52 - e));
+}
+// the double of an int 0 <= k < 2^31, from the bits
+__device__ __forceinline__ double small_to_double(int k) {
+    if (k <= 0) return 0.0;
+    const int msb = 31 - __clz(k);
+    const unsigned long long m = (static_cast<unsigned long long>(k) << (52 - msb)) & 0xFFFFFFFFFFFFFULL;
+    return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(1023 + msb) << 52) | m));
+}
+// fmax(a, b) on the bit patterns: doubles order like the integers b ^ (0x7FF..F if negative);
+// a NaN operand gives the other one
+__device__ __forceinline__ double fmax_bits(double a, double b) {
+    const long long x = dbits(a), y = dbits(b);
+    const bool nan_a = (x & 0x7FFFFFFFFFFFFFFFLL) > kInfBits, nan_b = (y & 0x7FFFFFFFFFFFFFFFLL) > kInfBits;
+    const long long kx = x ^ ((x >> 63) & 0x7FFFFFFFFFFFFFFFLL), ky = y ^ ((y >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+    return nan_a ? b : (nan_b ? a : (kx >= ky ? a : b));
+}
 // fmin(fmax(x, lo), hi) for 0 <= lo <= hi: NaN and values below lo give lo, +inf gives hi
 __device__ __forceinline__ double clamp_nonneg(double x, double lo, double hi) {
     const long long b = dbits(x);
@@ -147,10 +171,11 @@ __device__ __forceinline__ void t_range(double s, double mA2, double mB2, double
     double A = mA2 + m12 - (s + mA2 - mB2) * (s + m12 - m22) * inv2s;
     B = sqrt(kallen(s, mA2, mB2) * kallen_m(s, m1, m2)) * inv2s;
     double prod = (m12 - mA2) * (m22 - mB2) + (m12 * mB2 - m22 * mA2) * (m12 - m22 - mA2 + mB2) / s;
-    double big = (A <= 0.0) ? A - B : A + B;   // root without cancellation
-    double small = (big != 0.0) ? prod / big : 0.0;
-    double tplus = (A <= 0.0) ? small : big;  // closest to zero
-    double tminus = (A <= 0.0) ? big : small;
+    const bool a_nonpos = nonpos_bits(A);       // A <= 0, on the bits
+    double big = a_nonpos ? A - B : A + B;      // root without cancellation
+    double small = !zero_bits(big) ? prod / big : 0.0;
+    double tplus = a_nonpos ? small : big;      // closest to zero
+    double tminus = a_nonpos ? big : small;
     tabs_min = -tplus;
     tabs_max = -tminus;
 }

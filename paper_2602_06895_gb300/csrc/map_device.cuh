@@ -115,12 +115,14 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
     t_range(s, mA2, mB2, m1, m2, tlo, thi, B);
     double dlo = tabs - tlo, dhi = thi - tabs;
     bool near_lo = dlo <= dhi;
-    double iB = (B > 0.0) ? 1.0 / B : 0.0;
+    const bool b_pos = pos_bits(B);  // B > 0, on the bits
+    double iB = b_pos ? 1.0 / B : 0.0;
     double first = (near_lo ? dlo : dhi) * iB;  // 1 - cos (near_lo) or 1 + cos
-    double omc = (B > 0.0) ? (near_lo ? first : 2.0 - first) : 1.0;
-    double opc = (B > 0.0) ? (near_lo ? 2.0 - first : first) : 1.0;
+    double omc = b_pos ? (near_lo ? first : 2.0 - first) : 1.0;
+    double opc = b_pos ? (near_lo ? 2.0 - first : first) : 1.0;
     double cth = (omc <= opc) ? 1.0 - omc : opc - 1.0;
-    double sth = sqrt(fmax(omc * opc, 0.0));
+    const double so = omc * opc;
+    double sth = sqrt(pos_bits(so) ? so : 0.0);
     double sph, cph;
     sincospi(2.0 * rphi, &sph, &cph);
 
@@ -278,15 +280,16 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
         switch (op) {
             case PS_OP_VEGAS: {
                 double jac = 1.0;
-                const double nb = static_cast<double>(vbins);
+                const double nb = small_to_double(vbins);
                 op_loop<Fr>(0, na, 1, [&](int j) {
                     double r = ld(f, a[j]);
                     double rn = r * nb;
-                    int k = min(static_cast<int>(rn), vbins - 1);
+                    // the bin and its double from the bits (no FP64-pipe conversions)
+                    int k = min(floor_small(rn), vbins - 1);
                     k = max(k, 0);
                     const double* e = grid + j * (vbins + 1);
                     double e0 = e[k], wdt = e[k + 1] - e0;
-                    st(f, o[j], fma(rn - static_cast<double>(k), wdt, e0));
+                    st(f, o[j], fma(rn - small_to_double(k), wdt, e0));
                     jac *= nb * wdt;
                 });
                 st(f, o[na], jac);
@@ -397,7 +400,7 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
             case PS_OP_DIV: st(f, o[0], ld(f, a[0]) / ld(f, a[1])); break;
             case PS_OP_SQRT: st(f, o[0], sqrt(ld(f, a[0]))); break;
             case PS_OP_SQUARE: { double v = ld(f, a[0]); st(f, o[0], v * v); break; }
-            case PS_OP_MAX: st(f, o[0], fmax(ld(f, a[0]), ld(f, a[1]))); break;
+            case PS_OP_MAX: st(f, o[0], fmax_bits(ld(f, a[0]), ld(f, a[1]))); break;
             case PS_OP_MOM_ADD: stp(f, o[0], p4_add(ldp(f, a[0]), ldp(f, a[1]))); break;
             case PS_OP_MOM_SUB: stp(f, o[0], p4_sub(ldp(f, a[0]), ldp(f, a[1]))); break;
             case PS_OP_PDF_POWER: {
@@ -728,10 +731,11 @@ __device__ __forceinline__ void t_range(double s, double mA2, double mB2, double
     double A = mA2 + m12 - 0.5 * (s + mA2 - mB2) * (s + m12 - m22) * is;
     B = 0.5 * sqrt64(kallen64(s, mA2, mB2) * kallen64_m(s, m1, m2)) * is;
     double prod = (m12 - mA2) * (m22 - mB2) + (m12 * mB2 - m22 * mA2) * (m12 - m22 - mA2 + mB2) * is;
-    double big = (A <= 0.0) ? A - B : A + B;
-    double small = (big != 0.0) ? prod * rcp64(big) : 0.0;
-    tabs_min = -((A <= 0.0) ? small : big);
-    tabs_max = -((A <= 0.0) ? big : small);
+    const bool a_nonpos = nonpos_bits(A);  // A <= 0, on the bits
+    double big = a_nonpos ? A - B : A + B;
+    double small = !zero_bits(big) ? prod * rcp64(big) : 0.0;
+    tabs_min = -(a_nonpos ? small : big);
+    tabs_max = -(a_nonpos ? big : small);
 }
 
 __device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double tabs, double m1, double m2, double s,
@@ -749,10 +753,11 @@ __device__ __forceinline__ double two_to_two(float rphi, F4 pA, F4 pB, double ta
     t_range(s, mA2, mB2, m1, m2, tlo, thi, B);
     double dlo = tabs - tlo, dhi = thi - tabs;
     bool near_lo = dlo <= dhi;
-    double first = (B > 0.0) ? (near_lo ? dlo : dhi) * rcp64(B) : 1.0;  // 1 - cos or 1 + cos (FP64)
+    const bool b_pos = pos_bits(B);  // B > 0, on the bits
+    double first = b_pos ? (near_lo ? dlo : dhi) * rcp64(B) : 1.0;  // 1 - cos or 1 + cos (FP64)
     float f1 = d2f(first);
-    float omc = (B > 0.0) ? (near_lo ? f1 : 2.0f - f1) : 1.0f;
-    float opc = (B > 0.0) ? (near_lo ? 2.0f - f1 : f1) : 1.0f;
+    float omc = b_pos ? (near_lo ? f1 : 2.0f - f1) : 1.0f;
+    float opc = b_pos ? (near_lo ? 2.0f - f1 : f1) : 1.0f;
     float cth = (omc <= opc) ? 1.0f - omc : opc - 1.0f;
     float sth = sqrtf(fmaxf(omc * opc, 0.0f));
     float sph, cph;
@@ -1015,7 +1020,7 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
             case PS_OP_DIV: st(f, o[0], ld(f, a[0]) / ld(f, a[1])); break;
             case PS_OP_SQRT: st(f, o[0], mx::sqrt64(ld(f, a[0]))); break;
             case PS_OP_SQUARE: { double v = ld(f, a[0]); st(f, o[0], v * v); break; }
-            case PS_OP_MAX: st(f, o[0], fmax(ld(f, a[0]), ld(f, a[1]))); break;
+            case PS_OP_MAX: st(f, o[0], fmax_bits(ld(f, a[0]), ld(f, a[1]))); break;
             case PS_OP_MOM_ADD: mx::stp(f, o[0], mx::f4_add(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
             case PS_OP_MOM_SUB: mx::stp(f, o[0], mx::f4_sub(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
             case PS_OP_PDF_POWER: {

@@ -491,36 +491,36 @@ class Exec:
 
 
 def autotune(channels, events, precision="f64", blocks=(64, 128, 256), ctas=(1, 2, 3, 4), seed=1, reps=3,
-             device=0, jit=False):
+             device=0, jit=False, pairs=None):
     """Pick block_threads and CTAs per SM for a workload by timing ps_generate on it.
 
+    The candidates are blocks x ctas, or the (block_threads, ctas_per_sm) `pairs` when given.
     Every candidate compiles the program, generates the full event counts `reps` times after
     one warm-up and keeps the median CUDA-event time; returns (best options, table)."""
     import torch
 
     table = []
-    for b in blocks:
-        for k in ctas:
-            try:
-                prog = program_for(channels, block_threads=b, ctas_per_sm=k, device=device, precision=precision,
-                                   jit=jit)
-            except PSError:
-                continue
-            n_mom = channels[0]["n"] + 2
-            out, ws = prog.alloc(events, n_mom, x=channels[0]["hadronic"],
-                                 alpha=channels[0]["integrand"] == "pdf_sde", device=device)
+    for b, k in (pairs if pairs is not None else [(b, k) for b in blocks for k in ctas]):
+        try:
+            prog = program_for(channels, block_threads=b, ctas_per_sm=k, device=device, precision=precision,
+                               jit=jit)
+        except PSError:
+            continue
+        n_mom = channels[0]["n"] + 2
+        out, ws = prog.alloc(events, n_mom, x=channels[0]["hadronic"],
+                             alpha=channels[0]["integrand"] == "pdf_sde", device=device)
+        prog.generate(events, seed, out, ws)
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
             prog.generate(events, seed, out, ws)
-            times = []
-            for _ in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                prog.generate(events, seed, out, ws)
-                e1.record()
-                torch.cuda.synchronize()
-                times.append(e0.elapsed_time(e1))
-            times.sort()
-            table.append({"block_threads": b, "ctas_per_sm": k, "ms": times[len(times) // 2]})
-            del prog, out, ws
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        times.sort()
+        table.append({"block_threads": b, "ctas_per_sm": k, "ms": times[len(times) // 2]})
+        del prog, out, ws
     best = min(table, key=lambda t: t["ms"])
     return {"block_threads": best["block_threads"], "ctas_per_sm": best["ctas_per_sm"]}, table
 

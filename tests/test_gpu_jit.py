@@ -171,3 +171,28 @@ def test_split_program_2to8_replay_and_interpreter(torch_cuda, precision):
     for a, b in zip(res[False][1], res[True][1]):
         assert a["n"] == b["n"]
         assert abs(b["sum_w"] / a["sum_w"] - 1.0) < (1e-9 if precision == "f64" else 1e-4), (a, b)
+
+
+def test_compiled_512_thread_ctas(torch_cuda):
+    """A compiled program may run 512-thread CTAs (its slot files live in registers): on ragged
+    counts of the six 2->5 channels it gives the weights and statistics of the 128-thread form;
+    the interpreter refuses more than 256 threads."""
+    torch = torch_cuda
+    chans = W.multichannel_2to5()
+    counts = [700, 30_001, 0, 25_000, 40_959, 513]
+    res = []
+    for b, k in ((128, 4), (512, 1)):
+        prog = ps.program_for(chans, block_threads=b, ctas_per_sm=k, jit=True)
+        out, ws = prog.alloc(counts, 7, alpha=True)
+        prog.generate(counts, 99, out, ws)
+        torch.cuda.synchronize()
+        res.append((out["weight"].cpu().numpy(), prog.stats()))
+    (wa, sa), (wb, sb) = res
+    assert np.array_equal(wa == 0, wb == 0)
+    nz = wa != 0
+    assert np.max(np.abs(wb[nz] / wa[nz] - 1.0)) < 1e-12
+    for a, b in zip(sa, sb):
+        assert a["n"] == b["n"] and a["n_nonzero"] == b["n_nonzero"]
+        assert abs(b["sum_w"] - a["sum_w"]) <= 1e-13 * abs(a["sum_w"])
+    with pytest.raises(ps.PSError):
+        ps.program_for(chans, block_threads=512)
