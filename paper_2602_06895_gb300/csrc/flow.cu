@@ -251,6 +251,266 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Backward-pass GEMM: C[m, n] = sum_k A(m, k) B(k, n) with A(m, k) = A[m*lam + k*lak], unit
+// stride along k (lak == 1, "AK") or along m (lam == 1, "AM"), and B(k, n) = B[k*ldb + n].
+// BF16 operands, FP32 accumulation on mma.sync m16n8k16.  A CTA of 256 threads (8 warps)
+// computes a 128 x BN tile.  K moves through shared memory in steps of 32 with a three-stage
+// cp.async pipeline of 16-byte copies (zero-filled past the matrix edges), and ldmatrix feeds
+// the fragments (transposing where the unit stride is not along k).  Each shared-memory row is
+// stored with its 16-byte chunks XOR-permuted by the row index, so that the eight rows of one
+// ldmatrix phase fall in eight different bank groups.  Epilogues: atomic add (the split-K
+// weight gradients), the SiLU'-scaled BF16 adjoint with the column sums of the bias gradient,
+// or a plain FP32 store.  The split-K form with A unit-stride along k can also add the row sums
+// of A as its tiles pass through shared memory (the last layer's bias gradient from the
+// BF16 adjoint, without a second pass over it).
+namespace bwg {
+constexpr int kBM = 128, kBK = 32, kStages = 3, kThreads = 256;
+enum Epi { kAtomic = 0, kSiluGrad = 1, kStore = 2 };
+
+struct Args {
+    const bf16* A;
+    int64_t lam, lak;
+    const bf16* B;
+    int64_t ldb;
+    int M, N, K, kchunk;
+    float* C;          // kAtomic, kStore
+    int64_t ldc;
+    const float* Zs;   // kSiluGrad: pre-activations Z[m * ldz + n]
+    int64_t ldz;
+    bf16* Cb;          // kSiluGrad: the adjoint as bfloat16, Cb[m * ldcb + n]
+    int64_t ldcb;
+    float* colsum;     // kSiluGrad: column sums of the adjoint (bias gradient), atomic
+    float* rowsum;     // kAtomic with A unit-stride along k: row sums of A (bias gradient), atomic
+};
+
+constexpr size_t smem_bytes(int bn) { return static_cast<size_t>(kStages) * (kBM * kBK + kBK * bn) * sizeof(bf16); }
+
+__device__ __forceinline__ void cp16(bf16* dst, const bf16* src, int bytes) {
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(bytes));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+__device__ __forceinline__ void ldsm4(uint32_t* r, const bf16* p) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t* r, const bf16* p) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// shared-memory element offsets of the 16-byte chunk (row, chunk) in the three tile layouts:
+// A as [128 m][32 k] (AK), A as [32 k][128 m] (AM), B as [32 k][BN n]
+__device__ __forceinline__ int off_ak(int m, int c) { return m * kBK + ((c ^ ((m >> 1) & 3)) << 3); }
+__device__ __forceinline__ int off_am(int k, int c) { return k * kBM + ((c ^ (k & 7)) << 3); }
+template <int BN>
+__device__ __forceinline__ int off_b(int k, int c) {
+    if constexpr (BN == 16) return k * 16 + ((c ^ ((k >> 2) & 1)) << 3);
+    else return k * BN + ((c ^ (k & 7)) << 3);
+}
+
+// one stage: the A and B tiles of k in [kb, kb + 32) clipped to [.., k_end)
+template <int BN, bool kAM>
+__device__ __forceinline__ void load_stage(const Args& g, bf16* As, bf16* Bs, int m0, int n0, int kb, int k_end,
+                                           int tid) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {  // A: 512 chunks of 8 elements
+        const int id = tid + i * kThreads;
+        if constexpr (!kAM) {
+            const int r = id >> 2, c = id & 3;
+            const int m = m0 + r, k = kb + c * 8;
+            const int valid = (m < g.M) ? max(0, min(8, k_end - k)) : 0;
+            const bf16* src = valid > 0 ? g.A + static_cast<int64_t>(m) * g.lam + k : g.A;
+            cp16(As + off_ak(r, c), src, 2 * valid);
+        } else {
+            const int r = id >> 4, c = id & 15;
+            const int k = kb + r, m = m0 + c * 8;
+            const int valid = (k < k_end) ? max(0, min(8, g.M - m)) : 0;
+            const bf16* src = valid > 0 ? g.A + static_cast<int64_t>(k) * g.lak + m : g.A;
+            cp16(As + off_am(r, c), src, 2 * valid);
+        }
+    }
+    constexpr int kBChunks = kBK * BN / 8;  // B: 512 (BN 128) or 64 (BN 16) chunks
+#pragma unroll
+    for (int i = 0; i < (kBChunks + kThreads - 1) / kThreads; ++i) {
+        const int id = tid + i * kThreads;
+        if (id < kBChunks) {
+            const int r = id / (BN / 8), c = id % (BN / 8);
+            const int k = kb + r, n = n0 + c * 8;
+            const int valid = (k < k_end) ? max(0, min(8, g.N - n)) : 0;
+            const bf16* src = valid > 0 ? g.B + static_cast<int64_t>(k) * g.ldb + n : g.B;
+            cp16(Bs + off_b<BN>(r, c), src, 2 * valid);
+        }
+    }
+}
+
+template <int BN, bool kAM, int kEpi>
+__global__ void __launch_bounds__(kThreads, 2) k_gemm_bw(const __grid_constant__ Args g, int pairs) {
+    constexpr int WN = BN == 16 ? 1 : 4, WM = 8 / WN;  // warp grid
+    constexpr int TM = kBM / WM, TN = BN / WN;         // warp tile
+    constexpr int MI = TM / 16, NJ = TN / 8;
+    static_assert(NJ % 2 == 0, "B fragments come in pairs of n8 tiles");
+    extern __shared__ __align__(128) bf16 sm[];
+    bf16* As = sm;                            // kStages x [kBM * kBK]
+    bf16* Bs = sm + kStages * kBM * kBK;      // kStages x [kBK * BN]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm0 = (warp / WN) * TM, wn0 = (warp % WN) * TN;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int k_begin = blockIdx.z * g.kchunk;
+    const int k_end = min(g.K, k_begin + g.kchunk);
+    const int nk = k_end > k_begin ? (k_end - k_begin + kBK - 1) / kBK : 0;
+    float acc[MI][NJ][4];
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < nk) load_stage<BN, kAM>(g, As + s * kBM * kBK, Bs + s * kBK * BN, m0, n0, k_begin + s * kBK, k_end, tid);
+        cp_commit();
+    }
+    const int mat = lane >> 3, r8 = lane & 7;
+    float rs = 0.0f;  // row sums of A: row tid / 2, half tid % 2 of the 32 k of a stage
+    for (int kt = 0; kt < nk; ++kt) {
+        cp_wait<kStages - 2>();  // stage kt has landed (for this thread's copies) ...
+        __syncthreads();         // ... for every thread's, and stage kt - 1 is no longer read
+        const int nt = kt + kStages - 1;
+        if (nt < nk) {
+            const int sb = nt % kStages;
+            load_stage<BN, kAM>(g, As + sb * kBM * kBK, Bs + sb * kBK * BN, m0, n0, k_begin + nt * kBK, k_end, tid);
+        }
+        cp_commit();
+        const bf16* A_ = As + (kt % kStages) * kBM * kBK;
+        const bf16* B_ = Bs + (kt % kStages) * kBK * BN;
+#pragma unroll
+        for (int ks = 0; ks < kBK; ks += 16) {
+            uint32_t af[MI][4], bfr[NJ][2];
+#pragma unroll
+            for (int i = 0; i < MI; ++i) {
+                const int mb = wm0 + i * 16;
+                if constexpr (!kAM) {  // blocks (m, k): mat bit 0 -> m + 8, bit 1 -> k + 8
+                    ldsm4(af[i], A_ + off_ak(mb + r8 + (mat & 1) * 8, (ks >> 3) + (mat >> 1)));
+                } else {               // stored [k][m], transposed on the load
+                    ldsm4t(af[i], A_ + off_am(ks + r8 + (mat >> 1) * 8, (mb >> 3) + (mat & 1)));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NJ; j += 2) {  // blocks (k, n): mat bit 0 -> k + 8, bit 1 -> n + 8
+                uint32_t t[4];
+                ldsm4t(t, B_ + off_b<BN>(ks + r8 + (mat & 1) * 8, ((wn0 + j * 8) >> 3) + (mat >> 1)));
+                bfr[j][0] = t[0];
+                bfr[j][1] = t[1];
+                bfr[j + 1][0] = t[2];
+                bfr[j + 1][1] = t[3];
+            }
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) mma16816(acc[i][j], af[i], bfr[j]);
+        }
+        if constexpr (kEpi == kAtomic && !kAM) {
+            if (g.rowsum != nullptr) {
+                const int r = tid >> 1, hc = 2 * (tid & 1);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const uint4 q = *reinterpret_cast<const uint4*>(A_ + off_ak(r, hc + c));
+                    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 f2 = __bfloat1622float2(h2[e]);
+                        rs += f2.x + f2.y;
+                    }
+                }
+            }
+        }
+    }
+    cp_wait<0>();
+    if constexpr (kEpi == kAtomic && !kAM) {
+        if (g.rowsum != nullptr) {
+            rs += __shfl_xor_sync(0xffffffffu, rs, 1);
+            const int r = tid >> 1;
+            if ((tid & 1) == 0 && blockIdx.y == 0 && m0 + r < g.M) atomicAdd(g.rowsum + m0 + r, rs);
+        }
+    }
+
+    const int gq = lane >> 2, tq = lane & 3;
+    float cs[NJ][2];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) cs[j][0] = cs[j][1] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = m0 + wm0 + i * 16 + gq + 8 * h;
+                const int col = n0 + wn0 + j * 8 + 2 * tq;
+                if (row >= g.M || col >= g.N) continue;
+                const bool two = col + 1 < g.N;
+                float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
+                if constexpr (kEpi == kAtomic) {
+                    float* p = g.C + static_cast<int64_t>(row) * g.ldc + col;
+                    atomicAdd(p, v0);
+                    if (two) atomicAdd(p + 1, v1);
+                } else if constexpr (kEpi == kStore) {
+                    float* p = g.C + static_cast<int64_t>(row) * g.ldc + col;
+                    if (two && pairs) {
+                        *reinterpret_cast<float2*>(p) = make_float2(v0, v1);
+                    } else {
+                        p[0] = v0;
+                        if (two) p[1] = v1;
+                    }
+                } else {
+                    const float* z = g.Zs + static_cast<int64_t>(row) * g.ldz + col;
+                    bf16* q = g.Cb + static_cast<int64_t>(row) * g.ldcb + col;
+                    if (two && pairs) {
+                        const float2 zz = *reinterpret_cast<const float2*>(z);
+                        v0 *= silu_grad(zz.x);
+                        v1 *= silu_grad(zz.y);
+                        *reinterpret_cast<__nv_bfloat162*>(q) = __floats2bfloat162_rn(v0, v1);
+                    } else {
+                        v0 *= silu_grad(z[0]);
+                        q[0] = __float2bfloat16(v0);
+                        if (two) {
+                            v1 *= silu_grad(z[1]);
+                            q[1] = __float2bfloat16(v1);
+                        } else {
+                            v1 = 0.0f;
+                        }
+                    }
+                    cs[j][0] += v0;
+                    cs[j][1] += v1;
+                }
+            }
+    if constexpr (kEpi == kSiluGrad) {
+        if (g.colsum != nullptr) {  // the warp's column sums: over gq (lane bits 2-4), then one atomic
+#pragma unroll
+            for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float s = cs[j][e];
+                    s += __shfl_xor_sync(0xffffffffu, s, 4);
+                    s += __shfl_xor_sync(0xffffffffu, s, 8);
+                    s += __shfl_xor_sync(0xffffffffu, s, 16);
+                    const int col = n0 + wn0 + j * 8 + 2 * tq + e;
+                    if (gq == 0 && col < g.N && m0 + wm0 < g.M) atomicAdd(g.colsum + col, s);
+                }
+        }
+    }
+}
+}  // namespace bwg
+
+// ------------------------------------------------------------------------------------------
 // dual numbers with 7 tangents: (x, x_k, w_k, y_k, h_k, d_k, d_{k+1})
 struct Dual {
     float v;
@@ -561,9 +821,9 @@ __global__ void k_spline_inverse(int64_t B, int d, int K, const float* Xin, floa
 }
 
 // backward of one layer (see the header): inputs x^(l) (Xl), raw params, the adjoint gX of x^(l)
-// and the event coefficient c_b = w_b / sum w; outputs the raw-parameter adjoint G (fp32 and
-// bf16, parameter-major like Praw, padding rows zeroed) and the adjoint of x^(l+1) in gXn (the
-// conditioning dims get the MLP part later).
+// and the event coefficient c_b = w_b / sum w; outputs the raw-parameter adjoint Gb (bf16, and
+// G in fp32 when G is not null; parameter-major like Praw, padding rows zeroed) and the adjoint
+// of x^(l+1) in gXn (the conditioning dims get the MLP part later).
 template <int kK>
 __global__ void k_spline_backward(int64_t B, int d, int K, const float* Xl, const float* Praw, int64_t ldp,
                                   const __grid_constant__ LayerDesc ld, const float* gX, const double* wtot,
@@ -595,7 +855,7 @@ __global__ void k_spline_backward(int64_t B, int d, int K, const float* Xl, cons
             // y_k and h_k through the height softmax, d_k and d_{k+1} through softplus
             const float dotw = gt[1] * bn.sx + gt[2] * bn.pw;
             const float doth = gt[3] * bn.sy + gt[4] * bn.ph;
-            float* g = G + row0 * ldp + b;
+            float* g = G ? G + row0 * ldp + b : nullptr;
             bf16* gb = Gb + row0 * ldp + b;
             const float nmw = -bn.mw * kLog2e, nmh = -bn.mh * kLog2e;
             for (int i = 0; i < K; ++i) {
@@ -604,19 +864,21 @@ __global__ void k_spline_backward(int64_t B, int d, int K, const float* Xl, cons
                 float aw = i < bn.k ? gt[1] : (i == bn.k ? gt[2] : 0.0f);
                 float ah = i < bn.k ? gt[3] : (i == bn.k ? gt[4] : 0.0f);
                 float vw = cw * pw * (aw - dotw), vh = chh * ph * (ah - doth);
-                g[i * ldp] = vw;
+                if (G) {
+                    g[i * ldp] = vw;
+                    g[(K + i) * ldp] = vh;
+                }
                 gb[i * ldp] = __float2bfloat16(vw);
-                g[(K + i) * ldp] = vh;
                 gb[(K + i) * ldp] = __float2bfloat16(vh);
             }
             for (int i = 0; i <= K; ++i) {
                 float v = i == bn.k ? gt[5] * bn.sg0 : (i == bn.k + 1 ? gt[6] * bn.sg1 : 0.0f);
-                g[(2 * K + i) * ldp] = v;
+                if (G) g[(2 * K + i) * ldp] = v;
                 gb[(2 * K + i) * ldp] = __float2bfloat16(v);
             }
         }
         for (int p = ld.P; p < ld.Ppad; ++p) {
-            G[p * ldp + b] = 0.0f;
+            if (G) G[p * ldp + b] = 0.0f;
             Gb[p * ldp + b] = __float2bfloat16(0.0f);
         }
     }
@@ -1572,6 +1834,41 @@ int gemm(const GemmArgs& a0, int splits, cudaStream_t st) {
     return fcheck(cudaGetLastError(), "k_gemm");
 }
 
+// One backward GEMM on bwg::k_gemm_bw: false (nothing launched) when the operands break the
+// 16-byte rules of its cp.async copies (tensor starts aligned, row strides multiples of 8
+// elements), in which case the caller takes k_gemm.
+bool gemm_bw_fits(const bwg::Args& a, bool am) {
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    return al(a.A) && al(a.B) && (am ? a.lak : a.lam) % 8 == 0 && a.ldb % 8 == 0;
+}
+bool gemm_bw(bwg::Args a, bool am, int epi, int splits, cudaStream_t st, int* status) {
+    auto al = [](const void* p, uintptr_t m) { return (reinterpret_cast<uintptr_t>(p) & m) == 0; };
+    if (!gemm_bw_fits(a, am)) return false;
+    const bool narrow = a.N <= 16;
+    splits = std::max(1, splits);
+    a.kchunk = std::max(32, ((a.K + splits - 1) / splits + 31) / 32 * 32);
+    const int nz = std::max(1, (a.K + a.kchunk - 1) / a.kchunk);
+    const int bn = narrow ? 16 : 128;
+    const dim3 grid((a.M + bwg::kBM - 1) / bwg::kBM, (a.N + bn - 1) / bn, nz);
+    int pairs = 0;
+    if (epi == bwg::kStore) pairs = al(a.C, 7) && a.ldc % 2 == 0;
+    if (epi == bwg::kSiluGrad) pairs = al(a.Zs, 7) && a.ldz % 2 == 0 && al(a.Cb, 3) && a.ldcb % 2 == 0;
+    const size_t smem = bwg::smem_bytes(bn);
+    const int key = (narrow ? 100 : 0) + (am ? 10 : 0) + epi;
+    switch (key) {
+        case 0 + bwg::kAtomic: bwg::k_gemm_bw<128, false, bwg::kAtomic><<<grid, bwg::kThreads, smem, st>>>(a, pairs); break;
+        case 0 + bwg::kSiluGrad: bwg::k_gemm_bw<128, false, bwg::kSiluGrad><<<grid, bwg::kThreads, smem, st>>>(a, pairs); break;
+        case 10 + bwg::kAtomic: bwg::k_gemm_bw<128, true, bwg::kAtomic><<<grid, bwg::kThreads, smem, st>>>(a, pairs); break;
+        case 10 + bwg::kSiluGrad: bwg::k_gemm_bw<128, true, bwg::kSiluGrad><<<grid, bwg::kThreads, smem, st>>>(a, pairs); break;
+        case 110 + bwg::kAtomic: bwg::k_gemm_bw<16, true, bwg::kAtomic><<<grid, bwg::kThreads, smem, st>>>(a, pairs); break;
+        case 100 + bwg::kStore: bwg::k_gemm_bw<16, false, bwg::kStore><<<grid, bwg::kThreads, smem, st>>>(a, pairs); break;
+        default: return false;  // a shape the backward pass does not use
+    }
+    ps::count_launches(1);
+    *status = fcheck(cudaGetLastError(), "k_gemm_bw");
+    return true;
+}
+
 // MLP of layer l on the conditioning dims of Xl (activations kept for the backward pass)
 int mlp(ps_flow f, int l, int64_t B, const float* Xl, cudaStream_t st) {
     const FlowDesc& fd = f->fd;
@@ -1695,6 +1992,12 @@ int backward(ps_flow f, int64_t B, cudaStream_t st) {
         const int64_t want = (2 * f->sms + tiles - 1) / tiles;
         return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, B / 256)));
     };
+    // the same for the 128 x 128 (or 128 x 16) tiles of k_gemm_bw
+    auto split_bw = [&](int M, int N) {
+        const int64_t tiles = static_cast<int64_t>((M + 127) / 128) * (N <= 16 ? 1 : (N + 127) / 128);
+        const int64_t want = (2 * f->sms + tiles - 1) / tiles;
+        return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, B / 256)));
+    };
     for (int l = 0; l < fd.L; ++l) {
         const LayerDesc& ld = fd.layer[l];
         float* Xl = f->X + static_cast<int64_t>(l) * f->max_batch * d;
@@ -1705,51 +2008,95 @@ int backward(ps_flow f, int64_t B, cudaStream_t st) {
         bf16* A2 = f->A2 + static_cast<int64_t>(l) * f->max_batch * H;
         float* P = f->Praw + static_cast<int64_t>(l) * f->max_batch * f->Pmax;
         const int64_t ldg = f->max_batch;  // G, Gb and Praw are parameter-major
+        // last linear layer: dW3 += G^T A2, db3 += rowsum G, dA2 = G W3 and its SiLU' form.  The
+        // fast GEMM sums the rows of the BF16 adjoint itself; the fallback needs its FP32 copy.
+        const int Bi = static_cast<int>(B);
+        int s = PS_OK;
+        bwg::Args w{};
+        w.A = f->Gb; w.lam = ldg; w.lak = 1; w.B = A2; w.ldb = H;
+        w.M = ld.Ppad; w.N = H; w.K = Bi; w.C = f->grad + ld.off_W3; w.ldc = H; w.rowsum = f->grad + ld.off_b3;
+        const bool fast3 = gemm_bw_fits(w, false);
         auto kb = fd.K == 16 ? k_spline_backward<16> : k_spline_backward<0>;
-        kb<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xl, P, ldg, ld, f->gX, f->wtot, f->scal, f->G, f->Gb, f->gXn,
-                                       f->scal + 1);
-        // last linear layer: dW3 += G^T A2, db3 += colsum G, dA2 = G W3
-        GemmArgs g{};
-        g.A = f->Gb; g.lam = ldg; g.lak = 1; g.B = A2; g.lbn = 1; g.lbk = H;
-        g.M = ld.Ppad; g.N = H; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W3; g.ldc = H; g.atomic = 1;
-        int s = gemm(g, split_for(ld.Ppad, H), st);
+        kb<<<blocks(B, T), T, 0, st>>>(B, d, fd.K, Xl, P, ldg, ld, f->gX, f->wtot, f->scal, fast3 ? nullptr : f->G,
+                                       f->Gb, f->gXn, f->scal + 1);
+        if (!fast3 || !gemm_bw(w, false, bwg::kAtomic, split_bw(ld.Ppad, H), st, &s)) {
+            k_rowsum<<<dim3(std::min<unsigned>(blocks(B, 256), 4), ld.Ppad), 256, 0, st>>>(B, ldg, f->G,
+                                                                                             f->grad + ld.off_b3);
+            launches += 1;
+            GemmArgs g{};
+            g.A = f->Gb; g.lam = ldg; g.lak = 1; g.B = A2; g.lbn = 1; g.lbk = H;
+            g.M = ld.Ppad; g.N = H; g.K = Bi; g.C = f->grad + ld.off_W3; g.ldc = H; g.atomic = 1;
+            s = gemm(g, split_for(ld.Ppad, H), st);
+        }
         if (s != PS_OK) return s;
-        k_rowsum<<<dim3(std::min<unsigned>(blocks(B, 256), 4), ld.Ppad), 256, 0, st>>>(B, ldg, f->G,
-                                                                                         f->grad + ld.off_b3);
-        g = GemmArgs{};
-        g.A = f->Gb; g.lam = 1; g.lak = ldg; g.B = f->pb + ld.off_W3; g.lbn = 1; g.lbk = H;
-        g.M = static_cast<int>(B); g.N = H; g.K = ld.Ppad; g.C = f->dZ; g.ldc = H; g.Cb = f->dZb; g.ldcb = H;
-        g.act = 2; g.Zs = Z2;
-        s = gemm(g, 1, st);
+        // dA2 = G W3 (the adjoint of A2) times SiLU'(Z2): dZ2 as bfloat16; db2 += its column sums
+        w = bwg::Args{};
+        w.A = f->Gb; w.lam = 1; w.lak = ldg; w.B = f->pb + ld.off_W3; w.ldb = H;
+        w.M = Bi; w.N = H; w.K = ld.Ppad; w.Zs = Z2; w.ldz = H; w.Cb = f->dZb; w.ldcb = H;
+        w.colsum = f->grad + ld.off_b2;
+        if (!gemm_bw(w, true, bwg::kSiluGrad, 1, st, &s)) {
+            GemmArgs g{};
+            g.A = f->Gb; g.lam = 1; g.lak = ldg; g.B = f->pb + ld.off_W3; g.lbn = 1; g.lbk = H;
+            g.M = Bi; g.N = H; g.K = ld.Ppad; g.C = f->dZ; g.ldc = H; g.Cb = f->dZb; g.ldcb = H;
+            g.act = 2; g.Zs = Z2;
+            s = gemm(g, 1, st);
+            if (s == PS_OK) {
+                k_colsum<<<dim3(blocks(H, 64), colsum_rows), 64, 0, st>>>(B, H, f->dZ, f->grad + ld.off_b2);
+                launches += 1;
+            }
+        }
         if (s != PS_OK) return s;
-        // middle layer
-        g = GemmArgs{};
-        g.A = f->dZb; g.lam = 1; g.lak = H; g.B = A1; g.lbn = 1; g.lbk = H;
-        g.M = H; g.N = H; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W2; g.ldc = H; g.atomic = 1;
-        s = gemm(g, split_for(H, H), st);
+        // middle layer: dW2 += dZ2^T A1, dA1 = (dZ2 W2) x SiLU'(Z1), db1 += its column sums
+        w = bwg::Args{};
+        w.A = f->dZb; w.lam = 1; w.lak = H; w.B = A1; w.ldb = H;
+        w.M = H; w.N = H; w.K = Bi; w.C = f->grad + ld.off_W2; w.ldc = H;
+        if (!gemm_bw(w, true, bwg::kAtomic, split_bw(H, H), st, &s)) {
+            GemmArgs g{};
+            g.A = f->dZb; g.lam = 1; g.lak = H; g.B = A1; g.lbn = 1; g.lbk = H;
+            g.M = H; g.N = H; g.K = Bi; g.C = f->grad + ld.off_W2; g.ldc = H; g.atomic = 1;
+            s = gemm(g, split_for(H, H), st);
+        }
         if (s != PS_OK) return s;
-        k_colsum<<<dim3(blocks(H, 64), colsum_rows), 64, 0, st>>>(B, H, f->dZ, f->grad + ld.off_b2);
-        g = GemmArgs{};
-        g.A = f->dZb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W2; g.lbn = 1; g.lbk = H;
-        g.M = static_cast<int>(B); g.N = H; g.K = H; g.C = f->dA; g.ldc = H; g.Cb = f->dAb; g.ldcb = H;
-        g.act = 2; g.Zs = Z1;
-        s = gemm(g, 1, st);
+        w = bwg::Args{};
+        w.A = f->dZb; w.lam = H; w.lak = 1; w.B = f->pb + ld.off_W2; w.ldb = H;
+        w.M = Bi; w.N = H; w.K = H; w.Zs = Z1; w.ldz = H; w.Cb = f->dAb; w.ldcb = H;
+        w.colsum = f->grad + ld.off_b1;
+        if (!gemm_bw(w, false, bwg::kSiluGrad, 1, st, &s)) {
+            GemmArgs g{};
+            g.A = f->dZb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W2; g.lbn = 1; g.lbk = H;
+            g.M = Bi; g.N = H; g.K = H; g.C = f->dA; g.ldc = H; g.Cb = f->dAb; g.ldcb = H;
+            g.act = 2; g.Zs = Z1;
+            s = gemm(g, 1, st);
+            if (s == PS_OK) {
+                k_colsum<<<dim3(blocks(H, 64), colsum_rows), 64, 0, st>>>(B, H, f->dA, f->grad + ld.off_b1);
+                launches += 1;
+            }
+        }
         if (s != PS_OK) return s;
-        // first layer
-        g = GemmArgs{};
-        g.A = f->dAb; g.lam = 1; g.lak = H; g.B = In; g.lbn = 1; g.lbk = kInPad;
-        g.M = H; g.N = kInPad; g.K = static_cast<int>(B); g.C = f->grad + ld.off_W1; g.ldc = kInPad; g.atomic = 1;
-        s = gemm(g, split_for(H, kInPad), st);
+        // first layer: dW1 += dA1^T In, dIn = dA1 W1
+        w = bwg::Args{};
+        w.A = f->dAb; w.lam = 1; w.lak = H; w.B = In; w.ldb = kInPad;
+        w.M = H; w.N = kInPad; w.K = Bi; w.C = f->grad + ld.off_W1; w.ldc = kInPad;
+        if (!gemm_bw(w, true, bwg::kAtomic, split_bw(H, kInPad), st, &s)) {
+            GemmArgs g{};
+            g.A = f->dAb; g.lam = 1; g.lak = H; g.B = In; g.lbn = 1; g.lbk = kInPad;
+            g.M = H; g.N = kInPad; g.K = Bi; g.C = f->grad + ld.off_W1; g.ldc = kInPad; g.atomic = 1;
+            s = gemm(g, split_for(H, kInPad), st);
+        }
         if (s != PS_OK) return s;
-        k_colsum<<<dim3(blocks(H, 64), colsum_rows), 64, 0, st>>>(B, H, f->dA, f->grad + ld.off_b1);
-        g = GemmArgs{};
-        g.A = f->dAb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W1; g.lbn = 1; g.lbk = kInPad;
-        g.M = static_cast<int>(B); g.N = kInPad; g.K = H; g.C = f->dIn; g.ldc = kInPad;
-        s = gemm(g, 1, st);
+        w = bwg::Args{};
+        w.A = f->dAb; w.lam = H; w.lak = 1; w.B = f->pb + ld.off_W1; w.ldb = kInPad;
+        w.M = Bi; w.N = kInPad; w.K = H; w.C = f->dIn; w.ldc = kInPad;
+        if (!gemm_bw(w, false, bwg::kStore, 1, st, &s)) {
+            GemmArgs g{};
+            g.A = f->dAb; g.lam = H; g.lak = 1; g.B = f->pb + ld.off_W1; g.lbn = 1; g.lbk = kInPad;
+            g.M = Bi; g.N = kInPad; g.K = H; g.C = f->dIn; g.ldc = kInPad;
+            s = gemm(g, 1, st);
+        }
         if (s != PS_OK) return s;
         k_scatter<<<blocks(B, T), T, 0, st>>>(B, d, ld, f->dIn, f->gXn);
         std::swap(f->gX, f->gXn);
-        launches += 5;
+        launches += 2;  // spline backward, scatter (the GEMMs count themselves)
     }
     ps::count_launches(launches);
     return fcheck(cudaGetLastError(), "flow backward");
