@@ -9,8 +9,10 @@ and then frozen, 1e7 events per step, FP64.
 A step is one ps_generate call: in-kernel Philox4x32-10, VEGAS lookup, every map of the
 channel, the Jacobian product, integrand, cut_unphysical, SoA stores of the event record
 (6 momenta, x1, x2, w) and the per-channel reductions.  `value` is timed with CUDA
-events on the launching stream with the outputs resident in HBM; `e2e` adds the
-device->host read of the whole event record into pinned host memory every step.
+events on the launching stream with the outputs resident in HBM; `e2e` puts the whole event
+record of every step into pinned host memory: the map kernel stores it there directly (the GPU
+reaches the Grace memory over NVLink-C2C), timed on the host clock with the per-step read of the
+channel sums; the copy-engine form (HBM, then a copy on a second stream) is reported beside it.
 
 Every timed map runs the program compiled at creation (NVRTC, the slot file in registers;
 programs of more than six channels compiled one unit per channel and linked); `--no-jit` runs
@@ -377,14 +379,16 @@ def c1_leg(ps, W, torch, stream, local, events=100_000, reps=20):
 
 
 def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best=None, host_copy=False,
-                 total=None, chunk=None, jit=False):
+                 total=None, chunk=None, jit=False, zero_copy=False):
     """The 2->8 workload (six massless partons and two 173 GeV particles, 24 channels, SDE weights
     in-kernel) streamed: 1e8 events in chunks of 2^22, each chunk one persistent launch for all 24
     channels (CUDA graph, tiles and schedule from the autotuner) into one of two output buffers, its
     per-channel sums added on the device (streaming statistics, read once at the end).  With
     host_copy the record of each chunk also goes to pinned host memory on a second stream while
-    the next chunk is generated.  With jit the program is compiled (one unit per channel, compiled
-    in parallel and linked; the compile time is reported, outside the timed region)."""
+    the next chunk is generated; with zero_copy the map kernel writes the records straight into
+    pinned host memory (the GPU reaches it over NVLink-C2C), with no copy.  With jit the program is
+    compiled (one unit per channel, compiled in parallel and linked; the compile time is reported,
+    outside the timed region)."""
     import numpy as np
 
     from paper_2602_06895_gb300 import distributed as D
@@ -405,6 +409,9 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
     t_compile = time.perf_counter() - t_compile
     n_mom = chans[0]["n"] + 2
     bufs = [prog.alloc(split(chunk), n_mom, alpha=True, device=local) for _ in range(2)]
+    if zero_copy:  # the output tensors in pinned host memory, the workspaces on the device
+        bufs = [({k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()}, w)
+                for o, w in bufs]
     execs = [prog.exec_create(split(chunk), o, w) for o, w in bufs]
     plan = [(execs[k % 2], k % 2, chunk) for k in range(n_full)]
     if tail:
@@ -432,6 +439,8 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
         if host_copy and k >= 2:
             stream.wait_event(copied[b])  # the copy of the chunk that last used this buffer is done
         ex.launch(seed, D.step_offset(rank, world, chunk, k), stream)
+        if zero_copy:
+            d2h += sum((v[:, :n] if v.dim() == 2 else v[:n]).numel() * v.element_size() for v in bufs[b][0].values())
         if host_copy:
             gen = torch.cuda.Event()
             gen.record(stream)
@@ -486,11 +495,14 @@ def streamed_leg(ps, W, torch, stream, rank, world, local, precision="f64", best
         res["roofline"]["fp64_pipe_instr_per_event"] = MIXED_FP64_PIPE_PER_EVENT["2to8"]
     if table is not None:
         res["autotune_candidates"] = len(table)
-    if host_copy:
+    if host_copy or zero_copy:
         res["e2e"] = {"value": world * total / wall, "unit": "streamed events/s", "h2d_bytes_per_chunk": 16,
                       "d2h_bytes_per_chunk": int(d2h / len(plan)) + 40 * nc,
-                      "note": "event records of every chunk copied to pinned host memory on a second stream, "
-                              "double-buffered; timed on the host clock"}
+                      "note": ("the map kernel writes every chunk's event record straight into pinned host "
+                               "memory (zero-copy over NVLink-C2C), two buffers; timed on the host clock"
+                               if zero_copy else
+                               "event records of every chunk copied to pinned host memory on a second stream, "
+                               "double-buffered; timed on the host clock")}
     del execs, plan, bufs
     return res
 
@@ -945,9 +957,23 @@ def main():
     # the FP64 pipe's measured issue rate: the denominator of every FP64 roofline below
     peak = fp64_peak(ps, torch, local)
 
-    # end to end: same call, event record read back to pinned host memory every step
+    # end to end: same call with the event record in pinned host memory every step.  The headline
+    # form writes it there from the map kernel (zero-copy: the GPU stores over NVLink-C2C into the
+    # Grace memory); the copy-engine form (HBM, then cudaMemcpy on a second stream) is kept beside it.
     e2e = None
     if not args.no_e2e:
+        zc = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()} for _ in range(2)]
+        zc_bytes = sum(v.numel() * v.element_size() for k, v in out.items() if k != "momenta") + \
+            out["momenta"][:, :N].numel() * 8
+        prog.generate([N], SEED, zc[0], ws, event_offset=off(0), stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            prog.generate([N], SEED, zc[k % 2], ws, event_offset=off(k), stream=stream)
+            prog.stats(stream)  # per-channel sums to the host (synchronises the generation stream)
+        torch.cuda.synchronize()
+        dt_zc = time.perf_counter() - t0
+        del zc
         # two output buffers: step k's record goes to pinned host memory on a second stream while
         # step k+1 is generated; every step also reads its per-channel sums back to the host
         outs = [out, prog.alloc([N], 6, device=local)[0]]
@@ -974,9 +1000,13 @@ def main():
         copy_stream.synchronize()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        e2e = {"value": world * N * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": 16,
-               "copies": "each step's record to pinned host memory on a second stream (two buffers)",
-               "d2h_bytes_per_step": int(d2h + 40)}
+        e2e = {"value": world * N * args.steps / dt_zc, "unit": UNIT, "h2d_bytes_per_step": 16,
+               "d2h_bytes_per_step": int(zc_bytes + 40),
+               "copies": "the map kernel writes each step's record into pinned host memory (zero-copy over "
+                         "NVLink-C2C, two buffers); the per-channel sums are read back every step",
+               "copy_engine": {"value": world * N * args.steps / dt, "d2h_bytes_per_step": int(d2h + 40),
+                               "copies": "each step's record from HBM to pinned host memory on a second "
+                                         "stream (two buffers)"}}
 
     # mixed precision (FP32 bulk, FP64 islands) on the same events: same step, same grid
     mixed = None
@@ -1076,7 +1106,10 @@ def main():
         streamed = streamed_leg(ps, W, torch, stream, rank, world, local, jit=jit)
         if not args.no_e2e:
             streamed["e2e"] = streamed_leg(ps, W, torch, stream, rank, world, local, best=streamed["autotuned"],
-                                           host_copy=True, jit=jit)["e2e"]
+                                           zero_copy=True, jit=jit)["e2e"]
+            streamed["e2e"]["copy_engine"] = streamed_leg(ps, W, torch, stream, rank, world, local,
+                                                          best=streamed["autotuned"], host_copy=True,
+                                                          jit=jit)["e2e"]["value"]
         sm = streamed_leg(ps, W, torch, stream, rank, world, local, precision="mixed", jit=jit)
         streamed["mixed_precision"] = {k: sm.get(k) for k in ("value", "ms_total", "integral", "rel_err", "ess",
                                                               "effective_events_per_s", "autotuned", "roofline")}

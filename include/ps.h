@@ -265,7 +265,10 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
 int ps_program_set_vegas(ps_program p, int ch, int dims, int bins, const double* edges_host);
 int ps_program_get_vegas(ps_program p, int ch, int dims, int bins, double* edges_host);
 
-/* Output buffers (device, caller-owned, 16-byte aligned).  Event e of channel c is stored at
+/* Output buffers (caller-owned, 16-byte aligned, in memory the device can write: device memory,
+ * or pinned host memory, which the kernel then fills directly -- on a Grace-Blackwell node over
+ * NVLink-C2C, with no copy; the statistics still need the device workspace).  The writes are
+ * complete when the call's work on `stream` is.  Event e of channel c is stored at
  * column off_c + e, off_c = sum of the event counts of channels < c.  Momentum k, component
  * mu lives at momenta[(4k + mu) * ld + column].  momenta, x1, x2 and alpha hold double for a
  * PS_PRECISION_F64 program and float for a PS_PRECISION_MIXED program; weight is always double.

@@ -196,3 +196,26 @@ def test_compiled_512_thread_ctas(torch_cuda):
         assert abs(b["sum_w"] - a["sum_w"]) <= 1e-13 * abs(a["sum_w"])
     with pytest.raises(ps.PSError):
         ps.program_for(chans, block_threads=512)
+
+
+def test_outputs_in_pinned_host_memory(torch_cuda):
+    """The event record written straight into pinned host memory (zero-copy) is the record written
+    to device memory, bit for bit, and the statistics are the same."""
+    torch = torch_cuda
+    chans = W.multichannel_2to5()
+    counts = [1000, 20_000, 0, 7_001, 13_000, 511]
+    tot = sum(counts)
+    prog = ps.program_for(chans, jit=True)
+    out, ws = prog.alloc(counts, 7, alpha=True)
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    prog.generate(counts, 5, out, ws, event_offset=11)
+    sd = prog.stats()
+    prog.generate(counts, 5, host, ws, event_offset=11)
+    sh = prog.stats()
+    torch.cuda.synchronize()
+    for k, v in out.items():
+        a = v[:, :tot] if v.dim() == 2 else v[:tot]
+        b = host[k][:, :tot] if v.dim() == 2 else host[k][:tot]
+        assert torch.equal(a.cpu(), b), k
+    for a, b in zip(sd, sh):
+        assert a == b
