@@ -281,6 +281,10 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
             case PS_OP_VEGAS: {
                 double jac = 1.0;
                 const double nb = small_to_double(vbins);
+                // with a power-of-two bin count, prod_j (nb w_j) = (prod_j w_j) nb^na exactly (scaling
+                // by a power of two commutes with rounding): one multiply by nb^na, from its bits
+                const int q = __ffs(vbins) - 1;
+                const bool pow2 = (vbins & (vbins - 1)) == 0 && q * na <= 1000;
                 op_loop<Fr>(0, na, 1, [&](int j) {
                     double r = ld(f, a[j]);
                     double rn = r * nb;
@@ -290,8 +294,9 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
                     const double* e = grid + j * (vbins + 1);
                     double e0 = e[k], wdt = e[k + 1] - e0;
                     st(f, o[j], fma(rn - small_to_double(k), wdt, e0));
-                    jac *= nb * wdt;
+                    jac *= pow2 ? wdt : nb * wdt;
                 });
+                if (pow2) jac *= __longlong_as_double(static_cast<long long>(1023 + q * na) << 52);
                 st(f, o[na], jac);
                 break;
             }
