@@ -123,7 +123,9 @@ enum {
     PS_OP_MOM_ADD = 20, /* (p a, p b) -> (p a + b)      */
     PS_OP_MOM_SUB = 21, /* (p a, p b) -> (p a - b)      */
     /* synthetic parton density (x^alpha (1-x)^beta): (s x, i alpha, i beta [, s log x]) -> (s f);
-     * a given log x replaces the logarithm of x. */
+     * a given log x replaces the logarithm of x.  Pair form (s x1, i alpha, i beta, s log x1,
+     * s x2, s log x2) -> (s f(x1) f(x2)), with (x1 x2)^alpha = exp(alpha (log x1 + log x2)): one
+     * exponential for the two densities of a hadronic event. */
     PS_OP_PDF_POWER = 22,
     /* propagator denominator 1/((s - M^2)^2 + M^2 Gamma^2): (s s, i M, i Gamma) -> (s P). */
     PS_OP_PROPAGATOR = 23,

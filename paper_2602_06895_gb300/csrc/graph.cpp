@@ -182,8 +182,10 @@ int signature(const Graph& g, int op, const std::vector<Arg>& a, std::vector<int
             if (!expect({P, P})) return 0;
             *outs = {mo};
             return 1;
-        case PS_OP_PDF_POWER:  // optional 4th: log x
-            if (a.size() == 4 ? !expect({S, I, I, S}) : !expect({S, I, I})) return 0;
+        case PS_OP_PDF_POWER:  // optional 4th: log x; the pair form adds x2, log x2
+            if (a.size() == 6 ? !expect({S, I, I, S, S, S})
+                              : (a.size() == 4 ? !expect({S, I, I, S}) : !expect({S, I, I})))
+                return 0;
             *outs = {sc};
             return 1;
         case PS_OP_PROPAGATOR:
@@ -861,9 +863,11 @@ void build(const ps_channel_desc* all, int n_ch, int which, ps_graph g) {
     auto pdfs = [&]() -> int {
         std::vector<ps_arg> a1 = {B::V(x1), B::C(d->pdf_alpha), B::C(d->pdf_beta)}, a2 = a1;
         a2[0] = B::V(x2);
-        if (lx1 >= 0) {
+        if (lx1 >= 0) {  // the pair form: one exponential for both densities
             a1.push_back(B::V(lx1));
-            a2.push_back(B::V(lx2));
+            a1.push_back(B::V(x2));
+            a1.push_back(B::V(lx2));
+            return b.emit(PS_OP_PDF_POWER, a1, 1);
         }
         int f1 = b.emit(PS_OP_PDF_POWER, a1, 1);
         int f2 = b.emit(PS_OP_PDF_POWER, a2, 1);

@@ -409,15 +409,21 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
             case PS_OP_MOM_ADD: stp(f, o[0], p4_add(ldp(f, a[0]), ldp(f, a[1]))); break;
             case PS_OP_MOM_SUB: stp(f, o[0], p4_sub(ldp(f, a[0]), ldp(f, a[1]))); break;
             case PS_OP_PDF_POWER: {
+                // one density, or the pair f(x1) f(x2) = exp(alpha (log x1 + log x2)) (1-x1)^b (1-x2)^b
+                const bool pair = na == 6;
                 double x = ld(f, a[0]), al = ld(f, a[1]), be = ld(f, a[2]);
-                double fx = exp(al * (na > 3 ? ld(f, a[3]) : log(x)));
-                double y = 1.0 - x;
-                double fy;
-                if (be == 3.0) fy = y * y * y;
-                else if (be == 2.0) fy = y * y;
-                else if (be == 1.0) fy = y;
-                else if (be == 0.0) fy = 1.0;
-                else fy = pow(y, be);
+                double lx = na > 3 ? ld(f, a[3]) : log(x);
+                if (pair) lx += ld(f, a[5]);
+                double fx = exp(al * lx);
+                auto pw = [&](double y) {
+                    if (be == 3.0) return y * y * y;
+                    if (be == 2.0) return y * y;
+                    if (be == 1.0) return y;
+                    if (be == 0.0) return 1.0;
+                    return pow(y, be);
+                };
+                double fy = pw(1.0 - x);
+                if (pair) fy *= pw(1.0 - ld(f, a[4]));
                 st(f, o[0], fx * fy);
                 break;
             }
@@ -1030,16 +1036,22 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
             case PS_OP_MOM_SUB: mx::stp(f, o[0], mx::f4_sub(mx::ldp(f, a[0]), mx::ldp(f, a[1]))); break;
             case PS_OP_PDF_POWER: {
                 // x is a float value here (r_to_x1x2 of the mixed form), so 1 - x in float is the
-                // correctly rounded difference, as the FP64 difference rounded to float would be
+                // correctly rounded difference, as the FP64 difference rounded to float would be;
+                // the pair form as in the FP64 op
+                const bool pair = na == 6;
                 float x = mx::ldf(f, a[0]), al = mx::ldf(f, a[1]), be = mx::ldf(f, a[2]);
-                float fx = expf(al * (na > 3 ? mx::ldf(f, a[3]) : logf(x)));
-                float y = 1.0f - x;
-                float fy;
-                if (be == 3.0f) fy = y * y * y;
-                else if (be == 2.0f) fy = y * y;
-                else if (be == 1.0f) fy = y;
-                else if (be == 0.0f) fy = 1.0f;
-                else fy = powf(y, be);
+                float lx = na > 3 ? mx::ldf(f, a[3]) : logf(x);
+                if (pair) lx += mx::ldf(f, a[5]);
+                float fx = expf(al * lx);
+                auto pw = [&](float y) {
+                    if (be == 3.0f) return y * y * y;
+                    if (be == 2.0f) return y * y;
+                    if (be == 1.0f) return y;
+                    if (be == 0.0f) return 1.0f;
+                    return powf(y, be);
+                };
+                float fy = pw(1.0f - x);
+                if (pair) fy *= pw(1.0f - mx::ldf(f, a[4]));
                 mx::stf(f, o[0], fx * fy);
                 break;
             }
