@@ -139,6 +139,14 @@ __device__ __forceinline__ P4 boost_out(const P4& p, const BoostFrame& b) {
     double c = fma(qp, b.k, p.e * b.inv_m);
     return {(b.e * p.e + qp) * b.inv_m, p.x + b.x * c, p.y + b.y * c, p.z + b.z * c};
 }
+// The back-to-back daughters q1 = (e1, v) and q2 = (e2, -v) of a two-body decay, boosted out of
+// the same frame: q2 . b = -(q1 . b) exactly, so the dot product is formed once.
+__device__ __forceinline__ void boost_out_pair(const P4& q1, double e2, const BoostFrame& b, P4& p1, P4& p2) {
+    const double qp = b.x * q1.x + b.y * q1.y + b.z * q1.z;
+    const double c1 = fma(qp, b.k, q1.e * b.inv_m), c2 = fma(-qp, b.k, e2 * b.inv_m);
+    p1 = {(b.e * q1.e + qp) * b.inv_m, q1.x + b.x * c1, q1.y + b.y * c1, q1.z + b.z * c1};
+    p2 = {(b.e * e2 - qp) * b.inv_m, b.x * c2 - q1.x, b.y * c2 - q1.y, b.z * c2 - q1.z};
+}
 __device__ __forceinline__ P4 boost_in(const P4& p, const BoostFrame& b) {
     double qp = b.x * p.x + b.y * p.y + b.z * p.z;
     double c = fma(qp, b.k, -p.e * b.inv_m);

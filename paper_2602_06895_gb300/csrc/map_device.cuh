@@ -134,9 +134,7 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
     // Ry(theta_A) then Rz(phi_A)
     double rx = ca * vx + sa * vz, rz = -sa * vx + ca * vz;
     P4 q1 = {e1, cpa * rx - spa * vy, spa * rx + cpa * vy, rz};
-    P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
-    p1 = boost_out(q1, bf);
-    p2 = boost_out(q2, bf);
+    boost_out_pair(q1, e2, bf, p1, p2);
     return 0.5 * kPi * rsqrt(kallen(s, mA2, mB2));
 }
 
@@ -161,9 +159,7 @@ __device__ __forceinline__ double two_body(double rphi, double rth, double s0, d
     P4 q1 = {e1, pabs * sth * cph, pabs * sth * sph, pabs * cth};
     P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
     if (kBoost) {
-        const BoostFrame bf = boost_frame(p0, m0, inv_m0);
-        p1 = boost_out(q1, bf);
-        p2 = boost_out(q2, bf);
+        boost_out_pair(q1, e2, boost_frame(p0, m0, inv_m0), p1, p2);
     } else {
         p1 = q1;
         p2 = q2;
@@ -317,10 +313,12 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
             }
             case PS_OP_R_TO_X1X2: {
                 double r = ld(f, a[0]), shat = ld(f, a[1]), S = ld(f, a[2]);
-                double L = log(shat / S);
+                const double tau = shat / S;
+                double L = log(tau);
                 const double l1 = r * L, l2 = (1.0 - r) * L;  // log x1, log x2
-                st(f, o[0], exp(l1));
-                st(f, o[1], exp(l2));
+                const double x1 = exp(l1);
+                st(f, o[0], x1);
+                st(f, o[1], tau / x1);  // x1 x2 = tau: a division where a second exponential was
                 st(f, o[2], -L / S);
                 if (no > 3) {
                     st(f, o[3], l1);
@@ -413,7 +411,9 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
                 const bool pair = na == 6;
                 double x = ld(f, a[0]), al = ld(f, a[1]), be = ld(f, a[2]);
                 double lx = na > 3 ? ld(f, a[3]) : log(x);
-                if (pair) lx += ld(f, a[5]);
+                // an add that is never contracted with the product forming log x2 (a compiled
+                // program could fuse them; the interpreter's slot file rounds the product)
+                if (pair) lx = __dadd_rn(lx, ld(f, a[5]));
                 double fx = exp(al * lx);
                 auto pw = [&](double y) {
                     if (be == 3.0) return y * y * y;
@@ -1041,7 +1041,7 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
                 const bool pair = na == 6;
                 float x = mx::ldf(f, a[0]), al = mx::ldf(f, a[1]), be = mx::ldf(f, a[2]);
                 float lx = na > 3 ? mx::ldf(f, a[3]) : logf(x);
-                if (pair) lx += mx::ldf(f, a[5]);
+                if (pair) lx = __fadd_rn(lx, mx::ldf(f, a[5]));
                 float fx = expf(al * lx);
                 auto pw = [&](float y) {
                     if (be == 3.0f) return y * y * y;
