@@ -64,11 +64,11 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07
 # Re-captured on the current build (the Kallen function of decays and 2->2 blocks taken from the
 # masses, the per-tile statistics with six FP64 instructions per event, bins, maxima and sign
 # tests on the integer ALU, one exponential for both parton densities, x2 = tau / x1, the decay
-# daughters boosted with one dot product; profiles/fp64_pipe_probes.md): DFMA 374.1 + DADD 104.3
-# + DMUL 195.1 = 673.5 (1047.6 flops), 726.6 FP64-pipe instructions in all, 185.3 DRAM bytes per
-# event, pipe active 0.835 of the elapsed cycles -- the FP64 issue probe's saturating loop
-# reaches 0.84.
-COMPILED_COUNTERS = {"instr": 673.5, "flops": 1047.6, "dram": 185.3, "pipe": 0.835, "pipe_instr": 726.6}
+# daughters boosted with one dot product, the VEGAS bin widths staged with the grid;
+# profiles/fp64_pipe_probes.md): DFMA 374.1 + DADD 96.5 + DMUL 195.1 = 665.7 (1039.8 flops),
+# 718.8 FP64-pipe instructions in all, 185.2 DRAM bytes per event, pipe active 0.836 of the
+# elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
+COMPILED_COUNTERS = {"instr": 665.7, "flops": 1039.8, "dram": 185.2, "pipe": 0.836, "pipe_instr": 718.8}
 INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from

@@ -1313,7 +1313,8 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
                 for (int k = 0; k <= bins; ++k) p->h_grid.push_back(static_cast<double>(k) / bins);
             goff += dv * (bins + 1);
             hoff += dv * bins;
-            p->max_grid = std::max(p->max_grid, dv * (bins + 1));
+            // shared memory of a staged grid: the edges, then the bin widths
+            p->max_grid = std::max(p->max_grid, dv * (2 * bins + 1));
         }
     }
     p->grid_off.push_back(goff);

@@ -46,13 +46,9 @@ struct InterpPolicy {
         for (int i = tid; i < C.imm_len; i += B) s_imm[i] = lp.imm[C.imm_off + i];
         if (kMix)
             for (int i = tid; i < C.imm_len; i += B) s_immf[i] = static_cast<float>(lp.imm[C.imm_off + i]);
-        const int ng = C.vdims * (C.vbins + 1);
         float* s_gridf = reinterpret_cast<float*>(s_grid);  // mixed mode: the grid staged as float
-        if (kMix) {
-            for (int i = tid; i < ng; i += B) s_gridf[i] = static_cast<float>(lp.grid[C.grid_off + i]);
-        } else {
-            for (int i = tid; i < ng; i += B) s_grid[i] = lp.grid[C.grid_off + i];
-        }
+        if (kMix) dev::stage_grid(s_gridf, lp.grid + C.grid_off, C.vdims, C.vbins, tid, B);
+        else dev::stage_grid(s_grid, lp.grid + C.grid_off, C.vdims, C.vbins, tid, B);
         __syncthreads();
         out_pc = dev::find_output(s_code, C.code_len);
     }

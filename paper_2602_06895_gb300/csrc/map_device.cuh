@@ -267,6 +267,19 @@ __device__ __forceinline__ void sde_factor(double& den, double& P, const P4& q, 
     sde_factor_s(den, P, p4_sq(q), kind, M, G);
 }
 
+// A channel's VEGAS grid in shared memory: dims rows of bins + 1 edges, then dims rows of bins
+// widths e[k+1] - e[k], each the difference the lookup would form (in the staged precision, T
+// double or float), computed once per CTA and channel instead of once per event and dimension.
+template <class T>
+__device__ __forceinline__ void stage_grid(T* s, const double* g, int dims, int bins, int tid, int nthreads) {
+    const int ng = dims * (bins + 1);
+    for (int i = tid; i < ng; i += nthreads) s[i] = static_cast<T>(g[i]);
+    for (int i = tid; i < dims * bins; i += nthreads) {
+        const int j = i / bins, k = i % bins;
+        s[ng + i] = static_cast<T>(g[j * (bins + 1) + k + 1]) - static_cast<T>(g[j * (bins + 1) + k]);
+    }
+}
+
 // One instruction of the FP64 interpreter on frame Fr (the shared-memory slot file of the
 // interpreter kernel, or the register frame of a compiled channel).
 template <class Fr>
@@ -287,8 +300,8 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
                     // the bin and its double from the bits (no FP64-pipe conversions)
                     int k = min(floor_small(rn), vbins - 1);
                     k = max(k, 0);
-                    const double* e = grid + j * (vbins + 1);
-                    double e0 = e[k], wdt = e[k + 1] - e0;
+                    const double e0 = grid[j * (vbins + 1) + k];
+                    const double wdt = grid[na * (vbins + 1) + j * vbins + k];  // staged e[k+1] - e[k]
                     st(f, o[j], fma(rn - small_to_double(k), wdt, e0));
                     jac *= pow2 ? wdt : nb * wdt;
                 });
@@ -911,8 +924,8 @@ __device__ __forceinline__ void exec_op_mixed(const int op, const int32_t* a, co
                     float r = mx::ldf(f, a[j]);
                     float rn = r * nb;
                     int k = max(min(static_cast<int>(rn), vbins - 1), 0);
-                    const float* e = gridf + j * (vbins + 1);
-                    float e0 = e[k], wdt = e[k + 1] - e0;
+                    const float e0 = gridf[j * (vbins + 1) + k];
+                    const float wdt = gridf[na * (vbins + 1) + j * vbins + k];  // staged e[k+1] - e[k]
                     mx::stf(f, o[j], fmaf(rn - static_cast<float>(k), wdt, e0));
                     jac *= nb * wdt;
                 });
@@ -1266,12 +1279,10 @@ struct CompiledPolicy {
     const LaunchParams& lp;
     double* s_grid;
     __device__ __forceinline__ void stage(int c, const ChannelLaunch& C) {
-        const int ng = C.vdims * (C.vbins + 1);
-        float* s_gridf = reinterpret_cast<float*>(s_grid);
-        for (int i = threadIdx.x; i < ng; i += lp.block) {
-            if constexpr (kMix) s_gridf[i] = static_cast<float>(lp.grid[C.grid_off + i]);
-            else s_grid[i] = lp.grid[C.grid_off + i];
-        }
+        if constexpr (kMix)
+            stage_grid(reinterpret_cast<float*>(s_grid), lp.grid + C.grid_off, C.vdims, C.vbins, threadIdx.x, lp.block);
+        else
+            stage_grid(s_grid, lp.grid + C.grid_off, C.vdims, C.vbins, threadIdx.x, lp.block);
     }
     __device__ __forceinline__ double event(int c, const ChannelLaunch& C, int64_t ev, int64_t local, bool active) {
         return Events::run(c, lp, C, ev, local, active, s_grid, lp.status + 1);
