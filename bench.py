@@ -73,12 +73,12 @@ INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EV
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from
 # the ncu captures of one 2^20-event launch: the compiled program on the current build
-# (profiles/fp64_pipe_probes.md: 2544.7 + 1055.0 + 859.8); the interpreter's from an earlier build
+# (profiles/fp64_pipe_probes.md: 2513.7 + 1054.0 + 858.8); the interpreter's from an earlier build
 # (profiles/ps_map_kernel_c5_2to8.md, before the mass-based Kallen function; an upper bound).
-C5_FP64_INSTR_PER_EVENT = {"compiled": 4459.4, "interpreter": 6559.0}
+C5_FP64_INSTR_PER_EVENT = {"compiled": 4426.5, "interpreter": 6559.0}
 # The same for the compiled six-channel 2->5 program, from one 2e6-event launch in the benchmark's
-# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1078.9 + DADD 284.9 + DMUL 389.9.
-C3_FP64_INSTR_PER_EVENT = 1753.8
+# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1052.7 + DADD 283.9 + DMUL 388.9.
+C3_FP64_INSTR_PER_EVENT = 1725.6
 # FP64-pipe instructions in all (arithmetic and conversions) per event of the compiled mixed-precision
 # programs (profiles/fp64_pipe_probes.md): the FP64 pipe's share of the mixed form (with the
 # conversions on the integer ALU, 0.55-0.75 of its cycles: no longer the only bound).
@@ -86,7 +86,7 @@ C3_FP64_INSTR_PER_EVENT = 1753.8
 # CTA count caps the registers (65536 / (threads x CTAs)); the large CTAs keep more warps on the
 # same stretch of a long straight-line program, which the instruction cache rewards.
 JIT_SHAPES = ((128, 2), (128, 3), (128, 4), (256, 1), (256, 2), (256, 3), (512, 1))
-MIXED_FP64_PIPE_PER_EVENT = {"2to4": 60.4, "2to5": 313.6, "2to8": 435.6}
+MIXED_FP64_PIPE_PER_EVENT = {"2to4": 61.0, "2to5": 312.6, "2to8": 434.6}
 # FP64-pipe instructions per call of CUDA's double functions on the GB300, from the ncu counters of
 # ps_fp64_probe's function loops less the empty loop (profiles/fp64_pipe_probes.md); an add or a
 # multiply is one.  They convert the oracle's operation counts into the pipe's work.
