@@ -2112,7 +2112,10 @@ bool fused_ok(const FlowDesc& fd) {
 
 int ensure_gen(ps_flow f) {
     if (f->gen_X) return PS_OK;
-    const int64_t cap = int64_t(1) << 20;
+    // events per chunk of a generate call: each chunk runs one kernel per coupling layer, so large
+    // chunks spread each launch's fixed cost (weights into shared memory, TMEM allocation, the
+    // partly filled last round of tiles) over more tiles
+    const int64_t cap = int64_t(1) << 22;
     int s = fcheck(cudaMalloc(&f->gen_X, cap * f->fd.d * sizeof(float)), "cudaMalloc (flow sampling)");
     if (s == PS_OK) s = fcheck(cudaMalloc(&f->gen_ld, cap * sizeof(float)), "cudaMalloc (flow sampling)");
     if (s == PS_OK) s = fcheck(cudaMalloc(&f->gen_status, sizeof(unsigned long long)), "cudaMalloc (flow sampling)");

@@ -138,6 +138,32 @@ def test_sample_in_chunks_matches_one_call(torch_cuda):
     assert torch.equal(r1, r2) and torch.equal(l1, l2)
 
 
+def test_generate_across_its_internal_chunks(torch_cuda):
+    """A generate call longer than the fused path's internal chunk (2^22 events) equals two calls
+    split at an arbitrary event, with the second call's event offset: points, log-det and z."""
+    torch = torch_cuda
+    fl = ps.Flow(D, L, K, H, max_batch=4096)
+    p, _, _ = random_params(fl, 15)
+    fl.set_params(p)
+    n, n1 = (1 << 22) + 4099, 1_234_567
+    r = torch.empty((D, n), dtype=torch.float64, device="cuda")
+    ld = torch.empty(n, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    fl.generate(n, 21, r, ld, z, event_offset=5)
+    parts = []
+    for lo, hi in ((0, n1), (n1, n)):
+        rp = torch.empty((D, hi - lo), dtype=torch.float64, device="cuda")
+        lp = torch.empty(hi - lo, dtype=torch.float64, device="cuda")
+        zp = torch.empty_like(rp)
+        fl.generate(hi - lo, 21, rp, lp, zp, event_offset=5 + lo)
+        parts.append((rp, lp, zp))
+    torch.cuda.synchronize()
+    assert torch.equal(r, torch.cat([parts[0][0], parts[1][0]], dim=1))
+    assert torch.equal(ld, torch.cat([parts[0][1], parts[1][1]]))
+    assert torch.equal(z, torch.cat([parts[0][2], parts[1][2]], dim=1))
+    assert fl.status() == 0
+
+
 def test_inverse_matches_oracle_and_round_trips(torch_cuda):
     torch = torch_cuda
     fl = ps.Flow(D, L, K, H, max_batch=4096)
