@@ -326,13 +326,16 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
             }
             case PS_OP_R_TO_X1X2: {
                 double r = ld(f, a[0]), shat = ld(f, a[1]), S = ld(f, a[2]);
-                const double tau = shat / S;
+                // 1/S once (a constant that a compiled program folds; S is the collider's), then
+                // products in place of the two divisions by S
+                const double iS = 1.0 / S;
+                const double tau = shat * iS;
                 double L = log(tau);
                 const double l1 = r * L, l2 = (1.0 - r) * L;  // log x1, log x2
                 const double x1 = exp(l1);
                 st(f, o[0], x1);
                 st(f, o[1], tau / x1);  // x1 x2 = tau: a division where a second exponential was
-                st(f, o[2], -L / S);
+                st(f, o[2], -L * iS);
                 if (no > 3) {
                     st(f, o[3], l1);
                     st(f, o[4], l2);
