@@ -99,9 +99,11 @@ __device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin
 __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double tabs, double m1, double m2,
                                              double s, double mA2, double mB2, P4& p1, P4& p2) {
     P4 p0 = p4_add(pA, pB);
-    const double inv_s = 1.0 / s;
     double m0 = sqrt(s);
-    const BoostFrame bf = boost_frame(p0, m0, m0 * inv_s);  // 1/m0 = m0/s
+    // 1/m0 = m0/s and the boost's 1/(m0 (E0 + m0)) from one division, R = 1/(s (E0 + m0))
+    const double ep = p0.e + m0;
+    const double R = 1.0 / (s * ep);
+    const BoostFrame bf{p0.e, p0.x, p0.y, p0.z, m0 * (ep * R), m0 * R};
     P4 a = boost_in(pA, bf);
     double pt2 = a.x * a.x + a.y * a.y;
     bool has_pt = pos_bits(pt2);
@@ -144,8 +146,10 @@ template <bool kBoost>
 __device__ __forceinline__ double two_body(double rphi, double rth, double s0, double m1, double m2, P4 p0,
                                            P4& p1, P4& p2) {
     double m0 = sqrt(s0);
+    // 1/s0 by its own division: the Jacobian sqrt(lambda)/s0 must not pick up the rounding of the
+    // parent's energy (as a reciprocal shared with the boost's 1/(m0 (E0 + m0)) would)
     const double inv_s0 = 1.0 / s0;
-    const double inv_m0 = m0 * inv_s0;  // 1/m0 = m0/s0: one division per decay
+    const double inv_m0 = m0 * inv_s0;  // 1/m0 = m0/s0
     double m12 = m1 * m1, m22 = m2 * m2;
     // sqrt(lambda) = s0 exactly for two massless daughters
     double sl = (zero_bits(m12) && zero_bits(m22)) ? s0 : sqrt(kallen_m(s0, m1, m2));
