@@ -65,10 +65,11 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07
 # masses, the per-tile statistics with six FP64 instructions per event, bins, maxima and sign
 # tests on the integer ALU, one exponential for both parton densities, x2 = tau / x1, the decay
 # daughters boosted with one dot product, the VEGAS bin widths staged with the grid, the
-# collider's 1/S folded; profiles/fp64_pipe_probes.md): DFMA 360.1 + DADD 96.5 + DMUL 195.1
-# = 651.8 (1011.8 flops), 704.8 FP64-pipe instructions in all, 185.3 DRAM bytes per event, pipe
-# active 0.842 of the elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
-COMPILED_COUNTERS = {"instr": 651.8, "flops": 1011.8, "dram": 185.3, "pipe": 0.842, "pipe_instr": 704.8}
+# collider's 1/S folded, the azimuths from a 256-point table and short Taylor series;
+# profiles/fp64_pipe_probes.md): DFMA 338.0 + DADD 93.7 + DMUL 201.7 = 633.5 (971.4 flops),
+# 675.1 FP64-pipe instructions in all, 185.8 DRAM bytes per event, pipe active 0.845 of the
+# elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
+COMPILED_COUNTERS = {"instr": 633.5, "flops": 971.4, "dram": 185.8, "pipe": 0.845, "pipe_instr": 675.1}
 INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from

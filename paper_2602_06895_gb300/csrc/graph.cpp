@@ -1301,8 +1301,10 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
         p->max_imm = std::max(p->max_imm, static_cast<int>(C.imm.size()));
         p->max_slots = std::max(p->max_slots, C.n_slots);
     }
-    // default VEGAS grids: identity with 64 bins
+    // default VEGAS grids: identity with 64 bins.  A CTA's staged-grid region holds the azimuth
+    // table, then the grid's edges and bin widths.
     int goff = 0, hoff = 0;
+    p->max_grid = ps::kTrigDoubles;
     for (int c = 0; c < n_ch; ++c) {
         p->grid_off.push_back(goff);
         p->hist_off.push_back(hoff);
@@ -1313,8 +1315,7 @@ int ps_program_create(const ps_graph* graphs, int n_ch, const ps_options* opt, i
                 for (int k = 0; k <= bins; ++k) p->h_grid.push_back(static_cast<double>(k) / bins);
             goff += dv * (bins + 1);
             hoff += dv * bins;
-            // shared memory of a staged grid: the edges, then the bin widths
-            p->max_grid = std::max(p->max_grid, dv * (2 * bins + 1));
+            p->max_grid = std::max(p->max_grid, ps::kTrigDoubles + dv * (2 * bins + 1));
         }
     }
     p->grid_off.push_back(goff);

@@ -46,16 +46,21 @@ struct InterpPolicy {
         for (int i = tid; i < C.imm_len; i += B) s_imm[i] = lp.imm[C.imm_off + i];
         if (kMix)
             for (int i = tid; i < C.imm_len; i += B) s_immf[i] = static_cast<float>(lp.imm[C.imm_off + i]);
-        float* s_gridf = reinterpret_cast<float*>(s_grid);  // mixed mode: the grid staged as float
-        if (kMix) dev::stage_grid(s_gridf, lp.grid + C.grid_off, C.vdims, C.vbins, tid, B);
-        else dev::stage_grid(s_grid, lp.grid + C.grid_off, C.vdims, C.vbins, tid, B);
+        double* g = s_grid + kTrigDoubles;  // the grid after the azimuth table
+        if (kMix) {
+            dev::stage_grid(reinterpret_cast<float*>(g), lp.grid + C.grid_off, C.vdims, C.vbins, tid, B);
+        } else {
+            dev::stage_trig(s_grid, tid, B);
+            dev::stage_grid(g, lp.grid + C.grid_off, C.vdims, C.vbins, tid, B);
+        }
         __syncthreads();
         out_pc = dev::find_output(s_code, C.code_len);
     }
     __device__ __forceinline__ double event(int c, const ChannelLaunch& C, int64_t ev, int64_t local, bool active) {
         dev::load_inputs<kMix>(f, lp, c, C.n_random, ev, local, active);
-        if (kMix) dev::run_code_mixed(s_code, out_pc, f, reinterpret_cast<float*>(s_grid), C.vbins, lp.status + 1, active);
-        else dev::run_code(s_code, out_pc, f, s_grid, C.vbins, lp.status + 1, active);
+        double* g = s_grid + kTrigDoubles;
+        if (kMix) dev::run_code_mixed(s_code, out_pc, f, reinterpret_cast<float*>(g), C.vbins, lp.status + 1, active);
+        else dev::run_code(s_code, out_pc, f, g, C.vbins, lp.status + 1, active);
         return dev::store_outputs<kMix>(f, s_code + out_pc + 3, s_code[out_pc + 1], lp, C, local, active);
     }
 };
@@ -349,6 +354,19 @@ __global__ void __launch_bounds__(256) ps_mixed_helper_kernel(const In* in, Out*
     }
 }
 
+// The FP64 azimuth (ps_mixed_helpers, PS_MIXED_SINCOS_TURN): each CTA stages its table first.
+__global__ void __launch_bounds__(256) ps_turn_kernel(const double* in, double* out, int64_t n) {
+    __shared__ double t[kTrigDoubles];
+    dev::stage_trig(t, threadIdx.x, 256);
+    __syncthreads();
+    for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
+        double s, c;
+        dev::sincos_turn(in[i], t, s, c);
+        out[2 * i] = c;
+        out[2 * i + 1] = s;
+    }
+}
+
 // ---------------------------------------------------------------- allocation-free scratch
 // Fixed scratch for ps_generate_noalloc: kNoallocTiles per-tile partial-sum records (4 doubles
 // each, 4 MiB) in a file-scope device array.  Every device that loads the library holds it until
@@ -384,7 +402,7 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes, std::string* err) {
 extern "C" int ps_mixed_helpers(int kind, const void* in, void* out, int64_t n, void* stream) {
     using namespace ps;
     if (n < 0 || (n > 0 && (in == nullptr || out == nullptr))) return PS_ERR_INVALID_ARGUMENT;
-    if (kind < PS_MIXED_F2D || kind > PS_MIXED_RCP64) return PS_ERR_INVALID_ARGUMENT;
+    if (kind < PS_MIXED_F2D || kind > PS_MIXED_SINCOS_TURN) return PS_ERR_INVALID_ARGUMENT;
     if (n == 0) return PS_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152LL * 16);
@@ -399,8 +417,11 @@ extern "C" int ps_mixed_helpers(int kind, const void* in, void* out, int64_t n, 
         case PS_MIXED_SQRT64:
             ps_mixed_helper_kernel<PS_MIXED_SQRT64><<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), n);
             break;
-        default:
+        case PS_MIXED_RCP64:
             ps_mixed_helper_kernel<PS_MIXED_RCP64><<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), n);
+            break;
+        default:
+            ps_turn_kernel<<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), n);
             break;
     }
     if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;

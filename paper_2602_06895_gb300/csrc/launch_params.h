@@ -9,6 +9,11 @@ namespace ps {
 
 constexpr int kMaxChannels = 32;
 constexpr int kOpOutput = 1000;  // pseudo-op closing each channel's byte-code
+// The shared-memory region of a CTA's staged grid starts with a table of cos and sin of 2 pi k /
+// kTrigN (k < kTrigN, as (cos, sin) pairs), the FP64 kernels' azimuth table; the VEGAS grid
+// follows it.
+constexpr int kTrigN = 256;
+constexpr int kTrigDoubles = 2 * kTrigN;
 
 // ---------------------------------------------------------------- launch description
 struct ChannelLaunch {

@@ -15,6 +15,39 @@ namespace dev {
 using rng::philox4x32_10;
 using rng::unit_from_bits;
 
+// ---------------------------------------------------------------- azimuths
+// cos and sin of 2 pi k / kTrigN into t[2k], t[2k+1], from sincospi (once per CTA)
+__device__ __forceinline__ void stage_trig(double* t, int tid, int nthreads) {
+    for (int k = tid; k < kTrigN; k += nthreads) {
+        double s, c;
+        sincospi(2.0 * k / kTrigN, &s, &c);
+        t[2 * k] = c;
+        t[2 * k + 1] = s;
+    }
+}
+
+// sin and cos of phi = 2 pi r for r in [0, 1], table-driven: r kTrigN = k + f (exact; f in [0, 1)),
+// x = f 2 pi / kTrigN < 0.0246, then sin x and cos x by their Taylor series to x^7 and x^6 (the
+// first omitted terms are below 1e-17 of the result) and the angle-sum formulas with the
+// tabulated point k.  About 15 FP64 operations where sincospi takes about 25; a few ulps.  Other r
+// (outside [0, 1], NaN) take sincospi.
+__device__ __forceinline__ void sincos_turn(double r, const double* trig, double& s, double& c) {
+    if (static_cast<unsigned long long>(dbits(r)) > 0x3FF0000000000000ULL) {  // not in [+0, 1]
+        sincospi(2.0 * r, &s, &c);
+        return;
+    }
+    const double t = r * kTrigN;
+    const int k = floor_small(t);
+    const double f = t - small_to_double(k);
+    const double x = f * (kPi / (kTrigN / 2)), x2 = x * x;
+    const double sx = fma(x * x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), x);
+    const double cx = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    const int j = 2 * (k & (kTrigN - 1));  // r = 1 is the point k = 0 of the next turn
+    const double ck = trig[j], sk = trig[j + 1];
+    s = fma(sk, cx, ck * sx);
+    c = fma(ck, cx, -(sk * sx));
+}
+
 // ---------------------------------------------------------------- invariant maps (Sec. 2.2.1)
 // Power law G_nu / log map, anchored at x_min for nu <= 1 and at m^2 for nu > 1, so that
 // 1 + z >= 1 and x - m^2 (and, for nu <= 1, x - x_min) keep full precision:
@@ -97,7 +130,8 @@ __device__ __forceinline__ bool map_bw(double r, double M, double G, double xmin
 // (|t|_max - |t|)/B, whichever is smaller; the momentum is rotated by R(phi_A, theta_A)
 // = Rz(phi_A) Ry(theta_A) (Sec. 2.2.6) and boosted back.
 __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double tabs, double m1, double m2,
-                                             double s, double mA2, double mB2, P4& p1, P4& p2) {
+                                             double s, double mA2, double mB2, P4& p1, P4& p2,
+                                             const double* trig) {
     P4 p0 = p4_add(pA, pB);
     double m0 = sqrt(s);
     // 1/m0 = m0/s and the boost's 1/(m0 (E0 + m0)) from one division, R = 1/(s (E0 + m0))
@@ -126,7 +160,7 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
     const double so = omc * opc;
     double sth = sqrt(pos_bits(so) ? so : 0.0);
     double sph, cph;
-    sincospi(2.0 * rphi, &sph, &cph);
+    sincos_turn(rphi, trig, sph, cph);
 
     double m12 = m1 * m1, m22 = m2 * m2;
     double i2m0 = 0.5 * bf.inv_m;
@@ -144,7 +178,7 @@ __device__ __forceinline__ double two_to_two(double rphi, P4 pA, P4 pB, double t
 // phi = 2 pi r_phi, built at rest and optionally boosted to the frame of p0.
 template <bool kBoost>
 __device__ __forceinline__ double two_body(double rphi, double rth, double s0, double m1, double m2, P4 p0,
-                                           P4& p1, P4& p2) {
+                                           P4& p1, P4& p2, const double* trig) {
     double m0 = sqrt(s0);
     // 1/s0 by its own division: the Jacobian sqrt(lambda)/s0 must not pick up the rounding of the
     // parent's energy (as a reciprocal shared with the boost's 1/(m0 (E0 + m0)) would)
@@ -159,7 +193,7 @@ __device__ __forceinline__ double two_body(double rphi, double rth, double s0, d
     double cth = 2.0 * rth - 1.0;
     double sth = 2.0 * sqrt(rth * (1.0 - rth));
     double sph, cph;
-    sincospi(2.0 * rphi, &sph, &cph);
+    sincos_turn(rphi, trig, sph, cph);
     P4 q1 = {e1, pabs * sth * cph, pabs * sth * sph, pabs * cth};
     P4 q2 = {e2, -q1.x, -q1.y, -q1.z};
     if (kBoost) {
@@ -285,7 +319,8 @@ __device__ __forceinline__ void stage_grid(T* s, const double* g, int dims, int 
 }
 
 // One instruction of the FP64 interpreter on frame Fr (the shared-memory slot file of the
-// interpreter kernel, or the register frame of a compiled channel).
+// interpreter kernel, or the register frame of a compiled channel).  grid: the channel's staged
+// VEGAS grid in shared memory, preceded by the azimuth table (grid - kTrigDoubles).
 template <class Fr>
 __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const int32_t* o, const int na, const int no,
                                         const Fr& f, const double* grid, int vbins, unsigned long long* cut_count,
@@ -362,7 +397,8 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
             case PS_OP_TWO_TO_TWO_COM: {
                 P4 p1, p2;
                 double j = two_to_two(ld(f, a[0]), ldp(f, a[1]), ldp(f, a[2]), ld(f, a[3]), ld(f, a[4]),
-                                      ld(f, a[5]), ld(f, a[6]), ld(f, a[7]), ld(f, a[8]), p1, p2);
+                                      ld(f, a[5]), ld(f, a[6]), ld(f, a[7]), ld(f, a[8]), p1, p2,
+                                      grid - kTrigDoubles);
                 stp(f, o[0], p1);
                 stp(f, o[1], p2);
                 st(f, o[2], j);
@@ -371,7 +407,7 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
             case PS_OP_TWO_BODY_DECAY: {
                 P4 p1, p2;
                 double j = two_body<true>(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]),
-                                          ldp(f, a[5]), p1, p2);
+                                          ldp(f, a[5]), p1, p2, grid - kTrigDoubles);
                 stp(f, o[0], p1);
                 stp(f, o[1], p2);
                 st(f, o[2], j);
@@ -380,7 +416,7 @@ __device__ __forceinline__ void exec_op(const int op, const int32_t* a, const in
             case PS_OP_TWO_BODY_DECAY_COM: {
                 P4 p1, p2;
                 double j = two_body<false>(ld(f, a[0]), ld(f, a[1]), ld(f, a[2]), ld(f, a[3]), ld(f, a[4]),
-                                           P4{0, 0, 0, 0}, p1, p2);
+                                           P4{0, 0, 0, 0}, p1, p2, grid - kTrigDoubles);
                 stp(f, o[0], p1);
                 stp(f, o[1], p2);
                 st(f, o[2], j);
@@ -1286,13 +1322,16 @@ struct CompiledPolicy {
     const LaunchParams& lp;
     double* s_grid;
     __device__ __forceinline__ void stage(int c, const ChannelLaunch& C) {
-        if constexpr (kMix)
-            stage_grid(reinterpret_cast<float*>(s_grid), lp.grid + C.grid_off, C.vdims, C.vbins, threadIdx.x, lp.block);
-        else
-            stage_grid(s_grid, lp.grid + C.grid_off, C.vdims, C.vbins, threadIdx.x, lp.block);
+        double* g = s_grid + kTrigDoubles;  // after the azimuth table
+        if constexpr (kMix) {
+            stage_grid(reinterpret_cast<float*>(g), lp.grid + C.grid_off, C.vdims, C.vbins, threadIdx.x, lp.block);
+        } else {
+            stage_trig(s_grid, threadIdx.x, lp.block);
+            stage_grid(g, lp.grid + C.grid_off, C.vdims, C.vbins, threadIdx.x, lp.block);
+        }
     }
     __device__ __forceinline__ double event(int c, const ChannelLaunch& C, int64_t ev, int64_t local, bool active) {
-        return Events::run(c, lp, C, ev, local, active, s_grid, lp.status + 1);
+        return Events::run(c, lp, C, ev, local, active, s_grid + kTrigDoubles, lp.status + 1);
     }
 };
 

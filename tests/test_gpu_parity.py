@@ -489,3 +489,29 @@ def test_full_size_streamed_chunk_2to8(torch_cuda):
     chunk = W.C5_CHUNK
     counts = [chunk // 24 + (1 if c < chunk % 24 else 0) for c in range(24)]
     _multichannel_full_size(torch_cuda, chans, counts, 1005, 2 * chunk, 64, 4, 120, "2->8 chunk")
+
+
+def test_azimuth_table_matches_quad_precision(torch_cuda):
+    """The FP64 kernels' cos and sin of 2 pi r (a 256-point table and Taylor series of the
+    remaining angle) agree with a quad- or extended-precision evaluation to 6 ulps of 1,
+    over [0, 1] including the table points, the ends and their neighbours."""
+    torch = torch_cuda
+    rng = np.random.default_rng(42)
+    grid = np.arange(257) / 256.0
+    r = np.concatenate([rng.random(1 << 18), grid, np.nextafter(grid[1:], 0), np.nextafter(grid[:-1], 1),
+                        [0.0, 1.0, 0.5, 0.25, 0.75, 1e-300, 5e-324]])
+    rt = torch.from_numpy(r).cuda()
+    out = torch.empty(2 * r.size, dtype=torch.float64, device="cuda")
+    ps.mixed_helper("sincos_turn", rt, out)
+    o = out.cpu().numpy().reshape(-1, 2)
+    rl = r.astype(np.longdouble)
+    pi = np.longdouble("3.14159265358979323846264338327950288")
+    cl, sl = np.cos(2 * pi * rl), np.sin(2 * pi * rl)
+    err = np.maximum(np.abs(o[:, 0] - cl), np.abs(o[:, 1] - sl)).astype(np.float64)
+    assert err.max() < 6 * np.finfo(np.float64).eps, err.max()
+    # outside [0, 1] the sincospi fallback
+    rs = torch.tensor([-0.25, 1.5, -0.0], dtype=torch.float64, device="cuda")
+    o2 = torch.empty(6, dtype=torch.float64, device="cuda")
+    ps.mixed_helper("sincos_turn", rs, o2)
+    o2 = o2.cpu().numpy().reshape(-1, 2)
+    assert np.allclose(o2, [[0.0, -1.0], [-1.0, 0.0], [1.0, 0.0]], atol=1e-15)
