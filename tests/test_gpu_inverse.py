@@ -188,3 +188,47 @@ def test_global_weights_match_oracle(torch_cuda):
         check_rel(Jg.ravel(), J_o.ravel(), 1e-12, 1e-6, "J")
         check_rel(wg, w_o, 1e-12, 1e-6, "w")
         assert abs(wg.sum() / w_o.sum() - 1.0) <= 1e-8
+
+
+def test_alpha_partition_of_unity_on_device(torch_cuda):
+    """C3, the local multichannel weights of Sec. 2.1.1 (SDE strategy 2): alpha_j(p) =
+    P_j(p) / sum_k P_k(p) over the six channels, for the momenta of events of each channel.
+
+    On the device, the inverse kernel evaluates all six P_j from the same momenta.  The alpha_j
+    they give sum to one per event to a few eps, and the alpha that the forward kernel wrote for
+    the generating channel c (its own P_c from the sampled invariants, the others from momenta)
+    equals P_c / sum_k P_k from the inverse kernel within the propagators' rounding bound:
+    relative tol_c + sum_j alpha_j tol_j, with tol_j = 64 eps kappa_P of channel j.  The oracle's
+    alpha_j of the same momenta also sum to one and agree with the device's within that bound."""
+    torch = torch_cuda
+    eps = 2.0 ** -52
+    chans = W.multichannel_2to5()
+    M = len(chans)
+    N = 3001
+    for i in range(M):
+        prog, out = gpu_events(torch, chans, i, N, 90 + i)
+        mom_d, x1, x2 = out["momenta"][:, :N], out["x1"][:N], out["x2"][:N]
+        P = torch.empty((M, N), dtype=torch.float64, device="cuda")
+        for j in range(M):
+            r = torch.empty((W.n_random_dims(chans[j]), N), dtype=torch.float64, device="cuda")
+            ps.inverse_map(prog, j, chans[j], mom_d, x1, x2, r, P[j])
+        torch.cuda.synchronize()
+        keep = out["weight"][:N].cpu().numpy() > 0
+        assert keep.mean() > 0.99
+        mom, _ = host_events(chans[i], out, N)
+        mom = mom[keep]
+        Pg = P.cpu().numpy()[:, keep]
+        assert np.all(np.isfinite(Pg)) and np.all(Pg > 0)
+        a_dev = Pg / Pg.sum(axis=0)
+        assert np.max(np.abs(a_dev.sum(axis=0) - 1.0)) <= 8 * eps
+        tol = np.array([p_tolerance(chans, j, mom) for j in range(M)])
+        bound = tol[i] + np.sum(a_dev * tol, axis=0) + 16 * eps
+        a_fwd = out["alpha"][:N].cpu().numpy()[keep]
+        rel = np.abs(a_fwd / a_dev[i] - 1.0)
+        assert np.all(rel <= bound), (i, (rel / bound).max())
+        P_o = np.array([O.sde_weights(chans, j, mom) for j in range(M)])
+        a_o = P_o / P_o.sum(axis=0)
+        assert np.max(np.abs(a_o.sum(axis=0) - 1.0)) <= 8 * eps
+        for j in range(M):
+            bj = tol[j] + np.sum(a_dev * tol, axis=0) + 16 * eps
+            assert np.all(np.abs(a_dev[j] / a_o[j] - 1.0) <= bj), (i, j)
