@@ -74,12 +74,12 @@ INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EV
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from
 # the ncu captures of one 2^20-event launch: the compiled program on the current build
-# (profiles/fp64_pipe_probes.md: 2513.7 + 1054.0 + 858.8); the interpreter's from an earlier build
+# (profiles/fp64_pipe_probes.md: 2460.2 + 1050.5 + 886.5); the interpreter's from an earlier build
 # (profiles/ps_map_kernel_c5_2to8.md, before the mass-based Kallen function; an upper bound).
-C5_FP64_INSTR_PER_EVENT = {"compiled": 4426.5, "interpreter": 6559.0}
+C5_FP64_INSTR_PER_EVENT = {"compiled": 4397.2, "interpreter": 6559.0}
 # The same for the compiled six-channel 2->5 program, from one 2e6-event launch in the benchmark's
-# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1052.7 + DADD 283.9 + DMUL 388.9.
-C3_FP64_INSTR_PER_EVENT = 1725.6
+# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1003.1 + DADD 280.8 + DMUL 403.7.
+C3_FP64_INSTR_PER_EVENT = 1687.6
 # FP64-pipe instructions in all (arithmetic and conversions) per event of the compiled mixed-precision
 # programs (profiles/fp64_pipe_probes.md): the FP64 pipe's share of the mixed form (with the
 # conversions on the integer ALU, 0.55-0.75 of its cycles: no longer the only bound).
