@@ -1491,11 +1491,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_after();
     const uint32_t tg = tmem_holder + 256 * grp;                                 // this group's columns
     const uint32_t tlane = tg + (static_cast<uint32_t>(32 * (warp & 3)) << 16);  // this warp's TMEM lanes
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase = 0u;  // bit k: the parity this thread waits for next on completion barrier k
     // one bounded wait on barrier k of this group
     auto wait_on = [&](int k) {
-        if (!wait_phase(&mbar[grp][k], phase[k], wait_limit)) failed = 1;
-        phase[k] ^= 1u;
+        if (!wait_phase(&mbar[grp][k], (phase >> k) & 1u, wait_limit)) failed = 1;
+        phase ^= 1u << k;
         fence_after();
     };
 
@@ -1602,13 +1602,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t* v3 = v + 48;
                 PS_TMEM_LD8(v3, a + 48);
                 tmem_wait_ld();
+                // the biases four at a time (row 56q of b3s is 16-byte aligned), added in pairs
                 const float* bq = b3s + (q < 8 ? q * 56 : 0);
 #pragma unroll
-                for (int j = 0; j + 1 < PQ; j += 2) {
-                    const float2 t = __fadd2_rn(make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])),
-                                                make_float2(bq[j], bq[j + 1]));
-                    raw[j] = t.x;
-                    raw[j + 1] = t.y;
+                for (int j = 0; j + 3 < PQ; j += 4) {
+                    const float4 b = *reinterpret_cast<const float4*>(bq + j);
+                    const float2 t0 = __fadd2_rn(make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])),
+                                                 make_float2(b.x, b.y));
+                    const float2 t1 = __fadd2_rn(make_float2(__uint_as_float(v[j + 2]), __uint_as_float(v[j + 3])),
+                                                 make_float2(b.z, b.w));
+                    raw[j] = t0.x;
+                    raw[j + 1] = t0.y;
+                    raw[j + 2] = t1.x;
+                    raw[j + 3] = t1.y;
                 }
                 raw[PQ - 1] = __uint_as_float(v[PQ - 1]) + bq[PQ - 1];
             }
