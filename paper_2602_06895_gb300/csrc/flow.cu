@@ -694,30 +694,42 @@ __device__ __forceinline__ Bin locate_fixed(const float* raw, int64_t ld, float 
     b.ih = rcp_approx(zh);
     const float cw = 1.0f - K * kMinW, chh = 1.0f - K * kMinH;
     float cx = 0.0f, cy = 0.0f, csx = 0.0f, csy = 0.0f;
-    bool found = false;
-    b.k = K - 1;
+    // branch-free selection of the first bin whose right edge lies above v (the last otherwise):
+    // the edges rise strictly, so hit_i = s_i - s_(i-1) with s_i = [v < edge_i] is 1 for that bin
+    // alone, and sums of hit_i x value (exact: multiplies by 0 or 1, adds of +0) gather its values
+    float g[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float prev = 0.0f;
+    int below = 0;  // bins entirely below v: the index of the bin
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const float pw = w[i] * b.iw, ph = h[i] * b.ih;
         const float ww = kMinW + cw * pw, hh = kMinH + chh * ph;
-        const bool hit = !found && (i == K - 1 || (by_height ? v < cy + hh : v < cx + ww));
-        if (hit) {
-            b.k = i;
-            b.x0 = cx;
-            b.y0 = cy;
-            b.sx = csx;
-            b.sy = csy;
-            b.w = ww;
-            b.h = hh;
-            b.pw = pw;
-            b.ph = ph;
-            found = true;
-        }
+        const float s = (i == K - 1 || (by_height ? v < cy + hh : v < cx + ww)) ? 1.0f : 0.0f;
+        const float hit = s - prev;
+        below += s == 0.0f ? 1 : 0;
+        g[0] = __fmaf_rn(hit, cx, g[0]);
+        g[1] = __fmaf_rn(hit, cy, g[1]);
+        g[2] = __fmaf_rn(hit, csx, g[2]);
+        g[3] = __fmaf_rn(hit, csy, g[3]);
+        g[4] = __fmaf_rn(hit, ww, g[4]);
+        g[5] = __fmaf_rn(hit, hh, g[5]);
+        g[6] = __fmaf_rn(hit, pw, g[6]);
+        g[7] = __fmaf_rn(hit, ph, g[7]);
+        prev = s;
         cx += ww;
         cy += hh;
         csx += pw;
         csy += ph;
     }
+    b.k = below;
+    b.x0 = g[0];
+    b.y0 = g[1];
+    b.sx = g[2];
+    b.sy = g[3];
+    b.w = g[4];
+    b.h = g[5];
+    b.pw = g[6];
+    b.ph = g[7];
     const float a0 = raw[(2 * K + b.k) * ld], a1 = raw[(2 * K + b.k + 1) * ld];
     b.d0 = kMinD + softplus(a0);
     b.d1 = kMinD + softplus(a1);
@@ -1366,26 +1378,34 @@ __device__ __forceinline__ BinF locate_pairs(const float (&raw)[3 * K + 1], floa
     }
     const float2 iz = make_float2(rcp_approx(z.x), rcp_approx(z.y));
     const float2 c = make_float2(1.0f - K * kMinW, 1.0f - K * kMinH), mins = make_float2(kMinW, kMinH);
-    BinF b;
+    // The bin is the first i with v below its right edge (the last bin otherwise).  The edges rise
+    // strictly (every width is at least kMinW), so s_i = [v < edge_i] steps once from 0 to 1 and
+    // hit_i = s_i - s_(i-1) is 1 for that bin alone.  Its values are gathered without branches as
+    // sums of hit_i x value: a multiply by 0 or 1 and an add of +0 are exact, so the gathered
+    // values are the bin's own, bit for bit.
+    float2 lo = make_float2(0.0f, 0.0f), wh_sel = make_float2(0.0f, 0.0f);
     float a0 = 0.0f, a1 = 0.0f;
     float2 cum = make_float2(0.0f, 0.0f);
-    bool found = false;
+    float prev = 0.0f;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const float2 wh = __ffma2_rn(c, __fmul2_rn(e[i], iz), mins);  // (width, height) of bin i
         const float2 next = __fadd2_rn(cum, wh);
-        const bool hit = !found && (i == K - 1 || (by_height ? v < next.y : v < next.x));
-        if (hit) {
-            b.x0 = cum.x;
-            b.y0 = cum.y;
-            b.w = wh.x;
-            b.h = wh.y;
-            a0 = raw[2 * K + i];
-            a1 = raw[2 * K + i + 1];
-            found = true;
-        }
+        const float s = (i == K - 1 || (by_height ? v < next.y : v < next.x)) ? 1.0f : 0.0f;
+        const float hit = s - prev;
+        const float2 hh = make_float2(hit, hit);
+        lo = __ffma2_rn(hh, cum, lo);
+        wh_sel = __ffma2_rn(hh, wh, wh_sel);
+        a0 = __fmaf_rn(hit, raw[2 * K + i], a0);
+        a1 = __fmaf_rn(hit, raw[2 * K + i + 1], a1);
+        prev = s;
         cum = next;
     }
+    BinF b;
+    b.x0 = lo.x;
+    b.y0 = lo.y;
+    b.w = wh_sel.x;
+    b.h = wh_sel.y;
     b.d0 = kMinD + softplus(a0);
     b.d1 = kMinD + softplus(a1);
     return b;
