@@ -1204,7 +1204,9 @@ constexpr int kQRowsU = 56;         // W3 rows per transformed dim in shared mem
 constexpr int kTmemCols = 512;      // group g owns [256g, 256g + 256): two regions of 128 columns
 
 // Shared memory: the weights, then per group an input tile and an activation tile, the biases and
-// the log-det hand-over.  W3 holds the nb transformed dims at a stride of 56 rows plus 8 zero
+// the log-det hand-over.  W3 holds the nb transformed dims (each dim's rows in the interleaved
+// order of locate_pairs, so that a width and its height leave the MMA as a register pair, and
+// the layer-3 biases likewise) at a stride of 56 rows plus 8 zero
 // rows, so that the 64-row B operand of the last dim stays inside it (its rows 49..63 only feed
 // output columns that are never read).
 struct Smem {
@@ -1343,11 +1345,17 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bia
 }
 
 // The bin of v and what the forward and inverse bin formulas need, from raw parameters held in
-// registers (compile-time indices only): widths and heights are handled as pairs in paired FP32
-// arithmetic, softmax exponentials as 2^(a log2 e - max log2 e).
+// registers (compile-time indices only) in the interleaved order of the fused layer: width i at
+// 2i, height i at 2i + 1 (i < K), knot derivatives at 2K..3K.  Widths and heights are handled as
+// pairs in paired FP32 arithmetic, softmax exponentials as 2^(a log2 e - max log2 e).
 struct BinF {
     float x0, y0, w, h, d0, d1;
 };
+
+// Position in that interleaved order of spline parameter p (widths 0..K-1, heights K..2K-1,
+// derivatives 2K..3K), and the parameter at position j.
+__host__ __device__ constexpr int il_pos(int p, int K) { return p < K ? 2 * p : p < 2 * K ? 2 * (p - K) + 1 : p; }
+__host__ __device__ constexpr int il_param(int j, int K) { return j < 2 * K ? ((j & 1) ? K + (j >> 1) : (j >> 1)) : j; }
 
 template <int K>
 __device__ __forceinline__ BinF locate_pairs(const float (&raw)[3 * K + 1], float v, bool by_height) {
@@ -1356,8 +1364,8 @@ __device__ __forceinline__ BinF locate_pairs(const float (&raw)[3 * K + 1], floa
     float mxw[K], mxh[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        mxw[i] = raw[i];
-        mxh[i] = raw[K + i];
+        mxw[i] = raw[2 * i];
+        mxh[i] = raw[2 * i + 1];
     }
 #pragma unroll
     for (int s = K / 2; s > 0; s >>= 1)
@@ -1372,7 +1380,7 @@ __device__ __forceinline__ BinF locate_pairs(const float (&raw)[3 * K + 1], floa
     float2 z = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        const float2 t = __ffma2_rn(make_float2(raw[i], raw[K + i]), l2e, nm);
+        const float2 t = __ffma2_rn(make_float2(raw[2 * i], raw[2 * i + 1]), l2e, nm);
         e[i] = make_float2(ex2_approx(t.x), ex2_approx(t.y));
         z = __fadd2_rn(z, e[i]);
     }
@@ -1482,7 +1490,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int r = i >> 4, k = (i & 15) * 8;
         const int q = r / kQRowsU, j = r % kQRowsU;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (q < nb && j < PQ) v = *reinterpret_cast<const uint4*>(W3 + (q * PQ + j) * 128 + k);
+        if (q < nb && j < PQ) v = *reinterpret_cast<const uint4*>(W3 + (q * PQ + il_param(j, K)) * 128 + k);
         *reinterpret_cast<uint4*>(w3s + coff(r, k, 128)) = v;
     }
     for (int i = tid; i < 128; i += kThreads) {
@@ -1491,7 +1499,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = tid; i < 8 * 56; i += kThreads) {
         const int q = i / 56, j = i % 56;
-        b3s[i] = (q < nb && j < PQ) ? b3[q * PQ + j] : 0.0f;
+        b3s[i] = (q < nb && j < PQ) ? b3[q * PQ + il_param(j, K)] : 0.0f;
     }
     if (tid == 0) {
         failed = 0;
@@ -1647,7 +1655,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if constexpr (kTrain) {  // the raw spline parameters, parameter-major
                 if (valid && q < nb)
 #pragma unroll
-                    for (int j = 0; j < PQ; ++j) tr.P[static_cast<int64_t>(q * PQ + j) * tr.ldp + ev] = raw[j];
+                    for (int j = 0; j < PQ; ++j)
+                        tr.P[static_cast<int64_t>(q * PQ + j) * tr.ldp + ev] = raw[il_pos(j, K)];
             }
             if (valid && q < nb) {
                 const int jd = ld.tb[q];
@@ -1675,7 +1684,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (h == 1) lds[grp * kTile + row] = lsum;
         group_sync(grp);
-        if (h == 0 && valid) logdet[ev] += lsum + lds[grp * kTile + row];
+        // a reduction in memory (no value returned, so nothing waits on the load); the only
+        // update of this element in the launch, rounded as the plain add
+        if (h == 0 && valid) atomicAdd(logdet + ev, lsum + lds[grp * kTile + row]);
     }
     // drain: after a wait that ran out, MMAs may still be in flight; the TMEM is freed only after a
     // commit issued by each group behind all of its MMAs has arrived (default bound)
