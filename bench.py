@@ -65,21 +65,23 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07
 # masses, the per-tile statistics with six FP64 instructions per event, bins, maxima and sign
 # tests on the integer ALU, one exponential for both parton densities, x2 = tau / x1, the decay
 # daughters boosted with one dot product, the VEGAS bin widths staged with the grid, the
-# collider's 1/S folded, the azimuths from a 256-point table and short Taylor series;
-# profiles/fp64_pipe_probes.md): DFMA 338.0 + DADD 93.7 + DMUL 201.7 = 633.5 (971.4 flops),
-# 675.1 FP64-pipe instructions in all, 185.8 DRAM bytes per event, pipe active 0.845 of the
-# elapsed cycles -- the FP64 issue probe's saturating loop reaches 0.84.
-COMPILED_COUNTERS = {"instr": 633.5, "flops": 971.4, "dram": 185.8, "pipe": 0.845, "pipe_instr": 675.1}
+# collider's 1/S folded, the azimuths from a 256-point table and short Taylor series, the
+# Breit-Wigner map's tangent from a double-double table and its regions without branches;
+# profiles/fp64_pipe_probes.md): DFMA 331.9 + DADD 101.6 + DMUL 209.6 = 643.0 (974.9 flops),
+# 676.7 FP64-pipe instructions in all (688.5 in warp-issue slots x 32: lanes 0.983 busy),
+# 185.3 DRAM bytes per event, pipe active 0.845 of the elapsed cycles -- the FP64 issue probe's
+# saturating loop reaches 0.84.
+COMPILED_COUNTERS = {"instr": 643.0, "flops": 974.9, "dram": 185.3, "pipe": 0.845, "pipe_instr": 676.7}
 INTERPRETER_COUNTERS = {"instr": FP64_INSTR_PER_EVENT, "flops": FP64_FLOP_PER_EVENT, "dram": DRAM_BYTES_PER_EVENT,
                         "pipe": 0.854}
 # FP64 arithmetic instructions (DFMA + DADD + DMUL) per event of the 24-channel 2->8 workload, from
 # the ncu captures of one 2^20-event launch: the compiled program on the current build
-# (profiles/fp64_pipe_probes.md: 2460.2 + 1050.5 + 886.5); the interpreter's from an earlier build
+# (profiles/fp64_pipe_probes.md: 2451.3 + 1058.3 + 895.5); the interpreter's from an earlier build
 # (profiles/ps_map_kernel_c5_2to8.md, before the mass-based Kallen function; an upper bound).
-C5_FP64_INSTR_PER_EVENT = {"compiled": 4397.2, "interpreter": 6559.0}
+C5_FP64_INSTR_PER_EVENT = {"compiled": 4405.0, "interpreter": 6559.0}
 # The same for the compiled six-channel 2->5 program, from one 2e6-event launch in the benchmark's
-# channel proportions (profiles/fp64_pipe_probes.md): DFMA 1003.1 + DADD 280.8 + DMUL 403.7.
-C3_FP64_INSTR_PER_EVENT = 1687.6
+# channel proportions (profiles/fp64_pipe_probes.md): DFMA 998.1 + DADD 287.0 + DMUL 409.8.
+C3_FP64_INSTR_PER_EVENT = 1694.9
 # FP64-pipe instructions in all (arithmetic and conversions) per event of the compiled mixed-precision
 # programs (profiles/fp64_pipe_probes.md): the FP64 pipe's share of the mixed form (with the
 # conversions on the integer ALU, 0.55-0.75 of its cycles: no longer the only bound).

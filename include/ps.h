@@ -593,13 +593,16 @@ int ps_fp64_probe(int kind, int blocks, int iters, double* sink, void* stream);
  *                    1e-13 for normal x > 0; 0 for x <= 0 or NaN;
  *   PS_MIXED_RCP64   double -> double: 1/x the same way, for normal x of either sign;
  *   PS_MIXED_SINCOS_TURN  double r -> the doubles cos(2 pi r), sin(2 pi r) at out[2i], out[2i+1]:
- *                    the FP64 kernels' azimuth (a table of 256 points and short Taylor series).
+ *                    the FP64 kernels' azimuth (a table of 256 points and short Taylor series);
+ *   PS_MIXED_TAN_QUARTER  double x -> double tan(x) for |x| <= pi/4: the FP64 Breit-Wigner map's
+ *                    tangent (a double-double table of 129 points and a short Taylor series).
  * Returns PS_ERR_INVALID_ARGUMENT for an unknown kind, n < 0, or a null pointer with n > 0. */
 #define PS_MIXED_F2D 0
 #define PS_MIXED_D2F 1
 #define PS_MIXED_SQRT64 2
 #define PS_MIXED_RCP64 3
 #define PS_MIXED_SINCOS_TURN 4
+#define PS_MIXED_TAN_QUARTER 5
 int ps_mixed_helpers(int kind, const void* in, void* out, int64_t n, void* stream);
 
 #ifdef __cplusplus

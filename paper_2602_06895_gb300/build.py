@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kernels.cu", "graph.cpp", "flow.cu", "unweight.cu", "inverse.cu", "jit.cpp", "probe.cu"]
 # device headers that compiled programs (jit.cpp) hand to NVRTC, embedded as text
 JIT_HEADERS = [("map_device.cuh", CSRC), ("kin.cuh", CSRC), ("philox.cuh", CSRC), ("launch_params.h", CSRC),
-               ("ps.h", INCLUDE)]
+               ("tan_table.h", CSRC), ("ps.h", INCLUDE)]
 
 
 def nvcc():

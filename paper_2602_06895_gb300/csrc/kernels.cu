@@ -343,13 +343,14 @@ void count_launches(int n) { __atomic_add_fetch(&g_launches, static_cast<unsigne
 bool is_reduce_kernel(const void* func) { return func == reinterpret_cast<const void*>(ps_reduce_kernel); }
 
 // ---------------------------------------------------------------- mixed-form helpers
-// Elementwise application of one device helper of the mixed form (ps_mixed_helpers).
+// Elementwise application of one device helper of the map kernels (ps_mixed_helpers).
 template <int kKind, class In, class Out>
 __global__ void __launch_bounds__(256) ps_mixed_helper_kernel(const In* in, Out* out, int64_t n) {
     for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < n; i += static_cast<int64_t>(gridDim.x) * 256) {
         if constexpr (kKind == PS_MIXED_F2D) out[i] = dev::mx::f2d(in[i]);
         else if constexpr (kKind == PS_MIXED_D2F) out[i] = dev::mx::d2f(in[i]);
         else if constexpr (kKind == PS_MIXED_SQRT64) out[i] = dev::mx::sqrt64(in[i]);
+        else if constexpr (kKind == PS_MIXED_TAN_QUARTER) out[i] = dev::tan_quarter(in[i]);
         else out[i] = dev::mx::rcp64(in[i]);
     }
 }
@@ -402,7 +403,7 @@ int noalloc_scratch(int device, void** ptr, size_t* bytes, std::string* err) {
 extern "C" int ps_mixed_helpers(int kind, const void* in, void* out, int64_t n, void* stream) {
     using namespace ps;
     if (n < 0 || (n > 0 && (in == nullptr || out == nullptr))) return PS_ERR_INVALID_ARGUMENT;
-    if (kind < PS_MIXED_F2D || kind > PS_MIXED_SINCOS_TURN) return PS_ERR_INVALID_ARGUMENT;
+    if (kind < PS_MIXED_F2D || kind > PS_MIXED_TAN_QUARTER) return PS_ERR_INVALID_ARGUMENT;
     if (n == 0) return PS_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152LL * 16);
@@ -419,6 +420,9 @@ extern "C" int ps_mixed_helpers(int kind, const void* in, void* out, int64_t n, 
             break;
         case PS_MIXED_RCP64:
             ps_mixed_helper_kernel<PS_MIXED_RCP64><<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), n);
+            break;
+        case PS_MIXED_TAN_QUARTER:
+            ps_mixed_helper_kernel<PS_MIXED_TAN_QUARTER><<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), n);
             break;
         default:
             ps_turn_kernel<<<g, 256, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), n);

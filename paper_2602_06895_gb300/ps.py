@@ -539,13 +539,14 @@ def fp64_probe(kind, blocks, iters, sink, stream=None):
     _check(lib().ps_fp64_probe(PROBES[kind], blocks, iters, _ptr(sink), _stream_ptr(stream)), "ps_fp64_probe")
 
 
-MIXED_HELPERS = {"f2d": 0, "d2f": 1, "sqrt64": 2, "rcp64": 3, "sincos_turn": 4}
+MIXED_HELPERS = {"f2d": 0, "d2f": 1, "sqrt64": 2, "rcp64": 3, "sincos_turn": 4, "tan_quarter": 5}
 
 
 def mixed_helper(kind, x, out, stream=None):
     """Apply one device helper of the map kernels (ps_mixed_helpers) to the device tensor x into
     out (f2d: float32 -> float64; d2f: float64 -> float32; sqrt64, rcp64: float64 -> float64;
-    sincos_turn: float64 r -> (cos 2 pi r, sin 2 pi r) pairs, out twice as long)."""
+    sincos_turn: float64 r -> (cos 2 pi r, sin 2 pi r) pairs, out twice as long; tan_quarter:
+    float64 x -> tan x for |x| <= pi/4)."""
     _check(lib().ps_mixed_helpers(MIXED_HELPERS[kind], _ptr(x), _ptr(out), x.numel(), _stream_ptr(stream)),
            "ps_mixed_helpers")
 

@@ -515,3 +515,28 @@ def test_azimuth_table_matches_quad_precision(torch_cuda):
     ps.mixed_helper("sincos_turn", rs, o2)
     o2 = o2.cpu().numpy().reshape(-1, 2)
     assert np.allclose(o2, [[0.0, -1.0], [-1.0, 0.0], [1.0, 0.0]], atol=1e-15)
+
+
+def test_bw_tangent_matches_quad_precision(torch_cuda):
+    """The FP64 Breit-Wigner map's tangent (a double-double table at k pi/512 and the Taylor
+    series of the remainder) against a quad- or extended-precision tan over [-pi/4, pi/4], the
+    table points and their neighbours: within 2 ulps of the result everywhere, and the correctly
+    rounded double for at least 97 % of the arguments (as CUDA's and the host's tan nearly are)."""
+    torch = torch_cuda
+    rng = np.random.default_rng(43)
+    q = np.pi / 4
+    pts = np.arange(129) * (np.pi / 512)
+    pts = pts[pts <= q]
+    x = np.concatenate([rng.uniform(-q, q, 1 << 18), rng.uniform(-1e-3, 1e-3, 1 << 14), pts, -pts,
+                        np.nextafter(pts[1:], 0), np.nextafter(pts[:-1], 1), [0.0, -0.0, 1e-300, -5e-324, q, -q]])
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    ps.mixed_helper("tan_quarter", xt, out)
+    t = out.cpu().numpy()
+    ref = np.tan(x.astype(np.longdouble))
+    refd = ref.astype(np.float64)
+    ulp = np.spacing(np.abs(refd))
+    err = (np.abs(t.astype(np.longdouble) - ref) / ulp).astype(np.float64)
+    assert np.all(np.isfinite(t)) and err.max() <= 2.0, err.max()
+    assert np.mean(t == refd) >= 0.97, np.mean(t == refd)
+    assert np.all(np.signbit(t) == np.signbit(x))
