@@ -778,8 +778,8 @@ __device__ __forceinline__ void map_nu(float r, double m, double nu, double xmin
     if (!ok) { x = xmin; jac = 0.0; }
 }
 
-// Breit-Wigner: angles and tan in float (same endpoint-relative branches as the FP64 form),
-// s - m^2 and the assembly of x in FP64
+// Breit-Wigner: angles and tan in float (the same endpoint-relative regions as the FP64 form, as
+// one num/den chosen by selects with a single reciprocal), s - m^2 and the assembly of x in FP64
 __device__ __forceinline__ void map_bw(float r, double M, double G, double xmin, double xmax, double& x, double& jac,
                                        bool have_u1 = false, double u1 = 0.0) {
     double mg = M * G, m2 = M * M;
@@ -792,19 +792,12 @@ __device__ __forceinline__ void map_bw(float r, double M, double G, double xmin,
     bool low = u < -0.785398163f, high = u > 0.785398163f;
     float arg = low ? D * r : (high ? D * (1.0f - r) : u);
     float T = tanf(arg);
-    float sec2;
-    if (low) {
-        float rd = 1.0f / (1.0f - a * T);
-        x = xmin + f2d(mgf * (T * (1.0f + a * a) * rd));
-        sec2 = (1.0f + a * a) * (1.0f + T * T) * (rd * rd);
-    } else if (high) {
-        float rd = 1.0f / (1.0f + b * T);
-        x = m2 + f2d(mgf * ((b - T) * rd));
-        sec2 = (1.0f + b * b) * (1.0f + T * T) * (rd * rd);
-    } else {
-        x = m2 + f2d(mgf * T);
-        sec2 = 1.0f + T * T;
-    }
+    const float den = low ? 1.0f - a * T : (high ? 1.0f + b * T : 1.0f);
+    const float num = low ? T * (1.0f + a * a) : (high ? b - T : T);
+    const float kk = low ? 1.0f + a * a : (high ? 1.0f + b * b : 1.0f);
+    const float rd = 1.0f / den;  // 1 exactly in the middle region
+    x = (low ? xmin : m2) + f2d(mgf * (num * rd));
+    const float sec2 = kk * (1.0f + T * T) * (rd * rd);
     jac = f2d(D * mgf * sec2);
     x = clamp_nonneg(x, xmin, xmax);
     if (!ok) { x = xmin; jac = 0.0; }
