@@ -114,8 +114,9 @@ __device__ __forceinline__ bool map_nu(double r, double m, double nu, double xmi
 }
 
 // Breit-Wigner G_BW with a = tan u1, b = tan u2, D = atan2(b - a, 1 + ab), u = u1 + D r.
-// One tangent per event (tan_quarter) of the reduced angle arg (|arg| <= pi/4), chosen by selects, and each
-// region's closed form written as num/den, so that one reciprocal serves every event of a warp:
+// One tangent per event (tan_quarter) of the reduced angle arg (|arg| <= pi/4), chosen by
+// selects, and each region's closed form written as num/den, so that one reciprocal serves every
+// event of a warp and no region splits it:
 //   u < -pi/4: arg = D r,     den = 1 - aT, x = x_min + mG T(1+a^2)/den, 1+tan^2u = (1+a^2)(1+T^2)/den^2
 //   u >  pi/4: arg = D (1-r), den = 1 + bT, x = m^2 + mG (b-T)/den,      1+tan^2u = (1+b^2)(1+T^2)/den^2
 //   otherwise: arg = u,       den = 1,      x = m^2 + mG T,              1+tan^2u = 1+T^2
