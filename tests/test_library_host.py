@@ -122,3 +122,22 @@ def test_flow_unweight_inverse_argument_checks(built):
     assert L.ps_global_weights(0, 0, None, 0, None, 0, al, None, None, 0.0, 0.0, None, None, None) == \
         ps.PS_ERR_INVALID_ARGUMENT
     assert L.ps_flow_last_error().decode()  # the last failure left a message
+
+
+def test_helper_kinds_checked_on_host(built):
+    """ps_mixed_helpers (the map kernels' device helpers, exposed for their accuracy tests)
+    validates the kind, the count and the pointers on the host: every declared kind accepts an
+    empty request without touching a device, anything else is refused."""
+    import ctypes as C
+
+    L = built
+    kinds = [ps.MIXED_HELPERS[k] for k in ("f2d", "d2f", "sqrt64", "rcp64", "sincos_turn", "tan_quarter")]
+    assert kinds == list(range(6))
+    for k in kinds:
+        assert L.ps_mixed_helpers(k, None, None, 0, None) == 0
+    buf = (C.c_double * 4)()
+    for k in (-1, 6):
+        assert L.ps_mixed_helpers(k, buf, buf, 4, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_mixed_helpers(5, buf, buf, -1, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_mixed_helpers(5, None, buf, 4, None) == ps.PS_ERR_INVALID_ARGUMENT
+    assert L.ps_mixed_helpers(5, buf, None, 4, None) == ps.PS_ERR_INVALID_ARGUMENT
