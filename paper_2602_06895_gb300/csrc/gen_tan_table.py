@@ -13,7 +13,8 @@ import mpmath as mp
 N = 128  # intervals of [0, pi/4]
 
 
-def main():
+def render():
+    """The text of tan_table.h."""
     mp.mp.dps = 60
     h = mp.pi / (4 * N)
     hi, lo, sk = [], [], []
@@ -41,9 +42,13 @@ def main():
            f"constexpr int kTanN = {N};",
            f"constexpr double kTanH1 = {h1.hex()}, kTanH2 = {h2.hex()}, kTanInvH = {float(1 / h).hex()};",
            arr("kTanHi", hi), arr("kTanLo", lo), arr("kTanSq1", sk)]
+    return "\n".join(out)
+
+
+def main():
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tan_table.h")
     with open(path, "w") as f:
-        f.write("\n".join(out))
+        f.write(render())
 
 
 if __name__ == "__main__":

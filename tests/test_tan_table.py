@@ -60,3 +60,14 @@ def test_tangent_step_split():
     for k in range(n + 1):  # k h1 exact in double
         assert float(k * mp.mpf(h1)) == k * h1
     assert c["kTanInvH"] == float(1 / h)
+
+
+def test_header_is_the_generators_output():
+    """The committed header is exactly what gen_tan_table.py writes (no hand edits)."""
+    import importlib.util
+
+    gen = os.path.join(os.path.dirname(HDR), "gen_tan_table.py")
+    spec = importlib.util.spec_from_file_location("gen_tan_table", gen)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    assert mod.render() == open(HDR).read()
