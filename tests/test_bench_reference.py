@@ -52,3 +52,37 @@ def test_fp64_pipe_roofline_arithmetic():
     assert abs(r["flops"]["frac"] - 0.5639) < 1e-4
     n = bench.fp64_pipe_roofline(None, 6.28e8)
     assert n["achieved"] is None and n["frac"] is None and "flops" not in n
+
+
+def test_summary_fits_the_line_tail():
+    """Every leg's headline figure is repeated in one short `summary` object: with every leg
+    present it holds no missing value and stays under 1200 characters, so the last 1.5 kB of the
+    JSON line (where it is placed) carries all of them."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    v = 123456789.0123
+    line = {"value": v, "roofline": {"frac": 0.95, "frac_of_derived_peak": 0.79,
+                                     "fp64_peak": {"dfma_ginstr_per_s": 528.1, "sm_count": 152},
+                                     "method": {"fp64_pipe_equivalent_per_event": 1572.4}},
+            "e2e": {"value": v}, "interpreter": {"value": v},
+            "mixed_precision": {"value": v, "speedup_vs_fp64": 8.27, "fp64_pipe": {"frac": 0.74}},
+            "multichannel": {"value": v, "roofline": {"frac": 0.91}, "mixed_precision": {"value": v}},
+            "streamed_2to8": {"value": v, "roofline": {"frac": 0.97}, "e2e": {"value": v},
+                              "mixed_precision": {"value": v}},
+            "importance_2to8": {"mixed_n_eff_per_s_over_vegas_fp64": 12.17,
+                                "flow_mixed_map_n_eff_per_s_over_vegas_fp64": 2.227,
+                                "flow_n_eff_per_s_over_vegas_fp64": 0.8676},
+            "flow": {"ess_fraction_flow": 0.9911, "ess_fraction_vegas": 0.9027, "ess_per_s_flow": 3.4e8,
+                     "ess_per_s_vegas": 7.0e8, "mixed_map": {"ess_per_s_over_fp64_vegas": 0.7919},
+                     "sample_ms": 15.81, "train_ms_per_step": 1.866, "train_steps": 20000},
+            "unweighting": {"events_per_s": v}, "global_multichannel": {"events_per_s": v},
+            "cpu_baseline": {"value": v, "cores": 16}}
+    s = bench.summary(line)
+
+    def leaves(d):
+        for x in d.values():
+            yield from (leaves(x) if isinstance(x, dict) else [x])
+
+    assert all(x is not None for x in leaves(s))
+    assert len(json.dumps(s)) < 1200
